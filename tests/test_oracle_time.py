@@ -1,0 +1,127 @@
+"""Pins of the oracle's Williamson low-storage RK3 (Sec. 3), its CFL time
+step, and design-order convergence of the advected density pulse
+(Sec. 3.1) against the closed-form translation rho(x - u t)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2210_03523_gb300 import inputs as I
+from oracle_helpers import tensor_weights
+
+
+def test_williamson_rk3_order_conditions(orc):
+    """Turn the 2N-storage (A, B) pairs into a Butcher tableau and check the
+    four third-order conditions exactly."""
+    A, B = orc.rk_coeffs()
+    s = 3
+    # G_k = A_k G_{k-1} + dt R_{k-1};  Q_k = Q_{k-1} + B_k G_k; track coefficients of dt R_j
+    Gc = np.zeros(s)
+    Qc = np.zeros(s)
+    a = np.zeros((s, s))     # a[k] = coefficients of stage k's input state
+    for k in range(s):
+        a[k] = Qc
+        Gc = A[k] * Gc
+        Gc[k] += 1.0
+        Qc = Qc + B[k] * Gc
+    b = Qc
+    c = a.sum(1)
+    assert abs(b.sum() - 1) < 1e-15
+    assert abs(b @ c - 0.5) < 1e-15
+    assert abs(b @ c ** 2 - 1 / 3) < 1e-15
+    assert abs(b @ (a @ c) - 1 / 6) < 1e-15
+    np.testing.assert_allclose(c, [0.0, 1 / 3, 3 / 4], atol=1e-15)
+
+
+def test_rk3_step_is_third_order_taylor_on_linear_operator(orc):
+    """On the density-pulse family the residual is linear in rho:
+    R_rho(c + phi) = L phi.  One RK3 step must equal
+    (I + dt L + dt^2 L^2/2 + dt^3 L^3/6) applied to rho."""
+    ph = I.pulse_physics(mach=0.5, velocity=(0.6, 0.3, -0.2))
+    mi = I.box_mesh(2, orders=I.random_orders(8, 1, 4, 3), phys=ph)
+    m = orc.Mesh(mi)
+    xyz = m.coords()
+    q0 = I.pulse_state(xyz, m.orders, ph, width=0.4)
+    u = np.asarray(ph.qinf[1:4])
+    p0 = (ph.gamma - 1) * (ph.qinf[4] - 0.5 * u @ u)
+    off = m.off
+
+    def state_of(rho):
+        q = np.empty(5 * off[-1])
+        for e in range(m.n_elem):
+            blk = q[5 * off[e]:5 * off[e + 1]].reshape(5, -1)
+            r = rho[off[e]:off[e + 1]]
+            blk[0] = r
+            blk[1:4] = r[None] * u[:, None]
+            blk[4] = p0 / (ph.gamma - 1) + 0.5 * r * (u @ u)
+        return q
+
+    def rho_of(q):
+        return np.concatenate([m.elem(q, e)[0] for e in range(m.n_elem)])
+
+    def L(phi):
+        c = 10.0 * (1.0 + np.abs(phi).max())
+        return rho_of(m.residual(state_of(c + phi)))
+
+    rho = rho_of(q0)
+    dt = 0.02
+    L1 = L(rho)
+    L2 = L(L1)
+    L3 = L(L2)
+    expect = rho + dt * L1 + dt ** 2 / 2 * L2 + dt ** 3 / 6 * L3
+    q = q0.copy()
+    G = np.zeros_like(q)
+    m.rk_step(q, G, dt)
+    np.testing.assert_allclose(rho_of(q), expect, atol=1e-13)
+
+
+def test_max_dt_closed_form(orc):
+    """uniform state on an axis-aligned box of size h: J = h^3/8, J a^i = h^2/4 e_i"""
+    ph = I.pulse_physics(mach=0.3, velocity=(1.0, 0.5, 0.0))
+    mi = I.box_mesh(4, orders=(3, 2, 5), phys=ph)
+    m = orc.Mesh(mi)
+    q = I.uniform_state(m.orders, ph.qinf)
+    h = 0.5
+    u = np.array([1.0, 0.5, 0.0])
+    p = (ph.gamma - 1) * (ph.qinf[4] - 0.5 * u @ u)
+    c = math.sqrt(ph.gamma * p)
+    J, a = h ** 3 / 8, h ** 2 / 4
+    s = sum((N + 1) ** 2 * (a * abs(u[i]) + c * a) / (2 * J) for i, N in enumerate((3, 2, 5)))
+    assert abs(m.max_dt(q, 0.5) - 0.5 / s) < 1e-14 * (0.5 / s)
+
+
+def _l2_error(m, q, ph, t, width, center):
+    xyz = m.coords()
+    u = np.asarray(ph.qinf[1:4])
+    err = 0.0
+    for e in range(m.n_elem):
+        x = m.elem(xyz, e, 3)
+        exact = I.pulse_primitive(x[0] - u[0] * t, x[1] - u[1] * t, x[2] - u[2] * t, width=width, center=center,
+                                  images=1)
+        _, _, J = m.metrics(e)
+        err += ((m.elem(q, e)[0] - exact) ** 2 * tensor_weights(m.orders[e]) * J).sum()
+    return math.sqrt(err)
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_design_order_convergence(orc, N):
+    """L2 error of the advected pulse against rho(x - u t) (periodic-image
+    sum) decays like h^(N+1) on 2^3, 4^3, 8^3 meshes (observed 2.7 for N=2,
+    4.0 for N=3 at t=0.2; shorter times are dominated by the O(h^N)
+    pointwise residual truncation error)."""
+    ph = I.pulse_physics(mach=0.5, velocity=(1.0, 1.0, 0.0))
+    width, center, T = 0.6, (0.1, -0.05, 0.0), 0.2
+    errs = []
+    for nx in (2, 4, 8):
+        mi = I.box_mesh(nx, orders=(N, N, N), phys=ph)
+        m = orc.Mesh(mi)
+        q = I.pulse_state(m.coords(), m.orders, ph, width=width, center=center, images=1)
+        G = np.zeros_like(q)
+        dt0 = m.max_dt(q, 0.4)
+        nsteps = int(math.ceil(T / dt0))
+        dt = T / nsteps
+        for _ in range(nsteps):
+            m.rk_step(q, G, dt)
+        errs.append(_l2_error(m, q, ph, T, width, center))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > N + 1 - 0.6, (errs, rates)
