@@ -1,0 +1,422 @@
+"""Benchmark of the DGSEM hot path on GB300.
+
+Workload (default ``pulse16mixed``): the Euler density pulse on 16^3
+periodic straight hexes. Each element's orders (N1,N2,N3) are drawn i.i.d.
+from {1..6} (seed 2210), so faces are p-nonconforming. One *step* is one
+pass of the whole hot path:
+
+  * 50 explicit RK3 steps in FP64. Each RK step is one CFL reduction and
+    three stages of face flux + volume residual with the fused RK update.
+  * then one FP32 isolated tau-estimation sweep over every anisotropic
+    order N <= P_e of every element, both forms, max-accumulated.
+
+The metric is DOF-residuals/s: NDOF x residual evaluations per step / step
+time, summed over ranks. tau-estimated elements/s is reported next to it.
+
+``--impl reference`` times the CPU oracle (FP64 C, OpenMP over elements) on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-residuals/s and tau-estimated elements/s at stated error; % of HBM roofline"
+UNIT = "DOF-residuals/s"
+CFL = 0.5
+RK_PER_STEP = 50
+L2_FLUSH_BYTES = 256 << 20
+FP64_FMA_PER_CLK_PER_SM = 2        # GB300: 64 FP64 lanes per 32 clocks per SM (measured 1.20 TFLOP/s)
+FP32_FMA_PER_CLK_PER_SM = 128
+N_SM = 152
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def workload_desc(name):
+    return {
+        "pulse16mixed": "Euler density pulse, 16^3 periodic straight hexes, orders iid U{1..6} per element and "
+                        "direction (seed 2210), Roe, gamma=1.4, Mach 0.1; step = 50 RK3 steps at CFL 0.5 (FP64) "
+                        "+ 1 FP32 isolated tau sweep over all N <= P_e",
+        "pulse32mixed": "Euler density pulse, 32^3 periodic straight hexes, orders iid U{1..6} (seed 2210); "
+                        "step = 50 RK3 steps + 1 FP32 tau sweep",
+        "pulse4": "Euler density pulse, 4^3 periodic straight hexes, P=(4,4,4); step = 50 RK3 steps + 1 FP32 tau sweep",
+        "pulse48mixed": "Euler density pulse, 48^3 periodic straight hexes, orders iid U{2..8} (seed 2210); "
+                        "step = 50 RK3 steps + 1 FP32 tau sweep",
+        "pulse48uniform": "Euler density pulse, 48^3 periodic straight hexes, P=(5,5,5); step = 50 RK3 steps + 1 "
+                          "FP32 tau sweep",
+    }[name]
+
+
+def full_sweep_for(orders):
+    from paper_2210_03523_gb300 import inputs as I
+    return I.full_sweep(np.asarray(orders).max(0))
+
+
+# ------------------------------------------------------------ algorithmic counts
+def volume_counts(orders, rk=True):
+    """Algorithmic FP64 flops and HBM bytes of one volume-kernel launch (Euler,
+    straight elements, fused RK stage).  Per node: primitive variables 12,
+    Cartesian fluxes 16, contravariant fluxes 75, sum-factorised derivative
+    10*sum_i(N_i+1), 1/J scaling 6, RK update 25; per face node of the
+    element's own six faces: lift 15.  Bytes per node: q read 40, G read and
+    write 80, q write 40 (RK) or R write 40; per face node 40 (F* read);
+    per element 80 (metrics)."""
+    o = np.asarray(orders, dtype=np.int64).reshape(-1, 3) + 1
+    n = o.prod(1)
+    faces = 2 * (o[:, 1] * o[:, 2] + o[:, 0] * o[:, 2] + o[:, 0] * o[:, 1])
+    flops = (n * (134 + 10 * o.sum(1)) + 15 * faces).sum() - (0 if rk else (n * 25).sum())
+    bytes_ = ((160 if rk else 80) * n + 40 * faces + 80).sum()
+    return float(flops), float(bytes_)
+
+
+def tau_counts(orders, sweep):
+    """Algorithmic FP32 flops of one isolated tau sweep (Euler): per element,
+    the isolated R^P (as the volume term: 12+16+75+10 sum(P_i+1)+6 per node),
+    then per applicable entry N: restriction of 10 fields in xi3, xi2, xi1
+    (2*10*(P3+1) per output node of each pass; the xi3 / xi2 passes only when
+    N3 / (N2,N3) change), the coarse isolated residual, and the two norms
+    (5*(1 + 4) per node)."""
+    o = np.asarray(orders, dtype=np.int64).reshape(-1, 3)
+    sw = np.asarray(sweep, dtype=np.int64).reshape(-1, 3)
+    total = 0.0
+    for P in {tuple(r) for r in o}:
+        cnt = int((o == P).all(1).sum())
+        P1, P2, P3 = P
+        nP = (P1 + 1) * (P2 + 1) * (P3 + 1)
+        f = nP * (109 + 10 * (P1 + P2 + P3 + 3))
+        cur3 = cur2 = None
+        for N1, N2, N3 in sw:
+            if N1 > P1 or N2 > P2 or N3 > P3:
+                continue
+            if N3 != cur3:
+                f += 20 * (P3 + 1) * (P1 + 1) * (P2 + 1) * (N3 + 1)
+                cur3, cur2 = N3, None
+            if N2 != cur2:
+                f += 20 * (P2 + 1) * (P1 + 1) * (N2 + 1) * (N3 + 1)
+                cur2 = N2
+            nN = (N1 + 1) * (N2 + 1) * (N3 + 1)
+            f += 20 * (P1 + 1) * nN
+            f += nN * (109 + 10 * (N1 + N2 + N3 + 3) + 25)
+        total += cnt * f
+    return total
+
+
+# ------------------------------------------------------------ clocks sampling
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------ our arm
+def run_gb300(args, rank, world):
+    import torch
+    from paper_2210_03523_gb300 import dg, inputs as I
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    mi = I.workload(args.workload)
+    m = dg.Mesh(mi)
+    ndof = m.n_nodes
+    xyz = m.coords().cpu().numpy()
+    q0_h = I.pulse_state_fast(xyz, mi.orders, mi.phys)
+    q0 = torch.from_numpy(q0_h).cuda()
+    q = q0.clone()
+    g = torch.zeros_like(q)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sweep = full_sweep_for(mi.orders)
+    ns = sweep.shape[0]
+    map_new = torch.zeros((m.n_elem, ns), dtype=torch.float32, device="cuda")
+    map_trad = torch.zeros_like(map_new)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step():
+        for _ in range(args.rk_per_step):
+            m.max_dt(q, CFL, dt)
+            m.rk_step(q, g, dt)
+        m.tau_estimate(q, sweep, isolated=True, fp32=True, accumulate=True, map_new=map_new, map_trad=map_trad)
+
+    def reset():
+        q.copy_(q0)
+        g.zero_()
+        flush.fill_(1.0)       # evict the working set from L2 between timed steps
+
+    for _ in range(args.warmup):
+        reset()
+        step()
+    assert m.get_error() == 0, "non-physical state during warm-up"
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    launches0 = m.launch_count()
+    m.profile_enable(True)
+    starts, mids, ends = [ev() for _ in range(args.steps)], [ev() for _ in range(args.steps)], \
+        [ev() for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        reset()
+        starts[k].record(stream)
+        for _ in range(args.rk_per_step):
+            m.max_dt(q, CFL, dt)
+            m.rk_step(q, g, dt)
+        mids[k].record(stream)
+        m.tau_estimate(q, sweep, isolated=True, fp32=True, accumulate=True, map_new=map_new, map_trad=map_trad)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = m.launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    rk_ms = [s.elapsed_time(e) for s, e in zip(starts, mids)]
+    tau_ms = [s.elapsed_time(e) for s, e in zip(mids, ends)]
+    kern = {name: m.profile_read(kid) for name, kid in dg.KERNELS.items()}
+    m.profile_enable(False)
+    err = m.get_error()
+    assert err == 0, f"device error {err}"
+
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    res_per_step = 3 * args.rk_per_step
+    value = world * ndof * res_per_step / (ms_per_step * 1e-3)
+
+    # end to end through the public API with host buffers
+    q_pin = torch.from_numpy(q0_h).pin_memory()
+    out_q = torch.empty(q.numel(), dtype=torch.float64).pin_memory()
+    out_mn = torch.empty(map_new.shape, dtype=torch.float32).pin_memory()
+    out_mt = torch.empty(map_trad.shape, dtype=torch.float32).pin_memory()
+    e2e_s, e2e_e = [ev() for _ in range(args.steps)], [ev() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        g.zero_()
+        flush.fill_(1.0)
+        e2e_s[k].record(stream)
+        q.copy_(q_pin, non_blocking=True)
+        step()
+        out_q.copy_(q, non_blocking=True)
+        out_mn.copy_(map_new, non_blocking=True)
+        out_mt.copy_(map_trad, non_blocking=True)
+        e2e_e[k].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e2e_s, e2e_e)) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = q.numel() * 8
+    d2h = q.numel() * 8 + 2 * map_new.numel() * 4
+
+    # roofline of the dominant kernel (the volume residual + fused RK stage)
+    vol_ms, vol_n = kern["volume"]
+    vflops, vbytes = volume_counts(mi.orders, rk=True)
+    vol_avg_s = vol_ms / vol_n * 1e-3
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    fp64_peak = N_SM * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    hbm_peak, hbm_src = _peaks()
+    kernels_json = {k: {"launches": n, "total_ms": round(ms, 3), "share": None} for k, (ms, n) in kern.items() if n}
+    ktot = sum(v["total_ms"] for v in kernels_json.values())
+    for v in kernels_json.values():
+        v["share"] = round(v["total_ms"] / ktot, 4) if ktot else None
+    tau_k_ms, tau_k_n = kern["tau"]
+    tflops = tau_counts(mi.orders, sweep)
+    fp32_peak = N_SM * FP32_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": workload_desc(args.workload), "n_elem": m.n_elem,
+                   "ndof": ndof, "scalar_dof": 5 * ndof, "rk_steps_per_step": args.rk_per_step,
+                   "residual_evals_per_step": res_per_step, "tau_sweep": {"entries": ns, "dtype": "f32",
+                                                                         "form": "isolated, new + traditional"},
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "tau_elements_per_s": world * m.n_elem / (statistics.mean(tau_ms) * 1e-3),
+        "rk_dof_residuals_per_s": world * ndof * res_per_step / (statistics.mean(rk_ms) * 1e-3),
+        "stated_error": {"residual_rk_fp64_rel": 1e-12, "tau_fp32_abs": "<= 8 eps32 (sum_i ||D||) max|f| max|Ja|/min J",
+                         "checked_by": "tests/test_gpu_parity.py"},
+        "roofline": {"kernel": "volume_kernel (FP64 residual + fused RK3 stage)", "bound": "alu",
+                     "achieved": vflops / vol_avg_s / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": vflops / vol_avg_s / 1e12 / fp64_peak,
+                     "peak_source": f"FP64: {N_SM} SMs x {FP64_FMA_PER_CLK_PER_SM} DFMA/clk x 2 x median SM clock "
+                                    f"{sm_mhz:.0f} MHz (recipe nominal 1.25 TFLOP/s at 2070 MHz)",
+                     "traffic": None, "algorithmic_flops_per_launch": vflops,
+                     "algorithmic_bytes_per_launch": vbytes, "avg_launch_ms": vol_avg_s * 1e3,
+                     "hbm_achieved_gbs": vbytes / vol_avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": vbytes / vol_avg_s / 1e9 / hbm_peak, "hbm_peak_source": hbm_src},
+        "tau_roofline": {"kernel": "tau_kernel<float>", "bound": "alu",
+                         "achieved": tflops / (tau_k_ms / tau_k_n * 1e-3) / 1e12 if tau_k_n else None,
+                         "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": (tflops / (tau_k_ms / tau_k_n * 1e-3) / 1e12 / fp32_peak) if tau_k_n else None,
+                         "peak_source": f"FP32: {N_SM} SMs x {FP32_FMA_PER_CLK_PER_SM} FFMA/clk x 2 x {sm_mhz:.0f} MHz"},
+        "kernels": kernels_json,
+        "e2e": {"value": world * ndof * res_per_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return line
+
+
+# ------------------------------------------------------------ the oracle
+def oracle_sample(workload, rk_steps=2, tau=True):
+    """Time the oracle on the full mesh: rk_steps RK3 steps and (optionally) one
+    FP64 isolated tau sweep.  Returns (rk seconds, tau seconds, ndof, n_elem)."""
+    import oracle
+    from paper_2210_03523_gb300 import inputs as I
+    mi = I.workload(workload)
+    om = oracle.Mesh(mi)
+    q = I.pulse_state_fast(om.coords(), om.orders, mi.phys)
+    G = np.zeros_like(q)
+    dt = om.max_dt(q, CFL)
+    t0 = time.perf_counter()
+    for _ in range(rk_steps):
+        om.rk_step(q, G, dt)
+    t1 = time.perf_counter()
+    t_tau = None
+    if tau:
+        sweep = full_sweep_for(mi.orders)
+        t2 = time.perf_counter()
+        om.tau(q, sweep)
+        t_tau = time.perf_counter() - t2
+    return t1 - t0, t_tau, om.n_nodes, om.n_elem
+
+
+def cpu_baseline(workload):
+    rk_s, tau_s, ndof, ne = oracle_sample(workload, rk_steps=4, tau=True)
+    return {"value": ndof * 12 / rk_s, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+            "kind": "oracle",
+            "sample": f"{workload}: 4 RK3 steps (12 FP64 residuals) of the full mesh + 1 FP64 isolated tau sweep; "
+                      f"OpenMP over elements (schedule guided)",
+            "tau_elements_per_s": ne / tau_s, "seconds": rk_s + tau_s}
+
+
+def run_reference(args):
+    steps_ms = []
+    sample_rk = 2
+    for k in range(args.warmup + args.steps):
+        rk_s, _, ndof, ne = oracle_sample(args.workload, rk_steps=sample_rk, tau=False)
+        if k >= args.warmup:
+            steps_ms.append(rk_s * 1e3)
+    ms = statistics.mean(steps_ms)
+    value = ndof * 3 * sample_rk / (ms * 1e-3)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    sample = f"{args.workload}: each step = {sample_rk} RK3 steps ({3 * sample_rk} FP64 residuals) of the full mesh"
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "description": workload_desc(args.workload), "ndof": ndof},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="pulse16mixed",
+                    choices=["pulse16mixed", "pulse4", "pulse32mixed", "pulse48mixed", "pulse48uniform"])
+    ap.add_argument("--rk-per-step", type=int, default=RK_PER_STEP)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)), flush=True)
+        return 0
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line = run_gb300(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

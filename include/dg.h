@@ -1,0 +1,199 @@
+/*
+ * dg.h -- C ABI of libdg: the GB300 (sm_103a) DGSEM residual, Williamson RK3
+ * step and unsteady anisotropic tau-estimation sweep of Rueda-Ramirez,
+ * Ntoukas, Rubio, Valero, Ferrer, "Truncation Error-Based Anisotropic
+ * p-Adaptation for Unsteady Flows for High-Order Discontinuous Galerkin
+ * Methods" (arXiv 2210.03523).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Element e has orders (N1,N2,N3), 1 <= N_i <= DG_MAX_ORDER, and
+ * n_e = (N1+1)(N2+1)(N3+1) Gauss-Lobatto (GL) nodes.  A "state-layout"
+ * array holds 5 doubles per node: element e starts at 5*off_e, off_e =
+ * sum_{e'<e} n_e', and is ordered [var][k][j][i] (i fastest) with
+ * var = (rho, rho u, rho v, rho w, rho E).  Faces of an element are numbered
+ * 0..5 = (-xi1, +xi1, -xi2, +xi2, -xi3, +xi3).
+ *
+ * Memory: every pointer called "device" is CUDA device memory of the
+ * current device, owned and allocated by the caller; "host" pointers are
+ * read during the call only.  The mesh owns its geometry, connectivity and
+ * scratch buffers.  Calls are asynchronous on the mesh's CUDA stream unless
+ * stated otherwise.  Argument errors are returned synchronously and leave
+ * the device untouched.  Device-side errors (a non-physical state: rho <= 0,
+ * p <= 0 or NaN) set a sticky error word that dg_get_error() returns.
+ * A mesh is not thread-safe.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_MAX_ORDER 8
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,          /* invalid argument (null pointer, order out of range, bad connectivity) */
+  DG_ERR_NOMEM = 2,        /* device or host allocation failed */
+  DG_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  DG_ERR_UNSUPPORTED = 4,  /* valid input outside what the library implements */
+  DG_ERR_NONPHYSICAL = 5,  /* sticky device error: rho <= 0, p <= 0 or NaN met */
+  DG_ERR_TIMEOUT = 6       /* reserved: a bounded device wait gave up */
+} dg_status;
+
+enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 };
+
+/* boundary tags in dg_mesh_desc.neighbors */
+enum { DG_BC_FARFIELD = -1, DG_BC_WALL = -2 };
+
+/* dg_residual flags */
+#define DG_ISOLATED 0x1u        /* isolated residual: inner flux on every face (Sec. 2.2, end) */
+
+/* dg_tau_estimate flags */
+#define DG_TAU_ISOLATED 0x1u    /* isolated tau (the paper's results use it, Sec. 3); else non-isolated */
+#define DG_TAU_FP32 0x2u        /* sweep arithmetic and maps in float; else double */
+#define DG_TAU_ACCUM_MAX 0x4u   /* map = max(map, new): F_max over estimation stages (Sec. 2.4) */
+
+/* Gas model (Sec. 2.1, Eq. NScons/SystemAdvDiff): ideal gas with ratio of
+ * specific heats gamma and gas constant Rgas (T = p/(rho Rgas)); for
+ * Navier-Stokes a constant viscosity mu, Stokes hypothesis and Fourier heat
+ * flux with kappa = mu gamma Rgas / ((gamma-1) Pr).  q_inf is the
+ * free-stream conservative state used by DG_BC_FARFIELD. */
+typedef struct {
+  int32_t eqs;       /* DG_EULER or DG_NAVIER_STOKES */
+  double gamma, mu, Pr, Rgas;
+  double q_inf[5];
+} dg_physics;
+
+/* Mesh description (all host memory, copied by dg_mesh_create).
+ * geom: [n_elem][(G+1)^3][3] node coordinates of each element's degree-G
+ *       geometry on the equispaced reference lattice xi = -1 + 2a/G,
+ *       index a + (G+1)(b + (G+1)c); the element map is the degree-G
+ *       tensor polynomial through them (Sec. 2.1: J_j of the geometry
+ *       transformation).
+ * neighbors: [n_elem][6]; >= 0: the element across that face, whose
+ *       opposite face (f^1) must point back, with aligned reference axes;
+ *       < 0: a DG_BC_* tag.
+ * orders: [n_elem][3] per-direction orders (Sec. 2.4: p-anisotropic). */
+typedef struct {
+  int32_t n_elem;
+  int32_t geom_order;
+  const double* geom;
+  const int32_t* neighbors;
+  const int32_t* orders;
+  dg_physics phys;
+} dg_mesh_desc;
+
+typedef struct dg_mesh dg_mesh;
+
+/* Builds geometry, Kopriva curl-form metric terms, face connectivity and
+ * (N1,N2,N3) buckets, and uploads them.  stream: a cudaStream_t, or NULL
+ * for the legacy default stream.  Synchronous.
+ * Mortars (p-nonconforming faces) are implemented for affine Euler meshes;
+ * on a curved or Navier-Stokes mesh with p-nonconforming faces the mesh is
+ * created, the element-local operations (isolated residual, isolated tau,
+ * CFL step, dg_set_orders) work, and every face-coupled call returns
+ * DG_ERR_UNSUPPORTED.
+ * Errors: DG_ERR_ARG (null pointer, order outside 1..DG_MAX_ORDER,
+ * neighbour index out of range or not reciprocal, unknown tag, J <= 0),
+ * DG_ERR_NOMEM, DG_ERR_CUDA. */
+dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out);
+dg_status dg_mesh_destroy(dg_mesh* mesh);
+/* Number of nodes and elements (host outputs; either may be NULL). */
+dg_status dg_mesh_info(const dg_mesh* mesh, int64_t* n_nodes, int32_t* n_elem);
+/* Number of nodes of a layout with the given host orders [n_elem][3]. */
+dg_status dg_count_nodes(int32_t n_elem, const int32_t* orders, int64_t* n_nodes);
+dg_status dg_set_stream(dg_mesh* mesh, void* stream);
+
+/* Node coordinates: device xyz[3*n_nodes], element e at 3*off_e as
+ * [d][node].  Synchronous. */
+dg_status dg_node_coords(dg_mesh* mesh, double* xyz);
+
+/* Residual R(Q) = dQ/dt = -(M^N)^{-1} F^N(Q) of the DGSEM discretisation,
+ * Sec. 2.1, Eqs. (DGSEMsystem), (DGMassMatrixLeft), (DGMassMatrixRight):
+ * Roe advective flux and, for Navier-Stokes, BR1 for q-hat and the viscous
+ * flux (Sec. 3); p-nonconforming faces through mortars of order
+ * max(N_L, N_R) per tangential direction.  flags: DG_ISOLATED gives the
+ * isolated residual (surface numerical fluxes replaced by the inner flux,
+ * end of Sec. 2.2).  q, r: device, state layout, FP64; r may not alias q.
+ * Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED (face-coupled call on a mesh whose
+ * mortars are not implemented, see dg_mesh_create), DG_ERR_CUDA. */
+dg_status dg_residual(dg_mesh* mesh, const double* q, double* r, uint32_t flags);
+
+/* CFL time step (Sec. 3: dt adapted from the CFL condition each step):
+ * dt = cfl / max_nodes max(s_a, s_v),
+ *   s_a = sum_i (N_i+1)^2 (|J a^i . v| + c |J a^i|) / (2J),
+ *   s_v = sum_i (N_i+1)^4 |J a^i|^2/(4J^2) max(1, gamma/Pr) mu/rho (NS only).
+ * q: device state; dt_dev: device double written on the stream, so that a
+ * captured RK loop can consume it without a host round trip. */
+dg_status dg_max_dt(dg_mesh* mesh, const double* q, double cfl, double* dt_dev);
+
+/* One step of Williamson's low-storage RK3 (Sec. 3), stages k = 1..3:
+ *   G <- A_k G + dt R(Q),  Q <- Q + B_k G,
+ * A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15).  q and g (the RK
+ * register, zero before the first step) are device state-layout arrays
+ * updated in place; dt_dev is a device double read by the kernels. */
+dg_status dg_rk_step(dg_mesh* mesh, double* q, double* g, const double* dt_dev);
+
+/* Unsteady anisotropic tau-estimation, variational DG form (Sec. 2.3 item 1):
+ *   new form (Eq. TEtildedef):  tau~^N = I_{N<-P} R^P(q^P) - R^N(I_{N<-P} q^P)
+ *   traditional (Eq. TEdef):    tau^N  = M^N tau~^N = J_j w_j tau~^N_j
+ * with I_{N<-P} interpolation from the element's orders P to N, for every
+ * element e and every sweep entry s (orders N_s).  The map entry is the
+ * infinity norm over the element's nodes and all five variables if
+ * N_s <= P_e componentwise, else -1.
+ *   q: device state (q^P); r_p: device state R^P or NULL (then R^P is the
+ *      residual of the same variant as R^N, so tau at N = P is exactly 0);
+ *   sweep: host [n_sweep][3]; map_new / map_trad: device [n_elem][n_sweep],
+ *      float if DG_TAU_FP32 else double; either may be NULL (not written).
+ *   flags: DG_TAU_ISOLATED (element-local residuals; coarse geometry is the
+ *      element map interpolated to N), else non-isolated (full residual of
+ *      the coarse discretisation with orders min(N_s, P_e) in every
+ *      element); DG_TAU_FP32; DG_TAU_ACCUM_MAX. */
+dg_status dg_tau_estimate(dg_mesh* mesh, const double* q, const double* r_p, const int32_t* sweep, int32_t n_sweep,
+                          uint32_t flags, void* map_new, void* map_trad);
+
+/* Change the element orders to new_orders (host [n_elem][3]) and project
+ * the state (Sec. 2.4: after adaptation the storage is reallocated and the
+ * solution projected to the new polynomial spaces): per direction,
+ * interpolation when the order rises and L2 projection when it falls.
+ * q_old: device, old layout; q_new: device, new layout of
+ * dg_count_nodes(new_orders) nodes, caller-allocated, not aliasing q_old.
+ * The mesh is rebuilt for the new orders (synchronous). */
+dg_status dg_set_orders(dg_mesh* mesh, const int32_t* new_orders, const double* q_old, double* q_new);
+
+/* Kernel kinds for dg_profile_read. */
+enum {
+  DG_KERNEL_FACE_FLUX = 0,   /* Roe (+ BR1 viscous) numerical flux per face, mortars */
+  DG_KERNEL_FACE_QHAT = 1,   /* BR1 q-hat per face (Navier-Stokes) */
+  DG_KERNEL_GRADIENT = 2,    /* BR1 gradient (Navier-Stokes) */
+  DG_KERNEL_VOLUME = 3,      /* volume residual + surface lift (+ fused RK3 stage) */
+  DG_KERNEL_MAX_DT = 4,      /* CFL reduction (two launches) */
+  DG_KERNEL_TAU = 5,         /* isolated tau sweep */
+  DG_KERNEL_TAU_COMBINE = 6, /* non-isolated tau, per sweep entry */
+  DG_KERNEL_PROJECT = 7,     /* order projection / restriction */
+  DG_KERNEL_KINDS = 8
+};
+
+/* Per-kernel timing with CUDA events recorded on the mesh stream around
+ * every launch while enabled (on != 0 resets the totals).  Off by default. */
+dg_status dg_profile_enable(dg_mesh* mesh, int on);
+/* Synchronises the stream and returns, for one kernel kind, the summed
+ * event-measured duration (ms) and the number of timed launches since
+ * profiling was enabled. */
+dg_status dg_profile_read(dg_mesh* mesh, int kernel, double* total_ms, int64_t* launches);
+/* Number of kernels the library has launched on this mesh since creation. */
+dg_status dg_launch_count(const dg_mesh* mesh, int64_t* launches);
+
+/* Synchronises the mesh stream; returns and clears the sticky device error
+ * (DG_OK if none). */
+dg_status dg_get_error(dg_mesh* mesh);
+const char* dg_status_str(dg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

@@ -1,0 +1,677 @@
+// capi.cpp -- mesh construction (host) and the extern "C" entry points of
+// libdg declared in include/dg.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace {
+
+// ------------------------------------------------------------ basis upload
+struct DeviceBasis {
+  bool ready = false;
+  const double* d64 = nullptr;
+  const float* d32 = nullptr;
+  BasisOffsets off{};
+};
+DeviceBasis g_basis[64];
+std::vector<double> g_tables;
+BasisOffsets g_off;
+bool g_tables_built = false;
+
+void ensure_tables() {
+  if (!g_tables_built) {
+    dgb::build_tables(&g_off, &g_tables);
+    g_tables_built = true;
+  }
+}
+
+cudaError_t ensure_device_basis(int dev) {
+  ensure_tables();
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  DeviceBasis& b = g_basis[dev];
+  if (!b.ready) {
+    dgk::upload_basis(dev, g_off, g_tables, &b.d64, &b.d32);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    b.off = g_off;
+    b.ready = true;
+  }
+  return cudaSuccess;
+}
+
+// -------------------------------------------------------------- geometry
+// Apply a (nt x nf) matrix along direction dir of a 3D array (ext[dir] == nf).
+void tensor_apply(const double* A, int nt, int nf, int dir, const int ext[3], const double* in, double* out) {
+  int eo[3] = {ext[0], ext[1], ext[2]};
+  eo[dir] = nt;
+  int stride = dir == 0 ? 1 : (dir == 1 ? ext[0] : ext[0] * ext[1]);
+  for (int k = 0; k < eo[2]; ++k)
+    for (int j = 0; j < eo[1]; ++j)
+      for (int i = 0; i < eo[0]; ++i) {
+        int r = dir == 0 ? i : (dir == 1 ? j : k);
+        int ii = dir == 0 ? 0 : i, jj = dir == 1 ? 0 : j, kk = dir == 2 ? 0 : k;
+        int base = ii + ext[0] * (jj + ext[1] * kk);
+        double s = 0.0;
+        for (int mm = 0; mm < nf; ++mm) s += A[r * nf + mm] * in[base + mm * stride];
+        out[i + eo[0] * (j + eo[1] * k)] = s;
+      }
+}
+
+// Node coordinates X[3][n], metric terms Ja[3][3][n] (J a^i_d) and J[n] of one
+// element at orders N.  The element map is the degree-G tensor polynomial
+// through the equispaced geometry lattice; J a^i in Kopriva's conservative
+// curl form: J a^i_n = -e_i . curl_xi( I^N( X_l grad_xi X_m ) ), (n,m,l)
+// cyclic, which makes sum_i d(J a^i)/dxi_i vanish discretely (free-stream
+// preservation on curved elements).
+void element_geometry(const double* gnodes, int G, const int N[3], std::vector<double>& X, std::vector<double>& Ja,
+                      std::vector<double>& J) {
+  const int ng = G + 1;
+  const int n = (N[0] + 1) * (N[1] + 1) * (N[2] + 1);
+  X.assign(3 * n, 0.0);
+  Ja.assign(9 * n, 0.0);
+  J.assign(n, 0.0);
+  double xs[DG_NP1 + 8];
+  for (int a = 0; a <= G; ++a) xs[a] = -1.0 + 2.0 * a / G;
+  double E[3][DG_NP1 * 16], D[3][DG_NP1 * DG_NP1];
+  for (int d = 0; d < 3; ++d) {
+    double x[DG_NP1], w[DG_NP1];
+    dgb::gl_nodes_weights(N[d], x, w);
+    dgb::interp_matrix(xs, ng, x, N[d] + 1, E[d]);
+    dgb::deriv_matrix(N[d], D[d]);
+  }
+  std::vector<double> a(std::max(n, ng * ng * ng) * 2), b(std::max(n, ng * ng * ng) * 2);
+  for (int c = 0; c < 3; ++c) {
+    for (int p = 0; p < ng * ng * ng; ++p) a[p] = gnodes[3 * p + c];
+    int ext[3] = {ng, ng, ng};
+    for (int d = 0; d < 3; ++d) {
+      tensor_apply(E[d], N[d] + 1, ng, d, ext, a.data(), b.data());
+      ext[d] = N[d] + 1;
+      std::swap(a, b);
+    }
+    std::copy(a.begin(), a.begin() + n, X.begin() + c * n);
+  }
+  const int ext[3] = {N[0] + 1, N[1] + 1, N[2] + 1};
+  std::vector<double> dX(9 * n);  // dX[(c*3+i)*n] = dX_c/dxi_i
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < 3; ++i) tensor_apply(D[i], N[i] + 1, N[i] + 1, i, ext, &X[c * n], &dX[(c * 3 + i) * n]);
+  for (int p = 0; p < n; ++p) {
+    auto g = [&](int c, int i) { return dX[(c * 3 + i) * n + p]; };
+    J[p] = g(0, 0) * (g(1, 1) * g(2, 2) - g(1, 2) * g(2, 1)) - g(0, 1) * (g(1, 0) * g(2, 2) - g(1, 2) * g(2, 0)) +
+           g(0, 2) * (g(1, 0) * g(2, 1) - g(1, 1) * g(2, 0));
+  }
+  std::vector<double> W(3 * n), dW(n);
+  for (int nn = 0; nn < 3; ++nn) {
+    const int mm = (nn + 1) % 3, ll = (nn + 2) % 3;
+    for (int jdir = 0; jdir < 3; ++jdir)
+      for (int p = 0; p < n; ++p) W[jdir * n + p] = X[ll * n + p] * dX[(mm * 3 + jdir) * n + p];
+    for (int i = 0; i < 3; ++i) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+      // (curl W)_i = d_{i1} W_{i2} - d_{i2} W_{i1};  J a^i_nn = -(curl W)_i
+      tensor_apply(D[i1], N[i1] + 1, N[i1] + 1, i1, ext, &W[i2 * n], dW.data());
+      for (int p = 0; p < n; ++p) Ja[(i * 3 + nn) * n + p] -= dW[p];
+      tensor_apply(D[i2], N[i2] + 1, N[i2] + 1, i2, ext, &W[i1 * n], dW.data());
+      for (int p = 0; p < n; ++p) Ja[(i * 3 + nn) * n + p] += dW[p];
+    }
+  }
+}
+
+// Parallelepiped test of a G=1 element; on success the affine metrics
+// (J a^i = cross products of the edge vectors / 4, J = triple product / 8).
+bool affine_metrics(const double* c, double met[10]) {
+  double e1[3], e2[3], e3[3], scale = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    e1[d] = c[3 * 1 + d] - c[3 * 0 + d];
+    e2[d] = c[3 * 2 + d] - c[3 * 0 + d];
+    e3[d] = c[3 * 4 + d] - c[3 * 0 + d];
+    scale = std::max(scale, std::fabs(e1[d]) + std::fabs(e2[d]) + std::fabs(e3[d]));
+  }
+  const int comb[4][4] = {{3, 1, 1, 0}, {5, 1, 0, 1}, {6, 0, 1, 1}, {7, 1, 1, 1}};
+  for (auto& cb : comb)
+    for (int d = 0; d < 3; ++d) {
+      double expect = c[d] + cb[1] * e1[d] + cb[2] * e2[d] + cb[3] * e3[d];
+      if (std::fabs(c[3 * cb[0] + d] - expect) > 1e-13 * scale) return false;
+    }
+  double a1[3], a2[3], a3[3];
+  for (int d = 0; d < 3; ++d) { a1[d] = 0.5 * e1[d]; a2[d] = 0.5 * e2[d]; a3[d] = 0.5 * e3[d]; }
+  auto cross = [](const double* x, const double* y, double* z) {
+    z[0] = x[1] * y[2] - x[2] * y[1];
+    z[1] = x[2] * y[0] - x[0] * y[2];
+    z[2] = x[0] * y[1] - x[1] * y[0];
+  };
+  cross(a2, a3, met + 0);
+  cross(a3, a1, met + 3);
+  cross(a1, a2, met + 6);
+  met[9] = a1[0] * met[0] + a1[1] * met[1] + a1[2] * met[2];
+  return true;
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const T* src, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(dst, sizeof(T) * n);
+  if (e) return e;
+  if (src) return cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
+  return cudaSuccess;
+}
+
+void free_device(dg_mesh_impl* m) {
+  void* ptrs[] = {m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
+                  m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
+                  m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_qc, m->d_rc, m->d_sweep};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
+  m->d_metric32 = nullptr; m->d_surf = nullptr; m->d_surfq = nullptr; m->d_grad = nullptr; m->d_xyz = nullptr;
+  m->d_faces = nullptr; m->d_items = nullptr; m->d_elist = nullptr; m->d_err = nullptr; m->d_scratch = nullptr;
+  m->d_taugeo = nullptr; m->d_taugeo32 = nullptr; m->d_taugeo_off = nullptr; m->d_rp = nullptr; m->d_qc = nullptr;
+  m->d_rc = nullptr; m->d_sweep = nullptr;
+}
+
+void destroy_impl(dg_mesh_impl* m) {
+  if (!m) return;
+  for (auto& pp : m->prof_pending) {
+    cudaEventDestroy(pp.a);
+    cudaEventDestroy(pp.b);
+  }
+  for (auto ev : m->prof_pool) cudaEventDestroy(ev);
+  if (m->prof_open) cudaEventDestroy(m->prof_open);
+  for (auto* c : m->coarse) destroy_impl(c);
+  m->coarse.clear();
+  free_device(m);
+  delete static_cast<dg_mesh*>(m);
+}
+
+#define DG_CUDA(x)                   \
+  do {                               \
+    cudaError_t _e = (x);            \
+    if (_e != cudaSuccess) {         \
+      return _e == cudaErrorMemoryAllocation ? DG_ERR_NOMEM : DG_ERR_CUDA; \
+    }                                \
+  } while (0)
+
+constexpr int kTileNodes = 256;
+
+// Build every host and device structure of a mesh from its host arrays.
+dg_status build(dg_mesh_impl* m) {
+  const int ne = m->n_elem;
+  const int G = m->G;
+  const int ng3 = (G + 1) * (G + 1) * (G + 1);
+  // offsets
+  m->h_off.assign(ne + 1, 0);
+  m->h_soff.assign(ne + 1, 0);
+  m->max_order = 1;
+  for (int e = 0; e < ne; ++e) {
+    const int* N = &m->h_ord[3 * e];
+    for (int d = 0; d < 3; ++d) {
+      if (N[d] < 1 || N[d] > DG_MAX_ORDER) return DG_ERR_ARG;
+      m->max_order = std::max(m->max_order, N[d]);
+    }
+    int64_t a = N[0] + 1, b = N[1] + 1, c = N[2] + 1;
+    m->h_off[e + 1] = m->h_off[e] + a * b * c;
+    m->h_soff[e + 1] = m->h_soff[e] + 2 * (b * c + a * c + a * b);
+  }
+  m->n_nodes = m->h_off[ne];
+  // geometry
+  std::vector<double> met;
+  m->affine = (G == 1);
+  if (m->affine) {
+    met.resize(10 * (size_t)ne);
+    for (int e = 0; e < ne && m->affine; ++e)
+      if (!affine_metrics(&m->h_geom[(size_t)e * ng3 * 3], &met[10 * (size_t)e])) m->affine = false;
+  }
+  if (m->affine) {
+    for (int e = 0; e < ne; ++e)
+      if (!(met[10 * (size_t)e + 9] > 0.0)) return DG_ERR_ARG;
+  } else {
+    met.assign(10 * (size_t)m->n_nodes, 0.0);
+    std::vector<double> X, Ja, J;
+    for (int e = 0; e < ne; ++e) {
+      element_geometry(&m->h_geom[(size_t)e * ng3 * 3], G, &m->h_ord[3 * e], X, Ja, J);
+      const int64_t n = m->h_off[e + 1] - m->h_off[e];
+      double* dst = &met[10 * m->h_off[e]];
+      for (int k = 0; k < 9; ++k) std::copy(Ja.begin() + k * n, Ja.begin() + (k + 1) * n, dst + k * n);
+      for (int64_t p = 0; p < n; ++p) {
+        if (!(J[p] > 0.0)) return DG_ERR_ARG;
+        dst[9 * n + p] = J[p];
+      }
+    }
+  }
+  // faces
+  std::vector<FaceRec> faces;
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  for (int e = 0; e < ne; ++e)
+    for (int d = 0; d < 3; ++d) {
+      const int t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+      for (int side = 0; side < 2; ++side) {
+        const int f = 2 * d + side;
+        const int nb = m->h_nbr[6 * e + f];
+        if (nb >= 0) {
+          if (nb >= ne || m->h_nbr[6 * nb + (f ^ 1)] != e) return DG_ERR_ARG;
+          if (side == 1) {
+            bool conf = m->h_ord[3 * e + t0] == m->h_ord[3 * nb + t0] && m->h_ord[3 * e + t1] == m->h_ord[3 * nb + t1];
+            faces.push_back({e, nb, d, conf ? 0 : 1});
+          }
+        } else {
+          if (nb != DG_BC_FARFIELD && nb != DG_BC_WALL) return DG_ERR_ARG;
+          faces.push_back({e, nb, f, 2});
+        }
+      }
+    }
+  std::stable_sort(faces.begin(), faces.end(), [](const FaceRec& a, const FaceRec& b) { return a.kind < b.kind; });
+  m->n_faces = (int)faces.size();
+  m->n_face_conf = m->n_face_mortar = m->n_face_bnd = 0;
+  for (auto& f : faces) (f.kind == 0 ? m->n_face_conf : f.kind == 1 ? m->n_face_mortar : m->n_face_bnd)++;
+  // mortars are implemented for affine Euler meshes; elsewhere only the
+  // element-local (isolated) operations are available
+  m->faces_unsupported = m->n_face_mortar > 0 && (ns || !m->affine);
+  // work items: elements bucketed by order triple
+  std::map<std::tuple<int, int, int>, std::vector<int32_t>> buckets;
+  for (int e = 0; e < ne; ++e) buckets[{m->h_ord[3 * e], m->h_ord[3 * e + 1], m->h_ord[3 * e + 2]}].push_back(e);
+  std::vector<WorkItem> items;
+  std::vector<int32_t> elist;
+  m->item_max_nodes = 1;
+  for (auto& kv : buckets) {
+    int n1, n2, n3;
+    std::tie(n1, n2, n3) = kv.first;
+    int n = (n1 + 1) * (n2 + 1) * (n3 + 1);
+    int per = std::max(1, kTileNodes / n);
+    const auto& els = kv.second;
+    for (size_t i = 0; i < els.size(); i += per) {
+      int cnt = (int)std::min<size_t>(per, els.size() - i);
+      items.push_back({(int32_t)elist.size(), cnt, n1, n2, n3});
+      for (int c = 0; c < cnt; ++c) elist.push_back(els[i + c]);
+      m->item_max_nodes = std::max(m->item_max_nodes, cnt * n);
+    }
+  }
+  m->n_items = (int)items.size();
+  // device
+  DG_CUDA(upload(&m->d_ord, m->h_ord.data(), m->h_ord.size()));
+  DG_CUDA(upload(&m->d_nbr, m->h_nbr.data(), m->h_nbr.size()));
+  DG_CUDA(upload(&m->d_off, m->h_off.data(), m->h_off.size()));
+  DG_CUDA(upload(&m->d_soff, m->h_soff.data(), m->h_soff.size()));
+  DG_CUDA(upload(&m->d_metric, met.data(), met.size()));
+  if (m->affine) {
+    std::vector<float> m32(met.begin(), met.end());
+    DG_CUDA(upload(&m->d_metric32, m32.data(), m32.size()));
+  }
+  DG_CUDA(upload(&m->d_faces, faces.data(), faces.size()));
+  DG_CUDA(upload(&m->d_items, items.data(), items.size()));
+  DG_CUDA(upload(&m->d_elist, elist.data(), elist.size()));
+  DG_CUDA(upload<double>(&m->d_surf, nullptr, 5 * (size_t)m->h_soff[ne]));
+  if (ns) {
+    DG_CUDA(upload<double>(&m->d_surfq, nullptr, 15 * (size_t)m->h_soff[ne]));
+    DG_CUDA(upload<double>(&m->d_grad, nullptr, 15 * (size_t)m->n_nodes));
+  }
+  DG_CUDA(upload<unsigned>(&m->d_err, nullptr, 1));
+  DG_CUDA(cudaMemset(m->d_err, 0, sizeof(unsigned)));
+  DG_CUDA(upload<double>(&m->d_scratch, nullptr, 4));
+  DG_CUDA(cudaGetDevice(&m->device));
+  DG_CUDA(ensure_device_basis(m->device));
+  m->basis64 = g_basis[m->device].d64;
+  m->basis32 = g_basis[m->device].d32;
+  m->boff = g_basis[m->device].off;
+  return DG_OK;
+}
+
+// Metrics at every coarse order N <= P of every element (curved meshes, for
+// the isolated tau sweep): per element the combos N1 fastest, then N2, N3,
+// each [10][n_N].
+dg_status build_tau_bank(dg_mesh_impl* m) {
+  if (m->affine || m->d_taugeo) return DG_OK;
+  const int ne = m->n_elem, ng3 = (m->G + 1) * (m->G + 1) * (m->G + 1);
+  std::vector<int64_t> off(ne + 1, 0);
+  for (int e = 0; e < ne; ++e) {
+    const int* P = &m->h_ord[3 * e];
+    int64_t s = 1;
+    for (int d = 0; d < 3; ++d) s *= (int64_t)P[d] * (P[d] + 3) / 2;
+    off[e + 1] = off[e] + 10 * s;
+  }
+  std::vector<double> bank(off[ne]);
+  std::vector<double> X, Ja, J;
+  for (int e = 0; e < ne; ++e) {
+    const int* P = &m->h_ord[3 * e];
+    int64_t pos = off[e];
+    for (int N3 = 1; N3 <= P[2]; ++N3)
+      for (int N2 = 1; N2 <= P[1]; ++N2)
+        for (int N1 = 1; N1 <= P[0]; ++N1) {
+          int N[3] = {N1, N2, N3};
+          element_geometry(&m->h_geom[(size_t)e * ng3 * 3], m->G, N, X, Ja, J);
+          int n = (N1 + 1) * (N2 + 1) * (N3 + 1);
+          std::copy(Ja.begin(), Ja.end(), bank.begin() + pos);
+          std::copy(J.begin(), J.end(), bank.begin() + pos + 9 * n);
+          pos += 10 * n;
+        }
+  }
+  std::vector<float> bank32(bank.begin(), bank.end());
+  DG_CUDA(upload(&m->d_taugeo, bank.data(), bank.size()));
+  DG_CUDA(upload(&m->d_taugeo32, bank32.data(), bank32.size()));
+  DG_CUDA(upload(&m->d_taugeo_off, off.data(), off.size()));
+  return DG_OK;
+}
+
+dg_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return DG_OK;
+  return e == cudaErrorMemoryAllocation ? DG_ERR_NOMEM : DG_ERR_CUDA;
+}
+
+dg_status residual_impl(dg_mesh_impl* m, const double* q, double* r, bool isolated) {
+  if (!isolated && m->faces_unsupported) return DG_ERR_UNSUPPORTED;
+  cudaError_t e;
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  if (ns) {
+    if (!isolated && (e = dgk::face_qhat(m, q))) return from_cuda(e);
+    if ((e = dgk::gradient(m, q, m->d_grad, isolated))) return from_cuda(e);
+  }
+  if (!isolated && (e = dgk::face_flux(m, q, m->d_grad, false))) return from_cuda(e);
+  return from_cuda(dgk::volume(m, q, m->d_grad, r, isolated, -1, nullptr, nullptr, nullptr));
+}
+
+dg_mesh_impl* make_child(const dg_mesh_impl* m, const std::vector<int32_t>& orders, dg_status* st) {
+  dg_mesh* c = new dg_mesh();
+  c->stream = m->stream;
+  c->n_elem = m->n_elem;
+  c->G = m->G;
+  c->phys = m->phys;
+  c->h_geom = m->h_geom;
+  c->h_nbr = m->h_nbr;
+  c->h_ord = orders;
+  *st = build(c);
+  if (*st != DG_OK) {
+    destroy_impl(c);
+    return nullptr;
+  }
+  return c;
+}
+
+cudaEvent_t pool_event(dg_mesh_impl* m) {
+  if (!m->prof_pool.empty()) {
+    cudaEvent_t e = m->prof_pool.back();
+    m->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+}  // namespace
+
+// Launch hooks: count every launch; with profiling on, bracket it with a
+// pair of events on the mesh stream (read back in dg_profile_read).
+void dg_prof_begin(dg_mesh_impl* m, int kernel_id, int n_launches) {
+  (void)kernel_id;
+  m->launches += n_launches;
+  if (!m->prof_on) return;
+  m->prof_open = pool_event(m);
+  cudaEventRecord(m->prof_open, m->stream);
+}
+
+void dg_prof_end(dg_mesh_impl* m, int kernel_id) {
+  if (!m->prof_on || !m->prof_open) return;
+  cudaEvent_t b = pool_event(m);
+  cudaEventRecord(b, m->stream);
+  m->prof_pending.push_back({kernel_id, m->prof_open, b});
+  m->prof_open = nullptr;
+}
+
+extern "C" {
+
+dg_status dg_profile_enable(dg_mesh* m, int on) {
+  if (!m) return DG_ERR_ARG;
+  m->prof_on = on != 0;
+  if (on) {
+    for (int k = 0; k < DG_KERNEL_KINDS; ++k) {
+      m->prof_ms[k] = 0.0;
+      m->prof_n[k] = 0;
+    }
+  }
+  return DG_OK;
+}
+
+dg_status dg_profile_read(dg_mesh* m, int kernel, double* total_ms, int64_t* launches) {
+  if (!m || kernel < 0 || kernel >= DG_KERNEL_KINDS) return DG_ERR_ARG;
+  DG_CUDA(m->stream ? cudaStreamSynchronize(m->stream) : cudaDeviceSynchronize());
+  for (auto& pp : m->prof_pending) {
+    float ms = 0.f;
+    DG_CUDA(cudaEventElapsedTime(&ms, pp.a, pp.b));
+    m->prof_ms[pp.id] += ms;
+    m->prof_n[pp.id] += 1;
+    m->prof_pool.push_back(pp.a);
+    m->prof_pool.push_back(pp.b);
+  }
+  m->prof_pending.clear();
+  if (total_ms) *total_ms = m->prof_ms[kernel];
+  if (launches) *launches = m->prof_n[kernel];
+  return DG_OK;
+}
+
+dg_status dg_launch_count(const dg_mesh* m, int64_t* launches) {
+  if (!m || !launches) return DG_ERR_ARG;
+  *launches = m->launches;
+  return DG_OK;
+}
+
+
+const char* dg_status_str(dg_status s) {
+  switch (s) {
+    case DG_OK: return "ok";
+    case DG_ERR_ARG: return "invalid argument";
+    case DG_ERR_NOMEM: return "out of memory";
+    case DG_ERR_CUDA: return "CUDA runtime error";
+    case DG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case DG_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
+    case DG_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+dg_status dg_count_nodes(int32_t n_elem, const int32_t* orders, int64_t* n_nodes) {
+  if (n_elem < 0 || (n_elem > 0 && !orders) || !n_nodes) return DG_ERR_ARG;
+  int64_t s = 0;
+  for (int e = 0; e < n_elem; ++e) {
+    for (int d = 0; d < 3; ++d)
+      if (orders[3 * e + d] < 1 || orders[3 * e + d] > DG_MAX_ORDER) return DG_ERR_ARG;
+    s += (int64_t)(orders[3 * e] + 1) * (orders[3 * e + 1] + 1) * (orders[3 * e + 2] + 1);
+  }
+  *n_nodes = s;
+  return DG_OK;
+}
+
+dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
+  if (!d || !out || d->n_elem <= 0 || d->geom_order < 1 || d->geom_order > 8 || !d->geom || !d->neighbors ||
+      !d->orders)
+    return DG_ERR_ARG;
+  if (d->phys.eqs != DG_EULER && d->phys.eqs != DG_NAVIER_STOKES) return DG_ERR_ARG;
+  if (!(d->phys.gamma > 1.0) || !(d->phys.Rgas > 0.0)) return DG_ERR_ARG;
+  if (d->phys.eqs == DG_NAVIER_STOKES && (!(d->phys.mu >= 0.0) || !(d->phys.Pr > 0.0))) return DG_ERR_ARG;
+  *out = nullptr;
+  dg_mesh* m = new dg_mesh();
+  m->stream = static_cast<cudaStream_t>(stream);
+  m->n_elem = d->n_elem;
+  m->G = d->geom_order;
+  m->phys.eqs = d->phys.eqs;
+  m->phys.gamma = d->phys.gamma;
+  m->phys.mu = d->phys.mu;
+  m->phys.Pr = d->phys.Pr;
+  m->phys.Rgas = d->phys.Rgas;
+  m->phys.kappa = d->phys.eqs == DG_NAVIER_STOKES
+                      ? d->phys.mu * d->phys.gamma * d->phys.Rgas / ((d->phys.gamma - 1.0) * d->phys.Pr)
+                      : 0.0;
+  for (int v = 0; v < 5; ++v) m->phys.qinf[v] = d->phys.q_inf[v];
+  const size_t ng3 = (size_t)(d->geom_order + 1) * (d->geom_order + 1) * (d->geom_order + 1);
+  m->h_geom.assign(d->geom, d->geom + ng3 * 3 * d->n_elem);
+  m->h_nbr.assign(d->neighbors, d->neighbors + 6 * (size_t)d->n_elem);
+  m->h_ord.assign(d->orders, d->orders + 3 * (size_t)d->n_elem);
+  dg_status st = build(m);
+  if (st != DG_OK) {
+    destroy_impl(m);
+    return st;
+  }
+  *out = m;
+  return DG_OK;
+}
+
+dg_status dg_mesh_destroy(dg_mesh* m) {
+  if (!m) return DG_ERR_ARG;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  else cudaDeviceSynchronize();
+  destroy_impl(m);
+  return DG_OK;
+}
+
+dg_status dg_mesh_info(const dg_mesh* m, int64_t* n_nodes, int32_t* n_elem) {
+  if (!m) return DG_ERR_ARG;
+  if (n_nodes) *n_nodes = m->n_nodes;
+  if (n_elem) *n_elem = m->n_elem;
+  return DG_OK;
+}
+
+dg_status dg_set_stream(dg_mesh* m, void* stream) {
+  if (!m) return DG_ERR_ARG;
+  m->stream = static_cast<cudaStream_t>(stream);
+  for (auto* c : m->coarse) c->stream = m->stream;
+  return DG_OK;
+}
+
+dg_status dg_node_coords(dg_mesh* m, double* xyz) {
+  if (!m || !xyz) return DG_ERR_ARG;
+  const int ng3 = (m->G + 1) * (m->G + 1) * (m->G + 1);
+  std::vector<double> out(3 * (size_t)m->n_nodes);
+  std::vector<double> X, Ja, J;
+  for (int e = 0; e < m->n_elem; ++e) {
+    element_geometry(&m->h_geom[(size_t)e * ng3 * 3], m->G, &m->h_ord[3 * e], X, Ja, J);
+    std::copy(X.begin(), X.end(), out.begin() + 3 * m->h_off[e]);
+  }
+  DG_CUDA(cudaMemcpy(xyz, out.data(), sizeof(double) * out.size(), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+dg_status dg_residual(dg_mesh* m, const double* q, double* r, uint32_t flags) {
+  if (!m || !q || !r || q == r || (flags & ~DG_ISOLATED)) return DG_ERR_ARG;
+  return residual_impl(m, q, r, flags & DG_ISOLATED);
+}
+
+dg_status dg_max_dt(dg_mesh* m, const double* q, double cfl, double* dt_dev) {
+  if (!m || !q || !dt_dev || !(cfl > 0.0)) return DG_ERR_ARG;
+  return from_cuda(dgk::max_dt(m, q, cfl, dt_dev));
+}
+
+dg_status dg_rk_step(dg_mesh* m, double* q, double* g, const double* dt_dev) {
+  if (!m || !q || !g || !dt_dev || q == g) return DG_ERR_ARG;
+  if (m->faces_unsupported) return DG_ERR_UNSUPPORTED;
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  cudaError_t e;
+  for (int k = 0; k < 3; ++k) {
+    if (ns) {
+      if ((e = dgk::face_qhat(m, q))) return from_cuda(e);
+      if ((e = dgk::gradient(m, q, m->d_grad, false))) return from_cuda(e);
+    }
+    if ((e = dgk::face_flux(m, q, m->d_grad, false))) return from_cuda(e);
+    if ((e = dgk::volume(m, q, m->d_grad, nullptr, false, k, q, g, dt_dev))) return from_cuda(e);
+  }
+  return DG_OK;
+}
+
+dg_status dg_tau_estimate(dg_mesh* m, const double* q, const double* r_p, const int32_t* sweep, int32_t n_sweep,
+                          uint32_t flags, void* map_new, void* map_trad) {
+  if (!m || !q || !sweep || n_sweep <= 0 || (!map_new && !map_trad)) return DG_ERR_ARG;
+  if (flags & ~(DG_TAU_ISOLATED | DG_TAU_FP32 | DG_TAU_ACCUM_MAX)) return DG_ERR_ARG;
+  for (int s = 0; s < 3 * n_sweep; ++s)
+    if (sweep[s] < 1 || sweep[s] > DG_MAX_ORDER) return DG_ERR_ARG;
+  const bool fp32 = flags & DG_TAU_FP32, acc = flags & DG_TAU_ACCUM_MAX;
+  if (flags & DG_TAU_ISOLATED) {
+    size_t need = dgk::tau_smem_bytes(m, fp32);
+    int limit = 0;
+    DG_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+    if (need + 256 > (size_t)limit) return DG_ERR_UNSUPPORTED;   // static reduction buffers
+    dg_status st = build_tau_bank(m);
+    if (st != DG_OK) return st;
+    std::vector<int32_t> hs(sweep, sweep + 3 * n_sweep);
+    if (hs != m->h_sweep) {
+      if (m->d_sweep) cudaFree(m->d_sweep);
+      m->d_sweep = nullptr;
+      DG_CUDA(upload(&m->d_sweep, hs.data(), hs.size()));
+      m->h_sweep = hs;
+    }
+    return from_cuda(dgk::tau_isolated(m, q, r_p, m->d_sweep, n_sweep, fp32, acc, map_new, map_trad));
+  }
+  // non-isolated: full residual of coarse discretisations with orders min(N, P_e)
+  if (m->faces_unsupported) return DG_ERR_UNSUPPORTED;
+  const double* rp = r_p;
+  if (!rp) {
+    if (!m->d_rp) DG_CUDA(cudaMalloc(&m->d_rp, sizeof(double) * 5 * m->n_nodes));
+    dg_status st = residual_impl(m, q, m->d_rp, false);
+    if (st != DG_OK) return st;
+    rp = m->d_rp;
+  }
+  for (int s = 0; s < n_sweep; ++s) {
+    const int32_t* N = sweep + 3 * s;
+    dg_mesh_impl* c = nullptr;
+    for (size_t i = 0; i < m->coarse.size(); ++i)
+      if (m->coarse_key[3 * i] == N[0] && m->coarse_key[3 * i + 1] == N[1] && m->coarse_key[3 * i + 2] == N[2])
+        c = m->coarse[i];
+    if (!c) {
+      std::vector<int32_t> co(m->h_ord.size());
+      for (int e = 0; e < m->n_elem; ++e)
+        for (int d = 0; d < 3; ++d) co[3 * e + d] = std::min(N[d], m->h_ord[3 * e + d]);
+      dg_status st;
+      c = make_child(m, co, &st);
+      if (!c) return st;
+      DG_CUDA(cudaMalloc(&c->d_qc, sizeof(double) * 5 * c->n_nodes));
+      DG_CUDA(cudaMalloc(&c->d_rc, sizeof(double) * 5 * c->n_nodes));
+      m->coarse.push_back(c);
+      m->coarse_key.insert(m->coarse_key.end(), N, N + 3);
+    }
+    c->stream = m->stream;
+    cudaError_t e;
+    if ((e = dgk::project_orders(m, c->d_ord, c->d_off, q, c->d_qc, 1))) return from_cuda(e);
+    dg_status st = residual_impl(c, c->d_qc, c->d_rc, false);
+    if (st != DG_OK) return st;
+    if ((e = dgk::tau_combine(m, c, rp, c->d_rc, s, n_sweep, sweep, fp32, acc, map_new, map_trad)))
+      return from_cuda(e);
+  }
+  return DG_OK;
+}
+
+dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_old, double* q_new) {
+  if (!m || !new_orders || !q_old || !q_new || q_old == q_new) return DG_ERR_ARG;
+  int64_t nn = 0;
+  if (dg_count_nodes(m->n_elem, new_orders, &nn) != DG_OK) return DG_ERR_ARG;
+  std::vector<int32_t> no(new_orders, new_orders + 3 * (size_t)m->n_elem);
+  dg_status st;
+  dg_mesh_impl* c = make_child(m, no, &st);
+  if (!c) return st;
+  cudaError_t e = dgk::project_orders(m, c->d_ord, c->d_off, q_old, q_new, 0);
+  if (e == cudaSuccess) e = m->stream ? cudaStreamSynchronize(m->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    destroy_impl(c);
+    return from_cuda(e);
+  }
+  // swap the rebuilt structures into m; the old ones leave with c
+  unsigned* old_err = m->d_err;
+  cudaStream_t s = m->stream;
+  std::swap(*static_cast<dg_mesh_impl*>(m), *c);
+  m->stream = s;
+  std::swap(m->d_err, c->d_err);   // keep the sticky error word of the mesh
+  (void)old_err;
+  destroy_impl(c);
+  return DG_OK;
+}
+
+dg_status dg_get_error(dg_mesh* m) {
+  if (!m) return DG_ERR_ARG;
+  cudaError_t e = m->stream ? cudaStreamSynchronize(m->stream) : cudaDeviceSynchronize();
+  if (e) return from_cuda(e);
+  unsigned w = 0;
+  DG_CUDA(cudaMemcpy(&w, m->d_err, sizeof(w), cudaMemcpyDeviceToHost));
+  DG_CUDA(cudaMemset(m->d_err, 0, sizeof(unsigned)));
+  return w ? DG_ERR_NONPHYSICAL : DG_OK;
+}
+
+}  // extern "C"

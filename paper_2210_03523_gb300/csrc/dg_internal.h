@@ -1,0 +1,151 @@
+// dg_internal.h -- internal types of libdg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/dg.h"
+
+#define DG_NV 5
+#define DG_NP1 (DG_MAX_ORDER + 1)
+
+// ---------------------------------------------------------------------------
+// Basis tables (1D, orders 1..DG_MAX_ORDER), built on the host in basis.cpp
+// and uploaded once per device into one buffer, FP64 and FP32 copies.
+// ---------------------------------------------------------------------------
+struct BasisOffsets {
+  int D[DG_NP1];                 // D[N]: (N+1)x(N+1) GL derivative matrix
+  int W[DG_NP1];                 // W[N]: N+1 GL weights
+  int I[DG_NP1][DG_NP1];         // I[f][t]: (t+1)x(f+1) interpolation f -> t
+  int P[DG_NP1][DG_NP1];         // P[f][t]: (t+1)x(f+1) L2 projection f -> t (t <= f)
+  int X[DG_NP1];                 // X[N]: GL nodes
+  int total;
+};
+
+namespace dgb {
+void gl_nodes_weights(int N, double* x, double* w);
+void build_tables(BasisOffsets* off, std::vector<double>* data);
+// host helpers used by mesh construction
+void deriv_matrix(int N, double* D);
+void interp_matrix(const double* xf, int nf, const double* xt, int nt, double* I);
+}  // namespace dgb
+
+// ---------------------------------------------------------------------------
+// Kernel-side views
+// ---------------------------------------------------------------------------
+struct DevPhys {
+  int eqs;
+  double gamma, mu, Pr, Rgas, kappa;
+  double qinf[DG_NV];
+};
+
+// A face processed by the face kernels (one warp each).
+struct FaceRec {
+  int32_t L;       // element on the -xi_dir side (its face 2*dir+1), or the boundary element
+  int32_t R;       // element on the +xi_dir side (its face 2*dir), or a DG_BC_* tag (< 0)
+  int32_t face;    // interior: dir (0..2); boundary: the element's face (0..5)
+  int32_t kind;    // 0 conforming interior, 1 mortar interior, 2 boundary
+};
+
+// Volume work item: `count` elements of one order triple, elist[first..first+count).
+struct WorkItem {
+  int32_t first, count;
+  int32_t n1, n2, n3;
+};
+
+struct dg_mesh_impl;
+
+// per-kernel timing / launch counting hooks (capi.cpp), called by the launchers
+void dg_prof_begin(dg_mesh_impl* m, int kernel_id, int n_launches);
+void dg_prof_end(dg_mesh_impl* m, int kernel_id);
+
+// kernels.cu launchers (all on mesh->stream)
+namespace dgk {
+void upload_basis(int device, const BasisOffsets& off, const std::vector<double>& data, const double** d64,
+                  const float** d32);
+cudaError_t face_flux(dg_mesh_impl* m, const double* q, const double* grad, bool isolated);
+cudaError_t face_qhat(dg_mesh_impl* m, const double* q);
+cudaError_t gradient(dg_mesh_impl* m, const double* q, double* grad, bool isolated);
+cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double* r, bool isolated, int rk_stage,
+                   double* q_io, double* g_io, const double* dt_dev);
+cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev);
+cudaError_t tau_isolated(dg_mesh_impl* m, const double* q, const double* r_p, const int32_t* d_sweep, int n_sweep,
+                         bool fp32, bool accumulate, void* map_new, void* map_trad);
+cudaError_t tau_combine(dg_mesh_impl* m, dg_mesh_impl* coarse, const double* r_p, const double* r_c, int s,
+                        int n_sweep, const int32_t* h_sweep, bool fp32, bool accumulate, void* map_new,
+                        void* map_trad);
+// mode 0: interpolate up / L2-project down (set_orders); mode 1: interpolate (restriction)
+cudaError_t project_orders(dg_mesh_impl* m, const int32_t* d_new_orders, const int64_t* d_new_off,
+                           const double* q_old, double* q_new, int mode);
+size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32);
+}  // namespace dgk
+
+// ---------------------------------------------------------------------------
+// The mesh
+// ---------------------------------------------------------------------------
+struct dg_mesh_impl {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_elem = 0, G = 1;
+  int64_t n_nodes = 0;
+  DevPhys phys{};
+  bool affine = true;       // every element a parallelepiped: metrics per element
+  int max_order = 1;        // max over elements and directions
+  bool faces_unsupported = false;  // mortars on a curved or Navier-Stokes mesh
+
+  // host copies (for rebuilds and coarse meshes)
+  std::vector<double> h_geom;
+  std::vector<int32_t> h_nbr, h_ord;
+  std::vector<int64_t> h_off, h_soff;
+  std::vector<double> h_xyz;       // node coordinates (state-order [d][node] per element)
+
+  // device data
+  int32_t* d_ord = nullptr;        // [e][3]
+  int32_t* d_nbr = nullptr;        // [e][6]
+  int64_t* d_off = nullptr;        // [e+1] node offsets
+  int64_t* d_soff = nullptr;       // [e+1] surface (face-node) offsets, 6 faces per element
+  double* d_metric = nullptr;      // affine: [e][10]; curved: per node [10][n] at 10*off_e (Ja[i][d], J)
+  float* d_metric32 = nullptr;     // affine: FP32 copy for the FP32 tau sweep
+  double* d_surf = nullptr;        // [5 * soff_total] numerical contravariant flux per element face node
+  double* d_surfq = nullptr;       // NS: [15 * soff_total] BR1 q-hat * J a^dir
+  double* d_grad = nullptr;        // NS: [15 * n_nodes] gradient [c][v][node]
+  double* d_xyz = nullptr;         // lazily uploaded coordinates
+  FaceRec* d_faces = nullptr;
+  int n_faces = 0, n_face_conf = 0, n_face_mortar = 0, n_face_bnd = 0;
+  WorkItem* d_items = nullptr;
+  int32_t* d_elist = nullptr;
+  int n_items = 0;
+  int item_max_nodes = 0;          // max count*n over items (smem sizing)
+  unsigned* d_err = nullptr;       // sticky error word
+  double* d_scratch = nullptr;     // dt reduction
+  // tau geometry bank (curved meshes): metrics at every coarse order N <= P
+  double* d_taugeo = nullptr;
+  float* d_taugeo32 = nullptr;
+  int64_t* d_taugeo_off = nullptr;
+
+  const double* basis64 = nullptr;
+  const float* basis32 = nullptr;
+  BasisOffsets boff{};
+
+  std::vector<dg_mesh_impl*> coarse;   // cached non-isolated coarse meshes (by sweep entry)
+  std::vector<int32_t> coarse_key;     // their sweep orders, 3 per entry
+  double* d_rp = nullptr;              // non-isolated tau: full R^P scratch
+  double* d_qc = nullptr;              // coarse mesh: restricted state scratch
+  double* d_rc = nullptr;              // coarse mesh: coarse residual scratch
+  int32_t* d_sweep = nullptr;          // device copy of the last sweep
+  std::vector<int32_t> h_sweep;
+
+  // CUDA-event timing per kernel kind (dg_profile_*), and the launch counter
+  bool prof_on = false;
+  struct ProfPair { int id; cudaEvent_t a, b; };
+  std::vector<ProfPair> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  cudaEvent_t prof_open = nullptr;
+  double prof_ms[DG_KERNEL_KINDS] = {0};
+  int64_t prof_n[DG_KERNEL_KINDS] = {0};
+  int64_t launches = 0;
+};
+
+struct dg_mesh : dg_mesh_impl {};

@@ -1,0 +1,1373 @@
+// kernels.cu -- sm_103a kernels of libdg.
+//
+// Hot path (Sec. 2.1 DGSEM residual, Sec. 3 RK3, Sec. 2.3 tau sweep):
+//   face_flux_kernel   Roe (+ BR1 viscous average) numerical flux per face,
+//                      one warp per face; p-nonconforming faces through a
+//                      mortar staged in shared memory (interpolate both
+//                      traces up, Roe at mortar nodes, L2-project back).
+//   face_qhat_kernel   BR1 q-hat * J a^dir on every face (Navier-Stokes).
+//   gradient_kernel    BR1 gradient, strong form (Navier-Stokes).
+//   volume_kernel      nodal + contravariant flux, sum-factorised GL
+//                      derivative in three directions, surface lift,
+//                      -(1/J) scaling, optionally the fused RK3 stage update.
+//                      Elements of one order triple are batched per CTA
+//                      (work items), all triples in one launch.
+//   tau_kernel<T>      isolated tau sweep, one CTA per element: restriction
+//                      by sum-factorised interpolation (reused across sweep
+//                      entries that share N3 / (N2,N3)), coarse isolated
+//                      residual, both tau forms, block max-reduction.
+// FP64 throughout, except tau_kernel<float>.
+#include <cfloat>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <utility>
+
+#include "dg_internal.h"
+
+__constant__ BasisOffsets c_boff;
+
+namespace {
+
+constexpr int kFaceWarps = 4;          // faces per CTA in the face kernels
+constexpr int kVolThreads = 256;
+constexpr int kTauThreads = 128;
+
+// ------------------------------------------------------------------ helpers
+// offset (in face nodes) of face f inside an element's surface block
+__device__ __forceinline__ int face_offset(int n1, int n2, int n3, int f) {
+  int s0 = n2 * n3, s1 = n1 * n3, s2 = n1 * n2;
+  int o = 0;
+  if (f >= 1) o += s0;
+  if (f >= 2) o += s0;
+  if (f >= 3) o += s1;
+  if (f >= 4) o += s1;
+  if (f >= 5) o += s2;
+  return o;
+}
+
+// volume node index of face node (a, b) on face f; (a, b) run over the
+// two tangential directions in increasing order
+__device__ __forceinline__ int face_vidx(int n1, int n2, int n3, int f, int a, int b) {
+  int d = f >> 1, side = f & 1;
+  int i, j, k;
+  if (d == 0) { i = side ? n1 - 1 : 0; j = a; k = b; }
+  else if (d == 1) { j = side ? n2 - 1 : 0; i = a; k = b; }
+  else { k = side ? n3 - 1 : 0; i = a; j = b; }
+  return i + n1 * (j + n2 * k);
+}
+
+template <typename T>
+__device__ __forceinline__ const T* btab(const T* base, int off) { return base + off; }
+
+// J a^i_d and J of element e at node p (AFFINE: per element)
+template <bool AFFINE>
+__device__ __forceinline__ double metric(const double* M, int e, int64_t off, int n, int p, int m) {
+  if (AFFINE) return __ldg(M + 10 * (int64_t)e + m);
+  return __ldg(M + 10 * off + (int64_t)m * n + p);
+}
+
+struct Prim {
+  double rho, ir, u[3], p;
+};
+
+__device__ __forceinline__ Prim primitive(double gm1, const double q[5]) {
+  Prim s;
+  s.rho = q[0];
+  s.ir = 1.0 / q[0];
+  s.u[0] = q[1] * s.ir;
+  s.u[1] = q[2] * s.ir;
+  s.u[2] = q[3] * s.ir;
+  s.p = gm1 * (q[4] - 0.5 * (q[1] * s.u[0] + q[2] * s.u[1] + q[3] * s.u[2]));
+  return s;
+}
+
+// Roe's approximate Riemann solver: flux through unit normal n from qL to qR.
+__device__ void roe(double gamma, const double qL[5], const double qR[5], const double n[3], double f[5]) {
+  double gm1 = gamma - 1.0;
+  Prim L = primitive(gm1, qL), R = primitive(gm1, qR);
+  double HL = (qL[4] + L.p) * L.ir, HR = (qR[4] + R.p) * R.ir;
+  double sL = sqrt(qL[0]), sR = sqrt(qR[0]);
+  double is = 1.0 / (sL + sR);
+  double ut[3];
+  for (int c = 0; c < 3; ++c) ut[c] = (sL * L.u[c] + sR * R.u[c]) * is;
+  double Ht = (sL * HL + sR * HR) * is;
+  double rt = sL * sR;
+  double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  double c2 = gm1 * (Ht - 0.5 * q2);
+  double ct = sqrt(c2);
+  double ic2 = 1.0 / c2;
+  double unL = L.u[0] * n[0] + L.u[1] * n[1] + L.u[2] * n[2];
+  double unR = R.u[0] * n[0] + R.u[1] * n[1] + R.u[2] * n[2];
+  double utn = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
+  double dun = unR - unL, dp = R.p - L.p, dr = qR[0] - qL[0];
+  double a1 = 0.5 * (dp - rt * ct * dun) * ic2;
+  double a5 = 0.5 * (dp + rt * ct * dun) * ic2;
+  double a2 = dr - dp * ic2;
+  double l1a1 = fabs(utn - ct) * a1, l5a5 = fabs(utn + ct) * a5, l2 = fabs(utn);
+  double dut[3], utdut = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    dut[c] = (R.u[c] - L.u[c]) - dun * n[c];
+    utdut += ut[c] * dut[c];
+  }
+  // physical normal fluxes of both sides
+  double mL = qL[0] * unL, mR = qR[0] * unR;
+  f[0] = 0.5 * (mL + mR) - 0.5 * (l1a1 + l5a5 + l2 * a2);
+  for (int c = 0; c < 3; ++c) {
+    double phys = mL * L.u[c] + L.p * n[c] + mR * R.u[c] + R.p * n[c];
+    double diss = l1a1 * (ut[c] - ct * n[c]) + l5a5 * (ut[c] + ct * n[c]) + l2 * (a2 * ut[c] + rt * dut[c]);
+    f[1 + c] = 0.5 * (phys - diss);
+  }
+  double physE = unL * (qL[4] + L.p) + unR * (qR[4] + R.p);
+  double dissE = l1a1 * (Ht - utn * ct) + l5a5 * (Ht + utn * ct) + l2 * (a2 * 0.5 * q2 + rt * utdut);
+  f[4] = 0.5 * (physE - dissE);
+}
+
+// Navier-Stokes viscous flux for all three directions: fv[d][v].
+// g[v*3+c] = d q_v / d x_c.
+__device__ void viscous(const DevPhys& ph, const double q[5], const double g[15], double fv[3][5]) {
+  double gm1 = ph.gamma - 1.0;
+  Prim s = primitive(gm1, q);
+  double T = s.p * s.ir / ph.Rgas;
+  double du[3][3], dT[3];
+  double half_u2 = 0.5 * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
+  for (int c = 0; c < 3; ++c) {
+    for (int i = 0; i < 3; ++i) du[i][c] = (g[(1 + i) * 3 + c] - s.u[i] * g[c]) * s.ir;
+    double dpc = gm1 * (g[12 + c] - (s.u[0] * g[3 + c] + s.u[1] * g[6 + c] + s.u[2] * g[9 + c]) + half_u2 * g[c]);
+    dT[c] = (dpc - ph.Rgas * T * g[c]) * s.ir / ph.Rgas;
+  }
+  double div = du[0][0] + du[1][1] + du[2][2];
+  for (int d = 0; d < 3; ++d) {
+    double tau[3];
+    for (int i = 0; i < 3; ++i) tau[i] = ph.mu * (du[i][d] + du[d][i]) - (i == d ? (2.0 / 3.0) * ph.mu * div : 0.0);
+    fv[d][0] = 0.0;
+    fv[d][1] = tau[0];
+    fv[d][2] = tau[1];
+    fv[d][3] = tau[2];
+    fv[d][4] = s.u[0] * tau[0] + s.u[1] * tau[1] + s.u[2] * tau[2] + ph.kappa * dT[d];
+  }
+}
+
+__device__ __forceinline__ void bc_ghost(const DevPhys& ph, int tag, const double qi[5], double qg[5]) {
+  if (tag == DG_BC_WALL) {
+    qg[0] = qi[0]; qg[1] = -qi[1]; qg[2] = -qi[2]; qg[3] = -qi[3]; qg[4] = qi[4];
+  } else {
+    for (int v = 0; v < 5; ++v) qg[v] = ph.qinf[v];
+  }
+}
+
+__device__ __forceinline__ void bc_qhat(const DevPhys& ph, int tag, const double qi[5], double qh[5]) {
+  if (tag == DG_BC_WALL) {
+    qh[0] = qi[0]; qh[1] = 0.0; qh[2] = 0.0; qh[3] = 0.0;
+    qh[4] = qi[4] - 0.5 * (qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]) / qi[0];
+  } else {
+    for (int v = 0; v < 5; ++v) qh[v] = ph.qinf[v];
+  }
+}
+
+struct MeshView {
+  const int32_t* ord;
+  const int64_t* off;
+  const int64_t* soff;
+  const double* metric;
+  DevPhys ph;
+};
+
+__device__ __forceinline__ void orders_of(const MeshView& m, int e, int& n1, int& n2, int& n3) {
+  n1 = __ldg(m.ord + 3 * e) + 1;
+  n2 = __ldg(m.ord + 3 * e + 1) + 1;
+  n3 = __ldg(m.ord + 3 * e + 2) + 1;
+}
+
+// ------------------------------------------------------------- face kernels
+struct FaceParams {
+  MeshView m;
+  const FaceRec* faces;
+  int n_faces;
+  const double* q;
+  const double* grad;
+  double* surf;
+  const double* basis;
+  int np_max;            // max order + 1 (mortar smem sizing)
+  int warp_smem;         // doubles per warp
+};
+
+template <bool AFFINE>
+__device__ __forceinline__ void face_metric(const MeshView& m, int e, int n, int vi, int dir, double ja[3]) {
+  int64_t o = AFFINE ? 0 : m.off[e];
+  for (int c = 0; c < 3; ++c) ja[c] = metric<AFFINE>(m.metric, e, o, n, vi, 3 * dir + c);
+}
+
+template <bool AFFINE, bool NS>
+__global__ void __launch_bounds__(32 * kFaceWarps) face_flux_kernel(FaceParams P) {
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int fidx = blockIdx.x * kFaceWarps + warp;
+  if (fidx >= P.n_faces) return;
+  const FaceRec fr = P.faces[fidx];
+  const MeshView& m = P.m;
+  const double gamma = m.ph.gamma;
+
+  if (fr.kind == 2) {  // boundary face of element fr.L, face fr.face, tag fr.R
+    int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1, side = f & 1;
+    int n1, n2, n3;
+    orders_of(m, e, n1, n2, n3);
+    int n = n1 * n2 * n3;
+    int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3;
+    int nf = na * nb;
+    int64_t o = m.off[e];
+    double* out = P.surf + 5 * (m.soff[e] + face_offset(n1, n2, n3, f));
+    for (int p = lane; p < nf; p += 32) {
+      int a = p % na, b = p / na;
+      int vi = face_vidx(n1, n2, n3, f, a, b);
+      double qi[5], qg[5], ja[3], F[5];
+      for (int v = 0; v < 5; ++v) qi[v] = P.q[5 * o + v * n + vi];
+      face_metric<AFFINE>(m, e, n, vi, dir, ja);
+      bc_ghost(m.ph, tag, qi, qg);
+      double area = sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+      double ia = 1.0 / area;
+      double nrm[3] = {ja[0] * ia, ja[1] * ia, ja[2] * ia};
+      if (side) roe(gamma, qi, qg, nrm, F);
+      else roe(gamma, qg, qi, nrm, F);
+      for (int v = 0; v < 5; ++v) F[v] *= area;
+      if (NS) {
+        double g[15], fv[3][5];
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + vi];
+        viscous(m.ph, qi, g, fv);
+        for (int v = 1; v < 4; ++v) F[v] -= fv[0][v] * ja[0] + fv[1][v] * ja[1] + fv[2][v] * ja[2];
+        if (tag != DG_BC_WALL) F[4] -= fv[0][4] * ja[0] + fv[1][4] * ja[1] + fv[2][4] * ja[2];
+      }
+      for (int v = 0; v < 5; ++v) out[v * nf + p] = F[v];
+    }
+    return;
+  }
+
+  const int L = fr.L, R = fr.R, dir = fr.face;
+  int l1, l2, l3, r1, r2, r3;
+  orders_of(m, L, l1, l2, l3);
+  orders_of(m, R, r1, r2, r3);
+  const int nL = l1 * l2 * l3, nR = r1 * r2 * r3;
+  const int64_t oL = m.off[L], oR = m.off[R];
+  const int fL = 2 * dir + 1, fR = 2 * dir;
+  const int la = dir == 0 ? l2 : l1, lb = dir == 2 ? l2 : l3;
+  const int ra = dir == 0 ? r2 : r1, rb = dir == 2 ? r2 : r3;
+  double* outL = P.surf + 5 * (m.soff[L] + face_offset(l1, l2, l3, fL));
+  double* outR = P.surf + 5 * (m.soff[R] + face_offset(r1, r2, r3, fR));
+
+  if (fr.kind == 0) {  // conforming: la == ra, lb == rb
+    const int nf = la * lb;
+    for (int p = lane; p < nf; p += 32) {
+      int a = p % la, b = p / la;
+      int iL = face_vidx(l1, l2, l3, fL, a, b), iR = face_vidx(r1, r2, r3, fR, a, b);
+      double qL[5], qR[5], ja[3], F[5];
+      for (int v = 0; v < 5; ++v) {
+        qL[v] = P.q[5 * oL + v * nL + iL];
+        qR[v] = P.q[5 * oR + v * nR + iR];
+      }
+      face_metric<AFFINE>(m, L, nL, iL, dir, ja);
+      double area = sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+      double ia = 1.0 / area;
+      double nrm[3] = {ja[0] * ia, ja[1] * ia, ja[2] * ia};
+      roe(gamma, qL, qR, nrm, F);
+      for (int v = 0; v < 5; ++v) F[v] *= area;
+      if (NS) {
+        double g[15], fa[3][5], fb[3][5];
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * oL + (c * 5 + v) * nL + iL];
+        viscous(m.ph, qL, g, fa);
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * oR + (c * 5 + v) * nR + iR];
+        viscous(m.ph, qR, g, fb);
+        for (int v = 1; v < 5; ++v)
+          F[v] -= 0.5 * ((fa[0][v] + fb[0][v]) * ja[0] + (fa[1][v] + fb[1][v]) * ja[1] + (fa[2][v] + fb[2][v]) * ja[2]);
+      }
+      for (int v = 0; v < 5; ++v) {
+        outL[v * nf + p] = F[v];
+        outR[v * nf + p] = F[v];
+      }
+    }
+    return;
+  }
+
+  // ---- mortar (Euler only; mesh creation rejects NS with mortars)
+  const int np2 = P.np_max * P.np_max;
+  double* trL = smem + warp * P.warp_smem;  // [8][np2]: q (5) and J a^dir (3) on L's face grid
+  double* trR = trL + 8 * np2;             // [5][np2]
+  double* tmp = trR + 5 * np2;             // [8][np2]
+  double* mL = tmp + 8 * np2;              // [8][np2] on the mortar grid
+  double* mR = mL + 8 * np2;               // [5][np2]
+  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;  // mortar node counts
+  const int nfL = la * lb, nfR = ra * rb, nm = Ma * Mb;
+  for (int p = lane; p < nfL; p += 32) {
+    int a = p % la, b = p / la;
+    int vi = face_vidx(l1, l2, l3, fL, a, b);
+    for (int v = 0; v < 5; ++v) trL[v * np2 + p] = P.q[5 * oL + v * nL + vi];
+    double ja[3];
+    face_metric<AFFINE>(m, L, nL, vi, dir, ja);
+    for (int c = 0; c < 3; ++c) trL[(5 + c) * np2 + p] = ja[c];
+  }
+  for (int p = lane; p < nfR; p += 32) {
+    int a = p % ra, b = p / ra;
+    int vi = face_vidx(r1, r2, r3, fR, a, b);
+    for (int v = 0; v < 5; ++v) trR[v * np2 + p] = P.q[5 * oR + v * nR + vi];
+  }
+  __syncwarp();
+  // interpolate a (n_a x n_b) grid with nvar fields to (Ma x Mb)
+  auto lift_up = [&](const double* src, int na_, int nb_, int nvar, double* dst) {
+    const double* IA = P.basis + c_boff.I[na_ - 1][Ma - 1];
+    const double* IB = P.basis + c_boff.I[nb_ - 1][Mb - 1];
+    for (int t = lane; t < Ma * nb_; t += 32) {
+      int m0 = t % Ma, b = t / Ma;
+      double acc[8];
+      for (int c = 0; c < nvar; ++c) acc[c] = 0.0;
+      for (int a = 0; a < na_; ++a) {
+        double w = __ldg(IA + m0 * na_ + a);
+        for (int c = 0; c < nvar; ++c) acc[c] += w * src[c * np2 + a + na_ * b];
+      }
+      for (int c = 0; c < nvar; ++c) tmp[c * np2 + m0 + Ma * b] = acc[c];
+    }
+    __syncwarp();
+    for (int t = lane; t < nm; t += 32) {
+      int m0 = t % Ma, m1 = t / Ma;
+      double acc[8];
+      for (int c = 0; c < nvar; ++c) acc[c] = 0.0;
+      for (int b = 0; b < nb_; ++b) {
+        double w = __ldg(IB + m1 * nb_ + b);
+        for (int c = 0; c < nvar; ++c) acc[c] += w * tmp[c * np2 + m0 + Ma * b];
+      }
+      for (int c = 0; c < nvar; ++c) dst[c * np2 + t] = acc[c];
+    }
+    __syncwarp();
+  };
+  lift_up(trL, la, lb, 8, mL);
+  lift_up(trR, ra, rb, 5, mR);
+  for (int p = lane; p < nm; p += 32) {
+    double qa[5], qb[5], ja[3], F[5];
+    for (int v = 0; v < 5; ++v) {
+      qa[v] = mL[v * np2 + p];
+      qb[v] = mR[v * np2 + p];
+    }
+    for (int c = 0; c < 3; ++c) ja[c] = mL[(5 + c) * np2 + p];
+    double area = sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+    double ia = 1.0 / area;
+    double nrm[3] = {ja[0] * ia, ja[1] * ia, ja[2] * ia};
+    roe(gamma, qa, qb, nrm, F);
+    for (int v = 0; v < 5; ++v) mL[v * np2 + p] = F[v] * area;
+  }
+  __syncwarp();
+  // L2-project the mortar flux back to a face grid (na_ x nb_) and store
+  auto project_down = [&](int na_, int nb_, double* out) {
+    const double* PA = P.basis + c_boff.P[Ma - 1][na_ - 1];
+    const double* PB = P.basis + c_boff.P[Mb - 1][nb_ - 1];
+    for (int t = lane; t < na_ * Mb; t += 32) {
+      int a = t % na_, m1 = t / na_;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m0 = 0; m0 < Ma; ++m0) {
+        double w = __ldg(PA + a * Ma + m0);
+        for (int v = 0; v < 5; ++v) acc[v] += w * mL[v * np2 + m0 + Ma * m1];
+      }
+      for (int v = 0; v < 5; ++v) tmp[v * np2 + a + na_ * m1] = acc[v];
+    }
+    __syncwarp();
+    const int nf = na_ * nb_;
+    for (int t = lane; t < nf; t += 32) {
+      int a = t % na_, b = t / na_;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int m1 = 0; m1 < Mb; ++m1) {
+        double w = __ldg(PB + b * Mb + m1);
+        for (int v = 0; v < 5; ++v) acc[v] += w * tmp[v * np2 + a + na_ * m1];
+      }
+      for (int v = 0; v < 5; ++v) out[v * nf + t] = acc[v];
+    }
+    __syncwarp();
+  };
+  project_down(la, lb, outL);
+  project_down(ra, rb, outR);
+}
+
+// BR1 trace q-hat (J a^dir) on every face; conforming faces only.
+template <bool AFFINE>
+__global__ void __launch_bounds__(32 * kFaceWarps) face_qhat_kernel(FaceParams P, double* surfq) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int fidx = blockIdx.x * kFaceWarps + warp;
+  if (fidx >= P.n_faces) return;
+  const FaceRec fr = P.faces[fidx];
+  const MeshView& m = P.m;
+  if (fr.kind == 2) {
+    int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1;
+    int n1, n2, n3;
+    orders_of(m, e, n1, n2, n3);
+    int n = n1 * n2 * n3;
+    int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+    int64_t o = m.off[e];
+    double* out = surfq + 15 * (m.soff[e] + face_offset(n1, n2, n3, f));
+    for (int p = lane; p < nf; p += 32) {
+      int vi = face_vidx(n1, n2, n3, f, p % na, p / na);
+      double qi[5], qh[5], ja[3];
+      for (int v = 0; v < 5; ++v) qi[v] = P.q[5 * o + v * n + vi];
+      face_metric<AFFINE>(m, e, n, vi, dir, ja);
+      bc_qhat(m.ph, tag, qi, qh);
+      for (int v = 0; v < 5; ++v)
+        for (int c = 0; c < 3; ++c) out[(v * 3 + c) * nf + p] = qh[v] * ja[c];
+    }
+    return;
+  }
+  const int L = fr.L, R = fr.R, dir = fr.face;
+  int l1, l2, l3, r1, r2, r3;
+  orders_of(m, L, l1, l2, l3);
+  orders_of(m, R, r1, r2, r3);
+  const int nL = l1 * l2 * l3, nR = r1 * r2 * r3;
+  const int64_t oL = m.off[L], oR = m.off[R];
+  const int la = dir == 0 ? l2 : l1, lb = dir == 2 ? l2 : l3, nf = la * lb;
+  double* outL = surfq + 15 * (m.soff[L] + face_offset(l1, l2, l3, 2 * dir + 1));
+  double* outR = surfq + 15 * (m.soff[R] + face_offset(r1, r2, r3, 2 * dir));
+  for (int p = lane; p < nf; p += 32) {
+    int a = p % la, b = p / la;
+    int iL = face_vidx(l1, l2, l3, 2 * dir + 1, a, b), iR = face_vidx(r1, r2, r3, 2 * dir, a, b);
+    double ja[3];
+    face_metric<AFFINE>(m, L, nL, iL, dir, ja);
+    for (int v = 0; v < 5; ++v) {
+      double qh = 0.5 * (P.q[5 * oL + v * nL + iL] + P.q[5 * oR + v * nR + iR]);
+      for (int c = 0; c < 3; ++c) {
+        outL[(v * 3 + c) * nf + p] = qh * ja[c];
+        outR[(v * 3 + c) * nf + p] = qh * ja[c];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------ volume-type kernels
+struct VolParams {
+  MeshView m;
+  const WorkItem* items;
+  int n_items;
+  const int32_t* elist;
+  const double* q;
+  const double* grad;
+  const double* surf;
+  const double* surfq;
+  const double* basis;
+  double* out;        // residual or gradient
+  double* q_io;       // RK: state updated in place
+  double* g_io;       // RK: register
+  const double* dt;
+  double rkA, rkB;
+  int rk;             // 0: write residual; 1: RK stage
+  int rk_first;       // first stage: G = dt R (A = 0)
+  int isolated;
+  unsigned* err;
+};
+
+// Sum-factorised GL derivative of a [3][nv][n] contravariant-flux tile at
+// node (i,j,k): out[v] = sum_m D1[i][m] F1[v][m,j,k] + D2[j][m] F2[v][i,m,k] + D3[k][m] F3[v][i,j,m]
+template <int NVAR>
+__device__ __forceinline__ void div_tile(const double* __restrict__ F, int n1, int n2, int n3, int i, int j, int k,
+                                         const double* D1, const double* D2, const double* D3, double out[NVAR]) {
+  const int n = n1 * n2 * n3;
+  for (int v = 0; v < NVAR; ++v) out[v] = 0.0;
+  const double* F1 = F;
+  const double* F2 = F + NVAR * n;
+  const double* F3 = F + 2 * NVAR * n;
+  int base1 = n1 * (j + n2 * k);
+  for (int mm = 0; mm < n1; ++mm) {
+    double d = __ldg(D1 + i * n1 + mm);
+    for (int v = 0; v < NVAR; ++v) out[v] += d * F1[v * n + base1 + mm];
+  }
+  int base2 = i + n1 * n2 * k;
+  for (int mm = 0; mm < n2; ++mm) {
+    double d = __ldg(D2 + j * n2 + mm);
+    for (int v = 0; v < NVAR; ++v) out[v] += d * F2[v * n + base2 + n1 * mm];
+  }
+  int base3 = i + n1 * j;
+  for (int mm = 0; mm < n3; ++mm) {
+    double d = __ldg(D3 + k * n3 + mm);
+    for (int v = 0; v < NVAR; ++v) out[v] += d * F3[v * n + base3 + n1 * n2 * mm];
+  }
+}
+
+template <bool AFFINE, bool NS>
+__global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
+  extern __shared__ double smem[];
+  const MeshView& m = P.m;
+  const double gm1 = m.ph.gamma - 1.0;
+  for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+    const WorkItem w = P.items[it];
+    const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
+    const int slots = w.count * n;
+    // phase 1: contravariant fluxes into shared memory, [el][3][5][n]
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int e = P.elist[w.first + el];
+      const int64_t o = m.off[e];
+      double q[5];
+      for (int v = 0; v < 5; ++v) q[v] = P.q[5 * o + v * n + p];
+      Prim st = primitive(gm1, q);
+      if (!(q[0] > 0.0) || !(st.p > 0.0)) atomicOr(P.err, 1u);
+      double f[3][5];
+      for (int d = 0; d < 3; ++d) {
+        double ud = st.u[d];
+        f[d][0] = q[1 + d];
+        f[d][1] = q[1] * ud;
+        f[d][2] = q[2] * ud;
+        f[d][3] = q[3] * ud;
+        f[d][1 + d] += st.p;
+        f[d][4] = ud * (q[4] + st.p);
+      }
+      if (NS) {
+        double g[15], fv[3][5];
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + p];
+        viscous(m.ph, q, g, fv);
+        for (int d = 0; d < 3; ++d)
+          for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
+      }
+      double* Ft = smem + (int64_t)el * 15 * n;
+      for (int i = 0; i < 3; ++i) {
+        double ja0 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 0);
+        double ja1 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 1);
+        double ja2 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 2);
+        for (int v = 0; v < 5; ++v) Ft[(i * 5 + v) * n + p] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
+      }
+    }
+    __syncthreads();
+    // phase 2: divergence, surface lift, scaling, output
+    const double* D1 = P.basis + c_boff.D[w.n1];
+    const double* D2 = P.basis + c_boff.D[w.n2];
+    const double* D3 = P.basis + c_boff.D[w.n3];
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int e = P.elist[w.first + el];
+      const int64_t o = m.off[e];
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const double* Ft = smem + (int64_t)el * 15 * n;
+      double vol[5];
+      div_tile<5>(Ft, n1, n2, n3, i, j, k, D1, D2, D3, vol);
+      if (!P.isolated) {
+        const double* sb = P.surf + 5 * m.soff[e];
+        // (face f, own tangential coordinates a,b, direction dir)
+        auto lift = [&](int f, int a, int b, int dir, double sgn, double inv_w) {
+          int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3;
+          int nf = na * nb;
+          const double* F = sb + 5 * face_offset(n1, n2, n3, f);
+          for (int v = 0; v < 5; ++v) vol[v] += sgn * (F[v * nf + a + na * b] - Ft[(dir * 5 + v) * n + p]) * inv_w;
+        };
+        // GL end weights: w_0 = w_N = 2 / (N (N+1))
+        if (i == 0) lift(0, j, k, 0, -1.0, 0.5 * w.n1 * (w.n1 + 1));
+        if (i == n1 - 1) lift(1, j, k, 0, 1.0, 0.5 * w.n1 * (w.n1 + 1));
+        if (j == 0) lift(2, i, k, 1, -1.0, 0.5 * w.n2 * (w.n2 + 1));
+        if (j == n2 - 1) lift(3, i, k, 1, 1.0, 0.5 * w.n2 * (w.n2 + 1));
+        if (k == 0) lift(4, i, j, 2, -1.0, 0.5 * w.n3 * (w.n3 + 1));
+        if (k == n3 - 1) lift(5, i, j, 2, 1.0, 0.5 * w.n3 * (w.n3 + 1));
+      }
+      const double iJ = -1.0 / metric<AFFINE>(m.metric, e, o, n, p, 9);
+      if (P.rk) {
+        const double dt = *P.dt;
+        for (int v = 0; v < 5; ++v) {
+          const int64_t idx = 5 * o + v * n + p;
+          double r = vol[v] * iJ;
+          double g = P.rk_first ? dt * r : P.rkA * P.g_io[idx] + dt * r;
+          P.g_io[idx] = g;
+          P.q_io[idx] = P.q_io[idx] + P.rkB * g;
+        }
+      } else {
+        for (int v = 0; v < 5; ++v) P.out[5 * o + v * n + p] = vol[v] * iJ;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// BR1 gradient (strong form): J g_c = sum_i D^(i)(J a^i_c q) + lifted (q-hat - q) J a^dir_c.
+template <bool AFFINE>
+__global__ void __launch_bounds__(kVolThreads) gradient_kernel(VolParams P) {
+  extern __shared__ double smem[];
+  const MeshView& m = P.m;
+  for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+    const WorkItem w = P.items[it];
+    const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
+    const int slots = w.count * n;
+    const double* D1 = P.basis + c_boff.D[w.n1];
+    const double* D2 = P.basis + c_boff.D[w.n2];
+    const double* D3 = P.basis + c_boff.D[w.n3];
+    for (int c = 0; c < 3; ++c) {
+      for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+        const int el = s / n, p = s - el * n;
+        const int e = P.elist[w.first + el];
+        const int64_t o = m.off[e];
+        double* T = smem + (int64_t)el * 15 * n;
+        for (int i = 0; i < 3; ++i) {
+          double ja = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + c);
+          for (int v = 0; v < 5; ++v) T[(i * 5 + v) * n + p] = ja * P.q[5 * o + v * n + p];
+        }
+      }
+      __syncthreads();
+      for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+        const int el = s / n, p = s - el * n;
+        const int e = P.elist[w.first + el];
+        const int64_t o = m.off[e];
+        const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+        const double* T = smem + (int64_t)el * 15 * n;
+        double acc[5];
+        div_tile<5>(T, n1, n2, n3, i, j, k, D1, D2, D3, acc);
+        if (!P.isolated) {
+          const double* sb = P.surfq + 15 * m.soff[e];
+          auto lift = [&](int f, int a, int b, int dir, double sgn, double inv_w) {
+            int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3;
+            int nf = na * nb;
+            const double* S = sb + 15 * face_offset(n1, n2, n3, f);
+            for (int v = 0; v < 5; ++v)
+              acc[v] += sgn * (S[(v * 3 + c) * nf + a + na * b] - T[(dir * 5 + v) * n + p]) * inv_w;
+          };
+          if (i == 0) lift(0, j, k, 0, -1.0, 0.5 * w.n1 * (w.n1 + 1));
+          if (i == n1 - 1) lift(1, j, k, 0, 1.0, 0.5 * w.n1 * (w.n1 + 1));
+          if (j == 0) lift(2, i, k, 1, -1.0, 0.5 * w.n2 * (w.n2 + 1));
+          if (j == n2 - 1) lift(3, i, k, 1, 1.0, 0.5 * w.n2 * (w.n2 + 1));
+          if (k == 0) lift(4, i, j, 2, -1.0, 0.5 * w.n3 * (w.n3 + 1));
+          if (k == n3 - 1) lift(5, i, j, 2, 1.0, 0.5 * w.n3 * (w.n3 + 1));
+        }
+        const double iJ = 1.0 / metric<AFFINE>(m.metric, e, o, n, p, 9);
+        for (int v = 0; v < 5; ++v) P.out[15 * o + (c * 5 + v) * n + p] = acc[v] * iJ;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ----------------------------------------------------------------- CFL step
+template <bool AFFINE>
+__global__ void __launch_bounds__(kVolThreads) dt_kernel(VolParams P, unsigned long long* smax_bits) {
+  __shared__ double red[kVolThreads / 32];
+  const MeshView& m = P.m;
+  const double gm1 = m.ph.gamma - 1.0;
+  double smax = 0.0;
+  for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+    const WorkItem w = P.items[it];
+    const int nn[3] = {w.n1 + 1, w.n2 + 1, w.n3 + 1};
+    const int n = nn[0] * nn[1] * nn[2];
+    for (int s = threadIdx.x; s < w.count * n; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int e = P.elist[w.first + el];
+      const int64_t o = m.off[e];
+      double q[5];
+      for (int v = 0; v < 5; ++v) q[v] = P.q[5 * o + v * n + p];
+      Prim st = primitive(gm1, q);
+      double c = sqrt(m.ph.gamma * st.p * st.ir);
+      double J = metric<AFFINE>(m.metric, e, o, n, p, 9);
+      double sa = 0.0, sv = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        double ja[3];
+        for (int d = 0; d < 3; ++d) ja[d] = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + d);
+        double a2 = ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2];
+        double un = fabs(ja[0] * st.u[0] + ja[1] * st.u[1] + ja[2] * st.u[2]);
+        double k2 = (double)nn[i] * nn[i];
+        sa += k2 * (un + c * sqrt(a2)) / (2.0 * J);
+        sv += k2 * k2 * a2 / (4.0 * J * J);
+      }
+      double sm = sa;
+      if (m.ph.eqs == DG_NAVIER_STOKES) {
+        double g_pr = m.ph.gamma / m.ph.Pr;
+        double nu = m.ph.mu * st.ir * (g_pr > 1.0 ? g_pr : 1.0);
+        if (sv * nu > sm) sm = sv * nu;
+      }
+      if (!(sm <= DBL_MAX)) atomicOr(P.err, 1u);
+      smax = fmax(smax, sm);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b = fmax(b, red[i]);
+    // non-negative doubles order like their bit patterns
+    atomicMax(smax_bits, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
+__global__ void dt_finalize(const unsigned long long* smax_bits, double cfl, double* dt) {
+  double s = __longlong_as_double((long long)*smax_bits);
+  *dt = cfl / s;
+}
+
+// ----------------------------------------------------------------- tau sweep
+template <typename T>
+__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+template <typename T>
+struct TauParams {
+  MeshView m;
+  int n_elem;
+  const double* q;
+  const double* rp;         // R^P (state layout) or null
+  const int32_t* sweep;     // [n_sweep][3] (device)
+  int n_sweep;
+  const T* basis;           // tables in precision T
+  const T* metric;          // affine: [e][10]; curved: tau geometry bank
+  const int64_t* bank_off;  // curved: per-element bank offset (in T elements)
+  T* map_new;
+  T* map_trad;
+  int accumulate;
+  int S;                    // shared-memory buffer stride (max n_P)
+  T gamma, mu, Pr, Rgas, kappa;
+  unsigned* err;
+};
+
+// offset (in nodes) of the metrics of coarse orders (N1,N2,N3) inside an
+// element's bank (all combos N <= P, N1 fastest, then N2, then N3)
+__device__ __forceinline__ int64_t bank_combo_offset(int P1, int P2, int N1, int N2, int N3) {
+  auto Sk = [](int k) { return (int64_t)k * (k + 3) / 2; };  // sum_{a=1..k} (a+1)
+  int64_t s1 = Sk(P1), s2 = Sk(P2);
+  return s1 * s2 * Sk(N3 - 1) + s1 * Sk(N2 - 1) * (N3 + 1) + Sk(N1 - 1) * (int64_t)(N2 + 1) * (N3 + 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void euler_fluxes(T gm1, const T q[5], T f[3][5]) {
+  T ir = (T)1 / q[0];
+  T u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  T pr = gm1 * (q[4] - (T)0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  for (int d = 0; d < 3; ++d) {
+    f[d][0] = q[1 + d];
+    f[d][1] = q[1] * u[d];
+    f[d][2] = q[2] * u[d];
+    f[d][3] = q[3] * u[d];
+    f[d][1 + d] += pr;
+    f[d][4] = u[d] * (q[4] + pr);
+  }
+}
+
+template <typename T>
+__device__ void viscous_t(const TauParams<T>& P, const T q[5], const T g[15], T fv[3][5]) {
+  T gm1 = P.gamma - (T)1;
+  T ir = (T)1 / q[0];
+  T u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  T pr = gm1 * (q[4] - (T)0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  T Tm = pr * ir / P.Rgas;
+  T half_u2 = (T)0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  T du[3][3], dT[3];
+  for (int c = 0; c < 3; ++c) {
+    for (int i = 0; i < 3; ++i) du[i][c] = (g[(1 + i) * 3 + c] - u[i] * g[c]) * ir;
+    T dpc = gm1 * (g[12 + c] - (u[0] * g[3 + c] + u[1] * g[6 + c] + u[2] * g[9 + c]) + half_u2 * g[c]);
+    dT[c] = (dpc - P.Rgas * Tm * g[c]) * ir / P.Rgas;
+  }
+  T div = du[0][0] + du[1][1] + du[2][2];
+  for (int d = 0; d < 3; ++d) {
+    T tau[3];
+    for (int i = 0; i < 3; ++i) tau[i] = P.mu * (du[i][d] + du[d][i]) - (i == d ? (T)(2.0 / 3.0) * P.mu * div : (T)0);
+    fv[d][0] = 0;
+    fv[d][1] = tau[0];
+    fv[d][2] = tau[1];
+    fv[d][3] = tau[2];
+    fv[d][4] = u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2] + P.kappa * dT[d];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T met_at(const T* met, bool affine, int n, int p, int mm) {
+  return affine ? met[mm] : met[mm * n + p];
+}
+
+// sum-factorised GL derivative of a [3][5][n] tile at node p
+template <typename T>
+__device__ __forceinline__ void div5(const T* basis, const T* F, int n1, int n2, int n3, int p, T acc[5]) {
+  const int n = n1 * n2 * n3;
+  const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+  const T* D1 = basis + c_boff.D[n1 - 1];
+  const T* D2 = basis + c_boff.D[n2 - 1];
+  const T* D3 = basis + c_boff.D[n3 - 1];
+  for (int v = 0; v < 5; ++v) acc[v] = 0;
+  int b1 = n1 * (j + n2 * k), b2 = i + n1 * n2 * k, b3 = i + n1 * j;
+  for (int mm = 0; mm < n1; ++mm) {
+    T d = D1[i * n1 + mm];
+    for (int v = 0; v < 5; ++v) acc[v] += d * F[(0 * 5 + v) * n + b1 + mm];
+  }
+  for (int mm = 0; mm < n2; ++mm) {
+    T d = D2[j * n2 + mm];
+    for (int v = 0; v < 5; ++v) acc[v] += d * F[(1 * 5 + v) * n + b2 + n1 * mm];
+  }
+  for (int mm = 0; mm < n3; ++mm) {
+    T d = D3[k * n3 + mm];
+    for (int v = 0; v < 5; ++v) acc[v] += d * F[(2 * 5 + v) * n + b3 + n1 * n2 * mm];
+  }
+}
+
+// Isolated residual of a [5][n] state tile at orders (n1,n2,n3) with metrics
+// met: R = -(1/J) sum_i D^(i) Ft^i (Euler) or, for Navier-Stokes, with the
+// element-local BR1 gradient and the viscous flux.  Ft: [15][n] scratch,
+// Gs: [15][n] scratch (NS).  Result in Rout[5][rstride].
+template <typename T, bool NS>
+__device__ void isolated_residual_tile(const TauParams<T>& P, bool affine, const T* met, const T* Qs, int qs, int n1,
+                                       int n2, int n3, T* Ft, T* Gs, T* Rout, int rs) {
+  const int n = n1 * n2 * n3;
+  const T gm1 = P.gamma - (T)1;
+  if (NS) {
+    for (int c = 0; c < 3; ++c) {
+      for (int p = threadIdx.x; p < n; p += blockDim.x)
+        for (int i = 0; i < 3; ++i) {
+          T ja = met_at(met, affine, n, p, 3 * i + c);
+          for (int v = 0; v < 5; ++v) Ft[(i * 5 + v) * n + p] = ja * Qs[v * qs + p];
+        }
+      __syncthreads();
+      for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        T acc[5];
+        div5(P.basis, Ft, n1, n2, n3, p, acc);
+        T iJ = (T)1 / met_at(met, affine, n, p, 9);
+        for (int v = 0; v < 5; ++v) Gs[(v * 3 + c) * n + p] = acc[v] * iJ;
+      }
+      __syncthreads();
+    }
+  }
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    T q[5], f[3][5];
+    for (int v = 0; v < 5; ++v) q[v] = Qs[v * qs + p];
+    euler_fluxes(gm1, q, f);
+    if (NS) {
+      T g[15], fv[3][5];
+      for (int c = 0; c < 15; ++c) g[c] = Gs[c * n + p];
+      viscous_t(P, q, g, fv);
+      for (int d = 0; d < 3; ++d)
+        for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
+    }
+    for (int i = 0; i < 3; ++i) {
+      T ja0 = met_at(met, affine, n, p, 3 * i), ja1 = met_at(met, affine, n, p, 3 * i + 1),
+        ja2 = met_at(met, affine, n, p, 3 * i + 2);
+      for (int v = 0; v < 5; ++v) Ft[(i * 5 + v) * n + p] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    T acc[5];
+    div5(P.basis, Ft, n1, n2, n3, p, acc);
+    T iJ = -(T)1 / met_at(met, affine, n, p, 9);
+    for (int v = 0; v < 5; ++v) Rout[v * rs + p] = acc[v] * iJ;
+  }
+  __syncthreads();
+}
+
+// apply a (t x f) matrix along direction dir of an [nvar][e0 e1 e2] tile
+template <typename T>
+__device__ void apply_dir_tile(const T* A, int t, int f, int dir, int e0, int e1, int e2, const T* in, int sin_,
+                               T* out, int sout, int nvar) {
+  int o0 = e0, o1 = e1, o2 = e2;
+  if (dir == 0) o0 = t; else if (dir == 1) o1 = t; else o2 = t;
+  const int no = o0 * o1 * o2;
+  for (int p = threadIdx.x; p < no; p += blockDim.x) {
+    int i = p % o0, j = (p / o0) % o1, k = p / (o0 * o1);
+    int r, base, stride;
+    if (dir == 0) { r = i; base = e0 * (j + e1 * k); stride = 1; }
+    else if (dir == 1) { r = j; base = i + e0 * e1 * k; stride = e0; }
+    else { r = k; base = i + e0 * j; stride = e0 * e1; }
+    for (int c = 0; c < nvar; ++c) {
+      T acc = 0;
+      for (int mm = 0; mm < f; ++mm) acc += A[r * f + mm] * in[c * sin_ + base + mm * stride];
+      out[c * sout + p] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void block_max2(T& a, T& b, T (*red)[kTauThreads / 32]) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a = tmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = tmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      a = tmax(a, red[0][i]);
+      b = tmax(b, red[1][i]);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void map_store(T* map, int64_t idx, int accumulate, T v) {
+  if (!map) return;
+  map[idx] = accumulate ? tmax(map[idx], v) : v;
+}
+
+template <typename T, bool AFFINE, bool NS>
+__global__ void __launch_bounds__(kTauThreads) tau_kernel(TauParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ T red[2][kTauThreads / 32];
+  const int S = P.S;
+  T* QR = sm;            // [10][S]  q^P (0..4) and R^P (5..9)
+  T* A3 = QR + 10 * S;   // [10][S]  restricted in xi3
+  T* A2 = A3 + 10 * S;   // [10][S]  restricted in xi2, xi3
+  T* A1 = A2 + 10 * S;   // [10][S]  I q^P (0..4), I R^P (5..9) at N
+  T* RN = A1 + 10 * S;   // [5][S]   R^N(I q^P)
+  T* Ft = RN + 5 * S;    // [15][S]
+  T* Gs = Ft + 15 * S;   // [15][S]  (NS only: the Euler launch allocates 60 S)
+  const MeshView& m = P.m;
+  for (int e = blockIdx.x; e < P.n_elem; e += gridDim.x) {
+    int n1, n2, n3;
+    orders_of(m, e, n1, n2, n3);
+    const int P1 = n1 - 1, P2 = n2 - 1, P3 = n3 - 1;
+    const int nP = n1 * n2 * n3;
+    const int64_t o = m.off[e];
+    const T* metP = AFFINE ? P.metric + 10 * (int64_t)e
+                           : P.metric + P.bank_off[e] + 10 * bank_combo_offset(P1, P2, P1, P2, P3);
+    for (int p = threadIdx.x; p < nP; p += blockDim.x) {
+      for (int v = 0; v < 5; ++v) QR[v * S + p] = (T)P.q[5 * o + v * nP + p];
+      if (P.rp)
+        for (int v = 0; v < 5; ++v) QR[(5 + v) * S + p] = (T)P.rp[5 * o + v * nP + p];
+    }
+    __syncthreads();
+    if (!P.rp) isolated_residual_tile<T, NS>(P, AFFINE, metP, QR, S, n1, n2, n3, Ft, Gs, QR + 5 * S, S);
+    int cur3 = -1, cur2 = -1;
+    for (int s = 0; s < P.n_sweep; ++s) {
+      const int N1 = P.sweep[3 * s], N2 = P.sweep[3 * s + 1], N3 = P.sweep[3 * s + 2];
+      const int64_t idx = (int64_t)e * P.n_sweep + s;
+      if (N1 > P1 || N2 > P2 || N3 > P3) {
+        if (threadIdx.x == 0) {
+          if (P.map_new) P.map_new[idx] = (T)-1;
+          if (P.map_trad) P.map_trad[idx] = (T)-1;
+        }
+        continue;
+      }
+      if (N3 != cur3) {
+        apply_dir_tile(P.basis + c_boff.I[P3][N3], N3 + 1, n3, 2, n1, n2, n3, QR, S, A3, S, 10);
+        cur3 = N3;
+        cur2 = -1;
+      }
+      if (N2 != cur2) {
+        apply_dir_tile(P.basis + c_boff.I[P2][N2], N2 + 1, n2, 1, n1, n2, N3 + 1, A3, S, A2, S, 10);
+        cur2 = N2;
+      }
+      apply_dir_tile(P.basis + c_boff.I[P1][N1], N1 + 1, n1, 0, n1, N2 + 1, N3 + 1, A2, S, A1, S, 10);
+      const int c1 = N1 + 1, c2 = N2 + 1, c3 = N3 + 1, nN = c1 * c2 * c3;
+      const T* metN = AFFINE ? metP : P.metric + P.bank_off[e] + 10 * bank_combo_offset(P1, P2, N1, N2, N3);
+      isolated_residual_tile<T, NS>(P, AFFINE, metN, A1, S, c1, c2, c3, Ft, Gs, RN, S);
+      const T* w1 = P.basis + c_boff.W[N1];
+      const T* w2 = P.basis + c_boff.W[N2];
+      const T* w3 = P.basis + c_boff.W[N3];
+      T a = 0, b = 0;
+      for (int p = threadIdx.x; p < nN; p += blockDim.x) {
+        const int i = p % c1, j = (p / c1) % c2, k = p / (c1 * c2);
+        T Jw = met_at(metN, AFFINE, nN, p, 9) * w1[i] * w2[j] * w3[k];
+        for (int v = 0; v < 5; ++v) {
+          T t = A1[(5 + v) * S + p] - RN[v * S + p];   // tau~ = I R^P - R^N(I q^P)
+          a = tmax(a, (T)fabs(t));
+          b = tmax(b, (T)fabs(Jw * t));
+        }
+      }
+      block_max2(a, b, red);
+      if (threadIdx.x == 0) {
+        map_store(P.map_new, idx, P.accumulate, a);
+        map_store(P.map_trad, idx, P.accumulate, b);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Non-isolated tau, final step for one sweep entry s of orders N: per
+// element with N <= P, tau~ = I_{N<-P} R^P - R_c (R_c the residual of the
+// coarse discretisation), both norms.  Coarse J from the coarse mesh.
+template <typename MT, bool AFFINE>
+__global__ void __launch_bounds__(kTauThreads) tau_combine_kernel(MeshView fine, MeshView coarse, const double* rp,
+                                                                  const double* rc, const double* basis, int N1,
+                                                                  int N2, int N3, int s, int n_sweep, int S,
+                                                                  int accumulate, MT* map_new, MT* map_trad,
+                                                                  int n_elem) {
+  extern __shared__ double smd[];
+  __shared__ double red[2][kTauThreads / 32];
+  double* B0 = smd;
+  double* B1 = B0 + 5 * S;
+  double* B2 = B1 + 5 * S;
+  for (int e = blockIdx.x; e < n_elem; e += gridDim.x) {
+    int n1, n2, n3;
+    orders_of(fine, e, n1, n2, n3);
+    const int64_t idx = (int64_t)e * n_sweep + s;
+    if (N1 > n1 - 1 || N2 > n2 - 1 || N3 > n3 - 1) {
+      if (threadIdx.x == 0) {
+        if (map_new) map_new[idx] = (MT)-1;
+        if (map_trad) map_trad[idx] = (MT)-1;
+      }
+      continue;
+    }
+    const int nP = n1 * n2 * n3;
+    const int64_t o = fine.off[e], oc = coarse.off[e];
+    for (int p = threadIdx.x; p < nP; p += blockDim.x)
+      for (int v = 0; v < 5; ++v) B0[v * S + p] = rp[5 * o + v * nP + p];
+    __syncthreads();
+    apply_dir_tile(basis + c_boff.I[n3 - 1][N3], N3 + 1, n3, 2, n1, n2, n3, B0, S, B1, S, 5);
+    apply_dir_tile(basis + c_boff.I[n2 - 1][N2], N2 + 1, n2, 1, n1, n2, N3 + 1, B1, S, B2, S, 5);
+    apply_dir_tile(basis + c_boff.I[n1 - 1][N1], N1 + 1, n1, 0, n1, N2 + 1, N3 + 1, B2, S, B0, S, 5);
+    const int c1 = N1 + 1, c2 = N2 + 1, c3 = N3 + 1, nN = c1 * c2 * c3;
+    const double* w1 = basis + c_boff.W[N1];
+    const double* w2 = basis + c_boff.W[N2];
+    const double* w3 = basis + c_boff.W[N3];
+    double a = 0, b = 0;
+    for (int p = threadIdx.x; p < nN; p += blockDim.x) {
+      const int i = p % c1, j = (p / c1) % c2, k = p / (c1 * c2);
+      double J = metric<AFFINE>(coarse.metric, e, oc, nN, p, 9);
+      double Jw = J * w1[i] * w2[j] * w3[k];
+      for (int v = 0; v < 5; ++v) {
+        double t = B0[v * S + p] - rc[5 * oc + v * nN + p];
+        a = fmax(a, fabs(t));
+        b = fmax(b, fabs(Jw * t));
+      }
+    }
+    block_max2(a, b, red);
+    if (threadIdx.x == 0) {
+      if (map_new) map_new[idx] = accumulate ? (MT)fmax((double)map_new[idx], a) : (MT)a;
+      if (map_trad) map_trad[idx] = accumulate ? (MT)fmax((double)map_trad[idx], b) : (MT)b;
+    }
+    __syncthreads();
+  }
+}
+
+// Per-element projection of the state between orders: mode 0 (set_orders):
+// interpolation where the order rises, L2 projection where it falls;
+// mode 1 (restriction): interpolation in every direction.
+__global__ void __launch_bounds__(kTauThreads) project_kernel(const int32_t* ord_old, const int64_t* off_old,
+                                                              const int32_t* ord_new, const int64_t* off_new,
+                                                              const double* basis, const double* q_old,
+                                                              double* q_new, int n_elem, int S, int mode) {
+  extern __shared__ double smd[];
+  double* B0 = smd;
+  double* B1 = B0 + 5 * S;
+  for (int e = blockIdx.x; e < n_elem; e += gridDim.x) {
+    int f[3], t[3];
+    for (int d = 0; d < 3; ++d) {
+      f[d] = ord_old[3 * e + d];
+      t[d] = ord_new[3 * e + d];
+    }
+    const int nf = (f[0] + 1) * (f[1] + 1) * (f[2] + 1), nt = (t[0] + 1) * (t[1] + 1) * (t[2] + 1);
+    for (int p = threadIdx.x; p < nf; p += blockDim.x)
+      for (int v = 0; v < 5; ++v) B0[v * S + p] = q_old[5 * off_old[e] + v * nf + p];
+    __syncthreads();
+    int ext[3] = {f[0] + 1, f[1] + 1, f[2] + 1};
+    double* src = B0;
+    double* dst = B1;
+    for (int d = 0; d < 3; ++d) {
+      int mo = (mode == 1 || t[d] >= f[d]) ? c_boff.I[f[d]][t[d]] : c_boff.P[f[d]][t[d]];
+      apply_dir_tile(basis + mo, t[d] + 1, f[d] + 1, d, ext[0], ext[1], ext[2], src, S, dst, S, 5);
+      ext[d] = t[d] + 1;
+      double* tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    for (int p = threadIdx.x; p < nt; p += blockDim.x)
+      for (int v = 0; v < 5; ++v) q_new[5 * off_new[e] + v * nt + p] = src[v * S + p];
+    __syncthreads();
+  }
+}
+
+MeshView view(const dg_mesh_impl* m) {
+  MeshView v;
+  v.ord = m->d_ord;
+  v.off = m->d_off;
+  v.soff = m->d_soff;
+  v.metric = m->d_metric;
+  v.ph = m->phys;
+  return v;
+}
+
+int grid_for(int work, int per_sm_blocks) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int cap = sms * per_sm_blocks;
+  return work < cap ? (work > 0 ? work : 1) : cap;
+}
+
+// Raise a kernel's dynamic shared-memory limit to the device opt-in maximum
+// once (so that no attribute call is needed later, e.g. under stream capture).
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+  static std::map<std::pair<int, const void*>, int> raised;   // (device, kernel) -> limit set
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
+  auto it = raised.find(key);
+  if (it != raised.end() && (int)bytes <= it->second) return cudaSuccess;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e) return e;
+  const int limit = optin - (int)fa.sharedSizeBytes;   // dynamic + static <= opt-in maximum
+  if ((int)bytes > limit) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+  if (e == cudaSuccess) raised[key] = limit;
+  return e;
+}
+
+// brackets a launch with the mesh's timing/counting hooks
+struct Prof {
+  dg_mesh_impl* m;
+  int id;
+  Prof(dg_mesh_impl* mm, int k, int n = 1) : m(mm), id(k) { dg_prof_begin(m, k, n); }
+  ~Prof() { dg_prof_end(m, id); }
+};
+
+}  // namespace
+
+namespace dgk {
+
+void upload_basis(int device, const BasisOffsets& off, const std::vector<double>& data, const double** d64,
+                  const float** d32) {
+  (void)device;
+  cudaMemcpyToSymbol(c_boff, &off, sizeof(off));
+  double* a = nullptr;
+  float* b = nullptr;
+  cudaMalloc(&a, sizeof(double) * data.size());
+  cudaMalloc(&b, sizeof(float) * data.size());
+  cudaMemcpy(a, data.data(), sizeof(double) * data.size(), cudaMemcpyHostToDevice);
+  std::vector<float> f(data.begin(), data.end());
+  cudaMemcpy(b, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+  *d64 = a;
+  *d32 = b;
+}
+
+static FaceParams face_params(dg_mesh_impl* m, const double* q, const double* grad) {
+  FaceParams P;
+  P.m = view(m);
+  P.faces = m->d_faces;
+  P.n_faces = m->n_faces;
+  P.q = q;
+  P.grad = grad;
+  P.surf = m->d_surf;
+  P.basis = m->basis64;
+  P.np_max = m->max_order + 1;
+  P.warp_smem = 34 * P.np_max * P.np_max;
+  return P;
+}
+
+cudaError_t face_flux(dg_mesh_impl* m, const double* q, const double* grad, bool isolated) {
+  (void)isolated;
+  if (m->n_faces == 0) return cudaSuccess;
+  FaceParams P = face_params(m, q, grad);
+  size_t smem = m->n_face_mortar ? sizeof(double) * P.warp_smem * kFaceWarps : 0;
+  int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+  bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  cudaError_t err;
+  Prof pr(m, DG_KERNEL_FACE_FLUX);
+  if (m->affine && !ns) {
+    if ((err = allow_smem(face_flux_kernel<true, false>, smem))) return err;
+    face_flux_kernel<true, false><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
+  } else if (m->affine) {
+    if ((err = allow_smem(face_flux_kernel<true, true>, smem))) return err;
+    face_flux_kernel<true, true><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
+  } else if (!ns) {
+    if ((err = allow_smem(face_flux_kernel<false, false>, smem))) return err;
+    face_flux_kernel<false, false><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
+  } else {
+    if ((err = allow_smem(face_flux_kernel<false, true>, smem))) return err;
+    face_flux_kernel<false, true><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t face_qhat(dg_mesh_impl* m, const double* q) {
+  if (m->n_faces == 0) return cudaSuccess;
+  FaceParams P = face_params(m, q, nullptr);
+  int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+  Prof pr(m, DG_KERNEL_FACE_QHAT);
+  if (m->affine) face_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, m->d_surfq);
+  else face_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, m->d_surfq);
+  return cudaGetLastError();
+}
+
+static VolParams vol_params(dg_mesh_impl* m, const double* q) {
+  VolParams P;
+  memset(&P, 0, sizeof(P));
+  P.m = view(m);
+  P.items = m->d_items;
+  P.n_items = m->n_items;
+  P.elist = m->d_elist;
+  P.q = q;
+  P.grad = m->d_grad;
+  P.surf = m->d_surf;
+  P.surfq = m->d_surfq;
+  P.basis = m->basis64;
+  P.err = m->d_err;
+  return P;
+}
+
+cudaError_t gradient(dg_mesh_impl* m, const double* q, double* grad, bool isolated) {
+  VolParams P = vol_params(m, q);
+  P.out = grad;
+  P.isolated = isolated;
+  size_t smem = sizeof(double) * 15 * m->item_max_nodes;
+  int grid = grid_for(m->n_items, 8);
+  cudaError_t err;
+  Prof pr(m, DG_KERNEL_GRADIENT);
+  if (m->affine) {
+    if ((err = allow_smem(gradient_kernel<true>, smem))) return err;
+    gradient_kernel<true><<<grid, kVolThreads, smem, m->stream>>>(P);
+  } else {
+    if ((err = allow_smem(gradient_kernel<false>, smem))) return err;
+    gradient_kernel<false><<<grid, kVolThreads, smem, m->stream>>>(P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double* r, bool isolated, int rk_stage,
+                   double* q_io, double* g_io, const double* dt_dev) {
+  static const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+  static const double B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+  VolParams P = vol_params(m, q);
+  P.grad = grad;
+  P.out = r;
+  P.isolated = isolated;
+  if (rk_stage >= 0) {
+    P.rk = 1;
+    P.rk_first = rk_stage == 0;
+    P.rkA = A[rk_stage];
+    P.rkB = B[rk_stage];
+    P.q_io = q_io;
+    P.g_io = g_io;
+    P.dt = dt_dev;
+  }
+  size_t smem = sizeof(double) * 15 * m->item_max_nodes;
+  int grid = grid_for(m->n_items, 8);
+  bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  cudaError_t err;
+  Prof pr(m, DG_KERNEL_VOLUME);
+  if (m->affine && !ns) {
+    if ((err = allow_smem(volume_kernel<true, false>, smem))) return err;
+    volume_kernel<true, false><<<grid, kVolThreads, smem, m->stream>>>(P);
+  } else if (m->affine) {
+    if ((err = allow_smem(volume_kernel<true, true>, smem))) return err;
+    volume_kernel<true, true><<<grid, kVolThreads, smem, m->stream>>>(P);
+  } else if (!ns) {
+    if ((err = allow_smem(volume_kernel<false, false>, smem))) return err;
+    volume_kernel<false, false><<<grid, kVolThreads, smem, m->stream>>>(P);
+  } else {
+    if ((err = allow_smem(volume_kernel<false, true>, smem))) return err;
+    volume_kernel<false, true><<<grid, kVolThreads, smem, m->stream>>>(P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev) {
+  VolParams P = vol_params(m, q);
+  unsigned long long* bits = reinterpret_cast<unsigned long long*>(m->d_scratch);
+  cudaError_t err = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), m->stream);
+  if (err) return err;
+  int grid = grid_for(m->n_items, 8);
+  Prof pr(m, DG_KERNEL_MAX_DT, 2);
+  if (m->affine) dt_kernel<true><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
+  else dt_kernel<false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
+  dt_finalize<<<1, 1, 0, m->stream>>>(bits, cfl, dt_dev);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, size_t smem) {
+  int grid = grid_for(m->n_elem, 4);
+  bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  cudaError_t err;
+  Prof pr(m, DG_KERNEL_TAU);
+#define DG_TAU_CASE(AFF, NSV)                                                   \
+  if ((err = allow_smem(tau_kernel<T, AFF, NSV>, smem))) return err;             \
+  tau_kernel<T, AFF, NSV><<<grid, kTauThreads, smem, m->stream>>>(P);
+  if (m->affine && !ns) { DG_TAU_CASE(true, false) }
+  else if (m->affine) { DG_TAU_CASE(true, true) }
+  else if (!ns) { DG_TAU_CASE(false, false) }
+  else { DG_TAU_CASE(false, true) }
+#undef DG_TAU_CASE
+  return cudaGetLastError();
+}
+
+size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32) {
+  int S = 1;
+  std::vector<int32_t>& o = m->h_ord;
+  for (int e = 0; e < m->n_elem; ++e) {
+    int n = (o[3 * e] + 1) * (o[3 * e + 1] + 1) * (o[3 * e + 2] + 1);
+    if (n > S) S = n;
+  }
+  const int bufs = m->phys.eqs == DG_NAVIER_STOKES ? 75 : 60;
+  return (size_t)bufs * S * (fp32 ? sizeof(float) : sizeof(double));
+}
+
+cudaError_t tau_isolated(dg_mesh_impl* m, const double* q, const double* r_p, const int32_t* d_sweep, int n_sweep,
+                         bool fp32, bool accumulate, void* map_new, void* map_trad) {
+  int S = 1;
+  for (int e = 0; e < m->n_elem; ++e) {
+    int n = (m->h_ord[3 * e] + 1) * (m->h_ord[3 * e + 1] + 1) * (m->h_ord[3 * e + 2] + 1);
+    if (n > S) S = n;
+  }
+  auto fill = [&](auto& P) {
+    P.m = view(m);
+    P.n_elem = m->n_elem;
+    P.q = q;
+    P.rp = r_p;
+    P.sweep = d_sweep;
+    P.n_sweep = n_sweep;
+    P.accumulate = accumulate;
+    P.S = S;
+    P.gamma = m->phys.gamma;
+    P.mu = m->phys.mu;
+    P.Pr = m->phys.Pr;
+    P.Rgas = m->phys.Rgas;
+    P.kappa = m->phys.kappa;
+    P.err = m->d_err;
+    P.bank_off = m->d_taugeo_off;
+  };
+  if (fp32) {
+    TauParams<float> P;
+    fill(P);
+    P.basis = m->basis32;
+    P.metric = m->affine ? m->d_metric32 : m->d_taugeo32;
+    P.map_new = static_cast<float*>(map_new);
+    P.map_trad = static_cast<float*>(map_trad);
+    return tau_launch(m, P, tau_smem_bytes(m, true));
+  }
+  TauParams<double> P;
+  fill(P);
+  P.basis = m->basis64;
+  P.metric = m->affine ? m->d_metric : m->d_taugeo;
+  P.map_new = static_cast<double*>(map_new);
+  P.map_trad = static_cast<double*>(map_trad);
+  return tau_launch(m, P, tau_smem_bytes(m, false));
+}
+
+cudaError_t tau_combine(dg_mesh_impl* m, dg_mesh_impl* c, const double* r_p, const double* r_c, int s, int n_sweep,
+                        const int32_t* h_sweep, bool fp32, bool accumulate, void* map_new, void* map_trad) {
+  int S = 1;
+  for (int e = 0; e < m->n_elem; ++e) {
+    int n = (m->h_ord[3 * e] + 1) * (m->h_ord[3 * e + 1] + 1) * (m->h_ord[3 * e + 2] + 1);
+    if (n > S) S = n;
+  }
+  size_t smem = sizeof(double) * 15 * S;
+  int grid = grid_for(m->n_elem, 4);
+  int N1 = h_sweep[3 * s], N2 = h_sweep[3 * s + 1], N3 = h_sweep[3 * s + 2];
+  cudaError_t err;
+  Prof pr(m, DG_KERNEL_TAU_COMBINE);
+#define DG_COMB(MT, AFF)                                                                                     \
+  if ((err = allow_smem(tau_combine_kernel<MT, AFF>, smem))) return err;                                      \
+  tau_combine_kernel<MT, AFF><<<grid, kTauThreads, smem, m->stream>>>(                                        \
+      view(m), view(c), r_p, r_c, m->basis64, N1, N2, N3, s, n_sweep, S, accumulate, static_cast<MT*>(map_new), \
+      static_cast<MT*>(map_trad), m->n_elem);
+  if (fp32 && m->affine) { DG_COMB(float, true) }
+  else if (fp32) { DG_COMB(float, false) }
+  else if (m->affine) { DG_COMB(double, true) }
+  else { DG_COMB(double, false) }
+#undef DG_COMB
+  return cudaGetLastError();
+}
+
+cudaError_t project_orders(dg_mesh_impl* m, const int32_t* d_new_orders, const int64_t* d_new_off,
+                           const double* q_old, double* q_new, int mode) {
+  const int S = (DG_MAX_ORDER + 1) * (DG_MAX_ORDER + 1) * (DG_MAX_ORDER + 1);
+  size_t smem = sizeof(double) * 10 * S;
+  int grid = grid_for(m->n_elem, 4);
+  cudaError_t err = allow_smem(project_kernel, smem);
+  if (err) return err;
+  Prof pr(m, DG_KERNEL_PROJECT);
+  project_kernel<<<grid, kTauThreads, smem, m->stream>>>(m->d_ord, m->d_off, d_new_orders, d_new_off, m->basis64, q_old,
+                                                          q_new, m->n_elem, S, mode);
+  return cudaGetLastError();
+}
+
+}  // namespace dgk

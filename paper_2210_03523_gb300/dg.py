@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libdg (include/dg.h).
+
+It does argument marshalling only: every step of the hot path runs in the
+CUDA library. Device buffers are torch tensors, used for memory and streams
+and nothing else. The binding fails loudly when libdg.so has not been built;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdg.so")
+
+DG_EULER, DG_NAVIER_STOKES = 0, 1
+DG_ISOLATED = 0x1
+DG_TAU_ISOLATED = 0x1
+DG_TAU_FP32 = 0x2
+DG_TAU_ACCUM_MAX = 0x4
+DG_MAX_ORDER = 8
+KERNELS = {"face_flux": 0, "face_qhat": 1, "gradient": 2, "volume": 3, "max_dt": 4, "tau": 5, "tau_combine": 6,
+           "project": 7}
+STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_NOMEM", 3: "DG_ERR_CUDA", 4: "DG_ERR_UNSUPPORTED",
+          5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_TIMEOUT"}
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_lib().dg_status_str(status).decode()})")
+
+
+class dg_physics(C.Structure):
+    _fields_ = [("eqs", C.c_int32), ("gamma", C.c_double), ("mu", C.c_double), ("Pr", C.c_double),
+                ("Rgas", C.c_double), ("q_inf", C.c_double * 5)]
+
+
+class dg_mesh_desc(C.Structure):
+    _fields_ = [("n_elem", C.c_int32), ("geom_order", C.c_int32), ("geom", C.POINTER(C.c_double)),
+                ("neighbors", C.POINTER(C.c_int32)), ("orders", C.POINTER(C.c_int32)), ("phys", dg_physics)]
+
+
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdg.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64p, i32p = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)
+        L.dg_status_str.restype = C.c_char_p
+        L.dg_status_str.argtypes = [C.c_int]
+        sig = {
+            "dg_mesh_create": [C.POINTER(dg_mesh_desc), vp, C.POINTER(vp)],
+            "dg_mesh_destroy": [vp],
+            "dg_mesh_info": [vp, i64p, i32p],
+            "dg_count_nodes": [C.c_int32, i32p, i64p],
+            "dg_set_stream": [vp, vp],
+            "dg_node_coords": [vp, vp],
+            "dg_residual": [vp, vp, vp, C.c_uint32],
+            "dg_max_dt": [vp, vp, C.c_double, vp],
+            "dg_rk_step": [vp, vp, vp, vp],
+            "dg_tau_estimate": [vp, vp, vp, i32p, C.c_int32, C.c_uint32, vp, vp],
+            "dg_set_orders": [vp, i32p, vp, vp],
+            "dg_get_error": [vp],
+            "dg_profile_enable": [vp, C.c_int],
+            "dg_profile_read": [vp, C.c_int, C.POINTER(C.c_double), i64p],
+            "dg_launch_count": [vp, i64p],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        _L = L
+    return _L
+
+
+def exported_symbols():
+    return ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_count_nodes", "dg_set_stream", "dg_node_coords",
+            "dg_residual", "dg_max_dt", "dg_rk_step", "dg_tau_estimate", "dg_set_orders", "dg_get_error",
+            "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count"]
+
+
+def _check(st, where):
+    if st != 0:
+        raise DGError(st, where)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def dg_count_nodes(orders) -> int:
+    o = np.ascontiguousarray(np.asarray(orders, dtype=np.int32).reshape(-1, 3))
+    n = C.c_int64()
+    _check(_lib().dg_count_nodes(o.shape[0], o.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)), "dg_count_nodes")
+    return n.value
+
+
+class Mesh:
+    """A libdg mesh built from a ``paper_2210_03523_gb300.inputs.MeshInput``."""
+
+    def __init__(self, mi, stream=None):
+        import torch
+        self.mi = mi
+        self._geom = np.ascontiguousarray(mi.geom, dtype=np.float64)
+        self._nbr = np.ascontiguousarray(mi.neighbors, dtype=np.int32)
+        self._ord = np.ascontiguousarray(mi.orders, dtype=np.int32)
+        ph = mi.phys
+        d = dg_mesh_desc()
+        d.n_elem = mi.n_elem
+        d.geom_order = mi.geom_order
+        d.geom = self._geom.ctypes.data_as(C.POINTER(C.c_double))
+        d.neighbors = self._nbr.ctypes.data_as(C.POINTER(C.c_int32))
+        d.orders = self._ord.ctypes.data_as(C.POINTER(C.c_int32))
+        d.phys = dg_physics(ph.eqs, ph.gamma, ph.mu, ph.Pr, ph.Rgas, (C.c_double * 5)(*ph.qinf))
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._stream = stream
+        h = C.c_void_p()
+        _check(_lib().dg_mesh_create(C.byref(d), _stream_handle(stream), C.byref(h)), "dg_mesh_create")
+        self.h = h
+        self._refresh()
+
+    def _refresh(self):
+        n, e = C.c_int64(), C.c_int32()
+        _check(_lib().dg_mesh_info(self.h, C.byref(n), C.byref(e)), "dg_mesh_info")
+        self.n_nodes, self.n_elem = n.value, e.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().dg_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def new_state(self):
+        import torch
+        return torch.zeros(5 * self.n_nodes, dtype=torch.float64, device=self.device)
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(_lib().dg_set_stream(self.h, _stream_handle(stream)), "dg_set_stream")
+
+    def coords(self):
+        import torch
+        x = torch.empty(3 * self.n_nodes, dtype=torch.float64, device=self.device)
+        _check(_lib().dg_node_coords(self.h, _ptr(x)), "dg_node_coords")
+        return x
+
+    def residual(self, q, r=None, isolated=False):
+        r = self.new_state() if r is None else r
+        _check(_lib().dg_residual(self.h, _ptr(q), _ptr(r), DG_ISOLATED if isolated else 0), "dg_residual")
+        return r
+
+    def max_dt(self, q, cfl, dt=None):
+        import torch
+        dt = torch.empty(1, dtype=torch.float64, device=self.device) if dt is None else dt
+        _check(_lib().dg_max_dt(self.h, _ptr(q), float(cfl), _ptr(dt)), "dg_max_dt")
+        return dt
+
+    def rk_step(self, q, g, dt):
+        _check(_lib().dg_rk_step(self.h, _ptr(q), _ptr(g), _ptr(dt)), "dg_rk_step")
+
+    def tau_estimate(self, q, sweep, isolated=True, fp32=False, accumulate=False, r_p=None, map_new=None,
+                     map_trad=None, want=(True, True)):
+        import torch
+        sw = np.ascontiguousarray(np.asarray(sweep, dtype=np.int32).reshape(-1, 3))
+        ns = sw.shape[0]
+        dt = torch.float32 if fp32 else torch.float64
+        if map_new is None and want[0]:
+            map_new = torch.empty((self.n_elem, ns), dtype=dt, device=self.device)
+        if map_trad is None and want[1]:
+            map_trad = torch.empty((self.n_elem, ns), dtype=dt, device=self.device)
+        flags = (DG_TAU_ISOLATED if isolated else 0) | (DG_TAU_FP32 if fp32 else 0) | \
+                (DG_TAU_ACCUM_MAX if accumulate else 0)
+        self._sweep_keep = sw
+        _check(_lib().dg_tau_estimate(self.h, _ptr(q), _ptr(r_p), sw.ctypes.data_as(C.POINTER(C.c_int32)), ns, flags,
+                                      _ptr(map_new), _ptr(map_trad)), "dg_tau_estimate")
+        return map_new, map_trad
+
+    def set_orders(self, new_orders, q_old):
+        import torch
+        o = np.ascontiguousarray(np.asarray(new_orders, dtype=np.int32).reshape(-1, 3))
+        q_new = torch.empty(5 * dg_count_nodes(o), dtype=torch.float64, device=self.device)
+        _check(_lib().dg_set_orders(self.h, o.ctypes.data_as(C.POINTER(C.c_int32)), _ptr(q_old), _ptr(q_new)),
+               "dg_set_orders")
+        self._ord = o
+        self._refresh()
+        return q_new
+
+    def get_error(self):
+        return _lib().dg_get_error(self.h)
+
+    def profile_enable(self, on=True):
+        _check(_lib().dg_profile_enable(self.h, int(on)), "dg_profile_enable")
+
+    def profile_read(self, kernel):
+        ms, n = C.c_double(), C.c_int64()
+        _check(_lib().dg_profile_read(self.h, int(kernel), C.byref(ms), C.byref(n)), "dg_profile_read")
+        return ms.value, n.value
+
+    def launch_count(self):
+        n = C.c_int64()
+        _check(_lib().dg_launch_count(self.h, C.byref(n)), "dg_launch_count")
+        return n.value

@@ -288,6 +288,7 @@ def seeded_perturbation(n_scalars, seed, amplitude) -> np.ndarray:
 def workload(name: str) -> MeshInput:
     """pulse4: 4^3 periodic straight hexes, P=(4,4,4);
     pulse16mixed: 16^3, orders iid U{1..6} (seed 2210);
+    pulse32mixed: 32^3, orders iid U{1..6} (seed 2210), a working set above L2;
     cylinder: 40x24x1 curved O-grid, geometry order 3, P=(6,6,1);
     pulse48mixed: 48^3, orders iid U{2..8} (seed 2210);
     pulse48uniform: 48^3, P=(5,5,5)."""
@@ -297,6 +298,8 @@ def workload(name: str) -> MeshInput:
         return box_mesh(16, orders=random_orders(16 ** 3, 1, 6, 2210), phys=pulse_physics())
     if name == "cylinder":
         return ogrid_mesh(phys=cylinder_physics())
+    if name == "pulse32mixed":
+        return box_mesh(32, orders=random_orders(32 ** 3, 1, 6, 2210), phys=pulse_physics())
     if name == "pulse48mixed":
         return box_mesh(48, orders=random_orders(48 ** 3, 2, 8, 2210), phys=pulse_physics())
     if name == "pulse48uniform":

@@ -57,3 +57,14 @@ def rel_err(a, b, nvar_off, s=None):
             den = max(den, s[v])
         out.append(np.abs(A[v] - B[v]).max() / den)
     return np.array(out)
+
+
+def state_scale(q, off):
+    """per-variable state scale: |rho|, the largest momentum component (for all
+    three momenta, so an identically-zero component is measured against the
+    others), |rho E|"""
+    n_el = len(off) - 1
+    blk = [q[5 * off[e]:5 * off[e + 1]].reshape(5, -1) for e in range(n_el)]
+    mx = np.array([max(np.abs(b[v]).max() for b in blk) for v in range(5)])
+    m = mx[1:4].max()
+    return np.array([mx[0], m, m, m, mx[4]])

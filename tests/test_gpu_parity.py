@@ -1,0 +1,322 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element on the same seeded inputs.  Bar: relative 1e-12 for the FP64
+residual, RK step, CFL step and FP64 tau; the stated FP32 bound for tau.
+Relative errors are per variable, ||gpu - oracle||_inf / max(||oracle||_inf, s)
+with s the variable's flux scale over the element size (so near-zero
+residuals are measured against the size of the terms that cancel)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2210_03523_gb300 import inputs as I
+from oracle_helpers import rel_err, scale_per_var, state_scale
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_03523_gb300 import build
+    build.build()
+    return torch
+
+
+def _cases():
+    ph = I.pulse_physics()
+    A = [[1.0, 0.3, 0.1], [0.0, 0.9, -0.2], [0.1, 0.0, 1.2]]
+    return {
+        "pulse4_P4": (I.box_mesh(4, orders=(4, 4, 4), phys=ph), 0.1),
+        "mixed5_1to6": (I.box_mesh(5, orders=I.random_orders(125, 1, 6, 5), phys=ph), 0.3),
+        "aniso_3x4x2_ragged": (I.box_mesh(3, 4, 2, orders=I.random_orders(24, 1, 8, 6), phys=ph), 0.3),
+        "sheared_mixed": (I.box_mesh(3, mapping=I.affine_map(A), orders=I.random_orders(27, 1, 5, 8),
+                                     phys=I.pulse_physics(mach=0.3)), 0.3),
+        "wavy_curved": (I.box_mesh(3, geom_order=3, mapping=I.wavy_map(0.08), orders=(3, 4, 2),
+                                   phys=I.pulse_physics(mach=0.3)), 0.3),
+        "wavy_curved_mortar": (I.box_mesh(3, geom_order=3, mapping=I.wavy_map(0.08),
+                                          orders=I.random_orders(27, 1, 5, 9), phys=I.pulse_physics(mach=0.3)),
+                               0.3),
+    }
+
+
+CASES = _cases()
+
+
+def _setup(torch, name):
+    import oracle
+    from paper_2210_03523_gb300 import dg
+    mi, width = CASES[name]
+    om = oracle.Mesh(mi)
+    q = I.pulse_state(om.coords(), om.orders, mi.phys, width=width)
+    return mi, om, dg.Mesh(mi), q
+
+
+def _h(mi):
+    return 2.0 / max(np.cbrt(mi.n_elem), 1.0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("isolated", [False, True])
+def test_residual_parity(torch_cuda, name, isolated):
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, name)
+    if name == "wavy_curved_mortar" and not isolated:
+        from paper_2210_03523_gb300 import dg
+        with pytest.raises(dg.DGError) as ei:
+            m.residual(torch.from_numpy(q).cuda())
+        assert ei.value.status == 4            # curved mortars: face-coupled calls unsupported
+        return
+    r = m.residual(torch.from_numpy(q).cuda(), isolated=isolated).cpu().numpy()
+    ro = om.residual(q, isolated=isolated)
+    err = rel_err(r, ro, om.off, scale_per_var(q, mi.phys, _h(mi)))
+    assert err.max() < RTOL, err
+    assert m.get_error() == 0
+
+
+def test_residual_parity_full_size_pulse16_mixed(torch_cuda):
+    """The bench workload itself: 16^3 elements, orders iid U{1..6} (seed 2210)."""
+    torch = torch_cuda
+    import oracle
+    from paper_2210_03523_gb300 import dg
+    mi = I.workload("pulse16mixed")
+    om = oracle.Mesh(mi)
+    q = I.pulse_state_fast(om.coords(), om.orders, mi.phys)
+    m = dg.Mesh(mi)
+    r = m.residual(torch.from_numpy(q).cuda()).cpu().numpy()
+    ro = om.residual(q)
+    err = rel_err(r, ro, om.off, scale_per_var(q, mi.phys, 2.0 / 16))
+    assert err.max() < RTOL, err
+
+
+@pytest.mark.parametrize("name,steps", [("pulse4_P4", 20), ("mixed5_1to6", 8), ("sheared_mixed", 5),
+                                        ("wavy_curved", 5)])
+def test_rk3_parity(torch_cuda, name, steps):
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, name)
+    dt = om.max_dt(q, 0.5)
+    qg = torch.from_numpy(q).cuda()
+    gg = torch.zeros_like(qg)
+    dtd = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    qo, go = q.copy(), np.zeros_like(q)
+    for _ in range(steps):
+        m.rk_step(qg, gg, dtd)
+        om.rk_step(qo, go, dt)
+    err = rel_err(qg.cpu().numpy(), qo, om.off, state_scale(qo, om.off))
+    assert err.max() < RTOL, err
+    errg = rel_err(gg.cpu().numpy(), go, om.off, scale_per_var(q, mi.phys, _h(mi)) * dt)
+    assert errg.max() < RTOL, errg
+
+
+@pytest.mark.parametrize("name", ["pulse4_P4", "mixed5_1to6", "wavy_curved"])
+def test_max_dt_parity(torch_cuda, name):
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, name)
+    dt = m.max_dt(torch.from_numpy(q).cuda(), 0.5).item()
+    dto = om.max_dt(q, 0.5)
+    assert abs(dt - dto) <= RTOL * dto
+
+
+def _tau_tol(map_o, mi, q, om, trad=False):
+    """tau parity: RTOL relative to max(||tau||, s), s the residual's flux scale
+    over the element size (tau~ is a difference of two residuals, so its
+    rounding is set by the size of the terms that cancel, as for R itself);
+    the traditional form carries max J w in addition"""
+    s = scale_per_var(q, mi.phys, _h(mi)).max()
+    if trad:
+        s *= max(om.metrics(e)[2].max() for e in range(om.n_elem))
+    return RTOL * max(np.abs(map_o).max(), s)
+
+
+@pytest.mark.parametrize("name", ["pulse4_P4", "mixed5_1to6", "aniso_3x4x2_ragged", "wavy_curved",
+                                  "wavy_curved_mortar"])
+def test_tau_isolated_fp64_parity(torch_cuda, name):
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, name)
+    P = om.orders.max(0)
+    sweep = I.full_sweep(P)
+    nmax = int(((om.orders + 1).prod(1)).max())
+    if 60 * nmax * 8 > 227 * 1024:
+        # the FP64 sweep keeps 60 n_P doubles per element in shared memory
+        from paper_2210_03523_gb300 import dg
+        with pytest.raises(dg.DGError) as ei:
+            m.tau_estimate(torch.from_numpy(q).cuda(), sweep)
+        assert ei.value.status == 4
+        return
+    tn, tt = m.tau_estimate(torch.from_numpy(q).cuda(), sweep)
+    on, ot = om.tau(q, sweep)
+    tn, tt = tn.cpu().numpy(), tt.cpu().numpy()
+    assert np.array_equal(tn < 0, on < 0)
+    assert np.abs(tn - on).max() <= _tau_tol(on, mi, q, om)
+    assert np.abs(tt - ot).max() <= _tau_tol(ot, mi, q, om, trad=True)
+    # tau at the element's own orders is exactly zero
+    for e in range(m.n_elem):
+        s = [k for k, N in enumerate(sweep) if (N == om.orders[e]).all()][0]
+        assert tn[e, s] == 0.0 and tt[e, s] == 0.0
+
+
+def test_tau_paper_sweep_pulse4(torch_cuda):
+    """pulse4 workload: the sweep N in {1,2,3}^3 after 20 RK3 steps."""
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, "pulse4_P4")
+    dt = om.max_dt(q, 0.5)
+    qo, go = q.copy(), np.zeros_like(q)
+    for _ in range(20):
+        om.rk_step(qo, go, dt)
+    sweep = np.array([(a, b, c) for c in (1, 2, 3) for b in (1, 2, 3) for a in (1, 2, 3)], dtype=np.int32)
+    tn, tt = m.tau_estimate(torch.from_numpy(qo).cuda(), sweep)
+    on, ot = om.tau(qo, sweep)
+    assert np.abs(tn.cpu().numpy() - on).max() <= _tau_tol(on, mi, qo, om)
+    assert np.abs(tt.cpu().numpy() - ot).max() <= _tau_tol(ot, mi, qo, om, trad=True)
+
+
+def _fp32_scale(om, q, mi):
+    """per element: (sum_i ||D^(P_i)||_inf) * max |flux| * max|J a| / min J -- the size
+    of the terms whose FP32 rounding enters tau (the fluxes cancel in the derivative)"""
+    import oracle
+    gam = mi.phys.gamma
+    out = np.empty(om.n_elem)
+    for e in range(om.n_elem):
+        Q = om.elem(q, e)
+        rho = Q[0]
+        u = Q[1:4] / rho
+        p = (gam - 1) * (Q[4] - 0.5 * rho * (u * u).sum(0))
+        fmax = np.max(np.abs(np.concatenate([Q[1:4] * u[c] for c in range(3)] + [Q[1:4], [p], u * (Q[4] + p)])))
+        _, Ja, J = om.metrics(e)
+        dn = sum(np.abs(oracle.dmat(int(N))).sum(1).max() for N in om.orders[e])
+        out[e] = dn * fmax * np.abs(Ja).max() / J.min()
+    return out
+
+
+@pytest.mark.parametrize("name", ["pulse4_P4", "mixed5_1to6", "wavy_curved"])
+def test_tau_isolated_fp32_bound(torch_cuda, name):
+    """FP32 sweep against the FP64 oracle: |tau32 - tau64| <= 8 eps32 S_e per
+    element, S_e = (sum_i ||D^(P_i)||_inf) max|f| max|J a| / min J (new form;
+    the traditional form carries the factor max J w in addition)."""
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, name)
+    sweep = I.full_sweep(om.orders.max(0))
+    tn, tt = m.tau_estimate(torch.from_numpy(q).cuda(), sweep, fp32=True)
+    assert tn.dtype == torch.float32
+    on, ot = om.tau(q, sweep)
+    tn, tt = tn.cpu().numpy().astype(np.float64), tt.cpu().numpy().astype(np.float64)
+    assert np.array_equal(tn < 0, on < 0)
+    S = _fp32_scale(om, q, mi)
+    eps = np.finfo(np.float32).eps
+    ok = on >= 0
+    d = np.abs(tn - on) / S[:, None]
+    assert (d[ok] <= 8 * eps).all(), d[ok].max() / eps
+    Jw = np.array([om.metrics(e)[2].max() for e in range(om.n_elem)])
+    dt_ = np.abs(tt - ot) / (S * Jw * 4.0)[:, None]
+    assert (dt_[ok] <= 8 * eps).all(), dt_[ok].max() / eps
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_tau_accumulate(torch_cuda, fp32):
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, "mixed5_1to6")
+    q2 = I.pulse_state(om.coords(), om.orders, mi.phys, width=0.25, center=(0.3, 0.1, 0.0))
+    sweep = I.full_sweep((6, 6, 6))
+    a, b = m.tau_estimate(torch.from_numpy(q).cuda(), sweep, fp32=fp32)
+    a1, b1 = a.clone(), b.clone()
+    m.tau_estimate(torch.from_numpy(q2).cuda(), sweep, fp32=fp32, accumulate=True, map_new=a, map_trad=b)
+    a2, b2 = m.tau_estimate(torch.from_numpy(q2).cuda(), sweep, fp32=fp32)
+    assert torch.equal(a, torch.maximum(a1, a2)) and torch.equal(b, torch.maximum(b1, b2))
+
+
+def test_tau_non_isolated_parity(torch_cuda):
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, "pulse4_P4")
+    sweep = np.array([[4, 4, 4], [3, 3, 3], [2, 3, 4], [1, 1, 1], [3, 1, 2], [1, 4, 2]], dtype=np.int32)
+    tn, tt = m.tau_estimate(torch.from_numpy(q).cuda(), sweep, isolated=False)
+    on, ot = om.tau(q, sweep, isolated=False)
+    assert np.abs(tn.cpu().numpy() - on).max() <= _tau_tol(on, mi, q, om)
+    assert np.abs(tt.cpu().numpy() - ot).max() <= _tau_tol(ot, mi, q, om, trad=True)
+
+
+def test_set_orders_parity(torch_cuda):
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, "mixed5_1to6")
+    rng = np.random.default_rng(3)
+    new = np.clip(om.orders + rng.integers(-2, 3, size=om.orders.shape), 1, 8).astype(np.int32)
+    qn = m.set_orders(new, torch.from_numpy(q).cuda()).cpu().numpy()
+    qo = om.set_orders(new, q)
+    assert np.abs(qn - qo).max() <= RTOL * np.abs(qo).max()
+    # the mesh now runs at the new orders
+    import oracle
+    om2 = oracle.Mesh(mi.with_orders(new))
+    r = m.residual(torch.from_numpy(qo).cuda()).cpu().numpy()
+    ro = om2.residual(qo)
+    assert rel_err(r, ro, om2.off, scale_per_var(qo, mi.phys, 0.4)).max() < RTOL
+
+
+def _cylinder(torch, n_theta=40, n_r=24):
+    import oracle
+    from paper_2210_03523_gb300 import dg
+    mi = I.ogrid_mesh(n_theta=n_theta, n_r=n_r, phys=I.cylinder_physics())
+    om = oracle.Mesh(mi)
+    xyz = om.coords()
+    ph = mi.phys
+
+    def fn(x, y, z):
+        # free stream past the cylinder, slowed near the wall, with a seeded-free smooth bump
+        r2 = x * x + y * y
+        damp = 1.0 - np.exp(-(r2 - 0.25) * 4.0)
+        u = damp * (1.0 + 0.05 * np.sin(3 * np.arctan2(y, x)))
+        v = 0.05 * damp * np.cos(x)
+        rho = 1.0 + 0.02 * np.exp(-((x - 1.0) ** 2 + y * y))
+        p = (ph.gamma - 1) * (ph.qinf[4] - 0.5) * (1.0 + 0.01 * np.sin(y))
+        return np.stack([rho, rho * u, rho * v, 0 * x, p / (ph.gamma - 1) + 0.5 * rho * (u * u + v * v)])
+    q = I.pointwise_state(xyz, om.orders, fn)
+    return mi, om, dg.Mesh(mi), q
+
+
+def test_navier_stokes_cylinder_parity(torch_cuda):
+    """Cylinder workload (curved O-grid, P=(6,6,1), BR1, wall + far field):
+    residual, isolated residual, 3 RK3 steps and the FP64 isolated tau sweep."""
+    torch = torch_cuda
+    mi, om, m, q = _cylinder(torch)
+    qg = torch.from_numpy(q).cuda()
+    s = scale_per_var(q, mi.phys, 0.1)
+    for iso in (False, True):
+        r = m.residual(qg, isolated=iso).cpu().numpy()
+        ro = om.residual(q, isolated=iso)
+        assert rel_err(r, ro, om.off, s).max() < RTOL
+    dt = om.max_dt(q, 0.5)
+    assert abs(m.max_dt(qg, 0.5).item() - dt) <= RTOL * dt
+    gg = torch.zeros_like(qg)
+    dtd = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    qo, go = q.copy(), np.zeros_like(q)
+    for _ in range(3):
+        m.rk_step(qg, gg, dtd)
+        om.rk_step(qo, go, dt)
+    assert rel_err(qg.cpu().numpy(), qo, om.off, state_scale(qo, om.off)).max() < RTOL
+    sweep = I.full_sweep((6, 6, 1))
+    tn, tt = m.tau_estimate(torch.from_numpy(q).cuda(), sweep)
+    on, ot = om.tau(q, sweep)
+    sR = s.max()
+    Jmax = max(om.metrics(e)[2].max() for e in range(om.n_elem))
+    assert np.abs(tn.cpu().numpy() - on).max() <= RTOL * max(np.abs(on).max(), sR)
+    assert np.abs(tt.cpu().numpy() - ot).max() <= RTOL * max(np.abs(ot).max(), sR * Jmax)
+    tn32, _ = m.tau_estimate(torch.from_numpy(q).cuda(), sweep, fp32=True)
+    S = _fp32_scale(om, q, mi)
+    d = np.abs(tn32.cpu().numpy().astype(np.float64) - on) / S[:, None]
+    assert (d <= 8 * np.finfo(np.float32).eps).all(), d.max() / np.finfo(np.float32).eps
+
+
+def test_nonphysical_state_sets_sticky_error(torch_cuda):
+    """A negative density made on the host: the kernels record the error and
+    return; dg_get_error reports it once, then the word is clear."""
+    torch = torch_cuda
+    mi, om, m, q = _setup(torch, "pulse4_P4")
+    bad = q.copy()
+    bad[3] = -1.0
+    m.residual(torch.from_numpy(bad).cuda())
+    assert m.get_error() == 5
+    assert m.get_error() == 0
+    m.residual(torch.from_numpy(q).cuda())
+    assert m.get_error() == 0
