@@ -123,6 +123,34 @@ dg_status dg_node_coords(dg_mesh* mesh, double* xyz);
  * mortars are not implemented, see dg_mesh_create), DG_ERR_CUDA. */
 dg_status dg_residual(dg_mesh* mesh, const double* q, double* r, uint32_t flags);
 
+/* Residual without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not call cudaMalloc while
+ * they run, for instance code inside a framework whose pooling allocator
+ * already owns the device memory budget (a raw cudaMalloc there can fail or
+ * fragment the pool), or a loop that must not stall on the device-wide
+ * synchronisation that cudaMalloc / cudaFree may imply.
+ * It returns the same R(Q) as dg_residual(mesh, q, r, 0) for Euler meshes,
+ * but its face-flux scratch is one fixed array inside the library
+ * (DG_NOALLOC_SURF_DOUBLES = 4,194,304 doubles, 32 MiB, reserved on every
+ * GPU that loads the library until the process exits) instead of the
+ * mesh's buffer.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   q, r: device state-layout arrays as for dg_residual; r may not alias q.
+ *   The mesh's device must be the current device.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) once; make that first call before any stream
+ *   capture.
+ *   All calls share the one array: calls that overlap on the GPU (two
+ *   streams, two meshes) race on it and must be serialised by the caller.
+ *   Every call rewrites the whole part of the array it reads, so nothing
+ *   carries over from an earlier call.
+ * Errors: DG_ERR_ARG (null or aliased pointers, mesh device not current),
+ * DG_ERR_UNSUPPORTED (Navier-Stokes mesh, mortars not implemented, or a face
+ * buffer of more than DG_NOALLOC_SURF_DOUBLES doubles: 5 per element-face
+ * node, i.e. more than 838,860 element-face nodes), DG_ERR_CUDA. */
+#define DG_NOALLOC_SURF_DOUBLES 4194304
+dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double* r);
+
 /* CFL time step (Sec. 3: dt adapted from the CFL condition each step):
  * dt = cfl / max_nodes max(s_a, s_v),
  *   s_a = sum_i (N_i+1)^2 (|J a^i . v| + c |J a^i|) / (2J),

@@ -1061,6 +1061,11 @@ __global__ void __launch_bounds__(kTauThreads) project_kernel(const int32_t* ord
   }
 }
 
+MeshView view(const dg_mesh_impl* m);
+
+FaceParams dgk_face_params_for(dg_mesh_impl* m, const double* q, double* surf);
+VolParams dgk_vol_params_for(dg_mesh_impl* m, const double* q, const double* surf, double* r);
+
 MeshView view(const dg_mesh_impl* m) {
   MeshView v;
   v.ord = m->d_ord;
@@ -1108,6 +1113,35 @@ struct Prof {
   Prof(dg_mesh_impl* mm, int k, int n = 1) : m(mm), id(k) { dg_prof_begin(m, k, n); }
   ~Prof() { dg_prof_end(m, id); }
 };
+
+FaceParams dgk_face_params_for(dg_mesh_impl* m, const double* q, double* surf) {
+  FaceParams P;
+  P.m = view(m);
+  P.faces = m->d_faces;
+  P.n_faces = m->n_faces;
+  P.q = q;
+  P.grad = nullptr;
+  P.surf = surf;
+  P.basis = m->basis64;
+  P.np_max = m->max_order + 1;
+  P.warp_smem = 34 * P.np_max * P.np_max;
+  return P;
+}
+
+VolParams dgk_vol_params_for(dg_mesh_impl* m, const double* q, const double* surf, double* r) {
+  VolParams P;
+  memset(&P, 0, sizeof(P));
+  P.m = view(m);
+  P.items = m->d_items;
+  P.n_items = m->n_items;
+  P.elist = m->d_elist;
+  P.q = q;
+  P.surf = surf;
+  P.basis = m->basis64;
+  P.out = r;
+  P.err = m->d_err;
+  return P;
+}
 
 }  // namespace
 
@@ -1371,3 +1405,71 @@ cudaError_t project_orders(dg_mesh_impl* m, const int32_t* d_new_orders, const i
 }
 
 }  // namespace dgk
+
+// ---------------------------------------------------------------------------
+// dg_residual_noalloc: the Euler residual with its face-flux scratch in a
+// fixed device array instead of the mesh's buffer, for callers that may not
+// allocate device memory.
+// ---------------------------------------------------------------------------
+
+// 4 Mi doubles (32 MiB): the face buffer of up to 838,860 element-face nodes
+// (5 doubles each).  Every GPU that loads the library holds it until exit.
+static_assert(DG_NOALLOC_SURF_DOUBLES == (4u << 20), "fixed face-buffer size");
+static __device__ __align__(256) double g_noalloc_surf[DG_NOALLOC_SURF_DOUBLES];
+
+// Device address of g_noalloc_surf on device dev.  In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per
+// device with that device current (the caller's current device) and cached.
+static double* noalloc_surf_address(int dev, cudaError_t* err) {
+  static double* addr[64] = {};
+  *err = cudaSuccess;
+  if (dev < 0 || dev >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_surf);
+    if (e != cudaSuccess) {
+      *err = e;
+      return nullptr;
+    }
+    addr[dev] = static_cast<double*>(p);
+  }
+  return addr[dev];
+}
+
+extern "C" dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double* r) {
+  if (!mesh || !q || !r || q == r) return DG_ERR_ARG;
+  if (mesh->phys.eqs != DG_EULER || mesh->faces_unsupported) return DG_ERR_UNSUPPORTED;
+  const size_t need = 5 * (size_t)mesh->h_soff[mesh->n_elem];
+  if (need > DG_NOALLOC_SURF_DOUBLES) return DG_ERR_UNSUPPORTED;   // mesh too large for the fixed buffer
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DG_ERR_CUDA;
+  if (dev != mesh->device) return DG_ERR_ARG;                      // the mesh's device must be current
+  cudaError_t err;
+  double* surf = noalloc_surf_address(dev, &err);
+  if (!surf) return DG_ERR_CUDA;
+  // face pass: every element-face node of the buffer is written (interior
+  // faces for both sides, boundary faces for theirs) before the volume pass
+  // reads it, so nothing needs clearing between calls
+  FaceParams F = dgk_face_params_for(mesh, q, surf);
+  size_t fsmem = mesh->n_face_mortar ? sizeof(double) * F.warp_smem * kFaceWarps : 0;
+  int fgrid = (mesh->n_faces + kFaceWarps - 1) / kFaceWarps;
+  VolParams V = dgk_vol_params_for(mesh, q, surf, r);
+  size_t vsmem = sizeof(double) * 15 * mesh->item_max_nodes;
+  int vgrid = grid_for(mesh->n_items, 8);
+  if (mesh->affine) {
+    if ((err = allow_smem(face_flux_kernel<true, false>, fsmem))) return DG_ERR_CUDA;
+    if ((err = allow_smem(volume_kernel<true, false>, vsmem))) return DG_ERR_CUDA;
+    if (mesh->n_faces) face_flux_kernel<true, false><<<fgrid, 32 * kFaceWarps, fsmem, mesh->stream>>>(F);
+    volume_kernel<true, false><<<vgrid, kVolThreads, vsmem, mesh->stream>>>(V);
+  } else {
+    if ((err = allow_smem(face_flux_kernel<false, false>, fsmem))) return DG_ERR_CUDA;
+    if ((err = allow_smem(volume_kernel<false, false>, vsmem))) return DG_ERR_CUDA;
+    if (mesh->n_faces) face_flux_kernel<false, false><<<fgrid, 32 * kFaceWarps, fsmem, mesh->stream>>>(F);
+    volume_kernel<false, false><<<vgrid, kVolThreads, vsmem, mesh->stream>>>(V);
+  }
+  mesh->launches += mesh->n_faces ? 2 : 1;
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}

@@ -63,6 +63,7 @@ def _lib():
             "dg_set_stream": [vp, vp],
             "dg_node_coords": [vp, vp],
             "dg_residual": [vp, vp, vp, C.c_uint32],
+            "dg_residual_noalloc": [vp, vp, vp],
             "dg_max_dt": [vp, vp, C.c_double, vp],
             "dg_rk_step": [vp, vp, vp, vp],
             "dg_tau_estimate": [vp, vp, vp, i32p, C.c_int32, C.c_uint32, vp, vp],
@@ -83,7 +84,7 @@ def _lib():
 def exported_symbols():
     return ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_count_nodes", "dg_set_stream", "dg_node_coords",
             "dg_residual", "dg_max_dt", "dg_rk_step", "dg_tau_estimate", "dg_set_orders", "dg_get_error",
-            "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count"]
+            "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc"]
 
 
 def _check(st, where):
@@ -166,6 +167,12 @@ class Mesh:
     def residual(self, q, r=None, isolated=False):
         r = self.new_state() if r is None else r
         _check(_lib().dg_residual(self.h, _ptr(q), _ptr(r), DG_ISOLATED if isolated else 0), "dg_residual")
+        return r
+
+    def residual_noalloc(self, q, r):
+        """dg_residual_noalloc: same residual, face scratch in the library's fixed
+        device array; r must be a caller-allocated state-layout tensor."""
+        _check(_lib().dg_residual_noalloc(self.h, _ptr(q), _ptr(r)), "dg_residual_noalloc")
         return r
 
     def max_dt(self, q, cfl, dt=None):
