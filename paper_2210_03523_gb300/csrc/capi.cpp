@@ -123,7 +123,7 @@ void element_geometry(const double* gnodes, int G, const int N[3], std::vector<d
 
 // Parallelepiped test of a G=1 element; on success the affine metrics
 // (J a^i = cross products of the edge vectors / 4, J = triple product / 8).
-bool affine_metrics(const double* c, double met[10]) {
+bool affine_metrics(const double* c, double met[16]) {
   double e1[3], e2[3], e3[3], scale = 0.0;
   for (int d = 0; d < 3; ++d) {
     e1[d] = c[3 * 1 + d] - c[3 * 0 + d];
@@ -161,7 +161,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 }
 
 void free_device(dg_mesh_impl* m) {
-  void* ptrs[] = {m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
+  void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
                   m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
                   m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_qc, m->d_rc, m->d_sweep};
   for (void* p : ptrs)
@@ -170,7 +170,7 @@ void free_device(dg_mesh_impl* m) {
   m->d_metric32 = nullptr; m->d_surf = nullptr; m->d_surfq = nullptr; m->d_grad = nullptr; m->d_xyz = nullptr;
   m->d_faces = nullptr; m->d_items = nullptr; m->d_elist = nullptr; m->d_err = nullptr; m->d_scratch = nullptr;
   m->d_taugeo = nullptr; m->d_taugeo32 = nullptr; m->d_taugeo_off = nullptr; m->d_rp = nullptr; m->d_qc = nullptr;
-  m->d_rc = nullptr; m->d_sweep = nullptr;
+  m->d_rc = nullptr; m->d_sweep = nullptr; m->d_mfaces = nullptr; m->d_mbatches = nullptr;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
@@ -218,27 +218,37 @@ dg_status build(dg_mesh_impl* m) {
   }
   m->n_nodes = m->h_off[ne];
   // geometry
+  // metric record: fields 0..8 J a^i_d, 9 J, 10 1/J; affine: 16 doubles per
+  // element, curved: [11][n] per element
   std::vector<double> met;
   m->affine = (G == 1);
   if (m->affine) {
-    met.resize(10 * (size_t)ne);
+    met.assign(16 * (size_t)ne, 0.0);
     for (int e = 0; e < ne && m->affine; ++e)
-      if (!affine_metrics(&m->h_geom[(size_t)e * ng3 * 3], &met[10 * (size_t)e])) m->affine = false;
+      if (!affine_metrics(&m->h_geom[(size_t)e * ng3 * 3], &met[16 * (size_t)e])) m->affine = false;
   }
+  m->axis = m->affine;
   if (m->affine) {
-    for (int e = 0; e < ne; ++e)
-      if (!(met[10 * (size_t)e + 9] > 0.0)) return DG_ERR_ARG;
+    for (int e = 0; e < ne; ++e) {
+      double* r = &met[16 * (size_t)e];
+      if (!(r[9] > 0.0)) return DG_ERR_ARG;
+      r[10] = 1.0 / r[9];
+      for (int i = 0; i < 3; ++i)
+        for (int d = 0; d < 3; ++d)
+          if (i != d && r[3 * i + d] != 0.0) m->axis = false;
+    }
   } else {
-    met.assign(10 * (size_t)m->n_nodes, 0.0);
+    met.assign(11 * (size_t)m->n_nodes, 0.0);
     std::vector<double> X, Ja, J;
     for (int e = 0; e < ne; ++e) {
       element_geometry(&m->h_geom[(size_t)e * ng3 * 3], G, &m->h_ord[3 * e], X, Ja, J);
       const int64_t n = m->h_off[e + 1] - m->h_off[e];
-      double* dst = &met[10 * m->h_off[e]];
+      double* dst = &met[11 * m->h_off[e]];
       for (int k = 0; k < 9; ++k) std::copy(Ja.begin() + k * n, Ja.begin() + (k + 1) * n, dst + k * n);
       for (int64_t p = 0; p < n; ++p) {
         if (!(J[p] > 0.0)) return DG_ERR_ARG;
         dst[9 * n + p] = J[p];
+        dst[10 * n + p] = 1.0 / J[p];
       }
     }
   }
@@ -264,9 +274,42 @@ dg_status build(dg_mesh_impl* m) {
       }
     }
   std::stable_sort(faces.begin(), faces.end(), [](const FaceRec& a, const FaceRec& b) { return a.kind < b.kind; });
-  m->n_faces = (int)faces.size();
   m->n_face_conf = m->n_face_mortar = m->n_face_bnd = 0;
   for (auto& f : faces) (f.kind == 0 ? m->n_face_conf : f.kind == 1 ? m->n_face_mortar : m->n_face_bnd)++;
+  // p-nonconforming faces leave the warp-per-face list: batched by shape
+  std::map<std::tuple<int, int, int, int>, std::vector<int32_t>> msig;
+  std::vector<FaceRec> wfaces;
+  for (auto& f : faces) {
+    if (f.kind != 1) {
+      wfaces.push_back(f);
+      continue;
+    }
+    const int d = f.face, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+    auto key = std::make_tuple(m->h_ord[3 * f.L + t0] + 1, m->h_ord[3 * f.L + t1] + 1, m->h_ord[3 * f.R + t0] + 1,
+                               m->h_ord[3 * f.R + t1] + 1);
+    auto& v = msig[key];
+    v.push_back(f.L);
+    v.push_back(f.R);
+    v.push_back(d);
+  }
+  faces.swap(wfaces);
+  m->n_faces = (int)faces.size();
+  std::vector<int32_t> mfaces, mbatches;
+  m->mortar_smem = 0;
+  for (auto& kv : msig) {
+    int la, lb, ra, rb;
+    std::tie(la, lb, ra, rb) = kv.first;
+    const int nm = std::max(la, ra) * std::max(lb, rb);
+    const int per = std::max(1, kTileNodes / nm);
+    const int nf = (int)kv.second.size() / 3;
+    for (int i = 0; i < nf; i += per) {
+      const int cnt = std::min(per, nf - i);
+      mbatches.insert(mbatches.end(), {(int32_t)(mfaces.size() / 3), cnt, la, lb, ra, rb});
+      mfaces.insert(mfaces.end(), kv.second.begin() + 3 * i, kv.second.begin() + 3 * (i + cnt));
+      m->mortar_smem = std::max(m->mortar_smem, dg_mortar_smem_doubles(cnt, la, lb, ra, rb));
+    }
+  }
+  m->n_mbatches = (int)mbatches.size() / 6;
   // mortars are implemented for affine Euler meshes; elsewhere only the
   // element-local (isolated) operations are available
   m->faces_unsupported = m->n_face_mortar > 0 && (ns || !m->affine);
@@ -301,6 +344,8 @@ dg_status build(dg_mesh_impl* m) {
     DG_CUDA(upload(&m->d_metric32, m32.data(), m32.size()));
   }
   DG_CUDA(upload(&m->d_faces, faces.data(), faces.size()));
+  DG_CUDA(upload(&m->d_mfaces, mfaces.data(), mfaces.size()));
+  DG_CUDA(upload(&m->d_mbatches, mbatches.data(), mbatches.size()));
   DG_CUDA(upload(&m->d_items, items.data(), items.size()));
   DG_CUDA(upload(&m->d_elist, elist.data(), elist.size()));
   DG_CUDA(upload<double>(&m->d_surf, nullptr, 5 * (size_t)m->h_soff[ne]));

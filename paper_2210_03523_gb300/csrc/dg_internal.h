@@ -57,6 +57,9 @@ struct WorkItem {
 
 struct dg_mesh_impl;
 
+// shared memory (doubles) of a batch of `count` mortar faces of one shape
+size_t dg_mortar_smem_doubles(int count, int la, int lb, int ra, int rb);
+
 // per-kernel timing / launch counting hooks (capi.cpp), called by the launchers
 void dg_prof_begin(dg_mesh_impl* m, int kernel_id, int n_launches);
 void dg_prof_end(dg_mesh_impl* m, int kernel_id);
@@ -92,6 +95,7 @@ struct dg_mesh_impl {
   int64_t n_nodes = 0;
   DevPhys phys{};
   bool affine = true;       // every element a parallelepiped: metrics per element
+  bool axis = false;        // affine and every J a^i parallel to e_i (axis-aligned box)
   int max_order = 1;        // max over elements and directions
   bool faces_unsupported = false;  // mortars on a curved or Navier-Stokes mesh
 
@@ -106,14 +110,18 @@ struct dg_mesh_impl {
   int32_t* d_nbr = nullptr;        // [e][6]
   int64_t* d_off = nullptr;        // [e+1] node offsets
   int64_t* d_soff = nullptr;       // [e+1] surface (face-node) offsets, 6 faces per element
-  double* d_metric = nullptr;      // affine: [e][10]; curved: per node [10][n] at 10*off_e (Ja[i][d], J)
+  double* d_metric = nullptr;      // affine: [e][16] (J a^i_d, J, 1/J, pad); curved: [11][n] at 11*off_e
   float* d_metric32 = nullptr;     // affine: FP32 copy for the FP32 tau sweep
   double* d_surf = nullptr;        // [5 * soff_total] numerical contravariant flux per element face node
   double* d_surfq = nullptr;       // NS: [15 * soff_total] BR1 q-hat * J a^dir
   double* d_grad = nullptr;        // NS: [15 * n_nodes] gradient [c][v][node]
   double* d_xyz = nullptr;         // lazily uploaded coordinates
-  FaceRec* d_faces = nullptr;
+  FaceRec* d_faces = nullptr;      // conforming and boundary faces (one warp each)
   int n_faces = 0, n_face_conf = 0, n_face_mortar = 0, n_face_bnd = 0;
+  int32_t* d_mfaces = nullptr;     // p-nonconforming faces [L, R, dir], grouped by shape signature
+  int32_t* d_mbatches = nullptr;   // mortar batches [first, count, la, lb, ra, rb]
+  int n_mbatches = 0;
+  size_t mortar_smem = 0;          // doubles of shared memory of the largest batch
   WorkItem* d_items = nullptr;
   int32_t* d_elist = nullptr;
   int n_items = 0;

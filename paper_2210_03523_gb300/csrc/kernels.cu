@@ -60,11 +60,17 @@ __device__ __forceinline__ int face_vidx(int n1, int n2, int n3, int f, int a, i
 template <typename T>
 __device__ __forceinline__ const T* btab(const T* base, int off) { return base + off; }
 
-// J a^i_d and J of element e at node p (AFFINE: per element)
+// Metric record: field m of element e at node p.  Fields 0..8: J a^i_d
+// (index 3i+d); 9: J; 10: 1/J.  Affine meshes: one record of kAffStride
+// doubles per element; curved meshes: [kCurvedFields][n] per element at
+// kCurvedFields * off_e.
+constexpr int kAffStride = 16;
+constexpr int kCurvedFields = 11;
+
 template <bool AFFINE>
 __device__ __forceinline__ double metric(const double* M, int e, int64_t off, int n, int p, int m) {
-  if (AFFINE) return __ldg(M + 10 * (int64_t)e + m);
-  return __ldg(M + 10 * off + (int64_t)m * n + p);
+  if (AFFINE) return __ldg(M + kAffStride * (int64_t)e + m);
+  return __ldg(M + kCurvedFields * off + (int64_t)m * n + p);
 }
 
 struct Prim {
@@ -82,45 +88,88 @@ __device__ __forceinline__ Prim primitive(double gm1, const double q[5]) {
   return s;
 }
 
-// Roe's approximate Riemann solver: flux through unit normal n from qL to qR.
-__device__ void roe(double gamma, const double qL[5], const double qR[5], const double n[3], double f[5]) {
-  double gm1 = gamma - 1.0;
-  Prim L = primitive(gm1, qL), R = primitive(gm1, qR);
-  double HL = (qL[4] + L.p) * L.ir, HR = (qR[4] + R.p) * R.ir;
-  double sL = sqrt(qL[0]), sR = sqrt(qR[0]);
-  double is = 1.0 / (sL + sR);
+// Roe's approximate Riemann solver: flux through the unit normal n from qL
+// (behind) to qR (ahead).  AX >= 0: the normal is the unit vector e_AX (axis
+// aligned faces), n is not read.  sqrt(rho) and 1/rho come from one rsqrt,
+// as do the Roe sound speed and its inverse square.
+template <int AX>
+__device__ __forceinline__ double ncomp(const double n[3], int c) {
+  return AX >= 0 ? (c == AX ? 1.0 : 0.0) : n[c];
+}
+
+template <int AX>
+__device__ void roe_t(double gamma, const double qL[5], const double qR[5], const double n[3], double f[5]) {
+  const double gm1 = gamma - 1.0;
+  const double rsL = rsqrt(qL[0]), rsR = rsqrt(qR[0]);
+  const double sL = qL[0] * rsL, sR = qR[0] * rsR;      // sqrt(rho)
+  const double irL = rsL * rsL, irR = rsR * rsR;        // 1/rho
+  double uL[3], uR[3];
+  for (int c = 0; c < 3; ++c) {
+    uL[c] = qL[1 + c] * irL;
+    uR[c] = qR[1 + c] * irR;
+  }
+  const double pL = gm1 * (qL[4] - 0.5 * (qL[1] * uL[0] + qL[2] * uL[1] + qL[3] * uL[2]));
+  const double pR = gm1 * (qR[4] - 0.5 * (qR[1] * uR[0] + qR[2] * uR[1] + qR[3] * uR[2]));
+  const double HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
+  const double is = 1.0 / (sL + sR);
   double ut[3];
-  for (int c = 0; c < 3; ++c) ut[c] = (sL * L.u[c] + sR * R.u[c]) * is;
-  double Ht = (sL * HL + sR * HR) * is;
-  double rt = sL * sR;
-  double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
-  double c2 = gm1 * (Ht - 0.5 * q2);
-  double ct = sqrt(c2);
-  double ic2 = 1.0 / c2;
-  double unL = L.u[0] * n[0] + L.u[1] * n[1] + L.u[2] * n[2];
-  double unR = R.u[0] * n[0] + R.u[1] * n[1] + R.u[2] * n[2];
-  double utn = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
-  double dun = unR - unL, dp = R.p - L.p, dr = qR[0] - qL[0];
-  double a1 = 0.5 * (dp - rt * ct * dun) * ic2;
-  double a5 = 0.5 * (dp + rt * ct * dun) * ic2;
-  double a2 = dr - dp * ic2;
-  double l1a1 = fabs(utn - ct) * a1, l5a5 = fabs(utn + ct) * a5, l2 = fabs(utn);
+  for (int c = 0; c < 3; ++c) ut[c] = (sL * uL[c] + sR * uR[c]) * is;
+  const double Ht = (sL * HL + sR * HR) * is;
+  const double rt = sL * sR;
+  const double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  const double c2 = gm1 * (Ht - 0.5 * q2);
+  const double rc = rsqrt(c2);
+  const double ct = c2 * rc, ic2 = rc * rc;
+  double unL, unR, utn;
+  if (AX >= 0) {
+    unL = uL[AX];
+    unR = uR[AX];
+    utn = ut[AX];
+  } else {
+    unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
+    unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
+    utn = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
+  }
+  const double dun = unR - unL, dp = pR - pL, dr = qR[0] - qL[0];
+  const double rcd = rt * ct * dun;
+  const double a1 = 0.5 * (dp - rcd) * ic2;
+  const double a5 = 0.5 * (dp + rcd) * ic2;
+  const double a2 = dr - dp * ic2;
+  const double l1a1 = fabs(utn - ct) * a1, l5a5 = fabs(utn + ct) * a5, l2 = fabs(utn);
   double dut[3], utdut = 0.0;
   for (int c = 0; c < 3; ++c) {
-    dut[c] = (R.u[c] - L.u[c]) - dun * n[c];
+    dut[c] = (uR[c] - uL[c]) - dun * ncomp<AX>(n, c);
     utdut += ut[c] * dut[c];
   }
-  // physical normal fluxes of both sides
-  double mL = qL[0] * unL, mR = qR[0] * unR;
+  const double mL = qL[0] * unL, mR = qR[0] * unR;
   f[0] = 0.5 * (mL + mR) - 0.5 * (l1a1 + l5a5 + l2 * a2);
   for (int c = 0; c < 3; ++c) {
-    double phys = mL * L.u[c] + L.p * n[c] + mR * R.u[c] + R.p * n[c];
-    double diss = l1a1 * (ut[c] - ct * n[c]) + l5a5 * (ut[c] + ct * n[c]) + l2 * (a2 * ut[c] + rt * dut[c]);
+    const double nc = ncomp<AX>(n, c);
+    double phys = mL * uL[c] + mR * uR[c];
+    double diss = (l1a1 + l5a5) * ut[c] + l2 * (a2 * ut[c] + rt * dut[c]);
+    if (AX < 0 || c == AX) {
+      phys += (pL + pR) * nc;
+      diss += (l5a5 - l1a1) * ct * nc;
+    }
     f[1 + c] = 0.5 * (phys - diss);
   }
-  double physE = unL * (qL[4] + L.p) + unR * (qR[4] + R.p);
-  double dissE = l1a1 * (Ht - utn * ct) + l5a5 * (Ht + utn * ct) + l2 * (a2 * 0.5 * q2 + rt * utdut);
+  const double physE = unL * (qL[4] + pL) + unR * (qR[4] + pR);
+  const double dissE = (l1a1 + l5a5) * Ht + (l5a5 - l1a1) * utn * ct + l2 * (a2 * 0.5 * q2 + rt * utdut);
   f[4] = 0.5 * (physE - dissE);
+}
+
+// Roe on a face of direction dir: the axis-aligned variant when the mesh is
+// an axis-aligned box (normal e_dir), else the general one.
+template <bool AXIS>
+__device__ __forceinline__ void roe_face(double gamma, int dir, const double qL[5], const double qR[5],
+                                         const double n[3], double f[5]) {
+  if (AXIS) {
+    if (dir == 0) roe_t<0>(gamma, qL, qR, n, f);
+    else if (dir == 1) roe_t<1>(gamma, qL, qR, n, f);
+    else roe_t<2>(gamma, qL, qR, n, f);
+  } else {
+    roe_t<-1>(gamma, qL, qR, n, f);
+  }
 }
 
 // Navier-Stokes viscous flux for all three directions: fv[d][v].
@@ -198,7 +247,20 @@ __device__ __forceinline__ void face_metric(const MeshView& m, int e, int n, int
   for (int c = 0; c < 3; ++c) ja[c] = metric<AFFINE>(m.metric, e, o, n, vi, 3 * dir + c);
 }
 
-template <bool AFFINE, bool NS>
+__device__ __forceinline__ double unit_normal(const double ja[3], double nrm[3]) {
+  const double a2 = ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2];
+  const double ia = rsqrt(a2);
+  nrm[0] = ja[0] * ia;
+  nrm[1] = ja[1] * ia;
+  nrm[2] = ja[2] * ia;
+  return a2 * ia;   // |J a|
+}
+
+// One warp per face.  AFFINE: the face's J a^dir (hence its normal and area)
+// is one constant read from the element record; AXIS: in addition it is
+// aligned with e_dir.  kind 0: conforming interior; 2: boundary.  Writes the contravariant numerical flux F* in
+// the +xi_dir direction onto each side's own face grid.
+template <bool AFFINE, bool AXIS, bool NS>
 __global__ void __launch_bounds__(32 * kFaceWarps) face_flux_kernel(FaceParams P) {
   extern __shared__ double smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -209,26 +271,29 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_flux_kernel(FaceParams P
   const double gamma = m.ph.gamma;
 
   if (fr.kind == 2) {  // boundary face of element fr.L, face fr.face, tag fr.R
-    int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1, side = f & 1;
+    const int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1, side = f & 1;
     int n1, n2, n3;
     orders_of(m, e, n1, n2, n3);
-    int n = n1 * n2 * n3;
-    int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3;
-    int nf = na * nb;
-    int64_t o = m.off[e];
+    const int n = n1 * n2 * n3;
+    const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+    const int64_t o = m.off[e];
     double* out = P.surf + 5 * (m.soff[e] + face_offset(n1, n2, n3, f));
+    double ja[3], nrm[3], area = 0.0;
+    if (AFFINE) {
+      face_metric<true>(m, e, n, 0, dir, ja);
+      area = unit_normal(ja, nrm);
+    }
     for (int p = lane; p < nf; p += 32) {
-      int a = p % na, b = p / na;
-      int vi = face_vidx(n1, n2, n3, f, a, b);
-      double qi[5], qg[5], ja[3], F[5];
+      const int vi = face_vidx(n1, n2, n3, f, p % na, p / na);
+      double qi[5], qg[5], F[5];
       for (int v = 0; v < 5; ++v) qi[v] = P.q[5 * o + v * n + vi];
-      face_metric<AFFINE>(m, e, n, vi, dir, ja);
+      if (!AFFINE) {
+        face_metric<false>(m, e, n, vi, dir, ja);
+        area = unit_normal(ja, nrm);
+      }
       bc_ghost(m.ph, tag, qi, qg);
-      double area = sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
-      double ia = 1.0 / area;
-      double nrm[3] = {ja[0] * ia, ja[1] * ia, ja[2] * ia};
-      if (side) roe(gamma, qi, qg, nrm, F);
-      else roe(gamma, qg, qi, nrm, F);
+      if (side) roe_face<AXIS>(gamma, dir, qi, qg, nrm, F);
+      else roe_face<AXIS>(gamma, dir, qg, qi, nrm, F);
       for (int v = 0; v < 5; ++v) F[v] *= area;
       if (NS) {
         double g[15], fv[3][5];
@@ -250,26 +315,30 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_flux_kernel(FaceParams P
   const int nL = l1 * l2 * l3, nR = r1 * r2 * r3;
   const int64_t oL = m.off[L], oR = m.off[R];
   const int fL = 2 * dir + 1, fR = 2 * dir;
-  const int la = dir == 0 ? l2 : l1, lb = dir == 2 ? l2 : l3;
-  const int ra = dir == 0 ? r2 : r1, rb = dir == 2 ? r2 : r3;
+  const int la = dir == 0 ? l2 : l1, lb = dir == 2 ? l2 : l3;   // == R's (conforming)
   double* outL = P.surf + 5 * (m.soff[L] + face_offset(l1, l2, l3, fL));
   double* outR = P.surf + 5 * (m.soff[R] + face_offset(r1, r2, r3, fR));
+  double ja[3], nrm[3], area = 0.0;
+  if (AFFINE) {
+    face_metric<true>(m, L, nL, 0, dir, ja);
+    area = unit_normal(ja, nrm);
+  }
 
   if (fr.kind == 0) {  // conforming: la == ra, lb == rb
     const int nf = la * lb;
     for (int p = lane; p < nf; p += 32) {
-      int a = p % la, b = p / la;
-      int iL = face_vidx(l1, l2, l3, fL, a, b), iR = face_vidx(r1, r2, r3, fR, a, b);
-      double qL[5], qR[5], ja[3], F[5];
+      const int a = p % la, b = p / la;
+      const int iL = face_vidx(l1, l2, l3, fL, a, b), iR = face_vidx(r1, r2, r3, fR, a, b);
+      double qL[5], qR[5], F[5];
       for (int v = 0; v < 5; ++v) {
         qL[v] = P.q[5 * oL + v * nL + iL];
         qR[v] = P.q[5 * oR + v * nR + iR];
       }
-      face_metric<AFFINE>(m, L, nL, iL, dir, ja);
-      double area = sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
-      double ia = 1.0 / area;
-      double nrm[3] = {ja[0] * ia, ja[1] * ia, ja[2] * ia};
-      roe(gamma, qL, qR, nrm, F);
+      if (!AFFINE) {
+        face_metric<false>(m, L, nL, iL, dir, ja);
+        area = unit_normal(ja, nrm);
+      }
+      roe_face<AXIS>(gamma, dir, qL, qR, nrm, F);
       for (int v = 0; v < 5; ++v) F[v] *= area;
       if (NS) {
         double g[15], fa[3][5], fb[3][5];
@@ -290,100 +359,202 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_flux_kernel(FaceParams P
     return;
   }
 
-  // ---- mortar (Euler only; mesh creation rejects NS with mortars)
-  const int np2 = P.np_max * P.np_max;
-  double* trL = smem + warp * P.warp_smem;  // [8][np2]: q (5) and J a^dir (3) on L's face grid
-  double* trR = trL + 8 * np2;             // [5][np2]
-  double* tmp = trR + 5 * np2;             // [8][np2]
-  double* mL = tmp + 8 * np2;              // [8][np2] on the mortar grid
-  double* mR = mL + 8 * np2;               // [5][np2]
-  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;  // mortar node counts
-  const int nfL = la * lb, nfR = ra * rb, nm = Ma * Mb;
-  for (int p = lane; p < nfL; p += 32) {
-    int a = p % la, b = p / la;
-    int vi = face_vidx(l1, l2, l3, fL, a, b);
-    for (int v = 0; v < 5; ++v) trL[v * np2 + p] = P.q[5 * oL + v * nL + vi];
-    double ja[3];
-    face_metric<AFFINE>(m, L, nL, vi, dir, ja);
-    for (int c = 0; c < 3; ++c) trL[(5 + c) * np2 + p] = ja[c];
+  // p-nonconforming faces (kind 1) are handled by mortar_kernel in shape batches
+}
+
+// ------------------------------------------------------------ batched mortars
+// p-nonconforming faces of affine Euler meshes, batched by shape signature
+// (la, lb, ra, rb): the tangential node counts of the element behind the
+// face (L) and ahead of it (R).  One CTA per batch; every phase runs flat over
+// (face, point) of the batch, so the lanes stay busy whatever the shape:
+//   gather both traces -> interpolate up to the mortar (Ma = max(la, ra),
+//   Mb = max(lb, rb)) in two sum-factorised passes -> Roe at the mortar nodes
+//   -> L2-project the flux back to each side in two passes -> store F*.
+struct MortarBatch {
+  int32_t first, count, la, lb, ra, rb;
+};
+
+struct MortarParams {
+  MeshView m;
+  const MortarBatch* batches;
+  int n_batches;
+  const int32_t* faces;   // [face][3]: L, R, dir
+  const double* q;
+  double* surf;
+  const double* basis;
+};
+
+template <bool AXIS>
+__global__ void __launch_bounds__(kVolThreads) mortar_kernel(MortarParams P) {
+  extern __shared__ double smem[];
+  const MeshView& m = P.m;
+  const double gamma = m.ph.gamma;
+  for (int it = blockIdx.x; it < P.n_batches; it += gridDim.x) {
+    const MortarBatch B = P.batches[it];
+    const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb, cnt = B.count;
+    const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
+    const int nfl = la * lb, nfr = ra * rb, nm = Ma * Mb;
+    const bool upLa = la != Ma, upLb = lb != Mb, upRa = ra != Ma, upRb = rb != Mb;
+    const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+    double* TL = smem;                       // [cnt][5][nfl] L trace
+    double* TR = TL + cnt * 5 * nfl;         // [cnt][5][nfr] R trace
+    double* UL = TR + cnt * 5 * nfr;         // [cnt][5][uL]  pass temporaries
+    double* UR = UL + cnt * 5 * uL;          // [cnt][5][uR]
+    double* QL = UR + cnt * 5 * uR;          // [cnt][5][nm]  mortar states, then the flux
+    double* QR = QL + cnt * 5 * nm;          // [cnt][5][nm]
+    double* NR = QR + cnt * 5 * nm;          // [cnt][4] unit normal, area
+    // 1. gather traces, face normals
+    for (int t = threadIdx.x; t < cnt * (nfl + nfr); t += blockDim.x) {
+      const bool isL = t < cnt * nfl;
+      const int tt = isL ? t : t - cnt * nfl;
+      const int nf = isL ? nfl : nfr, na = isL ? la : ra;
+      const int f = tt / nf, p = tt - f * nf;
+      const int* fr = P.faces + 3 * (B.first + f);
+      const int e = isL ? fr[0] : fr[1], dir = fr[2];
+      int n1, n2, n3;
+      orders_of(m, e, n1, n2, n3);
+      const int n = n1 * n2 * n3;
+      const int vi = face_vidx(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir, p % na, p / na);
+      const int64_t o = m.off[e];
+      double* T = (isL ? TL + f * 5 * nfl : TR + f * 5 * nfr) + p;
+      for (int v = 0; v < 5; ++v) T[v * nf] = P.q[5 * o + v * n + vi];
+    }
+    for (int f = threadIdx.x; f < cnt; f += blockDim.x) {
+      const int* fr = P.faces + 3 * (B.first + f);
+      double ja[3], nrm[3];
+      for (int c = 0; c < 3; ++c) ja[c] = metric<true>(m.metric, fr[0], 0, 0, 0, 3 * fr[2] + c);
+      const double area = unit_normal(ja, nrm);
+      NR[4 * f + 0] = nrm[0];
+      NR[4 * f + 1] = nrm[1];
+      NR[4 * f + 2] = nrm[2];
+      NR[4 * f + 3] = area;
+    }
+    __syncthreads();
+    // 2. first interpolation pass (xi_a) for the sides that need it
+    const double* IaL = P.basis + c_boff.I[la - 1][Ma - 1];
+    const double* IaR = P.basis + c_boff.I[ra - 1][Ma - 1];
+    {
+      const int nL = upLa ? cnt * Ma * lb : 0, nR = upRa ? cnt * Ma * rb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int nb = isL ? lb : rb, na = isL ? la : ra, per = Ma * nb;
+        const int f = tt / per, x = tt - f * per, m0 = x % Ma, b = x / Ma;
+        const double* src = isL ? TL + f * 5 * nfl : TR + f * 5 * nfr;
+        const double* Ia = isL ? IaL : IaR;
+        double* dst = (isL ? UL + f * 5 * uL : UR + f * 5 * uR) + x;
+        const int nsrc = na * nb;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int a = 0; a < na; ++a) {
+          const double w = __ldg(Ia + m0 * na + a);
+          for (int v = 0; v < 5; ++v) acc[v] += w * src[v * nsrc + a + na * b];
+        }
+        for (int v = 0; v < 5; ++v) dst[v * per] = acc[v];
+      }
+    }
+    __syncthreads();
+    // 3. second interpolation pass (xi_b), or a copy, onto the mortar grid
+    const double* IbL = P.basis + c_boff.I[lb - 1][Mb - 1];
+    const double* IbR = P.basis + c_boff.I[rb - 1][Mb - 1];
+    for (int t = threadIdx.x; t < 2 * cnt * nm; t += blockDim.x) {
+      const bool isL = t < cnt * nm;
+      const int tt = isL ? t : t - cnt * nm;
+      const int f = tt / nm, x = tt - f * nm, m0 = x % Ma, m1 = x / Ma;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      const int nb = isL ? lb : rb;
+      // source grid (Ma x nb): the pass-a result, or the trace itself
+      const double* src = upa ? (isL ? UL + f * 5 * uL : UR + f * 5 * uR) : (isL ? TL + f * 5 * nfl : TR + f * 5 * nfr);
+      const int nsrc = Ma * nb;
+      double* dst = (isL ? QL : QR) + f * 5 * nm + x;
+      if (upb) {
+        const double* Ib = isL ? IbL : IbR;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int b = 0; b < nb; ++b) {
+          const double w = __ldg(Ib + m1 * nb + b);
+          for (int v = 0; v < 5; ++v) acc[v] += w * src[v * nsrc + m0 + Ma * b];
+        }
+        for (int v = 0; v < 5; ++v) dst[v * nm] = acc[v];
+      } else {
+        for (int v = 0; v < 5; ++v) dst[v * nm] = src[v * nsrc + m0 + Ma * m1];
+      }
+    }
+    __syncthreads();
+    // 4. Roe at the mortar nodes (flux scaled by the face area, stored in QL)
+    for (int t = threadIdx.x; t < cnt * nm; t += blockDim.x) {
+      const int f = t / nm, x = t - f * nm;
+      double qa[5], qb[5], F[5];
+      for (int v = 0; v < 5; ++v) {
+        qa[v] = QL[f * 5 * nm + v * nm + x];
+        qb[v] = QR[f * 5 * nm + v * nm + x];
+      }
+      const double nrm[3] = {NR[4 * f], NR[4 * f + 1], NR[4 * f + 2]};
+      roe_face<AXIS>(gamma, P.faces[3 * (B.first + f) + 2], qa, qb, nrm, F);
+      const double area = NR[4 * f + 3];
+      for (int v = 0; v < 5; ++v) QL[f * 5 * nm + v * nm + x] = F[v] * area;
+    }
+    __syncthreads();
+    // 5. first projection pass (xi_a) back to each side that needs it
+    const double* PaL = P.basis + c_boff.P[Ma - 1][la - 1];
+    const double* PaR = P.basis + c_boff.P[Ma - 1][ra - 1];
+    {
+      const int nL = upLa ? cnt * la * Mb : 0, nR = upRa ? cnt * ra * Mb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int na = isL ? la : ra, per = na * Mb;
+        const int f = tt / per, x = tt - f * per, a = x % na, m1 = x / na;
+        const double* Pa = isL ? PaL : PaR;
+        const double* src = QL + f * 5 * nm;
+        double* dst = (isL ? UL + f * 5 * uL : UR + f * 5 * uR) + x;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int m0 = 0; m0 < Ma; ++m0) {
+          const double w = __ldg(Pa + a * Ma + m0);
+          for (int v = 0; v < 5; ++v) acc[v] += w * src[v * nm + m0 + Ma * m1];
+        }
+        for (int v = 0; v < 5; ++v) dst[v * per] = acc[v];
+      }
+    }
+    __syncthreads();
+    // 6. second projection pass (xi_b), or a copy, onto each side's face grid
+    const double* PbL = P.basis + c_boff.P[Mb - 1][lb - 1];
+    const double* PbR = P.basis + c_boff.P[Mb - 1][rb - 1];
+    for (int t = threadIdx.x; t < cnt * (nfl + nfr); t += blockDim.x) {
+      const bool isL = t < cnt * nfl;
+      const int tt = isL ? t : t - cnt * nfl;
+      const int nf = isL ? nfl : nfr, na = isL ? la : ra;
+      const int f = tt / nf, x = tt - f * nf, a = x % na, b = x / na;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      // source grid (na x Mb): the pass-5 result, or the mortar flux itself
+      const double* src = upa ? (isL ? UL + f * 5 * uL : UR + f * 5 * uR) : QL + f * 5 * nm;
+      const int nsrc = na * Mb;
+      double out[5];
+      if (upb) {
+        const double* Pb = isL ? PbL : PbR;
+        for (int v = 0; v < 5; ++v) out[v] = 0.0;
+        for (int m1 = 0; m1 < Mb; ++m1) {
+          const double w = __ldg(Pb + b * Mb + m1);
+          for (int v = 0; v < 5; ++v) out[v] += w * src[v * nsrc + a + na * m1];
+        }
+      } else {
+        for (int v = 0; v < 5; ++v) out[v] = src[v * nsrc + a + na * b];
+      }
+      const int* fr = P.faces + 3 * (B.first + f);
+      const int e = isL ? fr[0] : fr[1], dir = fr[2];
+      int n1, n2, n3;
+      orders_of(m, e, n1, n2, n3);
+      double* dst = P.surf + 5 * (m.soff[e] + face_offset(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir)) + x;
+      for (int v = 0; v < 5; ++v) dst[v * nf] = out[v];
+    }
+    __syncthreads();
   }
-  for (int p = lane; p < nfR; p += 32) {
-    int a = p % ra, b = p / ra;
-    int vi = face_vidx(r1, r2, r3, fR, a, b);
-    for (int v = 0; v < 5; ++v) trR[v * np2 + p] = P.q[5 * oR + v * nR + vi];
-  }
-  __syncwarp();
-  // interpolate a (n_a x n_b) grid with nvar fields to (Ma x Mb)
-  auto lift_up = [&](const double* src, int na_, int nb_, int nvar, double* dst) {
-    const double* IA = P.basis + c_boff.I[na_ - 1][Ma - 1];
-    const double* IB = P.basis + c_boff.I[nb_ - 1][Mb - 1];
-    for (int t = lane; t < Ma * nb_; t += 32) {
-      int m0 = t % Ma, b = t / Ma;
-      double acc[8];
-      for (int c = 0; c < nvar; ++c) acc[c] = 0.0;
-      for (int a = 0; a < na_; ++a) {
-        double w = __ldg(IA + m0 * na_ + a);
-        for (int c = 0; c < nvar; ++c) acc[c] += w * src[c * np2 + a + na_ * b];
-      }
-      for (int c = 0; c < nvar; ++c) tmp[c * np2 + m0 + Ma * b] = acc[c];
-    }
-    __syncwarp();
-    for (int t = lane; t < nm; t += 32) {
-      int m0 = t % Ma, m1 = t / Ma;
-      double acc[8];
-      for (int c = 0; c < nvar; ++c) acc[c] = 0.0;
-      for (int b = 0; b < nb_; ++b) {
-        double w = __ldg(IB + m1 * nb_ + b);
-        for (int c = 0; c < nvar; ++c) acc[c] += w * tmp[c * np2 + m0 + Ma * b];
-      }
-      for (int c = 0; c < nvar; ++c) dst[c * np2 + t] = acc[c];
-    }
-    __syncwarp();
-  };
-  lift_up(trL, la, lb, 8, mL);
-  lift_up(trR, ra, rb, 5, mR);
-  for (int p = lane; p < nm; p += 32) {
-    double qa[5], qb[5], ja[3], F[5];
-    for (int v = 0; v < 5; ++v) {
-      qa[v] = mL[v * np2 + p];
-      qb[v] = mR[v * np2 + p];
-    }
-    for (int c = 0; c < 3; ++c) ja[c] = mL[(5 + c) * np2 + p];
-    double area = sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
-    double ia = 1.0 / area;
-    double nrm[3] = {ja[0] * ia, ja[1] * ia, ja[2] * ia};
-    roe(gamma, qa, qb, nrm, F);
-    for (int v = 0; v < 5; ++v) mL[v * np2 + p] = F[v] * area;
-  }
-  __syncwarp();
-  // L2-project the mortar flux back to a face grid (na_ x nb_) and store
-  auto project_down = [&](int na_, int nb_, double* out) {
-    const double* PA = P.basis + c_boff.P[Ma - 1][na_ - 1];
-    const double* PB = P.basis + c_boff.P[Mb - 1][nb_ - 1];
-    for (int t = lane; t < na_ * Mb; t += 32) {
-      int a = t % na_, m1 = t / na_;
-      double acc[5] = {0, 0, 0, 0, 0};
-      for (int m0 = 0; m0 < Ma; ++m0) {
-        double w = __ldg(PA + a * Ma + m0);
-        for (int v = 0; v < 5; ++v) acc[v] += w * mL[v * np2 + m0 + Ma * m1];
-      }
-      for (int v = 0; v < 5; ++v) tmp[v * np2 + a + na_ * m1] = acc[v];
-    }
-    __syncwarp();
-    const int nf = na_ * nb_;
-    for (int t = lane; t < nf; t += 32) {
-      int a = t % na_, b = t / na_;
-      double acc[5] = {0, 0, 0, 0, 0};
-      for (int m1 = 0; m1 < Mb; ++m1) {
-        double w = __ldg(PB + b * Mb + m1);
-        for (int v = 0; v < 5; ++v) acc[v] += w * tmp[v * np2 + a + na_ * m1];
-      }
-      for (int v = 0; v < 5; ++v) out[v * nf + t] = acc[v];
-    }
-    __syncwarp();
-  };
-  project_down(la, lb, outL);
-  project_down(ra, rb, outR);
+}
+
+// shared memory (doubles) of one mortar batch
+__host__ __device__ inline size_t mortar_batch_smem(const MortarBatch& B) {
+  const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb;
+  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
+  const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+  return (size_t)B.count * (5 * (la * lb + ra * rb + uL + uR + 2 * Ma * Mb) + 4);
 }
 
 // BR1 trace q-hat (J a^dir) on every face; conforming faces only.
@@ -486,7 +657,15 @@ __device__ __forceinline__ void div_tile(const double* __restrict__ F, int n1, i
   }
 }
 
-template <bool AFFINE, bool NS>
+// Volume residual of one work item per iteration (a tile of same-order
+// elements), in four shared-memory phases:
+//  1. per node: primitive variables, contravariant fluxes Ft^i = J a^i . f
+//     (AXIS: J a^i = (J a^i_i) e_i, so Ft^i = J a^i_i f_i);
+//  2. per node: sum-factorised GL derivative sum_i D^(i) Ft^i -> V;
+//  3. per face node, one direction at a time (the two faces of a direction
+//     touch disjoint nodes): V += +-(F* - Ft^dir)/w_end, with every lane busy;
+//  4. per node: R = -V/J, written or fused into the RK3 stage.
+template <bool AFFINE, bool AXIS, bool NS>
 __global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
   extern __shared__ double smem[];
   const MeshView& m = P.m;
@@ -495,83 +674,112 @@ __global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
     const WorkItem w = P.items[it];
     const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
     const int slots = w.count * n;
-    // phase 1: contravariant fluxes into shared memory, [el][3][5][n]
+    double* Ft = smem;                                // [count][3][5][n]
+    double* V = smem + (size_t)w.count * 15 * n;      // [count][5][n]
+    // phase 1
     for (int s = threadIdx.x; s < slots; s += blockDim.x) {
       const int el = s / n, p = s - el * n;
       const int e = P.elist[w.first + el];
       const int64_t o = m.off[e];
       double q[5];
       for (int v = 0; v < 5; ++v) q[v] = P.q[5 * o + v * n + p];
-      Prim st = primitive(gm1, q);
-      if (!(q[0] > 0.0) || !(st.p > 0.0)) atomicOr(P.err, 1u);
-      double f[3][5];
-      for (int d = 0; d < 3; ++d) {
-        double ud = st.u[d];
-        f[d][0] = q[1 + d];
-        f[d][1] = q[1] * ud;
-        f[d][2] = q[2] * ud;
-        f[d][3] = q[3] * ud;
-        f[d][1 + d] += st.p;
-        f[d][4] = ud * (q[4] + st.p);
-      }
-      if (NS) {
-        double g[15], fv[3][5];
-        for (int v = 0; v < 5; ++v)
-          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + p];
-        viscous(m.ph, q, g, fv);
-        for (int d = 0; d < 3; ++d)
-          for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
-      }
-      double* Ft = smem + (int64_t)el * 15 * n;
-      for (int i = 0; i < 3; ++i) {
-        double ja0 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 0);
-        double ja1 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 1);
-        double ja2 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 2);
-        for (int v = 0; v < 5; ++v) Ft[(i * 5 + v) * n + p] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
+      const double ir = 1.0 / q[0];
+      const double u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+      const double pr = gm1 * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+      if (!(q[0] > 0.0) || !(pr > 0.0)) atomicOr(P.err, 1u);
+      double* F = Ft + (size_t)el * 15 * n;
+      if (AXIS && !NS) {
+        const double Epr = q[4] + pr;
+        for (int i = 0; i < 3; ++i) {
+          const double a = metric<true>(m.metric, e, 0, n, p, 4 * i);   // J a^i_i
+          const double uc = a * u[i];                                     // contravariant velocity
+          F[(i * 5 + 0) * n + p] = q[0] * uc;
+          F[(i * 5 + 1) * n + p] = q[1] * uc;
+          F[(i * 5 + 2) * n + p] = q[2] * uc;
+          F[(i * 5 + 3) * n + p] = q[3] * uc;
+          F[(i * 5 + 1 + i) * n + p] += a * pr;
+          F[(i * 5 + 4) * n + p] = uc * Epr;
+        }
+      } else {
+        double f[3][5];
+        for (int d = 0; d < 3; ++d) {
+          f[d][0] = q[1 + d];
+          f[d][1] = q[1] * u[d];
+          f[d][2] = q[2] * u[d];
+          f[d][3] = q[3] * u[d];
+          f[d][1 + d] += pr;
+          f[d][4] = u[d] * (q[4] + pr);
+        }
+        if (NS) {
+          double g[15], fv[3][5];
+          for (int v = 0; v < 5; ++v)
+            for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + p];
+          viscous(m.ph, q, g, fv);
+          for (int d = 0; d < 3; ++d)
+            for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
+        }
+        for (int i = 0; i < 3; ++i) {
+          const double ja0 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 0);
+          const double ja1 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 1);
+          const double ja2 = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + 2);
+          for (int v = 0; v < 5; ++v) F[(i * 5 + v) * n + p] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
+        }
       }
     }
     __syncthreads();
-    // phase 2: divergence, surface lift, scaling, output
+    // phase 2
     const double* D1 = P.basis + c_boff.D[w.n1];
     const double* D2 = P.basis + c_boff.D[w.n2];
     const double* D3 = P.basis + c_boff.D[w.n3];
     for (int s = threadIdx.x; s < slots; s += blockDim.x) {
       const int el = s / n, p = s - el * n;
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      double vol[5];
+      div_tile<5>(Ft + (size_t)el * 15 * n, n1, n2, n3, i, j, k, D1, D2, D3, vol);
+      double* Vv = V + (size_t)el * 5 * n;
+      for (int v = 0; v < 5; ++v) Vv[v * n + p] = vol[v];
+    }
+    __syncthreads();
+    // phase 3
+    if (!P.isolated) {
+      for (int dir = 0; dir < 3; ++dir) {
+        const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, fsz = na * nb;
+        const int Nd = dir == 0 ? w.n1 : (dir == 1 ? w.n2 : w.n3);
+        const double inv_w = 0.5 * Nd * (Nd + 1);   // 1 / w_0 = 1 / w_N = N(N+1)/2
+        const int per_el = 2 * fsz;
+        for (int s = threadIdx.x; s < w.count * per_el; s += blockDim.x) {
+          const int el = s / per_el, r = s - el * per_el;
+          const int side = r / fsz, fn = r - side * fsz;
+          const int f = 2 * dir + side;
+          const int p = face_vidx(n1, n2, n3, f, fn % na, fn / na);
+          const int e = P.elist[w.first + el];
+          const double* Fs = P.surf + 5 * (m.soff[e] + face_offset(n1, n2, n3, f)) + fn;
+          const double* F = Ft + (size_t)el * 15 * n + dir * 5 * n + p;
+          double* Vv = V + (size_t)el * 5 * n + p;
+          const double sg = side ? inv_w : -inv_w;
+          for (int v = 0; v < 5; ++v) Vv[v * n] += sg * (Fs[v * fsz] - F[v * n]);
+        }
+        __syncthreads();
+      }
+    }
+    // phase 4
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
       const int e = P.elist[w.first + el];
       const int64_t o = m.off[e];
-      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
-      const double* Ft = smem + (int64_t)el * 15 * n;
-      double vol[5];
-      div_tile<5>(Ft, n1, n2, n3, i, j, k, D1, D2, D3, vol);
-      if (!P.isolated) {
-        const double* sb = P.surf + 5 * m.soff[e];
-        // (face f, own tangential coordinates a,b, direction dir)
-        auto lift = [&](int f, int a, int b, int dir, double sgn, double inv_w) {
-          int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3;
-          int nf = na * nb;
-          const double* F = sb + 5 * face_offset(n1, n2, n3, f);
-          for (int v = 0; v < 5; ++v) vol[v] += sgn * (F[v * nf + a + na * b] - Ft[(dir * 5 + v) * n + p]) * inv_w;
-        };
-        // GL end weights: w_0 = w_N = 2 / (N (N+1))
-        if (i == 0) lift(0, j, k, 0, -1.0, 0.5 * w.n1 * (w.n1 + 1));
-        if (i == n1 - 1) lift(1, j, k, 0, 1.0, 0.5 * w.n1 * (w.n1 + 1));
-        if (j == 0) lift(2, i, k, 1, -1.0, 0.5 * w.n2 * (w.n2 + 1));
-        if (j == n2 - 1) lift(3, i, k, 1, 1.0, 0.5 * w.n2 * (w.n2 + 1));
-        if (k == 0) lift(4, i, j, 2, -1.0, 0.5 * w.n3 * (w.n3 + 1));
-        if (k == n3 - 1) lift(5, i, j, 2, 1.0, 0.5 * w.n3 * (w.n3 + 1));
-      }
-      const double iJ = -1.0 / metric<AFFINE>(m.metric, e, o, n, p, 9);
+      const double miJ = -metric<AFFINE>(m.metric, e, o, n, p, 10);
+      const double* Vv = V + (size_t)el * 5 * n + p;
       if (P.rk) {
         const double dt = *P.dt;
         for (int v = 0; v < 5; ++v) {
           const int64_t idx = 5 * o + v * n + p;
-          double r = vol[v] * iJ;
-          double g = P.rk_first ? dt * r : P.rkA * P.g_io[idx] + dt * r;
+          const double r = Vv[v * n] * miJ;
+          const double g = P.rk_first ? dt * r : P.rkA * P.g_io[idx] + dt * r;
           P.g_io[idx] = g;
           P.q_io[idx] = P.q_io[idx] + P.rkB * g;
         }
       } else {
-        for (int v = 0; v < 5; ++v) P.out[5 * o + v * n + p] = vol[v] * iJ;
+        for (int v = 0; v < 5; ++v) P.out[5 * o + v * n + p] = Vv[v * n] * miJ;
       }
     }
     __syncthreads();
@@ -626,7 +834,7 @@ __global__ void __launch_bounds__(kVolThreads) gradient_kernel(VolParams P) {
           if (k == 0) lift(4, i, j, 2, -1.0, 0.5 * w.n3 * (w.n3 + 1));
           if (k == n3 - 1) lift(5, i, j, 2, 1.0, 0.5 * w.n3 * (w.n3 + 1));
         }
-        const double iJ = 1.0 / metric<AFFINE>(m.metric, e, o, n, p, 9);
+        const double iJ = metric<AFFINE>(m.metric, e, o, n, p, 10);
         for (int v = 0; v < 5; ++v) P.out[15 * o + (c * 5 + v) * n + p] = acc[v] * iJ;
       }
       __syncthreads();
@@ -911,7 +1119,7 @@ __global__ void __launch_bounds__(kTauThreads) tau_kernel(TauParams<T> P) {
     const int P1 = n1 - 1, P2 = n2 - 1, P3 = n3 - 1;
     const int nP = n1 * n2 * n3;
     const int64_t o = m.off[e];
-    const T* metP = AFFINE ? P.metric + 10 * (int64_t)e
+    const T* metP = AFFINE ? P.metric + kAffStride * (int64_t)e
                            : P.metric + P.bank_off[e] + 10 * bank_combo_offset(P1, P2, P1, P2, P3);
     for (int p = threadIdx.x; p < nP; p += blockDim.x) {
       for (int v = 0; v < 5; ++v) QR[v * S + p] = (T)P.q[5 * o + v * nP + p];
@@ -1124,7 +1332,7 @@ FaceParams dgk_face_params_for(dg_mesh_impl* m, const double* q, double* surf) {
   P.surf = surf;
   P.basis = m->basis64;
   P.np_max = m->max_order + 1;
-  P.warp_smem = 34 * P.np_max * P.np_max;
+  P.warp_smem = 25 * P.np_max * P.np_max;
   return P;
 }
 
@@ -1143,7 +1351,82 @@ VolParams dgk_vol_params_for(dg_mesh_impl* m, const double* q, const double* sur
   return P;
 }
 
+template <bool AFF, bool AX, bool NSV>
+cudaError_t launch_face(dg_mesh_impl* m, const FaceParams& P, size_t smem, int grid) {
+  cudaError_t err = allow_smem(face_flux_kernel<AFF, AX, NSV>, smem);
+  if (err) return err;
+  face_flux_kernel<AFF, AX, NSV><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_face(dg_mesh_impl* m, const FaceParams& P, size_t smem, int grid) {
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  if (m->axis) return ns ? launch_face<true, true, true>(m, P, smem, grid) : launch_face<true, true, false>(m, P, smem, grid);
+  if (m->affine)
+    return ns ? launch_face<true, false, true>(m, P, smem, grid) : launch_face<true, false, false>(m, P, smem, grid);
+  return ns ? launch_face<false, false, true>(m, P, smem, grid) : launch_face<false, false, false>(m, P, smem, grid);
+}
+
+template <bool AFF, bool AX, bool NSV>
+cudaError_t launch_volume(dg_mesh_impl* m, const VolParams& P, size_t smem, int grid) {
+  cudaError_t err = allow_smem(volume_kernel<AFF, AX, NSV>, smem);
+  if (err) return err;
+  volume_kernel<AFF, AX, NSV><<<grid, kVolThreads, smem, m->stream>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_volume(dg_mesh_impl* m, const VolParams& P, size_t smem, int grid) {
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  if (m->axis)
+    return ns ? launch_volume<true, true, true>(m, P, smem, grid) : launch_volume<true, true, false>(m, P, smem, grid);
+  if (m->affine)
+    return ns ? launch_volume<true, false, true>(m, P, smem, grid) : launch_volume<true, false, false>(m, P, smem, grid);
+  return ns ? launch_volume<false, false, true>(m, P, smem, grid) : launch_volume<false, false, false>(m, P, smem, grid);
+}
+
+// Every numerical face flux into the face buffer surf: conforming and
+// boundary faces one warp each, p-nonconforming faces in shape batches.
+cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* grad, double* surf) {
+  cudaError_t err;
+  if (m->n_faces) {
+    FaceParams P = dgk_face_params_for(m, q, surf);
+    P.grad = grad;
+    const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+    if ((err = dispatch_face(m, P, 0, grid))) return err;
+  }
+  if (m->n_mbatches) {
+    MortarParams M;
+    M.m = view(m);
+    M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
+    M.n_batches = m->n_mbatches;
+    M.faces = m->d_mfaces;
+    M.q = q;
+    M.surf = surf;
+    M.basis = m->basis64;
+    const size_t smem = sizeof(double) * m->mortar_smem;
+    const int grid = grid_for(m->n_mbatches, 8);
+    if (m->axis) {
+      if ((err = allow_smem(mortar_kernel<true>, smem))) return err;
+      mortar_kernel<true><<<grid, kVolThreads, smem, m->stream>>>(M);
+    } else {
+      if ((err = allow_smem(mortar_kernel<false>, smem))) return err;
+      mortar_kernel<false><<<grid, kVolThreads, smem, m->stream>>>(M);
+    }
+    if ((err = cudaGetLastError())) return err;
+  }
+  return cudaSuccess;
+}
+
+size_t mortar_smem_doubles(int count, int la, int lb, int ra, int rb) {
+  MortarBatch B{0, count, la, lb, ra, rb};
+  return mortar_batch_smem(B);
+}
+
 }  // namespace
+
+size_t dg_mortar_smem_doubles(int count, int la, int lb, int ra, int rb) {
+  return mortar_smem_doubles(count, la, lb, ra, rb);
+}
 
 namespace dgk {
 
@@ -1172,33 +1455,14 @@ static FaceParams face_params(dg_mesh_impl* m, const double* q, const double* gr
   P.surf = m->d_surf;
   P.basis = m->basis64;
   P.np_max = m->max_order + 1;
-  P.warp_smem = 34 * P.np_max * P.np_max;
+  P.warp_smem = 25 * P.np_max * P.np_max;
   return P;
 }
 
 cudaError_t face_flux(dg_mesh_impl* m, const double* q, const double* grad, bool isolated) {
   (void)isolated;
-  if (m->n_faces == 0) return cudaSuccess;
-  FaceParams P = face_params(m, q, grad);
-  size_t smem = m->n_face_mortar ? sizeof(double) * P.warp_smem * kFaceWarps : 0;
-  int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
-  bool ns = m->phys.eqs == DG_NAVIER_STOKES;
-  cudaError_t err;
-  Prof pr(m, DG_KERNEL_FACE_FLUX);
-  if (m->affine && !ns) {
-    if ((err = allow_smem(face_flux_kernel<true, false>, smem))) return err;
-    face_flux_kernel<true, false><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
-  } else if (m->affine) {
-    if ((err = allow_smem(face_flux_kernel<true, true>, smem))) return err;
-    face_flux_kernel<true, true><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
-  } else if (!ns) {
-    if ((err = allow_smem(face_flux_kernel<false, false>, smem))) return err;
-    face_flux_kernel<false, false><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
-  } else {
-    if ((err = allow_smem(face_flux_kernel<false, true>, smem))) return err;
-    face_flux_kernel<false, true><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
-  }
-  return cudaGetLastError();
+  Prof pr(m, DG_KERNEL_FACE_FLUX, (m->n_faces ? 1 : 0) + (m->n_mbatches ? 1 : 0));
+  return launch_all_faces(m, q, grad, m->d_surf);
 }
 
 cudaError_t face_qhat(dg_mesh_impl* m, const double* q) {
@@ -1262,25 +1526,10 @@ cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double*
     P.g_io = g_io;
     P.dt = dt_dev;
   }
-  size_t smem = sizeof(double) * 15 * m->item_max_nodes;
+  size_t smem = sizeof(double) * 20 * m->item_max_nodes;
   int grid = grid_for(m->n_items, 8);
-  bool ns = m->phys.eqs == DG_NAVIER_STOKES;
-  cudaError_t err;
   Prof pr(m, DG_KERNEL_VOLUME);
-  if (m->affine && !ns) {
-    if ((err = allow_smem(volume_kernel<true, false>, smem))) return err;
-    volume_kernel<true, false><<<grid, kVolThreads, smem, m->stream>>>(P);
-  } else if (m->affine) {
-    if ((err = allow_smem(volume_kernel<true, true>, smem))) return err;
-    volume_kernel<true, true><<<grid, kVolThreads, smem, m->stream>>>(P);
-  } else if (!ns) {
-    if ((err = allow_smem(volume_kernel<false, false>, smem))) return err;
-    volume_kernel<false, false><<<grid, kVolThreads, smem, m->stream>>>(P);
-  } else {
-    if ((err = allow_smem(volume_kernel<false, true>, smem))) return err;
-    volume_kernel<false, true><<<grid, kVolThreads, smem, m->stream>>>(P);
-  }
-  return cudaGetLastError();
+  return dispatch_volume(m, P, smem, grid);
 }
 
 cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev) {
@@ -1453,23 +1702,11 @@ extern "C" dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double*
   // face pass: every element-face node of the buffer is written (interior
   // faces for both sides, boundary faces for theirs) before the volume pass
   // reads it, so nothing needs clearing between calls
-  FaceParams F = dgk_face_params_for(mesh, q, surf);
-  size_t fsmem = mesh->n_face_mortar ? sizeof(double) * F.warp_smem * kFaceWarps : 0;
-  int fgrid = (mesh->n_faces + kFaceWarps - 1) / kFaceWarps;
+  if (launch_all_faces(mesh, q, nullptr, surf) != cudaSuccess) return DG_ERR_CUDA;
   VolParams V = dgk_vol_params_for(mesh, q, surf, r);
-  size_t vsmem = sizeof(double) * 15 * mesh->item_max_nodes;
+  size_t vsmem = sizeof(double) * 20 * mesh->item_max_nodes;
   int vgrid = grid_for(mesh->n_items, 8);
-  if (mesh->affine) {
-    if ((err = allow_smem(face_flux_kernel<true, false>, fsmem))) return DG_ERR_CUDA;
-    if ((err = allow_smem(volume_kernel<true, false>, vsmem))) return DG_ERR_CUDA;
-    if (mesh->n_faces) face_flux_kernel<true, false><<<fgrid, 32 * kFaceWarps, fsmem, mesh->stream>>>(F);
-    volume_kernel<true, false><<<vgrid, kVolThreads, vsmem, mesh->stream>>>(V);
-  } else {
-    if ((err = allow_smem(face_flux_kernel<false, false>, fsmem))) return DG_ERR_CUDA;
-    if ((err = allow_smem(volume_kernel<false, false>, vsmem))) return DG_ERR_CUDA;
-    if (mesh->n_faces) face_flux_kernel<false, false><<<fgrid, 32 * kFaceWarps, fsmem, mesh->stream>>>(F);
-    volume_kernel<false, false><<<vgrid, kVolThreads, vsmem, mesh->stream>>>(V);
-  }
-  mesh->launches += mesh->n_faces ? 2 : 1;
+  if (dispatch_volume(mesh, V, vsmem, vgrid) != cudaSuccess) return DG_ERR_CUDA;
+  mesh->launches += 1 + (mesh->n_faces ? 1 : 0) + (mesh->n_mbatches ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
 }
