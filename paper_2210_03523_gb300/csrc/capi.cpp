@@ -163,18 +163,20 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 void free_device(dg_mesh_impl* m) {
   void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
                   m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
-                  m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_qc, m->d_rc, m->d_sweep};
+                  m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
   m->d_metric32 = nullptr; m->d_surf = nullptr; m->d_surfq = nullptr; m->d_grad = nullptr; m->d_xyz = nullptr;
   m->d_faces = nullptr; m->d_items = nullptr; m->d_elist = nullptr; m->d_err = nullptr; m->d_scratch = nullptr;
   m->d_taugeo = nullptr; m->d_taugeo32 = nullptr; m->d_taugeo_off = nullptr; m->d_rp = nullptr; m->d_qc = nullptr;
-  m->d_rc = nullptr; m->d_sweep = nullptr; m->d_mfaces = nullptr; m->d_mbatches = nullptr;
+  m->d_rc = nullptr; m->d_sweep = nullptr; m->d_mfaces = nullptr; m->d_mbatches = nullptr; m->d_rp32 = nullptr;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
   if (!m) return;
+  for (auto& c : m->tau_classes) cudaFree(c.d_list);
+  m->tau_classes.clear();
   for (auto& pp : m->prof_pending) {
     cudaEventDestroy(pp.a);
     cudaEventDestroy(pp.b);
@@ -352,6 +354,27 @@ dg_status build(dg_mesh_impl* m) {
   if (ns) {
     DG_CUDA(upload<double>(&m->d_surfq, nullptr, 15 * (size_t)m->h_soff[ne]));
     DG_CUDA(upload<double>(&m->d_grad, nullptr, 15 * (size_t)m->n_nodes));
+  }
+  // isolated tau: the work items grouped by tile size (count * n_P) into
+  // shared-memory size classes
+  {
+    const int bounds[5] = {64, 128, 256, 512, 1000};
+    std::vector<std::vector<int32_t>> cls(5);
+    std::vector<int> cS(5, 0);
+    for (int i = 0; i < (int)items.size(); ++i) {
+      const WorkItem& w = items[i];
+      const int tile = w.count * (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
+      int k = 0;
+      while (tile > bounds[k]) ++k;
+      cls[k].push_back(i);
+      cS[k] = std::max(cS[k], tile);
+    }
+    for (int k = 0; k < 5; ++k) {
+      if (cls[k].empty()) continue;
+      dg_mesh_impl::TauClass c{nullptr, (int)cls[k].size(), cS[k]};
+      DG_CUDA(upload(&c.d_list, cls[k].data(), cls[k].size()));
+      m->tau_classes.push_back(c);
+    }
   }
   DG_CUDA(upload<unsigned>(&m->d_err, nullptr, 1));
   DG_CUDA(cudaMemset(m->d_err, 0, sizeof(unsigned)));
@@ -637,6 +660,8 @@ dg_status dg_tau_estimate(dg_mesh* m, const double* q, const double* r_p, const 
     if (need + 256 > (size_t)limit) return DG_ERR_UNSUPPORTED;   // static reduction buffers
     dg_status st = build_tau_bank(m);
     if (st != DG_OK) return st;
+    if (!r_p && fp32 && !m->d_rp32) DG_CUDA(cudaMalloc(&m->d_rp32, sizeof(float) * 5 * m->n_nodes));
+    if (!r_p && !fp32 && !m->d_rp) DG_CUDA(cudaMalloc(&m->d_rp, sizeof(double) * 5 * m->n_nodes));
     std::vector<int32_t> hs(sweep, sweep + 3 * n_sweep);
     if (hs != m->h_sweep) {
       if (m->d_sweep) cudaFree(m->d_sweep);

@@ -139,7 +139,10 @@ struct dg_mesh_impl {
 
   std::vector<dg_mesh_impl*> coarse;   // cached non-isolated coarse meshes (by sweep entry)
   std::vector<int32_t> coarse_key;     // their sweep orders, 3 per entry
-  double* d_rp = nullptr;              // non-isolated tau: full R^P scratch
+  double* d_rp = nullptr;              // tau: R^P scratch (full R^P non-isolated, isolated R^P FP64 sweep)
+  float* d_rp32 = nullptr;             // tau: isolated R^P scratch of the FP32 sweep
+  struct TauClass { int32_t* d_list; int n; int S; };
+  std::vector<TauClass> tau_classes;   // work items grouped by tile size (shared-memory size class)
   double* d_qc = nullptr;              // coarse mesh: restricted state scratch
   double* d_rc = nullptr;              // coarse mesh: coarse residual scratch
   int32_t* d_sweep = nullptr;          // device copy of the last sweep

@@ -911,12 +911,17 @@ struct TauParams {
   const int32_t* sweep;     // [n_sweep][3] (device)
   int n_sweep;
   const T* basis;           // tables in precision T
-  const T* metric;          // affine: [e][10]; curved: tau geometry bank
+  const T* metric;          // affine: [e][kAffStride]; curved: tau geometry bank [10][n_N] per combo
   const int64_t* bank_off;  // curved: per-element bank offset (in T elements)
   T* map_new;
   T* map_trad;
   int accumulate;
-  int S;                    // shared-memory buffer stride (max n_P)
+  int S;                    // shared-memory buffer stride (max n_P of the size class)
+  const WorkItem* items;    // tiles of same-order elements (the volume work items)
+  const int32_t* elist;     // their element list
+  const int32_t* ilist;     // items of this launch (one shared-memory size class)
+  int n_list;
+  T* rp_scratch;            // isolated R^P at P, state layout, when rp is null
   T gamma, mu, Pr, Rgas, kappa;
   unsigned* err;
 };
@@ -999,13 +1004,18 @@ __device__ __forceinline__ void div5(const T* basis, const T* F, int n1, int n2,
   }
 }
 
-// Isolated residual of a [5][n] state tile at orders (n1,n2,n3) with metrics
-// met: R = -(1/J) sum_i D^(i) Ft^i (Euler) or, for Navier-Stokes, with the
-// element-local BR1 gradient and the viscous flux.  Ft: [15][n] scratch,
-// Gs: [15][n] scratch (NS).  Result in Rout[5][rstride].
+// Isolated residual of a [5][n] state tile Qs (stride qs) at orders
+// (n1,n2,n3) with metrics met: R = -(1/J) sum_i D^(i) Ft^i (Euler) or, for
+// Navier-Stokes, with the element-local BR1 gradient and the viscous flux.
+// Ft: [15][n] scratch; Gs: [15][n] scratch (NS).  Either writes R to
+// Rout[5][rs], or (IR != null) folds it into the tau norms: per node
+// t = IR - R (IR = I R^P, stride of the tile), a = max |t|,
+// b = max |J w_i w_j w_k t| (w1, w2, the GL weights in xi1, xi2; xi3 from
+// the basis table), accumulated into *na, *nb.
 template <typename T, bool NS>
-__device__ void isolated_residual_tile(const TauParams<T>& P, bool affine, const T* met, const T* Qs, int qs, int n1,
-                                       int n2, int n3, T* Ft, T* Gs, T* Rout, int rs) {
+__device__ void tau_residual(const TauParams<T>& P, bool affine, const T* met, const T* Qs, int qs, int n1, int n2,
+                             int n3, T* Ft, T* Gs, T* Rout, int rs, const T* IR, const T* w1, const T* w2, T* na,
+                             T* nb) {
   const int n = n1 * n2 * n3;
   const T gm1 = P.gamma - (T)1;
   if (NS) {
@@ -1043,11 +1053,28 @@ __device__ void isolated_residual_tile(const TauParams<T>& P, bool affine, const
     }
   }
   __syncthreads();
+  const T* w3 = P.basis + c_boff.W[n3 - 1];
+  T a = 0, b = 0;
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     T acc[5];
     div5(P.basis, Ft, n1, n2, n3, p, acc);
-    T iJ = -(T)1 / met_at(met, affine, n, p, 9);
-    for (int v = 0; v < 5; ++v) Rout[v * rs + p] = acc[v] * iJ;
+    const T J = met_at(met, affine, n, p, 9);
+    const T iJ = -(T)1 / J;
+    if (IR) {
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const T Jw = J * w1[i] * w2[j] * w3[k];
+      for (int v = 0; v < 5; ++v) {
+        const T t = IR[v * qs + p] - acc[v] * iJ;   // tau~ = I R^P - R^N(I q^P)
+        a = tmax(a, (T)fabs(t));
+        b = tmax(b, (T)fabs(Jw * t));
+      }
+    } else {
+      for (int v = 0; v < 5; ++v) Rout[v * rs + p] = acc[v] * iJ;
+    }
+  }
+  if (IR) {
+    *na = a;
+    *nb = b;
   }
   __syncthreads();
 }
@@ -1099,76 +1126,235 @@ __device__ __forceinline__ void map_store(T* map, int64_t idx, int accumulate, T
   map[idx] = accumulate ? tmax(map[idx], v) : v;
 }
 
+template <typename T>
+__device__ __forceinline__ T mul_rn(T a, T b);
+template <>
+__device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <>
+__device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+
+// non-negative floating-point values order like their bit patterns
+__device__ __forceinline__ void smax_bits(unsigned int* slot, float v) { atomicMax(slot, __float_as_uint(v)); }
+__device__ __forceinline__ void smax_bits(unsigned long long* slot, double v) {
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+template <typename T>
+struct Bits;
+template <>
+struct Bits<float> {
+  typedef unsigned int type;
+  static __device__ __forceinline__ float val(type b) { return __uint_as_float(b); }
+};
+template <>
+struct Bits<double> {
+  typedef unsigned long long type;
+  static __device__ __forceinline__ double val(type b) { return __longlong_as_double((long long)b); }
+};
+
+// metrics of tile element el at coarse orders (N1,N2,N3) (P: its own orders)
+template <typename T, bool AFFINE>
+__device__ __forceinline__ const T* tile_met(const TauParams<T>& P, int e, int P1, int P2, int N1, int N2, int N3) {
+  if (AFFINE) return P.metric + kAffStride * (int64_t)e;
+  return P.metric + P.bank_off[e] + 10 * bank_combo_offset(P1, P2, N1, N2, N3);
+}
+
+// Isolated residual of a tile of cnt same-order elements, state X[el][5][n]
+// (element stride xs) at orders (n1,n2,n3): R = -(1/J) sum_i D^(i) Ft^i, with
+// the element-local BR1 gradient and viscous flux for Navier-Stokes.  Either
+// writes R to Rout (element e's R at Rout + 5*off_e, [5][n]), or folds it into
+// the tau norms: t = IR - R with IR = X + 5*n (the restricted I R^P), per
+// element max |t| and max |J w t| into the shared slots na[el], nb[el].
 template <typename T, bool AFFINE, bool NS>
-__global__ void __launch_bounds__(kTauThreads) tau_kernel(TauParams<T> P) {
+__device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int cnt, int P1, int P2, int N1, int N2,
+                                  int N3, const T* X, int xs, T* Ft, T* Gs, T* Rout,
+                                  typename Bits<T>::type* na, typename Bits<T>::type* nb) {
+  const int n1 = N1 + 1, n2 = N2 + 1, n3 = N3 + 1, n = n1 * n2 * n3, pts = cnt * n;
+  const T gm1 = P.gamma - (T)1;
+  const MeshView& m = P.m;
+  if (NS) {
+    for (int c = 0; c < 3; ++c) {
+      for (int t = threadIdx.x; t < pts; t += blockDim.x) {
+        const int el = t / n, p = t - el * n;
+        const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
+        for (int i = 0; i < 3; ++i) {
+          T ja = met_at(met, AFFINE, n, p, 3 * i + c);
+          for (int v = 0; v < 5; ++v) Ft[el * 15 * n + (i * 5 + v) * n + p] = ja * X[el * xs + v * n + p];
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < pts; t += blockDim.x) {
+        const int el = t / n, p = t - el * n;
+        const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
+        T acc[5];
+        div5(P.basis, Ft + el * 15 * n, n1, n2, n3, p, acc);
+        T iJ = (T)1 / met_at(met, AFFINE, n, p, 9);
+        for (int v = 0; v < 5; ++v) Gs[el * 15 * n + (v * 3 + c) * n + p] = acc[v] * iJ;
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < pts; t += blockDim.x) {
+    const int el = t / n, p = t - el * n;
+    const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
+    T q[5], f[3][5];
+    for (int v = 0; v < 5; ++v) q[v] = X[el * xs + v * n + p];
+    euler_fluxes(gm1, q, f);
+    if (NS) {
+      T g[15], fv[3][5];
+      for (int c = 0; c < 15; ++c) g[c] = Gs[el * 15 * n + c * n + p];
+      viscous_t(P, q, g, fv);
+      for (int d = 0; d < 3; ++d)
+        for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
+    }
+    for (int i = 0; i < 3; ++i) {
+      T ja0 = met_at(met, AFFINE, n, p, 3 * i), ja1 = met_at(met, AFFINE, n, p, 3 * i + 1),
+        ja2 = met_at(met, AFFINE, n, p, 3 * i + 2);
+      for (int v = 0; v < 5; ++v)
+        Ft[el * 15 * n + (i * 5 + v) * n + p] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
+    }
+  }
+  if (na && threadIdx.x < cnt) {
+    na[threadIdx.x] = 0;
+    nb[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  const T* w1 = P.basis + c_boff.W[N1];
+  const T* w2 = P.basis + c_boff.W[N2];
+  const T* w3 = P.basis + c_boff.W[N3];
+  for (int t = threadIdx.x; t < pts; t += blockDim.x) {
+    const int el = t / n, p = t - el * n;
+    const int e = els[el];
+    const T* met = tile_met<T, AFFINE>(P, e, P1, P2, N1, N2, N3);
+    T acc[5];
+    div5(P.basis, Ft + el * 15 * n, n1, n2, n3, p, acc);
+    const T J = met_at(met, AFFINE, n, p, 9);
+    const T iJ = -(T)1 / J;
+    if (na) {
+      // R rounded exactly as when stored, so that tau at N = P is exactly 0
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const T Jw = J * w1[i] * w2[j] * w3[k];
+      T a = 0, b = 0;
+      for (int v = 0; v < 5; ++v) {
+        const T r = mul_rn(acc[v], iJ);
+        const T tt = X[el * xs + (5 + v) * n + p] - r;   // tau~ = I R^P - R^N(I q^P)
+        a = tmax(a, (T)fabs(tt));
+        b = tmax(b, (T)fabs(Jw * tt));
+      }
+      smax_bits(na + el, a);
+      smax_bits(nb + el, b);
+    } else {
+      const int64_t o = m.off[e];
+      for (int v = 0; v < 5; ++v) Rout[5 * o + v * n + p] = mul_rn(acc[v], iJ);
+    }
+  }
+  __syncthreads();
+}
+
+// Isolated tau sweep over tiles of same-order elements (the volume work
+// items), one tile per CTA iteration: every phase runs over all points of
+// all elements of the tile, so small coarse orders still fill the lanes.
+template <typename T, bool AFFINE, bool NS>
+__global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  __shared__ T red[2][kTauThreads / 32];
-  const int S = P.S;
-  T* QR = sm;            // [10][S]  q^P (0..4) and R^P (5..9)
-  T* A3 = QR + 10 * S;   // [10][S]  restricted in xi3
-  T* A2 = A3 + 10 * S;   // [10][S]  restricted in xi2, xi3
-  T* A1 = A2 + 10 * S;   // [10][S]  I q^P (0..4), I R^P (5..9) at N
-  T* RN = A1 + 10 * S;   // [5][S]   R^N(I q^P)
-  T* Ft = RN + 5 * S;    // [15][S]
-  T* Gs = Ft + 15 * S;   // [15][S]  (NS only: the Euler launch allocates 60 S)
+  typedef typename Bits<T>::type B;
+  __shared__ B na[kVolThreads], nb[kVolThreads];
+  const int S = P.S;     // tile capacity in nodes (max count * n_P of the class)
+  T* A3 = sm;            // [el][10][pts3]  q^P, R^P restricted in xi3
+  T* A2 = A3 + 10 * S;   // [el][10][pts2]  ... in xi2, xi3
+  T* A1 = A2 + 10 * S;   // [el][10][nN]    I q^P (0..4), I R^P (5..9) at N
+  T* Ft = A1 + 10 * S;   // [el][15][nN]
+  T* Gs = Ft + 15 * S;   // [el][15][nN]    (NS only: the Euler launch allocates 45 S)
   const MeshView& m = P.m;
-  for (int e = blockIdx.x; e < P.n_elem; e += gridDim.x) {
-    int n1, n2, n3;
-    orders_of(m, e, n1, n2, n3);
-    const int P1 = n1 - 1, P2 = n2 - 1, P3 = n3 - 1;
-    const int nP = n1 * n2 * n3;
-    const int64_t o = m.off[e];
-    const T* metP = AFFINE ? P.metric + kAffStride * (int64_t)e
-                           : P.metric + P.bank_off[e] + 10 * bank_combo_offset(P1, P2, P1, P2, P3);
-    for (int p = threadIdx.x; p < nP; p += blockDim.x) {
-      for (int v = 0; v < 5; ++v) QR[v * S + p] = (T)P.q[5 * o + v * nP + p];
-      if (P.rp)
-        for (int v = 0; v < 5; ++v) QR[(5 + v) * S + p] = (T)P.rp[5 * o + v * nP + p];
+  for (int li = blockIdx.x; li < P.n_list; li += gridDim.x) {
+    const WorkItem w = P.items[P.ilist[li]];
+    const int32_t* els = P.elist + w.first;
+    const int cnt = w.count;
+    const int P1 = w.n1, P2 = w.n2, P3 = w.n3, n1 = P1 + 1, n2 = P2 + 1, n3 = P3 + 1, nP = n1 * n2 * n3;
+    T* rpS = P.rp_scratch;
+    if (!P.rp) {  // isolated R^P, once per element, into the scratch
+      for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
+        const int el = t / nP, p = t - el * nP;
+        const int64_t o = m.off[els[el]];
+        for (int v = 0; v < 5; ++v) A1[el * 10 * nP + v * nP + p] = (T)P.q[5 * o + v * nP + p];
+      }
+      __syncthreads();
+      tau_tile_residual<T, AFFINE, NS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, Ft, Gs, rpS, nullptr, nullptr);
     }
-    __syncthreads();
-    if (!P.rp) isolated_residual_tile<T, NS>(P, AFFINE, metP, QR, S, n1, n2, n3, Ft, Gs, QR + 5 * S, S);
     int cur3 = -1, cur2 = -1;
     for (int s = 0; s < P.n_sweep; ++s) {
       const int N1 = P.sweep[3 * s], N2 = P.sweep[3 * s + 1], N3 = P.sweep[3 * s + 2];
-      const int64_t idx = (int64_t)e * P.n_sweep + s;
       if (N1 > P1 || N2 > P2 || N3 > P3) {
-        if (threadIdx.x == 0) {
+        for (int el = threadIdx.x; el < cnt; el += blockDim.x) {
+          const int64_t idx = (int64_t)els[el] * P.n_sweep + s;
           if (P.map_new) P.map_new[idx] = (T)-1;
           if (P.map_trad) P.map_trad[idx] = (T)-1;
         }
         continue;
       }
-      if (N3 != cur3) {
-        apply_dir_tile(P.basis + c_boff.I[P3][N3], N3 + 1, n3, 2, n1, n2, n3, QR, S, A3, S, 10);
+      const int c1 = N1 + 1, c2 = N2 + 1, c3 = N3 + 1, nN = c1 * c2 * c3;
+      const int n12 = n1 * n2;
+      if (N3 != cur3) {  // xi3 straight from q^P and R^P in global memory
+        const T* I3 = P.basis + c_boff.I[P3][N3];
+        const int per = n12 * c3;
+        for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
+          const int el = t / per, x = t - el * per, ij = x % n12, k = x / n12;
+          const int64_t o = m.off[els[el]];
+          T acc[10];
+          for (int c = 0; c < 10; ++c) acc[c] = 0;
+          for (int mm = 0; mm < n3; ++mm) {
+            const T wk = I3[k * n3 + mm];
+            const int src = ij + n12 * mm;
+            for (int v = 0; v < 5; ++v) acc[v] += wk * (T)P.q[5 * o + v * nP + src];
+            if (P.rp)
+              for (int v = 0; v < 5; ++v) acc[5 + v] += wk * (T)P.rp[5 * o + v * nP + src];
+            else
+              for (int v = 0; v < 5; ++v) acc[5 + v] += wk * rpS[5 * o + v * nP + src];
+          }
+          for (int c = 0; c < 10; ++c) A3[el * 10 * per + c * per + x] = acc[c];
+        }
+        __syncthreads();
         cur3 = N3;
         cur2 = -1;
       }
-      if (N2 != cur2) {
-        apply_dir_tile(P.basis + c_boff.I[P2][N2], N2 + 1, n2, 1, n1, n2, N3 + 1, A3, S, A2, S, 10);
+      if (N2 != cur2) {  // xi2
+        const T* I2 = P.basis + c_boff.I[P2][N2];
+        const int pin = n12 * c3, per = n1 * c2 * c3;
+        for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
+          const int el = t / per, x = t - el * per, i = x % n1, j = (x / n1) % c2, k = x / (n1 * c2);
+          const T* src = A3 + el * 10 * pin + i + n12 * k;
+          T acc[10];
+          for (int c = 0; c < 10; ++c) acc[c] = 0;
+          for (int mm = 0; mm < n2; ++mm) {
+            const T wj = I2[j * n2 + mm];
+            for (int c = 0; c < 10; ++c) acc[c] += wj * src[c * pin + n1 * mm];
+          }
+          for (int c = 0; c < 10; ++c) A2[el * 10 * per + c * per + x] = acc[c];
+        }
+        __syncthreads();
         cur2 = N2;
       }
-      apply_dir_tile(P.basis + c_boff.I[P1][N1], N1 + 1, n1, 0, n1, N2 + 1, N3 + 1, A2, S, A1, S, 10);
-      const int c1 = N1 + 1, c2 = N2 + 1, c3 = N3 + 1, nN = c1 * c2 * c3;
-      const T* metN = AFFINE ? metP : P.metric + P.bank_off[e] + 10 * bank_combo_offset(P1, P2, N1, N2, N3);
-      isolated_residual_tile<T, NS>(P, AFFINE, metN, A1, S, c1, c2, c3, Ft, Gs, RN, S);
-      const T* w1 = P.basis + c_boff.W[N1];
-      const T* w2 = P.basis + c_boff.W[N2];
-      const T* w3 = P.basis + c_boff.W[N3];
-      T a = 0, b = 0;
-      for (int p = threadIdx.x; p < nN; p += blockDim.x) {
-        const int i = p % c1, j = (p / c1) % c2, k = p / (c1 * c2);
-        T Jw = met_at(metN, AFFINE, nN, p, 9) * w1[i] * w2[j] * w3[k];
-        for (int v = 0; v < 5; ++v) {
-          T t = A1[(5 + v) * S + p] - RN[v * S + p];   // tau~ = I R^P - R^N(I q^P)
-          a = tmax(a, (T)fabs(t));
-          b = tmax(b, (T)fabs(Jw * t));
+      {  // xi1
+        const T* I1 = P.basis + c_boff.I[P1][N1];
+        const int pin = n1 * c2 * c3;
+        for (int t = threadIdx.x; t < cnt * nN; t += blockDim.x) {
+          const int el = t / nN, x = t - el * nN, i = x % c1, jk = x / c1;
+          const T* src = A2 + el * 10 * pin + n1 * jk;
+          T acc[10];
+          for (int c = 0; c < 10; ++c) acc[c] = 0;
+          for (int mm = 0; mm < n1; ++mm) {
+            const T wi = I1[i * n1 + mm];
+            for (int c = 0; c < 10; ++c) acc[c] += wi * src[c * pin + mm];
+          }
+          for (int c = 0; c < 10; ++c) A1[el * 10 * nN + c * nN + x] = acc[c];
         }
+        __syncthreads();
       }
-      block_max2(a, b, red);
-      if (threadIdx.x == 0) {
-        map_store(P.map_new, idx, P.accumulate, a);
-        map_store(P.map_trad, idx, P.accumulate, b);
+      tau_tile_residual<T, AFFINE, NS>(P, els, cnt, P1, P2, N1, N2, N3, A1, 10 * nN, Ft, Gs, nullptr, na, nb);
+      for (int el = threadIdx.x; el < cnt; el += blockDim.x) {
+        const int64_t idx = (int64_t)els[el] * P.n_sweep + s;
+        map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na[el]));
+        map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb[el]));
       }
       __syncthreads();
     }
@@ -1545,41 +1731,47 @@ cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev)
   return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, size_t smem) {
-  int grid = grid_for(m->n_elem, 4);
-  bool ns = m->phys.eqs == DG_NAVIER_STOKES;
-  cudaError_t err;
-  Prof pr(m, DG_KERNEL_TAU);
-#define DG_TAU_CASE(AFF, NSV)                                                   \
-  if ((err = allow_smem(tau_kernel<T, AFF, NSV>, smem))) return err;             \
-  tau_kernel<T, AFF, NSV><<<grid, kTauThreads, smem, m->stream>>>(P);
-  if (m->affine && !ns) { DG_TAU_CASE(true, false) }
-  else if (m->affine) { DG_TAU_CASE(true, true) }
-  else if (!ns) { DG_TAU_CASE(false, false) }
-  else { DG_TAU_CASE(false, true) }
-#undef DG_TAU_CASE
-  return cudaGetLastError();
+// Shared memory of the isolated sweep for a class of elements with at most
+// S nodes: restriction buffers A3, A2, A1 (10 S each) and fluxes (15 S), plus
+// the BR1 gradient (15 S) for Navier-Stokes.
+size_t tau_smem_for(int S, bool ns, bool fp32) {
+  return (size_t)(ns ? 60 : 45) * S * (fp32 ? sizeof(float) : sizeof(double));
 }
 
 size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32) {
-  int S = 1;
-  std::vector<int32_t>& o = m->h_ord;
-  for (int e = 0; e < m->n_elem; ++e) {
-    int n = (o[3 * e] + 1) * (o[3 * e + 1] + 1) * (o[3 * e + 2] + 1);
-    if (n > S) S = n;
+  size_t mx = 0;
+  for (auto& c : m->tau_classes) mx = std::max(mx, tau_smem_for(c.S, m->phys.eqs == DG_NAVIER_STOKES, fp32));
+  return mx;
+}
+
+template <typename T>
+static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  cudaError_t err;
+  Prof pr(m, DG_KERNEL_TAU, (int)m->tau_classes.size());
+  P.items = m->d_items;
+  P.elist = m->d_elist;
+  for (auto& c : m->tau_classes) {
+    P.ilist = c.d_list;
+    P.n_list = c.n;
+    P.S = c.S;
+    const size_t smem = tau_smem_for(c.S, ns, fp32);
+    const int grid = grid_for(c.n, 16);
+#define DG_TAU_CASE(AFF, NSV)                                                   \
+  if ((err = allow_smem(tau_kernel<T, AFF, NSV>, smem))) return err;             \
+  tau_kernel<T, AFF, NSV><<<grid, kVolThreads, smem, m->stream>>>(P);
+    if (m->affine && !ns) { DG_TAU_CASE(true, false) }
+    else if (m->affine) { DG_TAU_CASE(true, true) }
+    else if (!ns) { DG_TAU_CASE(false, false) }
+    else { DG_TAU_CASE(false, true) }
+#undef DG_TAU_CASE
+    if ((err = cudaGetLastError())) return err;
   }
-  const int bufs = m->phys.eqs == DG_NAVIER_STOKES ? 75 : 60;
-  return (size_t)bufs * S * (fp32 ? sizeof(float) : sizeof(double));
+  return cudaSuccess;
 }
 
 cudaError_t tau_isolated(dg_mesh_impl* m, const double* q, const double* r_p, const int32_t* d_sweep, int n_sweep,
                          bool fp32, bool accumulate, void* map_new, void* map_trad) {
-  int S = 1;
-  for (int e = 0; e < m->n_elem; ++e) {
-    int n = (m->h_ord[3 * e] + 1) * (m->h_ord[3 * e + 1] + 1) * (m->h_ord[3 * e + 2] + 1);
-    if (n > S) S = n;
-  }
   auto fill = [&](auto& P) {
     P.m = view(m);
     P.n_elem = m->n_elem;
@@ -1588,7 +1780,6 @@ cudaError_t tau_isolated(dg_mesh_impl* m, const double* q, const double* r_p, co
     P.sweep = d_sweep;
     P.n_sweep = n_sweep;
     P.accumulate = accumulate;
-    P.S = S;
     P.gamma = m->phys.gamma;
     P.mu = m->phys.mu;
     P.Pr = m->phys.Pr;
@@ -1604,7 +1795,8 @@ cudaError_t tau_isolated(dg_mesh_impl* m, const double* q, const double* r_p, co
     P.metric = m->affine ? m->d_metric32 : m->d_taugeo32;
     P.map_new = static_cast<float*>(map_new);
     P.map_trad = static_cast<float*>(map_trad);
-    return tau_launch(m, P, tau_smem_bytes(m, true));
+    P.rp_scratch = m->d_rp32;
+    return tau_launch(m, P, true);
   }
   TauParams<double> P;
   fill(P);
@@ -1612,7 +1804,8 @@ cudaError_t tau_isolated(dg_mesh_impl* m, const double* q, const double* r_p, co
   P.metric = m->affine ? m->d_metric : m->d_taugeo;
   P.map_new = static_cast<double*>(map_new);
   P.map_trad = static_cast<double*>(map_trad);
-  return tau_launch(m, P, tau_smem_bytes(m, false));
+  P.rp_scratch = m->d_rp;
+  return tau_launch(m, P, false);
 }
 
 cudaError_t tau_combine(dg_mesh_impl* m, dg_mesh_impl* c, const double* r_p, const double* r_c, int s, int n_sweep,
