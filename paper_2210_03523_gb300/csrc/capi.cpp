@@ -177,6 +177,13 @@ void destroy_impl(dg_mesh_impl* m) {
   if (!m) return;
   for (auto& c : m->tau_classes) cudaFree(c.d_list);
   m->tau_classes.clear();
+  for (auto& c : m->vol_classes) cudaFree(c.d_list);
+  m->vol_classes.clear();
+  for (auto* u : m->tau_units) if (u) cudaFree(u);
+  m->tau_units.clear();
+  if (m->d_tgroups) cudaFree(m->d_tgroups);
+  if (m->d_tgentries) cudaFree(m->d_tgentries);
+  m->d_tgroups = m->d_tgentries = nullptr;
   for (auto& pp : m->prof_pending) {
     cudaEventDestroy(pp.a);
     cudaEventDestroy(pp.b);
@@ -221,7 +228,7 @@ dg_status build(dg_mesh_impl* m) {
   m->n_nodes = m->h_off[ne];
   // geometry
   // metric record: fields 0..8 J a^i_d, 9 J, 10 1/J; affine: 16 doubles per
-  // element, curved: [11][n] per element
+  // element with 11..13 |J a^i|, curved: [11][n] per element
   std::vector<double> met;
   m->affine = (G == 1);
   if (m->affine) {
@@ -235,6 +242,8 @@ dg_status build(dg_mesh_impl* m) {
       double* r = &met[16 * (size_t)e];
       if (!(r[9] > 0.0)) return DG_ERR_ARG;
       r[10] = 1.0 / r[9];
+      for (int i = 0; i < 3; ++i)
+        r[11 + i] = std::sqrt(r[3 * i] * r[3 * i] + r[3 * i + 1] * r[3 * i + 1] + r[3 * i + 2] * r[3 * i + 2]);
       for (int i = 0; i < 3; ++i)
         for (int d = 0; d < 3; ++d)
           if (i != d && r[3 * i + d] != 0.0) m->axis = false;
@@ -335,6 +344,7 @@ dg_status build(dg_mesh_impl* m) {
     }
   }
   m->n_items = (int)items.size();
+  m->h_items = items;
   // device
   DG_CUDA(upload(&m->d_ord, m->h_ord.data(), m->h_ord.size()));
   DG_CUDA(upload(&m->d_nbr, m->h_nbr.data(), m->h_nbr.size()));
@@ -374,6 +384,23 @@ dg_status build(dg_mesh_impl* m) {
       dg_mesh_impl::TauClass c{nullptr, (int)cls[k].size(), cS[k]};
       DG_CUDA(upload(&c.d_list, cls[k].data(), cls[k].size()));
       m->tau_classes.push_back(c);
+    }
+    // volume kernels: tiles up to 400 nodes (<= 64 KB of FP64 shared memory,
+    // three CTAs per SM) in one launch, larger tiles in a second one
+    std::vector<int32_t> vs, vl;
+    int Ss = 0, Sl = 0;
+    for (int i = 0; i < (int)items.size(); ++i) {
+      const WorkItem& w = items[i];
+      const int tile = w.count * (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
+      if (tile <= 400) { vs.push_back(i); Ss = std::max(Ss, tile); }
+      else { vl.push_back(i); Sl = std::max(Sl, tile); }
+    }
+    for (int k = 0; k < 2; ++k) {
+      auto& v = k ? vl : vs;
+      if (v.empty()) continue;
+      dg_mesh_impl::TauClass c{nullptr, (int)v.size(), k ? Sl : Ss};
+      DG_CUDA(upload(&c.d_list, v.data(), v.size()));
+      m->vol_classes.push_back(c);
     }
   }
   DG_CUDA(upload<unsigned>(&m->d_err, nullptr, 1));
@@ -420,6 +447,53 @@ dg_status build_tau_bank(dg_mesh_impl* m) {
   DG_CUDA(upload(&m->d_taugeo, bank.data(), bank.size()));
   DG_CUDA(upload(&m->d_taugeo32, bank32.data(), bank32.size()));
   DG_CUDA(upload(&m->d_taugeo_off, off.data(), off.size()));
+  return DG_OK;
+}
+
+// Work units of the isolated sweep for the current sweep list: the entries
+// grouped by (N2, N3), and per shared-memory class the (item, group) pairs
+// whose group reaches at least one entry within the item's orders.
+dg_status build_tau_units(dg_mesh_impl* m) {
+  std::map<std::pair<int, int>, std::vector<int32_t>> grp;
+  const int ns = (int)m->h_sweep.size() / 3;
+  for (int s = 0; s < ns; ++s) {
+    auto& v = grp[{m->h_sweep[3 * s + 1], m->h_sweep[3 * s + 2]}];
+    v.push_back(s);
+    v.push_back(m->h_sweep[3 * s]);
+  }
+  std::vector<int32_t> groups, gentries;
+  std::vector<int> gmin1;    // smallest N1 of each group
+  for (auto& kv : grp) {
+    int mn = 1 << 30;
+    for (size_t i = 1; i < kv.second.size(); i += 2) mn = std::min(mn, kv.second[i]);
+    groups.insert(groups.end(), {kv.first.first, kv.first.second, (int32_t)(gentries.size() / 2),
+                                 (int32_t)(kv.second.size() / 2)});
+    gentries.insert(gentries.end(), kv.second.begin(), kv.second.end());
+    gmin1.push_back(mn);
+  }
+  for (auto* u : m->tau_units) if (u) cudaFree(u);
+  m->tau_units.assign(m->tau_classes.size(), nullptr);
+  m->tau_n_units.assign(m->tau_classes.size(), 0);
+  if (m->d_tgroups) cudaFree(m->d_tgroups);
+  if (m->d_tgentries) cudaFree(m->d_tgentries);
+  m->d_tgroups = m->d_tgentries = nullptr;
+  DG_CUDA(upload(&m->d_tgroups, groups.data(), groups.size()));
+  DG_CUDA(upload(&m->d_tgentries, gentries.data(), gentries.size()));
+  for (size_t k = 0; k < m->tau_classes.size(); ++k) {
+    std::vector<int32_t> ilist(m->tau_classes[k].n);
+    DG_CUDA(cudaMemcpy(ilist.data(), m->tau_classes[k].d_list, sizeof(int32_t) * ilist.size(), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> units;
+    for (int it : ilist) {
+      const WorkItem& w = m->h_items[it];
+      for (size_t g = 0; g < groups.size() / 4; ++g)
+        if (groups[4 * g] <= w.n2 && groups[4 * g + 1] <= w.n3 && gmin1[g] <= w.n1) {
+          units.push_back(it);
+          units.push_back((int32_t)g);
+        }
+    }
+    m->tau_n_units[k] = (int)units.size() / 2;
+    DG_CUDA(upload(&m->tau_units[k], units.data(), units.size()));
+  }
   return DG_OK;
 }
 
@@ -668,6 +742,8 @@ dg_status dg_tau_estimate(dg_mesh* m, const double* q, const double* r_p, const 
       m->d_sweep = nullptr;
       DG_CUDA(upload(&m->d_sweep, hs.data(), hs.size()));
       m->h_sweep = hs;
+      dg_status st2 = build_tau_units(m);
+      if (st2 != DG_OK) return st2;
     }
     return from_cuda(dgk::tau_isolated(m, q, r_p, m->d_sweep, n_sweep, fp32, acc, map_new, map_trad));
   }

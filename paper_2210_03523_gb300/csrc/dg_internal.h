@@ -143,6 +143,14 @@ struct dg_mesh_impl {
   float* d_rp32 = nullptr;             // tau: isolated R^P scratch of the FP32 sweep
   struct TauClass { int32_t* d_list; int n; int S; };
   std::vector<TauClass> tau_classes;   // work items grouped by tile size (shared-memory size class)
+  std::vector<TauClass> vol_classes;   // the same items split in two for the volume kernels (<= 400 nodes, larger)
+  // isolated sweep units for the last sweep: (item, group) per class, groups of
+  // entries sharing (N2, N3) [N2, N3, first, count], entries [sweep index, N1]
+  std::vector<int32_t*> tau_units;
+  std::vector<int> tau_n_units;
+  int32_t* d_tgroups = nullptr;
+  int32_t* d_tgentries = nullptr;
+  std::vector<WorkItem> h_items;
   double* d_qc = nullptr;              // coarse mesh: restricted state scratch
   double* d_rc = nullptr;              // coarse mesh: coarse residual scratch
   int32_t* d_sweep = nullptr;          // device copy of the last sweep

@@ -61,9 +61,9 @@ template <typename T>
 __device__ __forceinline__ const T* btab(const T* base, int off) { return base + off; }
 
 // Metric record: field m of element e at node p.  Fields 0..8: J a^i_d
-// (index 3i+d); 9: J; 10: 1/J.  Affine meshes: one record of kAffStride
-// doubles per element; curved meshes: [kCurvedFields][n] per element at
-// kCurvedFields * off_e.
+// (index 3i+d); 9: J; 10: 1/J; affine records also 11..13: |J a^i|.
+// Affine meshes: one record of kAffStride doubles per element; curved
+// meshes: [kCurvedFields][n] per element at kCurvedFields * off_e.
 constexpr int kAffStride = 16;
 constexpr int kCurvedFields = 11;
 
@@ -612,7 +612,8 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_qhat_kernel(FaceParams P
 struct VolParams {
   MeshView m;
   const WorkItem* items;
-  int n_items;
+  int n_items;              // number of work items to run (entries of ilist, or all items)
+  const int32_t* ilist;     // items of this launch (one shared-memory size class), or null for all
   const int32_t* elist;
   const double* q;
   const double* grad;
@@ -671,7 +672,7 @@ __global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
   const MeshView& m = P.m;
   const double gm1 = m.ph.gamma - 1.0;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[it];
+    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
     const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
     const int slots = w.count * n;
     double* Ft = smem;                                // [count][3][5][n]
@@ -792,7 +793,7 @@ __global__ void __launch_bounds__(kVolThreads) gradient_kernel(VolParams P) {
   extern __shared__ double smem[];
   const MeshView& m = P.m;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[it];
+    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
     const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
     const int slots = w.count * n;
     const double* D1 = P.basis + c_boff.D[w.n1];
@@ -843,46 +844,60 @@ __global__ void __launch_bounds__(kVolThreads) gradient_kernel(VolParams P) {
 }
 
 // ----------------------------------------------------------------- CFL step
-template <bool AFFINE>
+// CFL inverse time scale per node, max-reduced over the mesh:
+//   s = max(s_a, s_v),  s_a = 1/(2J) sum_i (N_i+1)^2 (|J a^i . v| + c |J a^i|),
+//   s_v = 1/(4J^2) sum_i (N_i+1)^4 |J a^i|^2 max(1, gamma/Pr) mu/rho  (NS).
+// Affine meshes read 1/J and |J a^i| from the element record (fields 10 and
+// 11..13); AXIS meshes use |J a^i . v| = J a^i_i |v_i|.
+template <bool AFFINE, bool AXIS>
 __global__ void __launch_bounds__(kVolThreads) dt_kernel(VolParams P, unsigned long long* smax_bits) {
   __shared__ double red[kVolThreads / 32];
   const MeshView& m = P.m;
   const double gm1 = m.ph.gamma - 1.0;
+  const bool ns = m.ph.eqs == DG_NAVIER_STOKES;
+  const double g_pr = m.ph.gamma / m.ph.Pr;
   double smax = 0.0;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[it];
-    const int nn[3] = {w.n1 + 1, w.n2 + 1, w.n3 + 1};
-    const int n = nn[0] * nn[1] * nn[2];
+    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    const double k2[3] = {(double)(w.n1 + 1) * (w.n1 + 1), (double)(w.n2 + 1) * (w.n2 + 1),
+                          (double)(w.n3 + 1) * (w.n3 + 1)};
+    const int n = (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
     for (int s = threadIdx.x; s < w.count * n; s += blockDim.x) {
       const int el = s / n, p = s - el * n;
       const int e = P.elist[w.first + el];
       const int64_t o = m.off[e];
       double q[5];
       for (int v = 0; v < 5; ++v) q[v] = P.q[5 * o + v * n + p];
-      Prim st = primitive(gm1, q);
-      double c = sqrt(m.ph.gamma * st.p * st.ir);
-      double J = metric<AFFINE>(m.metric, e, o, n, p, 9);
+      const double ir = 1.0 / q[0];
+      const double u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+      const double pr = gm1 * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+      const double c = sqrt(m.ph.gamma * pr * ir);
+      const double iJ = metric<AFFINE>(m.metric, e, o, n, p, 10);
       double sa = 0.0, sv = 0.0;
       for (int i = 0; i < 3; ++i) {
-        double ja[3];
-        for (int d = 0; d < 3; ++d) ja[d] = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + d);
-        double a2 = ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2];
-        double un = fabs(ja[0] * st.u[0] + ja[1] * st.u[1] + ja[2] * st.u[2]);
-        double k2 = (double)nn[i] * nn[i];
-        sa += k2 * (un + c * sqrt(a2)) / (2.0 * J);
-        sv += k2 * k2 * a2 / (4.0 * J * J);
+        double un, a;
+        if (AXIS) {
+          a = metric<true>(m.metric, e, 0, n, p, 4 * i);
+          un = a * fabs(u[i]);
+        } else {
+          double ja[3];
+          for (int d = 0; d < 3; ++d) ja[d] = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + d);
+          un = fabs(ja[0] * u[0] + ja[1] * u[1] + ja[2] * u[2]);
+          a = AFFINE ? metric<true>(m.metric, e, 0, n, p, 11 + i) : sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+        }
+        sa += k2[i] * (un + c * a);
+        sv += k2[i] * k2[i] * a * a;
       }
-      double sm = sa;
-      if (m.ph.eqs == DG_NAVIER_STOKES) {
-        double g_pr = m.ph.gamma / m.ph.Pr;
-        double nu = m.ph.mu * st.ir * (g_pr > 1.0 ? g_pr : 1.0);
-        if (sv * nu > sm) sm = sv * nu;
+      double sm = 0.5 * iJ * sa;
+      if (ns) {
+        const double nu = m.ph.mu * ir * (g_pr > 1.0 ? g_pr : 1.0);
+        sm = fmax(sm, 0.25 * iJ * iJ * sv * nu);
       }
       if (!(sm <= DBL_MAX)) atomicOr(P.err, 1u);
       smax = fmax(smax, sm);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  for (int off = 16; off > 0; off >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, off));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -919,7 +934,10 @@ struct TauParams {
   int S;                    // shared-memory buffer stride (max n_P of the size class)
   const WorkItem* items;    // tiles of same-order elements (the volume work items)
   const int32_t* elist;     // their element list
-  const int32_t* ilist;     // items of this launch (one shared-memory size class)
+  const int32_t* ilist;     // prologue: items of this launch (one shared-memory size class)
+  const int2* units;        // sweep: (item, group) units of this launch
+  const int4* groups;       // sweep entries grouped by (N2, N3): N2, N3, first, count
+  const int2* gentries;     // group entries: sweep index, N1
   int n_list;
   T* rp_scratch;            // isolated R^P at P, state layout, when rp is null
   T gamma, mu, Pr, Rgas, kappa;
@@ -1250,9 +1268,47 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
   __syncthreads();
 }
 
-// Isolated tau sweep over tiles of same-order elements (the volume work
-// items), one tile per CTA iteration: every phase runs over all points of
-// all elements of the tile, so small coarse orders still fill the lanes.
+// Prologue of the isolated sweep, one tile per CTA iteration: the isolated
+// R^P of every element (into the scratch, unless the caller gave R^P), and
+// -1 in the maps for every sweep entry the element's orders cannot reach.
+template <typename T, bool AFFINE, bool NS>
+__global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int S = P.S;
+  T* A1 = sm + 20 * S;
+  T* Ft = A1 + 10 * S;
+  T* Gs = Ft + 15 * S;
+  const MeshView& m = P.m;
+  for (int li = blockIdx.x; li < P.n_list; li += gridDim.x) {
+    const WorkItem w = P.items[P.ilist[li]];
+    const int32_t* els = P.elist + w.first;
+    const int cnt = w.count;
+    const int P1 = w.n1, P2 = w.n2, P3 = w.n3, nP = (P1 + 1) * (P2 + 1) * (P3 + 1);
+    for (int t = threadIdx.x; t < cnt * P.n_sweep; t += blockDim.x) {
+      const int el = t / P.n_sweep, s = t - el * P.n_sweep;
+      if (P.sweep[3 * s] > P1 || P.sweep[3 * s + 1] > P2 || P.sweep[3 * s + 2] > P3) {
+        const int64_t idx = (int64_t)els[el] * P.n_sweep + s;
+        if (P.map_new) P.map_new[idx] = (T)-1;
+        if (P.map_trad) P.map_trad[idx] = (T)-1;
+      }
+    }
+    if (P.rp) continue;
+    for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
+      const int el = t / nP, p = t - el * nP;
+      const int64_t o = m.off[els[el]];
+      for (int v = 0; v < 5; ++v) A1[el * 10 * nP + v * nP + p] = (T)P.q[5 * o + v * nP + p];
+    }
+    __syncthreads();
+    tau_tile_residual<T, AFFINE, NS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, Ft, Gs, P.rp_scratch, nullptr,
+                                     nullptr);
+  }
+}
+
+// The sweep proper, one (tile, group) unit per CTA iteration; a group is the
+// sweep entries sharing (N2, N3).  The unit restricts q^P and R^P in xi3 and
+// xi2 once, then runs every entry of the group: restriction in xi1, coarse
+// isolated residual fused with both tau norms, map store.
 template <typename T, bool AFFINE, bool NS>
 __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1266,74 +1322,57 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   T* Ft = A1 + 10 * S;   // [el][15][nN]
   T* Gs = Ft + 15 * S;   // [el][15][nN]    (NS only: the Euler launch allocates 45 S)
   const MeshView& m = P.m;
-  for (int li = blockIdx.x; li < P.n_list; li += gridDim.x) {
-    const WorkItem w = P.items[P.ilist[li]];
+  for (int ui = blockIdx.x; ui < P.n_list; ui += gridDim.x) {
+    const int2 u = P.units[ui];
+    const WorkItem w = P.items[u.x];
+    const int4 g = P.groups[u.y];      // N2, N3, first entry, entry count
     const int32_t* els = P.elist + w.first;
     const int cnt = w.count;
     const int P1 = w.n1, P2 = w.n2, P3 = w.n3, n1 = P1 + 1, n2 = P2 + 1, n3 = P3 + 1, nP = n1 * n2 * n3;
-    T* rpS = P.rp_scratch;
-    if (!P.rp) {  // isolated R^P, once per element, into the scratch
-      for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
-        const int el = t / nP, p = t - el * nP;
+    const int N2 = g.x, N3 = g.y, c2 = N2 + 1, c3 = N3 + 1, n12 = n1 * n2;
+    const T* rpS = P.rp_scratch;
+    {  // xi3 straight from q^P and R^P in global memory
+      const T* I3 = P.basis + c_boff.I[P3][N3];
+      const int per = n12 * c3;
+      for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
+        const int el = t / per, x = t - el * per, ij = x % n12, k = x / n12;
         const int64_t o = m.off[els[el]];
-        for (int v = 0; v < 5; ++v) A1[el * 10 * nP + v * nP + p] = (T)P.q[5 * o + v * nP + p];
+        T acc[10];
+        for (int c = 0; c < 10; ++c) acc[c] = 0;
+        for (int mm = 0; mm < n3; ++mm) {
+          const T wk = I3[k * n3 + mm];
+          const int src = ij + n12 * mm;
+          for (int v = 0; v < 5; ++v) acc[v] += wk * (T)P.q[5 * o + v * nP + src];
+          if (P.rp)
+            for (int v = 0; v < 5; ++v) acc[5 + v] += wk * (T)P.rp[5 * o + v * nP + src];
+          else
+            for (int v = 0; v < 5; ++v) acc[5 + v] += wk * rpS[5 * o + v * nP + src];
+        }
+        for (int c = 0; c < 10; ++c) A3[el * 10 * per + c * per + x] = acc[c];
       }
       __syncthreads();
-      tau_tile_residual<T, AFFINE, NS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, Ft, Gs, rpS, nullptr, nullptr);
     }
-    int cur3 = -1, cur2 = -1;
-    for (int s = 0; s < P.n_sweep; ++s) {
-      const int N1 = P.sweep[3 * s], N2 = P.sweep[3 * s + 1], N3 = P.sweep[3 * s + 2];
-      if (N1 > P1 || N2 > P2 || N3 > P3) {
-        for (int el = threadIdx.x; el < cnt; el += blockDim.x) {
-          const int64_t idx = (int64_t)els[el] * P.n_sweep + s;
-          if (P.map_new) P.map_new[idx] = (T)-1;
-          if (P.map_trad) P.map_trad[idx] = (T)-1;
+    {  // xi2
+      const T* I2 = P.basis + c_boff.I[P2][N2];
+      const int pin = n12 * c3, per = n1 * c2 * c3;
+      for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
+        const int el = t / per, x = t - el * per, i = x % n1, j = (x / n1) % c2, k = x / (n1 * c2);
+        const T* src = A3 + el * 10 * pin + i + n12 * k;
+        T acc[10];
+        for (int c = 0; c < 10; ++c) acc[c] = 0;
+        for (int mm = 0; mm < n2; ++mm) {
+          const T wj = I2[j * n2 + mm];
+          for (int c = 0; c < 10; ++c) acc[c] += wj * src[c * pin + n1 * mm];
         }
-        continue;
+        for (int c = 0; c < 10; ++c) A2[el * 10 * per + c * per + x] = acc[c];
       }
-      const int c1 = N1 + 1, c2 = N2 + 1, c3 = N3 + 1, nN = c1 * c2 * c3;
-      const int n12 = n1 * n2;
-      if (N3 != cur3) {  // xi3 straight from q^P and R^P in global memory
-        const T* I3 = P.basis + c_boff.I[P3][N3];
-        const int per = n12 * c3;
-        for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
-          const int el = t / per, x = t - el * per, ij = x % n12, k = x / n12;
-          const int64_t o = m.off[els[el]];
-          T acc[10];
-          for (int c = 0; c < 10; ++c) acc[c] = 0;
-          for (int mm = 0; mm < n3; ++mm) {
-            const T wk = I3[k * n3 + mm];
-            const int src = ij + n12 * mm;
-            for (int v = 0; v < 5; ++v) acc[v] += wk * (T)P.q[5 * o + v * nP + src];
-            if (P.rp)
-              for (int v = 0; v < 5; ++v) acc[5 + v] += wk * (T)P.rp[5 * o + v * nP + src];
-            else
-              for (int v = 0; v < 5; ++v) acc[5 + v] += wk * rpS[5 * o + v * nP + src];
-          }
-          for (int c = 0; c < 10; ++c) A3[el * 10 * per + c * per + x] = acc[c];
-        }
-        __syncthreads();
-        cur3 = N3;
-        cur2 = -1;
-      }
-      if (N2 != cur2) {  // xi2
-        const T* I2 = P.basis + c_boff.I[P2][N2];
-        const int pin = n12 * c3, per = n1 * c2 * c3;
-        for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
-          const int el = t / per, x = t - el * per, i = x % n1, j = (x / n1) % c2, k = x / (n1 * c2);
-          const T* src = A3 + el * 10 * pin + i + n12 * k;
-          T acc[10];
-          for (int c = 0; c < 10; ++c) acc[c] = 0;
-          for (int mm = 0; mm < n2; ++mm) {
-            const T wj = I2[j * n2 + mm];
-            for (int c = 0; c < 10; ++c) acc[c] += wj * src[c * pin + n1 * mm];
-          }
-          for (int c = 0; c < 10; ++c) A2[el * 10 * per + c * per + x] = acc[c];
-        }
-        __syncthreads();
-        cur2 = N2;
-      }
+      __syncthreads();
+    }
+    for (int ge = 0; ge < g.w; ++ge) {
+      const int2 ent = P.gentries[g.z + ge];   // sweep index, N1
+      const int s = ent.x, N1 = ent.y;
+      if (N1 > P1) continue;
+      const int c1 = N1 + 1, nN = c1 * c2 * c3;
       {  // xi1
         const T* I1 = P.basis + c_boff.I[P1][N1];
         const int pin = n1 * c2 * c3;
@@ -1561,7 +1600,7 @@ cudaError_t launch_volume(dg_mesh_impl* m, const VolParams& P, size_t smem, int 
   return cudaGetLastError();
 }
 
-cudaError_t dispatch_volume(dg_mesh_impl* m, const VolParams& P, size_t smem, int grid) {
+cudaError_t dispatch_volume_one(dg_mesh_impl* m, const VolParams& P, size_t smem, int grid) {
   const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
   if (m->axis)
     return ns ? launch_volume<true, true, true>(m, P, smem, grid) : launch_volume<true, true, false>(m, P, smem, grid);
@@ -1606,6 +1645,21 @@ cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* gra
 size_t mortar_smem_doubles(int count, int la, int lb, int ra, int rb) {
   MortarBatch B{0, count, la, lb, ra, rb};
   return mortar_batch_smem(B);
+}
+
+// The volume kernel once per volume class (tiles up to kVolSplitNodes nodes,
+// and the larger ones), each launch with the shared memory of its largest
+// tile (20 doubles per node), so that a few large elements do not lower the
+// occupancy of all the others.
+cudaError_t dispatch_volume(dg_mesh_impl* m, const VolParams& P0, size_t, int) {
+  cudaError_t err;
+  for (auto& c : m->vol_classes) {
+    VolParams P = P0;
+    P.ilist = c.d_list;
+    P.n_items = c.n;
+    if ((err = dispatch_volume_one(m, P, sizeof(double) * 20 * c.S, grid_for(c.n, 8)))) return err;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -1681,18 +1735,23 @@ cudaError_t gradient(dg_mesh_impl* m, const double* q, double* grad, bool isolat
   VolParams P = vol_params(m, q);
   P.out = grad;
   P.isolated = isolated;
-  size_t smem = sizeof(double) * 15 * m->item_max_nodes;
-  int grid = grid_for(m->n_items, 8);
   cudaError_t err;
-  Prof pr(m, DG_KERNEL_GRADIENT);
-  if (m->affine) {
-    if ((err = allow_smem(gradient_kernel<true>, smem))) return err;
-    gradient_kernel<true><<<grid, kVolThreads, smem, m->stream>>>(P);
-  } else {
-    if ((err = allow_smem(gradient_kernel<false>, smem))) return err;
-    gradient_kernel<false><<<grid, kVolThreads, smem, m->stream>>>(P);
+  Prof pr(m, DG_KERNEL_GRADIENT, (int)m->vol_classes.size());
+  for (auto& c : m->vol_classes) {   // one launch per tile-size class (15 doubles per node)
+    P.ilist = c.d_list;
+    P.n_items = c.n;
+    const size_t smem = sizeof(double) * 15 * c.S;
+    const int grid = grid_for(c.n, 8);
+    if (m->affine) {
+      if ((err = allow_smem(gradient_kernel<true>, smem))) return err;
+      gradient_kernel<true><<<grid, kVolThreads, smem, m->stream>>>(P);
+    } else {
+      if ((err = allow_smem(gradient_kernel<false>, smem))) return err;
+      gradient_kernel<false><<<grid, kVolThreads, smem, m->stream>>>(P);
+    }
+    if ((err = cudaGetLastError())) return err;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double* r, bool isolated, int rk_stage,
@@ -1712,10 +1771,8 @@ cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double*
     P.g_io = g_io;
     P.dt = dt_dev;
   }
-  size_t smem = sizeof(double) * 20 * m->item_max_nodes;
-  int grid = grid_for(m->n_items, 8);
-  Prof pr(m, DG_KERNEL_VOLUME);
-  return dispatch_volume(m, P, smem, grid);
+  Prof pr(m, DG_KERNEL_VOLUME, (int)m->vol_classes.size());
+  return dispatch_volume(m, P, 0, 0);
 }
 
 cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev) {
@@ -1725,8 +1782,9 @@ cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev)
   if (err) return err;
   int grid = grid_for(m->n_items, 8);
   Prof pr(m, DG_KERNEL_MAX_DT, 2);
-  if (m->affine) dt_kernel<true><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
-  else dt_kernel<false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
+  if (m->axis) dt_kernel<true, true><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
+  else if (m->affine) dt_kernel<true, false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
+  else dt_kernel<false, false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
   dt_finalize<<<1, 1, 0, m->stream>>>(bits, cfl, dt_dev);
   return cudaGetLastError();
 }
@@ -1748,24 +1806,37 @@ template <typename T>
 static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
   const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
   cudaError_t err;
-  Prof pr(m, DG_KERNEL_TAU, (int)m->tau_classes.size());
+  Prof pr(m, DG_KERNEL_TAU, 2 * (int)m->tau_classes.size());
   P.items = m->d_items;
   P.elist = m->d_elist;
-  for (auto& c : m->tau_classes) {
-    P.ilist = c.d_list;
-    P.n_list = c.n;
-    P.S = c.S;
-    const size_t smem = tau_smem_for(c.S, ns, fp32);
-    const int grid = grid_for(c.n, 16);
-#define DG_TAU_CASE(AFF, NSV)                                                   \
-  if ((err = allow_smem(tau_kernel<T, AFF, NSV>, smem))) return err;             \
-  tau_kernel<T, AFF, NSV><<<grid, kVolThreads, smem, m->stream>>>(P);
-    if (m->affine && !ns) { DG_TAU_CASE(true, false) }
-    else if (m->affine) { DG_TAU_CASE(true, true) }
-    else if (!ns) { DG_TAU_CASE(false, false) }
-    else { DG_TAU_CASE(false, true) }
+  P.groups = reinterpret_cast<const int4*>(m->d_tgroups);
+  P.gentries = reinterpret_cast<const int2*>(m->d_tgentries);
+  // prologue over every class first, then the sweep units of every class
+  for (int phase = 0; phase < 2; ++phase) {
+    for (size_t k = 0; k < m->tau_classes.size(); ++k) {
+      const auto& c = m->tau_classes[k];
+      P.S = c.S;
+      P.ilist = c.d_list;
+      P.units = reinterpret_cast<const int2*>(m->tau_units[k]);
+      P.n_list = phase == 0 ? c.n : m->tau_n_units[k];
+      if (P.n_list == 0) continue;
+      const size_t smem = tau_smem_for(c.S, ns, fp32);
+      const int grid = grid_for(P.n_list, 16);
+#define DG_TAU_CASE(AFF, NSV)                                                                  \
+  if (phase == 0) {                                                                             \
+    if ((err = allow_smem(tau_prologue_kernel<T, AFF, NSV>, smem))) return err;                 \
+    tau_prologue_kernel<T, AFF, NSV><<<grid, kVolThreads, smem, m->stream>>>(P);                \
+  } else {                                                                                      \
+    if ((err = allow_smem(tau_kernel<T, AFF, NSV>, smem))) return err;                          \
+    tau_kernel<T, AFF, NSV><<<grid, kVolThreads, smem, m->stream>>>(P);                         \
+  }
+      if (m->affine && !ns) { DG_TAU_CASE(true, false) }
+      else if (m->affine) { DG_TAU_CASE(true, true) }
+      else if (!ns) { DG_TAU_CASE(false, false) }
+      else { DG_TAU_CASE(false, true) }
 #undef DG_TAU_CASE
-    if ((err = cudaGetLastError())) return err;
+      if ((err = cudaGetLastError())) return err;
+    }
   }
   return cudaSuccess;
 }
@@ -1897,9 +1968,9 @@ extern "C" dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double*
   // reads it, so nothing needs clearing between calls
   if (launch_all_faces(mesh, q, nullptr, surf) != cudaSuccess) return DG_ERR_CUDA;
   VolParams V = dgk_vol_params_for(mesh, q, surf, r);
-  size_t vsmem = sizeof(double) * 20 * mesh->item_max_nodes;
-  int vgrid = grid_for(mesh->n_items, 8);
+  size_t vsmem = 0;
+  int vgrid = 0;
   if (dispatch_volume(mesh, V, vsmem, vgrid) != cudaSuccess) return DG_ERR_CUDA;
-  mesh->launches += 1 + (mesh->n_faces ? 1 : 0) + (mesh->n_mbatches ? 1 : 0);
+  mesh->launches += (int64_t)mesh->vol_classes.size() + (mesh->n_faces ? 1 : 0) + (mesh->n_mbatches ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
 }
