@@ -1518,11 +1518,13 @@ int grid_for(int work, int per_sm_blocks) {
 }
 
 // Raise a kernel's dynamic shared-memory limit to the device opt-in maximum
-// once (so that no attribute call is needed later, e.g. under stream capture).
+// minus its static shared memory, once per kernel and device (so that no
+// attribute call is needed later, e.g. under stream capture).  Done for any
+// dynamic size: the default limit of 48 KB covers static + dynamic.
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
   static std::map<std::pair<int, const void*>, int> raised;   // (device, kernel) -> limit set
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes == 0) return cudaSuccess;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
