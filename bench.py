@@ -312,6 +312,12 @@ def run_gb300(args, rank, world):
     h2d = q.numel() * 8
     d2h = q.numel() * 8 + 2 * map_new.numel() * 4
 
+    # static p-adaptation selection on the accumulated map (Sec. 2.4, approach 2,
+    # jump condition (b)); timed once, outside the step
+    t0 = time.perf_counter()
+    sel = m.select_orders(map_new, sweep, 1.0, 1, 8, 2)
+    select_ms = (time.perf_counter() - t0) * 1e3
+
     # roofline of the dominant kernel (the volume residual + fused RK stage)
     vol_ms, vol_n = kern["volume"]
     vflops, vbytes = volume_counts(mi.orders, rk=True)
@@ -355,6 +361,8 @@ def run_gb300(args, rank, world):
                          "frac": (tflops / (tau_k_ms / tau_k_n * 1e-3) / 1e12 / fp32_peak) if tau_k_n else None,
                          "peak_source": f"FP32: {N_SM} SMs x {FP32_FMA_PER_CLK_PER_SM} FFMA/clk x 2 x {sm_mhz:.0f} MHz"},
         "kernels": kernels_json,
+        "select_orders": {"ms": select_ms, "tau_max": 1.0, "jump_rule": "N_i >= N_j - 1",
+                          "mean_order_after": float(np.mean(sel)), "synchronous_host_call": True},
         "e2e": {"value": job_value(world, ndof, res_per_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),

@@ -193,6 +193,23 @@ dg_status dg_tau_estimate(dg_mesh* mesh, const double* q, const double* r_p, con
  * The mesh is rebuilt for the new orders (synchronous). */
 dg_status dg_set_orders(dg_mesh* mesh, const int32_t* new_orders, const double* q_old, double* q_new);
 
+/* Static p-adaptation, order selection (Sec. 2.4, approach 2; with the
+ * degree-jump conditions of Sec. 3.1, Eqs. N23 and N_1).  From a total
+ * truncation-error map (a dg_tau_estimate map, usually F_max-accumulated
+ * over the estimation stages), for every element: the sweep entry N with
+ * 0 <= map < tau_max and n_min <= N_i <= n_max of fewest degrees of freedom
+ * prod_i (N_i+1), the first in sweep order on ties; n_max in every
+ * direction when no entry qualifies (entries above the element's own orders
+ * are -1 and never qualify).  Then the jump condition, as the least orders
+ * at or above the selection that satisfy it: jump_rule 1: N_i^e >=
+ * floor(2 N_i^j / 3); 2: N_i^e >= N_i^j - 1 for every face neighbour j;
+ * 0: none.  map: device [n_elem][n_sweep], float if map_fp32 else double;
+ * sweep: host, the list the map was built with; orders_out: host
+ * [n_elem][3], ready for dg_set_orders.  Synchronous.
+ * Errors: DG_ERR_ARG (null pointers, tau_max <= 0, bad bounds or rule). */
+dg_status dg_select_orders(dg_mesh* mesh, const void* map, int32_t map_fp32, const int32_t* sweep, int32_t n_sweep,
+                           double tau_max, int32_t n_min, int32_t n_max, int32_t jump_rule, int32_t* orders_out);
+
 /* Kernel kinds for dg_profile_read. */
 enum {
   DG_KERNEL_FACE_FLUX = 0,   /* Roe (+ BR1 viscous) numerical flux per face, mortars */
@@ -203,7 +220,8 @@ enum {
   DG_KERNEL_TAU = 5,         /* isolated tau sweep */
   DG_KERNEL_TAU_COMBINE = 6, /* non-isolated tau, per sweep entry */
   DG_KERNEL_PROJECT = 7,     /* order projection / restriction */
-  DG_KERNEL_KINDS = 8
+  DG_KERNEL_SELECT = 8,      /* order selection and degree-jump sweeps */
+  DG_KERNEL_KINDS = 9
 };
 
 /* Per-kernel timing with CUDA events recorded on the mesh stream around

@@ -65,6 +65,7 @@ def lib():
         L.orc_euler_flux.argtypes = [C.c_double, dp, C.c_int, dp]
         L.orc_visc_flux.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp, C.c_int, dp]
         L.orc_rk_coeffs.argtypes = [dp, dp]
+        L.orc_select_orders.argtypes = [C.c_int, C.c_int, ip, dp, C.c_double, C.c_int, C.c_int, C.c_int, ip, ip]
         _lib = L
     return _lib
 
@@ -229,3 +230,16 @@ class Mesh:
         """view of element e in a state-layout array: [nvar, n_e]"""
         n = self.off[e + 1] - self.off[e]
         return a[nvar * self.off[e]: nvar * self.off[e + 1]].reshape(nvar, n)
+
+
+def select_orders(map_, sweep, tau_max, n_min, n_max, jump_rule, neighbors):
+    """Static p-adaptation selection (approach 2) and jump rule: 0 none,
+    1 floor(2N/3) (Eq. N23), 2 N-1 (Eq. N_1).  map_: [n_elem, n_sweep]."""
+    m = _f64(map_)
+    n_elem, ns = m.shape
+    sw = _i32(sweep).reshape(-1, 3)
+    nb = _i32(neighbors).reshape(-1, 6)
+    out = np.empty((n_elem, 3), dtype=np.int32)
+    lib().orc_select_orders(n_elem, ns, _i(sw), _d(m), float(tau_max), int(n_min), int(n_max), int(jump_rule),
+                            _i(nb), _i(out))
+    return out

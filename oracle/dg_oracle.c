@@ -1150,3 +1150,55 @@ void orc_set_orders(void* h, const int* new_ord, const double* q_old, double* q_
     for (int d = 0; d < 3; ++d) free(mats[d]);
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* 10. Static p-adaptation: order selection from the total truncation-error */
+/*     map (Sec. 2.4, approach 2) and the degree-jump conditions (Sec. 3.1)  */
+/* ------------------------------------------------------------------------ */
+
+/* For every element: among the sweep entries N with 0 <= map[e][s] < tau_max
+ * and n_min <= N_i <= n_max, the one with the fewest degrees of freedom
+ * NDOF = prod_i (N_i + 1) (Table 1); the first such entry in sweep order on
+ * ties.  With no such entry the element gets n_max in every direction (the
+ * secure choice when the error is not known to be below tau_max).
+ * Then the jump condition is enforced as the least fixed point above the
+ * selection: rule 1 (Eq. N23) N_i^e >= max_j floor(2 N_i^j / 3), rule 2
+ * (Eq. N_1) N_i^e >= max_j (N_i^j - 1), over the face neighbours j of e
+ * (aligned axes: direction i of the neighbour is direction i of e), rule 0:
+ * none.  Orders are raised by Jacobi sweeps until nothing changes. */
+void orc_select_orders(int n_elem, int n_sweep, const int* sweep, const double* map, double tau_max, int n_min,
+                       int n_max, int jump_rule, const int* nbr, int* out) {
+  for (int e = 0; e < n_elem; ++e) {
+    long best = -1;
+    int bs = -1;
+    for (int s = 0; s < n_sweep; ++s) {
+      const double v = map[(long)e * n_sweep + s];
+      const int* N = sweep + 3 * s;
+      int ok = v >= 0.0 && v < tau_max;
+      for (int d = 0; d < 3; ++d) ok = ok && N[d] >= n_min && N[d] <= n_max;
+      if (!ok) continue;
+      long nd = (long)(N[0] + 1) * (N[1] + 1) * (N[2] + 1);
+      if (best < 0 || nd < best) { best = nd; bs = s; }
+    }
+    for (int d = 0; d < 3; ++d) out[3 * e + d] = bs >= 0 ? sweep[3 * bs + d] : n_max;
+  }
+  if (jump_rule == 0) return;
+  int* tmp = malloc(sizeof(int) * 3 * n_elem);
+  for (int changed = 1; changed;) {
+    changed = 0;
+    memcpy(tmp, out, sizeof(int) * 3 * n_elem);
+    for (int e = 0; e < n_elem; ++e)
+      for (int d = 0; d < 3; ++d) {
+        int need = tmp[3 * e + d];
+        for (int f = 0; f < 6; ++f) {
+          int j = nbr[6 * e + f];
+          if (j < 0) continue;
+          int nj = tmp[3 * j + d];
+          int lim = jump_rule == 1 ? (2 * nj) / 3 : nj - 1;
+          if (lim > need) need = lim;
+        }
+        if (need > out[3 * e + d]) { out[3 * e + d] = need; changed = 1; }
+      }
+  }
+  free(tmp);
+}

@@ -1976,3 +1976,115 @@ extern "C" dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double*
   mesh->launches += (int64_t)mesh->vol_classes.size() + (mesh->n_faces ? 1 : 0) + (mesh->n_mbatches ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Static p-adaptation (Sec. 2.4, approach 2): order selection from a total
+// truncation-error map and the degree-jump conditions of Sec. 3.1.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Per element: the sweep entry with 0 <= map < tau_max and n_min <= N_i <=
+// n_max of fewest degrees of freedom prod_i (N_i+1), the first in sweep
+// order on ties; n_max in every direction when none qualifies.
+template <typename T>
+__global__ void select_kernel(const T* map, const int32_t* sweep, int n_sweep, int n_elem, double tau_max, int n_min,
+                              int n_max, int32_t* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_elem) return;
+  long long best = -1;
+  int bs = -1;
+  const T* row = map + (int64_t)e * n_sweep;
+  for (int s = 0; s < n_sweep; ++s) {
+    const double v = (double)row[s];
+    const int N0 = sweep[3 * s], N1 = sweep[3 * s + 1], N2 = sweep[3 * s + 2];
+    if (!(v >= 0.0 && v < tau_max)) continue;
+    if (N0 < n_min || N1 < n_min || N2 < n_min || N0 > n_max || N1 > n_max || N2 > n_max) continue;
+    const long long nd = (long long)(N0 + 1) * (N1 + 1) * (N2 + 1);
+    if (best < 0 || nd < best) {
+      best = nd;
+      bs = s;
+    }
+  }
+  for (int d = 0; d < 3; ++d) out[3 * e + d] = bs >= 0 ? sweep[3 * bs + d] : n_max;
+}
+
+// One Jacobi sweep of the jump condition: rule 1 (Eq. N23) N_i^e >=
+// floor(2 N_i^j / 3), rule 2 (Eq. N_1) N_i^e >= N_i^j - 1 over the face
+// neighbours j; sets *changed when an order rose.
+__global__ void jump_kernel(const int32_t* cur, int32_t* nxt, const int32_t* nbr, int n_elem, int rule,
+                            int* changed) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_elem) return;
+  for (int d = 0; d < 3; ++d) {
+    int need = cur[3 * e + d];
+    for (int f = 0; f < 6; ++f) {
+      const int j = nbr[6 * e + f];
+      if (j < 0) continue;
+      const int nj = cur[3 * j + d];
+      const int lim = rule == 1 ? (2 * nj) / 3 : nj - 1;
+      need = lim > need ? lim : need;
+    }
+    if (need != cur[3 * e + d]) *changed = 1;
+    nxt[3 * e + d] = need;
+  }
+}
+
+}  // namespace
+
+extern "C" dg_status dg_select_orders(dg_mesh* m, const void* map, int32_t map_fp32, const int32_t* sweep,
+                                      int32_t n_sweep, double tau_max, int32_t n_min, int32_t n_max,
+                                      int32_t jump_rule, int32_t* orders_out) {
+  if (!m || !map || !sweep || n_sweep <= 0 || !orders_out || !(tau_max > 0.0)) return DG_ERR_ARG;
+  if (n_min < 1 || n_max > DG_MAX_ORDER || n_min > n_max || jump_rule < 0 || jump_rule > 2) return DG_ERR_ARG;
+  for (int s = 0; s < 3 * n_sweep; ++s)
+    if (sweep[s] < 1 || sweep[s] > DG_MAX_ORDER) return DG_ERR_ARG;
+  const int ne = m->n_elem;
+  int32_t *d_sw = nullptr, *d_a = nullptr, *d_b = nullptr;
+  int* d_flag = nullptr;
+  dg_status st = DG_OK;
+  auto fail = [&](cudaError_t e) { st = e == cudaErrorMemoryAllocation ? DG_ERR_NOMEM : DG_ERR_CUDA; };
+  cudaError_t e;
+  if ((e = cudaMalloc(&d_sw, sizeof(int32_t) * 3 * n_sweep)) || (e = cudaMalloc(&d_a, sizeof(int32_t) * 3 * ne)) ||
+      (e = cudaMalloc(&d_b, sizeof(int32_t) * 3 * ne)) || (e = cudaMalloc(&d_flag, sizeof(int)))) {
+    fail(e);
+  } else if ((e = cudaMemcpyAsync(d_sw, sweep, sizeof(int32_t) * 3 * n_sweep, cudaMemcpyHostToDevice, m->stream))) {
+    fail(e);
+  } else {
+    const int grid = (ne + 127) / 128;
+    dg_prof_begin(m, DG_KERNEL_SELECT, 1);
+    if (map_fp32)
+      select_kernel<float><<<grid, 128, 0, m->stream>>>(static_cast<const float*>(map), d_sw, n_sweep, ne, tau_max,
+                                                         n_min, n_max, d_a);
+    else
+      select_kernel<double><<<grid, 128, 0, m->stream>>>(static_cast<const double*>(map), d_sw, n_sweep, ne,
+                                                          tau_max, n_min, n_max, d_a);
+    dg_prof_end(m, DG_KERNEL_SELECT);
+    if ((e = cudaGetLastError())) fail(e);
+    // jump condition: Jacobi sweeps to the least fixed point (orders only
+    // rise, bounded by n_max, so at most n_max * n_elem sweeps; in practice
+    // a few)
+    for (int it = 0; st == DG_OK && jump_rule && it <= DG_MAX_ORDER * ne + 1; ++it) {
+      int flag = 0;
+      if ((e = cudaMemsetAsync(d_flag, 0, sizeof(int), m->stream))) { fail(e); break; }
+      dg_prof_begin(m, DG_KERNEL_SELECT, 1);
+      jump_kernel<<<grid, 128, 0, m->stream>>>(d_a, d_b, m->d_nbr, ne, jump_rule, d_flag);
+      dg_prof_end(m, DG_KERNEL_SELECT);
+      if ((e = cudaGetLastError())) { fail(e); break; }
+      if ((e = cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream))) { fail(e); break; }
+      if ((e = cudaStreamSynchronize(m->stream))) { fail(e); break; }
+      std::swap(d_a, d_b);
+      if (!flag) break;
+    }
+    if (st == DG_OK) {
+      if ((e = cudaMemcpyAsync(orders_out, d_a, sizeof(int32_t) * 3 * ne, cudaMemcpyDeviceToHost, m->stream)))
+        fail(e);
+      else if ((e = cudaStreamSynchronize(m->stream)))
+        fail(e);
+    }
+  }
+  cudaFree(d_sw);
+  cudaFree(d_a);
+  cudaFree(d_b);
+  cudaFree(d_flag);
+  return st;
+}

@@ -22,7 +22,7 @@ DG_TAU_FP32 = 0x2
 DG_TAU_ACCUM_MAX = 0x4
 DG_MAX_ORDER = 8
 KERNELS = {"face_flux": 0, "face_qhat": 1, "gradient": 2, "volume": 3, "max_dt": 4, "tau": 5, "tau_combine": 6,
-           "project": 7}
+           "project": 7, "select": 8}
 STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_NOMEM", 3: "DG_ERR_CUDA", 4: "DG_ERR_UNSUPPORTED",
           5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_TIMEOUT"}
 
@@ -64,6 +64,8 @@ def _lib():
             "dg_node_coords": [vp, vp],
             "dg_residual": [vp, vp, vp, C.c_uint32],
             "dg_residual_noalloc": [vp, vp, vp],
+            "dg_select_orders": [vp, vp, C.c_int32, i32p, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_int32,
+                                 i32p],
             "dg_max_dt": [vp, vp, C.c_double, vp],
             "dg_rk_step": [vp, vp, vp, vp],
             "dg_tau_estimate": [vp, vp, vp, i32p, C.c_int32, C.c_uint32, vp, vp],
@@ -84,7 +86,7 @@ def _lib():
 def exported_symbols():
     return ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_count_nodes", "dg_set_stream", "dg_node_coords",
             "dg_residual", "dg_max_dt", "dg_rk_step", "dg_tau_estimate", "dg_set_orders", "dg_get_error",
-            "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc"]
+            "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc", "dg_select_orders"]
 
 
 def _check(st, where):
@@ -210,6 +212,18 @@ class Mesh:
         self._ord = o
         self._refresh()
         return q_new
+
+    def select_orders(self, map_, sweep, tau_max, n_min=1, n_max=DG_MAX_ORDER, jump_rule=0):
+        """Static p-adaptation selection (approach 2) from a device tau map; returns
+        host orders [n_elem, 3] for set_orders."""
+        import torch
+        sw = np.ascontiguousarray(np.asarray(sweep, dtype=np.int32).reshape(-1, 3))
+        out = np.empty((self.n_elem, 3), dtype=np.int32)
+        _check(_lib().dg_select_orders(self.h, _ptr(map_), int(map_.dtype == torch.float32),
+                                       sw.ctypes.data_as(C.POINTER(C.c_int32)), sw.shape[0], float(tau_max),
+                                       int(n_min), int(n_max), int(jump_rule), out.ctypes.data_as(C.POINTER(C.c_int32))),
+               "dg_select_orders")
+        return out
 
     def get_error(self):
         return _lib().dg_get_error(self.h)
