@@ -65,7 +65,12 @@ def lib():
         L.orc_euler_flux.argtypes = [C.c_double, dp, C.c_int, dp]
         L.orc_visc_flux.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp, C.c_int, dp]
         L.orc_rk_coeffs.argtypes = [dp, dp]
-        L.orc_select_orders.argtypes = [C.c_int, C.c_int, ip, dp, C.c_double, C.c_int, C.c_int, C.c_int, ip, ip]
+        L.orc_select_orders.argtypes = [C.c_int, C.c_int, ip, dp, C.c_double, C.c_int, C.c_int, C.c_int, ip, ip,
+                                        C.c_int, ip]
+        L.orc_tau_extrapolate.argtypes = [C.c_int, ip, C.c_int, ip, dp, C.c_int, ip, C.c_int, C.c_double, C.c_int,
+                                          C.c_int, dp]
+        L.orc_advance.restype = C.c_int
+        L.orc_advance.argtypes = [C.c_void_p, dp, dp, C.c_double, dp, C.c_double, C.c_int]
         _lib = L
     return _lib
 
@@ -197,6 +202,14 @@ class Mesh:
     def max_dt(self, q, cfl):
         return lib().orc_max_dt(self.h, _d(_f64(q)), float(cfl))
 
+    def advance(self, q, G, cfl, t, t_end, max_steps=1 << 30):
+        """CFL-adaptive RK3 steps from t to t_end (the last one shortened to
+        land on t_end); q and G advance in place.  Returns (t, steps)."""
+        assert q.dtype == np.float64 and G.dtype == np.float64 and q.flags.c_contiguous and G.flags.c_contiguous
+        tt = C.c_double(t)
+        n = lib().orc_advance(self.h, _d(q), _d(G), float(cfl), C.byref(tt), float(t_end), int(max_steps))
+        return tt.value, n
+
     def tau(self, q, sweep, isolated=True, rP=None, accumulate=None):
         """Returns (tau_new, tau_trad) maps [n_elem, n_sweep]; accumulate=(new, trad)
         maps to max-accumulate into (modified in place and returned)."""
@@ -232,14 +245,40 @@ class Mesh:
         return a[nvar * self.off[e]: nvar * self.off[e + 1]].reshape(nvar, n)
 
 
-def select_orders(map_, sweep, tau_max, n_min, n_max, jump_rule, neighbors):
+def select_orders(map_, sweep, tau_max, n_min, n_max, jump_rule, neighbors, prev=None, max_decrease=-1):
     """Static p-adaptation selection (approach 2) and jump rule: 0 none,
-    1 floor(2N/3) (Eq. N23), 2 N-1 (Eq. N_1).  map_: [n_elem, n_sweep]."""
+    1 floor(2N/3) (Eq. N23), 2 N-1 (Eq. N_1).  map_: [n_elem, n_sweep].
+    prev / max_decrease: an order falls by at most max_decrease below prev
+    (dynamic adaptation, Sec. 3.2); max_decrease < 0: no limit."""
     m = _f64(map_)
     n_elem, ns = m.shape
     sw = _i32(sweep).reshape(-1, 3)
     nb = _i32(neighbors).reshape(-1, 6)
     out = np.empty((n_elem, 3), dtype=np.int32)
+    pv = _i32(prev).reshape(-1, 3) if prev is not None else None
     lib().orc_select_orders(n_elem, ns, _i(sw), _d(m), float(tau_max), int(n_min), int(n_max), int(jump_rule),
-                            _i(nb), _i(out))
+                            _i(nb), _i(pv) if pv is not None else None, int(max_decrease), _i(out))
+    return out
+
+
+def tau_extrapolate(map_, orders, sweep, targets, n_fit=0, decoupled=False, accumulate=None, tau_floor=0.0):
+    """Truncation-error extrapolation to N_i >= P_i (reading stated in
+    dg_oracle.c).  map_: [n_elem, n_sweep] over sweep; orders: [n_elem, 3]
+    (P); targets: [n_target, 3].  Returns [n_elem, n_target]; accumulate: an
+    array of that shape to max-accumulate into (modified and returned);
+    tau_floor: a direction whose value just below P is at or under it counts
+    as resolved."""
+    m = _f64(map_)
+    n_elem, ns = m.shape
+    sw = _i32(sweep).reshape(-1, 3)
+    assert sw.shape[0] == ns
+    P = _i32(orders).reshape(-1, 3)
+    tg = _i32(targets).reshape(-1, 3)
+    if accumulate is not None:
+        out = accumulate
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == (n_elem, tg.shape[0])
+    else:
+        out = np.empty((n_elem, tg.shape[0]))
+    lib().orc_tau_extrapolate(n_elem, _i(P), ns, _i(sw), _d(m), tg.shape[0], _i(tg), int(n_fit), float(tau_floor),
+                              int(decoupled), int(accumulate is not None), _d(out))
     return out

@@ -985,6 +985,24 @@ double orc_max_dt(void* h, const double* q, double cfl) {
   return cfl / smax;
 }
 
+/* Time integration to a given time (Sec. 3.1: the time-step size follows
+ * the CFL condition at every step).  Steps of size orc_max_dt from *t; the
+ * step that would pass t_end is shortened to land on it exactly.  At most
+ * max_steps steps; returns the number taken and leaves *t at the new time. */
+int orc_advance(void* h, double* q, double* G, double cfl, double* t, double t_end, int max_steps) {
+  int n = 0;
+  while (n < max_steps && *t < t_end) {
+    double dt = orc_max_dt(h, q, cfl);
+    const double rem = t_end - *t;
+    const int last = dt >= rem;
+    if (last) dt = rem;
+    orc_rk_step(h, q, G, dt);
+    *t = last ? t_end : *t + dt;
+    ++n;
+  }
+  return n;
+}
+
 /* ------------------------------------------------------------------------ */
 /* 8. Truncation-error estimation (Sec. 2.2, 2.3)                             */
 /* ------------------------------------------------------------------------ */
@@ -1167,7 +1185,7 @@ void orc_set_orders(void* h, const int* new_ord, const double* q_old, double* q_
  * (aligned axes: direction i of the neighbour is direction i of e), rule 0:
  * none.  Orders are raised by Jacobi sweeps until nothing changes. */
 void orc_select_orders(int n_elem, int n_sweep, const int* sweep, const double* map, double tau_max, int n_min,
-                       int n_max, int jump_rule, const int* nbr, int* out) {
+                       int n_max, int jump_rule, const int* nbr, const int* prev, int max_decrease, int* out) {
   for (int e = 0; e < n_elem; ++e) {
     long best = -1;
     int bs = -1;
@@ -1181,6 +1199,14 @@ void orc_select_orders(int n_elem, int n_sweep, const int* sweep, const double* 
       if (best < 0 || nd < best) { best = nd; bs = s; }
     }
     for (int d = 0; d < 3; ++d) out[3 * e + d] = bs >= 0 ? sweep[3 * bs + d] : n_max;
+    /* dynamic adaptation, Sec. 3.2: an order falls by at most max_decrease
+       per adaptation stage */
+    if (prev && max_decrease >= 0)
+      for (int d = 0; d < 3; ++d) {
+        int lo = prev[3 * e + d] - max_decrease;
+        if (lo > n_max) lo = n_max;
+        if (out[3 * e + d] < lo) out[3 * e + d] = lo;
+      }
   }
   if (jump_rule == 0) return;
   int* tmp = malloc(sizeof(int) * 3 * n_elem);
@@ -1201,4 +1227,102 @@ void orc_select_orders(int n_elem, int n_sweep, const int* sweep, const double* 
       }
   }
   free(tmp);
+}
+
+/* ------------------------------------------------------------------------
+ * Truncation-error extrapolation to N_i >= P_i (Sec. 2.3 mentions it, Sec. 2.4
+ * needs it for approach 2; the method itself is in the authors' earlier
+ * anisotropic work).  The reading used here, step by step, for one element
+ * with orders P and its map over the sweep list:
+ *   1. directional values: d_i(n) = map at the orders P with N_i = n, for
+ *      n = 1 .. P_i - 1 (only the entries present in the sweep);
+ *   2. a least-squares line through (n, ln d_i(n)) over the last n_fit of
+ *      those points (all of them when n_fit <= 0); the direction is
+ *      extrapolable when at least two points are positive and the slope is
+ *      negative (exponential decay, the asymptotic range).  Then
+ *      e_i(n) = exp(a_i + b_i n) for n >= P_i;
+ *   3. d_i(P_i - 1) <= tau_floor (resolved below P: exactly zero when
+ *      tau_floor = 0, or at the roundoff level of the estimate): e_i(n) = 0;
+ *   4. otherwise e_i(n) = +infinity for n >= P_i (Sec. 2.4, the "high
+ *      value" assigned when extrapolation is not possible);
+ *   5. the value at a target N:
+ *        coupled:   map(min(N, P)) + sum over N_i >= P_i of e_i(N_i), with
+ *                   map(P) = 0 and -1 when min(N, P) is not in the sweep;
+ *        decoupled: sum_i c_i(N_i), c_i(n) = d_i(n) for n < P_i, e_i(n)
+ *                   otherwise (-1 when a needed d_i is missing).
+ * out: [n_elem][n_target]; accumulate: out = max(out, value).
+ * ---------------------------------------------------------------------- */
+static int sweep_find(const int* sweep, int n_sweep, int a, int b, int c) {
+  for (int s = 0; s < n_sweep; ++s)
+    if (sweep[3 * s] == a && sweep[3 * s + 1] == b && sweep[3 * s + 2] == c) return s;
+  return -1;
+}
+
+void orc_tau_extrapolate(int n_elem, const int* orders, int n_sweep, const int* sweep, const double* map,
+                         int n_target, const int* target, int n_fit, double tau_floor, int decoupled, int accumulate,
+                         double* out) {
+  for (int e = 0; e < n_elem; ++e) {
+    const int* P = orders + 3 * e;
+    const double* row = map + (long)e * n_sweep;
+    double dv[3][NMAX];      /* directional values, -1 = missing */
+    int kind[3];             /* 0: exponential fit, 1: zero, 2: infinity */
+    double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i) {
+      for (int n = 1; n < P[i]; ++n) {
+        int Nn[3] = {P[0], P[1], P[2]};
+        Nn[i] = n;
+        int s = sweep_find(sweep, n_sweep, Nn[0], Nn[1], Nn[2]);
+        dv[i][n] = s >= 0 ? row[s] : -1.0;
+      }
+      kind[i] = 2;
+      if (P[i] >= 2 && dv[i][P[i] - 1] >= 0.0 && dv[i][P[i] - 1] <= tau_floor) {
+        kind[i] = 1;
+        continue;
+      }
+      int lo = n_fit > 0 ? P[i] - n_fit : 1;
+      if (lo < 1) lo = 1;
+      double sx = 0, sy = 0, sxx = 0, sxy = 0;
+      int m = 0;
+      for (int n = lo; n < P[i]; ++n) {
+        if (!(dv[i][n] > 0.0)) continue;
+        double y = log(dv[i][n]);
+        sx += n; sy += y; sxx += (double)n * n; sxy += n * y;
+        ++m;
+      }
+      if (m < 2) continue;
+      double xm = sx / m, ym = sy / m;
+      double slope = (sxy - m * xm * ym) / (sxx - m * xm * xm);
+      if (!(slope < 0.0)) continue;
+      b[i] = slope;
+      a[i] = ym - slope * xm;
+      kind[i] = 0;
+    }
+    for (int t = 0; t < n_target; ++t) {
+      const int* N = target + 3 * t;
+      double v;
+      if (!decoupled) {
+        int Nc[3];
+        for (int i = 0; i < 3; ++i) Nc[i] = N[i] < P[i] ? N[i] : P[i];
+        if (Nc[0] == P[0] && Nc[1] == P[1] && Nc[2] == P[2]) {
+          v = 0.0;
+        } else {
+          int s = sweep_find(sweep, n_sweep, Nc[0], Nc[1], Nc[2]);
+          v = s >= 0 ? row[s] : -1.0;
+        }
+        if (v >= 0.0)
+          for (int i = 0; i < 3; ++i)
+            if (N[i] >= P[i]) v += kind[i] == 0 ? exp(a[i] + b[i] * N[i]) : kind[i] == 1 ? 0.0 : INFINITY;
+      } else {
+        v = 0.0;
+        for (int i = 0; i < 3 && v >= 0.0; ++i) {
+          double c;
+          if (N[i] < P[i]) c = dv[i][N[i]];
+          else c = kind[i] == 0 ? exp(a[i] + b[i] * N[i]) : kind[i] == 1 ? 0.0 : INFINITY;
+          v = c < 0.0 ? -1.0 : v + c;
+        }
+      }
+      double* o = out + (long)e * n_target + t;
+      *o = accumulate ? (v > *o ? v : *o) : v;
+    }
+  }
 }
