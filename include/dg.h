@@ -193,22 +193,75 @@ dg_status dg_tau_estimate(dg_mesh* mesh, const double* q, const double* r_p, con
  * The mesh is rebuilt for the new orders (synchronous). */
 dg_status dg_set_orders(dg_mesh* mesh, const int32_t* new_orders, const double* q_old, double* q_new);
 
-/* Static p-adaptation, order selection (Sec. 2.4, approach 2; with the
- * degree-jump conditions of Sec. 3.1, Eqs. N23 and N_1).  From a total
- * truncation-error map (a dg_tau_estimate map, usually F_max-accumulated
- * over the estimation stages), for every element: the sweep entry N with
- * 0 <= map < tau_max and n_min <= N_i <= n_max of fewest degrees of freedom
- * prod_i (N_i+1), the first in sweep order on ties; n_max in every
- * direction when no entry qualifies (entries above the element's own orders
- * are -1 and never qualify).  Then the jump condition, as the least orders
- * at or above the selection that satisfy it: jump_rule 1: N_i^e >=
- * floor(2 N_i^j / 3); 2: N_i^e >= N_i^j - 1 for every face neighbour j;
- * 0: none.  map: device [n_elem][n_sweep], float if map_fp32 else double;
- * sweep: host, the list the map was built with; orders_out: host
- * [n_elem][3], ready for dg_set_orders.  Synchronous.
+/* p-adaptation, order selection (Sec. 2.4, approach 2; with the degree-jump
+ * conditions of Sec. 3.1, Eqs. N23 and N_1).  From a total truncation-error
+ * map (a dg_tau_estimate map, F_max-accumulated over the estimation stages
+ * of the static strategy, or a dg_tau_extrapolate map over a target list),
+ * for every element: the sweep entry N with 0 <= map < tau_max and
+ * n_min <= N_i <= n_max of fewest degrees of freedom prod_i (N_i+1), the
+ * first in sweep order on ties; n_max in every direction when no entry
+ * qualifies (entries above the element's own orders are -1 and never
+ * qualify).  max_decrease >= 0 (dynamic adaptation, Sec. 3.3: the orders
+ * fall by at most one per stage) raises each order to at least the mesh's
+ * current order minus max_decrease (capped at n_max); < 0: no limit.  Then
+ * the jump condition, as the least orders at or above that selection that
+ * satisfy it: jump_rule 1: N_i^e >= floor(2 N_i^j / 3); 2: N_i^e >=
+ * N_i^j - 1 for every face neighbour j; 0: none.  map: device
+ * [n_elem][n_sweep], float if map_fp32 else double; sweep: host, the list
+ * the map was built over; orders_out: host [n_elem][3], ready for
+ * dg_set_orders.  Synchronous.
  * Errors: DG_ERR_ARG (null pointers, tau_max <= 0, bad bounds or rule). */
 dg_status dg_select_orders(dg_mesh* mesh, const void* map, int32_t map_fp32, const int32_t* sweep, int32_t n_sweep,
-                           double tau_max, int32_t n_min, int32_t n_max, int32_t jump_rule, int32_t* orders_out);
+                           double tau_max, int32_t n_min, int32_t n_max, int32_t jump_rule, int32_t max_decrease,
+                           int32_t* orders_out);
+
+/* Truncation-error extrapolation to N_i >= P_i (Sec. 2.3; Sec. 2.4:
+ * approach 2 needs the extrapolated map of every estimation stage, and a
+ * direction that cannot be extrapolated gets a high value).  For every
+ * element with orders P and its map over the sweep (a dg_tau_estimate map):
+ *   d_i(n): the map at the orders P with N_i = n < P_i (the directional
+ *     entries present in the sweep);
+ *   fit: the least-squares line through (n, ln d_i(n)) over the last n_fit
+ *     points below P_i (all when n_fit <= 0), positive values only; with at
+ *     least two points and a negative slope, e_i(n) = exp(a_i + b_i n);
+ *     if d_i(P_i - 1) <= tau_floor the direction is resolved, e_i = 0;
+ *     otherwise e_i = +infinity (P_i <= 2 always ends here);
+ *   value at a target N: coupled (default): map(min(N, P)) + sum over
+ *     N_i >= P_i of e_i(N_i), with map(P) = 0 and -1 when min(N, P) is not
+ *     in the sweep; DG_EXTRAP_DECOUPLED: sum_i c_i(N_i), c_i(n) = d_i(n)
+ *     below P_i and e_i(n) from P_i on (-1 when a needed d_i is missing),
+ *     which needs only the sum_i (P_i - 1) directional sweep entries.
+ * map: device [n_elem][n_sweep], float if map_fp32 else double; sweep:
+ * host [n_sweep][3]; targets: host [n_targets][3], n_targets <= 512;
+ * map_out: device [n_elem][n_targets] of the map's type; DG_EXTRAP_ACCUM_MAX
+ * accumulates map_out = max(map_out, value) (F_max over stages).
+ * Arithmetic in double.  Errors: DG_ERR_ARG. */
+#define DG_EXTRAP_DECOUPLED 0x1u
+#define DG_EXTRAP_ACCUM_MAX 0x2u
+dg_status dg_tau_extrapolate(dg_mesh* mesh, const void* map, int32_t map_fp32, const int32_t* sweep, int32_t n_sweep,
+                             const int32_t* targets, int32_t n_targets, int32_t n_fit, double tau_floor, uint32_t flags,
+                             void* map_out);
+
+/* Time integration to a given time (Sec. 3.1: the time step follows the
+ * CFL condition at every step): Williamson RK3 steps of
+ *   dt = min(cfl / max_nodes max(s_a, s_v), t_end - t)     (dg_max_dt's scale)
+ * from the device time *t_dev; the step that reaches t_end sets *t_dev =
+ * t_end exactly, and steps after it are empty (dt = 0 leaves q unchanged:
+ * the first stage discards g).  At most max_steps steps.
+ * t_end = +infinity: exactly max_steps CFL steps, asynchronous on the mesh
+ * stream.  Otherwise the call returns once *t_dev = t_end or max_steps steps
+ * were taken, reading the time back between batches of steps.
+ * Steps run in batches captured once as CUDA graphs (on a private stream,
+ * replayed on the mesh stream) and cached per (q, g, t_dev, batch size);
+ * DG_ADVANCE_EAGER, or enabled profiling, launches them one by one instead.
+ * q, g: device state and RK register as for dg_rk_step; t_dev: device
+ * double; steps_out (host, optional): steps with dt > 0 in this call (a
+ * synchronising read).  The cached graphs hold the buffers' addresses: free
+ * q, g or t_dev only after the mesh, or pass other buffers (new graphs).
+ * Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED (as dg_rk_step), DG_ERR_CUDA. */
+#define DG_ADVANCE_EAGER 0x1u
+dg_status dg_advance(dg_mesh* mesh, double* q, double* g, double* t_dev, double t_end, double cfl, int64_t max_steps,
+                     uint32_t flags, int64_t* steps_out);
 
 /* Kernel kinds for dg_profile_read. */
 enum {
@@ -216,12 +269,13 @@ enum {
   DG_KERNEL_FACE_QHAT = 1,   /* BR1 q-hat per face (Navier-Stokes) */
   DG_KERNEL_GRADIENT = 2,    /* BR1 gradient (Navier-Stokes) */
   DG_KERNEL_VOLUME = 3,      /* volume residual + surface lift (+ fused RK3 stage) */
-  DG_KERNEL_MAX_DT = 4,      /* CFL reduction (two launches) */
+  DG_KERNEL_MAX_DT = 4,      /* CFL reduction and its finalisation (two launches) */
   DG_KERNEL_TAU = 5,         /* isolated tau sweep */
   DG_KERNEL_TAU_COMBINE = 6, /* non-isolated tau, per sweep entry */
   DG_KERNEL_PROJECT = 7,     /* order projection / restriction */
   DG_KERNEL_SELECT = 8,      /* order selection and degree-jump sweeps */
-  DG_KERNEL_KINDS = 9
+  DG_KERNEL_EXTRAP = 9,      /* truncation-error extrapolation */
+  DG_KERNEL_KINDS = 10
 };
 
 /* Per-kernel timing with CUDA events recorded on the mesh stream around

@@ -163,7 +163,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 void free_device(dg_mesh_impl* m) {
   void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
                   m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
-                  m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep};
+                  m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
@@ -171,6 +171,7 @@ void free_device(dg_mesh_impl* m) {
   m->d_faces = nullptr; m->d_items = nullptr; m->d_elist = nullptr; m->d_err = nullptr; m->d_scratch = nullptr;
   m->d_taugeo = nullptr; m->d_taugeo32 = nullptr; m->d_taugeo_off = nullptr; m->d_rp = nullptr; m->d_qc = nullptr;
   m->d_rc = nullptr; m->d_sweep = nullptr; m->d_mfaces = nullptr; m->d_mbatches = nullptr; m->d_rp32 = nullptr;
+  m->d_adv = nullptr;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
@@ -192,6 +193,7 @@ void destroy_impl(dg_mesh_impl* m) {
   if (m->prof_open) cudaEventDestroy(m->prof_open);
   for (auto* c : m->coarse) destroy_impl(c);
   m->coarse.clear();
+  dg_advance_release(m);
   free_device(m);
   delete static_cast<dg_mesh*>(m);
 }

@@ -83,7 +83,13 @@ cudaError_t tau_combine(dg_mesh_impl* m, dg_mesh_impl* coarse, const double* r_p
 cudaError_t project_orders(dg_mesh_impl* m, const int32_t* d_new_orders, const int64_t* d_new_off,
                            const double* q_old, double* q_new, int mode);
 size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32);
+// CFL reduction only: *bits = max over nodes of the inverse time-step scale
+// (as the bit pattern of a non-negative double)
+cudaError_t max_dt_bits(dg_mesh_impl* m, const double* q, unsigned long long* bits);
 }  // namespace dgk
+
+// releases the dg_advance graphs and capture stream of a mesh
+void dg_advance_release(dg_mesh_impl* m);
 
 // ---------------------------------------------------------------------------
 // The mesh
@@ -165,6 +171,14 @@ struct dg_mesh_impl {
   double prof_ms[DG_KERNEL_KINDS] = {0};
   int64_t prof_n[DG_KERNEL_KINDS] = {0};
   int64_t launches = 0;
+
+  // dg_advance: device block {cfl, t_end, dt, steps}, the capture stream and
+  // the instantiated step batches, keyed by the caller's buffers
+  double* d_adv = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool adv_warm = false;             // one eager step taken (kernel attributes set)
+  struct AdvGraph { const void *q, *g, *t; int steps; cudaGraphExec_t exec; int64_t launches; };
+  std::vector<AdvGraph> adv_graphs;
 };
 
 struct dg_mesh : dg_mesh_impl {};

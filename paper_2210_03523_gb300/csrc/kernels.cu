@@ -1777,16 +1777,23 @@ cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double*
   return dispatch_volume(m, P, 0, 0);
 }
 
-cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev) {
+cudaError_t max_dt_bits(dg_mesh_impl* m, const double* q, unsigned long long* bits) {
   VolParams P = vol_params(m, q);
-  unsigned long long* bits = reinterpret_cast<unsigned long long*>(m->d_scratch);
   cudaError_t err = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), m->stream);
   if (err) return err;
   int grid = grid_for(m->n_items, 8);
-  Prof pr(m, DG_KERNEL_MAX_DT, 2);
+  Prof pr(m, DG_KERNEL_MAX_DT, 1);
   if (m->axis) dt_kernel<true, true><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
   else if (m->affine) dt_kernel<true, false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
   else dt_kernel<false, false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
+  return cudaGetLastError();
+}
+
+cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev) {
+  unsigned long long* bits = reinterpret_cast<unsigned long long*>(m->d_scratch);
+  cudaError_t err = max_dt_bits(m, q, bits);
+  if (err) return err;
+  Prof pr(m, DG_KERNEL_MAX_DT, 1);
   dt_finalize<<<1, 1, 0, m->stream>>>(bits, cfl, dt_dev);
   return cudaGetLastError();
 }
@@ -1988,7 +1995,7 @@ namespace {
 // order on ties; n_max in every direction when none qualifies.
 template <typename T>
 __global__ void select_kernel(const T* map, const int32_t* sweep, int n_sweep, int n_elem, double tau_max, int n_min,
-                              int n_max, int32_t* out) {
+                              int n_max, const int32_t* prev, int max_decrease, int32_t* out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_elem) return;
   long long best = -1;
@@ -2005,7 +2012,15 @@ __global__ void select_kernel(const T* map, const int32_t* sweep, int n_sweep, i
       bs = s;
     }
   }
-  for (int d = 0; d < 3; ++d) out[3 * e + d] = bs >= 0 ? sweep[3 * bs + d] : n_max;
+  for (int d = 0; d < 3; ++d) {
+    int o = bs >= 0 ? sweep[3 * bs + d] : n_max;
+    if (max_decrease >= 0) {   // dynamic adaptation: fall by at most max_decrease below the current order
+      int lo = prev[3 * e + d] - max_decrease;
+      lo = lo > n_max ? n_max : lo;
+      o = o < lo ? lo : o;
+    }
+    out[3 * e + d] = o;
+  }
 }
 
 // One Jacobi sweep of the jump condition: rule 1 (Eq. N23) N_i^e >=
@@ -2033,7 +2048,7 @@ __global__ void jump_kernel(const int32_t* cur, int32_t* nxt, const int32_t* nbr
 
 extern "C" dg_status dg_select_orders(dg_mesh* m, const void* map, int32_t map_fp32, const int32_t* sweep,
                                       int32_t n_sweep, double tau_max, int32_t n_min, int32_t n_max,
-                                      int32_t jump_rule, int32_t* orders_out) {
+                                      int32_t jump_rule, int32_t max_decrease, int32_t* orders_out) {
   if (!m || !map || !sweep || n_sweep <= 0 || !orders_out || !(tau_max > 0.0)) return DG_ERR_ARG;
   if (n_min < 1 || n_max > DG_MAX_ORDER || n_min > n_max || jump_rule < 0 || jump_rule > 2) return DG_ERR_ARG;
   for (int s = 0; s < 3 * n_sweep; ++s)
@@ -2054,10 +2069,10 @@ extern "C" dg_status dg_select_orders(dg_mesh* m, const void* map, int32_t map_f
     dg_prof_begin(m, DG_KERNEL_SELECT, 1);
     if (map_fp32)
       select_kernel<float><<<grid, 128, 0, m->stream>>>(static_cast<const float*>(map), d_sw, n_sweep, ne, tau_max,
-                                                         n_min, n_max, d_a);
+                                                         n_min, n_max, m->d_ord, max_decrease, d_a);
     else
       select_kernel<double><<<grid, 128, 0, m->stream>>>(static_cast<const double*>(map), d_sw, n_sweep, ne,
-                                                          tau_max, n_min, n_max, d_a);
+                                                          tau_max, n_min, n_max, m->d_ord, max_decrease, d_a);
     dg_prof_end(m, DG_KERNEL_SELECT);
     if ((e = cudaGetLastError())) fail(e);
     // jump condition: Jacobi sweeps to the least fixed point (orders only

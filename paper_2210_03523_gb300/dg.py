@@ -21,8 +21,11 @@ DG_TAU_ISOLATED = 0x1
 DG_TAU_FP32 = 0x2
 DG_TAU_ACCUM_MAX = 0x4
 DG_MAX_ORDER = 8
+DG_EXTRAP_DECOUPLED = 0x1
+DG_EXTRAP_ACCUM_MAX = 0x2
+DG_ADVANCE_EAGER = 0x1
 KERNELS = {"face_flux": 0, "face_qhat": 1, "gradient": 2, "volume": 3, "max_dt": 4, "tau": 5, "tau_combine": 6,
-           "project": 7, "select": 8}
+           "project": 7, "select": 8, "extrap": 9}
 STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_NOMEM", 3: "DG_ERR_CUDA", 4: "DG_ERR_UNSUPPORTED",
           5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_TIMEOUT"}
 
@@ -65,7 +68,10 @@ def _lib():
             "dg_residual": [vp, vp, vp, C.c_uint32],
             "dg_residual_noalloc": [vp, vp, vp],
             "dg_select_orders": [vp, vp, C.c_int32, i32p, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_int32,
-                                 i32p],
+                                 C.c_int32, i32p],
+            "dg_tau_extrapolate": [vp, vp, C.c_int32, i32p, C.c_int32, i32p, C.c_int32, C.c_int32, C.c_double,
+                                   C.c_uint32, vp],
+            "dg_advance": [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int64, C.c_uint32, i64p],
             "dg_max_dt": [vp, vp, C.c_double, vp],
             "dg_rk_step": [vp, vp, vp, vp],
             "dg_tau_estimate": [vp, vp, vp, i32p, C.c_int32, C.c_uint32, vp, vp],
@@ -86,7 +92,8 @@ def _lib():
 def exported_symbols():
     return ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_count_nodes", "dg_set_stream", "dg_node_coords",
             "dg_residual", "dg_max_dt", "dg_rk_step", "dg_tau_estimate", "dg_set_orders", "dg_get_error",
-            "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc", "dg_select_orders"]
+            "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc",
+            "dg_select_orders", "dg_tau_extrapolate", "dg_advance"]
 
 
 def _check(st, where):
@@ -96,6 +103,24 @@ def _check(st, where):
 
 def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1, 3))
+
+
+def _p32(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _check_map(t, n_elem, n_cols, device, dtype=None):
+    """A device map must be a contiguous [n_elem, n_cols] float32/float64 tensor."""
+    import torch
+    ok = (isinstance(t, torch.Tensor) and t.device == device and t.is_contiguous() and
+          tuple(t.shape) == (n_elem, n_cols) and t.dtype in (torch.float32, torch.float64) and
+          (dtype is None or t.dtype == dtype))
+    if not ok:
+        raise ValueError(f"map: expected a contiguous float32/float64 [{n_elem}, {n_cols}] tensor on {device}")
 
 
 def _stream_handle(stream):
@@ -168,22 +193,26 @@ class Mesh:
 
     def residual(self, q, r=None, isolated=False):
         r = self.new_state() if r is None else r
+        self._check_state(q, r)
         _check(_lib().dg_residual(self.h, _ptr(q), _ptr(r), DG_ISOLATED if isolated else 0), "dg_residual")
         return r
 
     def residual_noalloc(self, q, r):
         """dg_residual_noalloc: same residual, face scratch in the library's fixed
         device array; r must be a caller-allocated state-layout tensor."""
+        self._check_state(q, r)
         _check(_lib().dg_residual_noalloc(self.h, _ptr(q), _ptr(r)), "dg_residual_noalloc")
         return r
 
     def max_dt(self, q, cfl, dt=None):
         import torch
+        self._check_state(q)
         dt = torch.empty(1, dtype=torch.float64, device=self.device) if dt is None else dt
         _check(_lib().dg_max_dt(self.h, _ptr(q), float(cfl), _ptr(dt)), "dg_max_dt")
         return dt
 
     def rk_step(self, q, g, dt):
+        self._check_state(q, g)
         _check(_lib().dg_rk_step(self.h, _ptr(q), _ptr(g), _ptr(dt)), "dg_rk_step")
 
     def tau_estimate(self, q, sweep, isolated=True, fp32=False, accumulate=False, r_p=None, map_new=None,
@@ -196,6 +225,10 @@ class Mesh:
             map_new = torch.empty((self.n_elem, ns), dtype=dt, device=self.device)
         if map_trad is None and want[1]:
             map_trad = torch.empty((self.n_elem, ns), dtype=dt, device=self.device)
+        self._check_state(q, r_p)
+        for mp in (map_new, map_trad):
+            if mp is not None:
+                _check_map(mp, self.n_elem, ns, self.device, dt)
         flags = (DG_TAU_ISOLATED if isolated else 0) | (DG_TAU_FP32 if fp32 else 0) | \
                 (DG_TAU_ACCUM_MAX if accumulate else 0)
         self._sweep_keep = sw
@@ -206,6 +239,9 @@ class Mesh:
     def set_orders(self, new_orders, q_old):
         import torch
         o = np.ascontiguousarray(np.asarray(new_orders, dtype=np.int32).reshape(-1, 3))
+        if o.shape[0] != self.n_elem:
+            raise ValueError(f"new_orders: expected [{self.n_elem}, 3]")
+        self._check_state(q_old)
         q_new = torch.empty(5 * dg_count_nodes(o), dtype=torch.float64, device=self.device)
         _check(_lib().dg_set_orders(self.h, o.ctypes.data_as(C.POINTER(C.c_int32)), _ptr(q_old), _ptr(q_new)),
                "dg_set_orders")
@@ -213,17 +249,58 @@ class Mesh:
         self._refresh()
         return q_new
 
-    def select_orders(self, map_, sweep, tau_max, n_min=1, n_max=DG_MAX_ORDER, jump_rule=0):
-        """Static p-adaptation selection (approach 2) from a device tau map; returns
-        host orders [n_elem, 3] for set_orders."""
+    def select_orders(self, map_, sweep, tau_max, n_min=1, n_max=DG_MAX_ORDER, jump_rule=0, max_decrease=-1):
+        """p-adaptation order selection (approach 2) from a device tau map over
+        sweep; max_decrease >= 0 bounds the fall below the current orders.
+        Returns host orders [n_elem, 3] for set_orders."""
         import torch
-        sw = np.ascontiguousarray(np.asarray(sweep, dtype=np.int32).reshape(-1, 3))
+        sw = _i32(sweep)
+        _check_map(map_, self.n_elem, sw.shape[0], self.device)
         out = np.empty((self.n_elem, 3), dtype=np.int32)
-        _check(_lib().dg_select_orders(self.h, _ptr(map_), int(map_.dtype == torch.float32),
-                                       sw.ctypes.data_as(C.POINTER(C.c_int32)), sw.shape[0], float(tau_max),
-                                       int(n_min), int(n_max), int(jump_rule), out.ctypes.data_as(C.POINTER(C.c_int32))),
-               "dg_select_orders")
+        _check(_lib().dg_select_orders(self.h, _ptr(map_), int(map_.dtype == torch.float32), _p32(sw), sw.shape[0],
+                                       float(tau_max), int(n_min), int(n_max), int(jump_rule), int(max_decrease),
+                                       _p32(out)), "dg_select_orders")
         return out
+
+    def tau_extrapolate(self, map_, sweep, targets, n_fit=0, tau_floor=0.0, decoupled=False, out=None,
+                        accumulate=False):
+        """dg_tau_extrapolate: the map over sweep extended to the target list
+        (device [n_elem, n_targets], the map's dtype)."""
+        import torch
+        sw, tg = _i32(sweep), _i32(targets)
+        _check_map(map_, self.n_elem, sw.shape[0], self.device)
+        if out is None:
+            out = torch.empty((self.n_elem, tg.shape[0]), dtype=map_.dtype, device=self.device)
+        _check_map(out, self.n_elem, tg.shape[0], self.device, map_.dtype)
+        flags = (DG_EXTRAP_DECOUPLED if decoupled else 0) | (DG_EXTRAP_ACCUM_MAX if accumulate else 0)
+        _check(_lib().dg_tau_extrapolate(self.h, _ptr(map_), int(map_.dtype == torch.float32), _p32(sw), sw.shape[0],
+                                         _p32(tg), tg.shape[0], int(n_fit), float(tau_floor), flags, _ptr(out)),
+               "dg_tau_extrapolate")
+        return out
+
+    def advance(self, q, g, t, t_end, cfl, max_steps=1 << 40, eager=False, count=False):
+        """dg_advance: CFL-adaptive RK3 steps from the device time t (a 1-element
+        float64 tensor, updated) to t_end; t_end = inf runs exactly max_steps
+        steps asynchronously.  Returns the number of steps when count."""
+        import torch
+        self._check_state(q, g)
+        if not (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.numel() >= 1 and t.device == self.device):
+            raise ValueError("t: a float64 device tensor")
+        n = C.c_int64()
+        _check(_lib().dg_advance(self.h, _ptr(q), _ptr(g), _ptr(t), float(t_end), float(cfl), int(max_steps),
+                                 DG_ADVANCE_EAGER if eager else 0, C.byref(n) if count else None), "dg_advance")
+        return n.value if count else None
+
+    def _check_state(self, *states):
+        """State-layout device tensors: float64, contiguous, 5 * n_nodes values."""
+        import torch
+        for x in states:
+            if x is None:
+                continue
+            if not (isinstance(x, torch.Tensor) and x.dtype == torch.float64 and x.is_contiguous() and
+                    x.device == self.device and x.numel() == 5 * self.n_nodes):
+                raise ValueError(f"state: expected a contiguous float64 tensor of {5 * self.n_nodes} values on "
+                                 f"{self.device}")
 
     def get_error(self):
         return _lib().dg_get_error(self.h)
