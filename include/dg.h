@@ -265,7 +265,7 @@ dg_status dg_advance(dg_mesh* mesh, double* q, double* g, double* t_dev, double 
 
 /* Kernel kinds for dg_profile_read. */
 enum {
-  DG_KERNEL_FACE_FLUX = 0,   /* Roe (+ BR1 viscous) numerical flux per face, mortars */
+  DG_KERNEL_FACE_FLUX = 0,   /* Roe (+ BR1 viscous) numerical flux on conforming and boundary faces */
   DG_KERNEL_FACE_QHAT = 1,   /* BR1 q-hat per face (Navier-Stokes) */
   DG_KERNEL_GRADIENT = 2,    /* BR1 gradient (Navier-Stokes) */
   DG_KERNEL_VOLUME = 3,      /* volume residual + surface lift (+ fused RK3 stage) */
@@ -275,7 +275,8 @@ enum {
   DG_KERNEL_PROJECT = 7,     /* order projection / restriction */
   DG_KERNEL_SELECT = 8,      /* order selection and degree-jump sweeps */
   DG_KERNEL_EXTRAP = 9,      /* truncation-error extrapolation */
-  DG_KERNEL_KINDS = 10
+  DG_KERNEL_MORTAR = 10,     /* p-nonconforming faces: mortar interpolation, Roe, L2 projection */
+  DG_KERNEL_KINDS = 11
 };
 
 /* Per-kernel timing with CUDA events recorded on the mesh stream around

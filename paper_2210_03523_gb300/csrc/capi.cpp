@@ -1,6 +1,7 @@
 // capi.cpp -- mesh construction (host) and the extern "C" entry points of
 // libdg declared in include/dg.h.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -289,11 +290,15 @@ dg_status build(dg_mesh_impl* m) {
   std::stable_sort(faces.begin(), faces.end(), [](const FaceRec& a, const FaceRec& b) { return a.kind < b.kind; });
   m->n_face_conf = m->n_face_mortar = m->n_face_bnd = 0;
   for (auto& f : faces) (f.kind == 0 ? m->n_face_conf : f.kind == 1 ? m->n_face_mortar : m->n_face_bnd)++;
-  // p-nonconforming faces leave the warp-per-face list: batched by shape
+  // p-nonconforming faces leave the warp-per-face list: batched by shape.  On
+  // affine Euler meshes the conforming interior faces join them: the batched
+  // kernel keeps every lane busy, while one warp per face leaves lanes idle
+  // whenever a face has not a multiple of 32 nodes.
   std::map<std::tuple<int, int, int, int>, std::vector<int32_t>> msig;
   std::vector<FaceRec> wfaces;
+  const bool batch_conforming = !ns && m->affine;
   for (auto& f : faces) {
-    if (f.kind != 1) {
+    if (!(f.kind == 1 || (f.kind == 0 && batch_conforming))) {
       wfaces.push_back(f);
       continue;
     }
@@ -315,6 +320,17 @@ dg_status build(dg_mesh_impl* m) {
     const int nm = std::max(la, ra) * std::max(lb, rb);
     const int per = std::max(1, kTileNodes / nm);
     const int nf = (int)kv.second.size() / 3;
+    // faces of one direction together: the axis-aligned Roe flux branches on
+    // the direction, so a warp that spans two directions runs both variants
+    {
+      std::vector<std::array<int32_t, 3>> fs(nf);
+      for (int i = 0; i < nf; ++i) fs[i] = {kv.second[3 * i], kv.second[3 * i + 1], kv.second[3 * i + 2]};
+      std::stable_sort(fs.begin(), fs.end(), [](const std::array<int32_t, 3>& a, const std::array<int32_t, 3>& b) {
+        return a[2] < b[2];
+      });
+      for (int i = 0; i < nf; ++i)
+        for (int k = 0; k < 3; ++k) kv.second[3 * i + k] = fs[i][k];
+    }
     for (int i = 0; i < nf; i += per) {
       const int cnt = std::min(per, nf - i);
       mbatches.insert(mbatches.end(), {(int32_t)(mfaces.size() / 3), cnt, la, lb, ra, rb});

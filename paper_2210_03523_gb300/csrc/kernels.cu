@@ -138,7 +138,8 @@ __device__ void roe_t(double gamma, const double qL[5], const double qR[5], cons
   const double l1a1 = fabs(utn - ct) * a1, l5a5 = fabs(utn + ct) * a5, l2 = fabs(utn);
   double dut[3], utdut = 0.0;
   for (int c = 0; c < 3; ++c) {
-    dut[c] = (uR[c] - uL[c]) - dun * ncomp<AX>(n, c);
+    // tangential velocity jump; on an axis normal only component AX has a normal part
+    dut[c] = (AX < 0 || c == AX) ? (uR[c] - uL[c]) - dun * ncomp<AX>(n, c) : uR[c] - uL[c];
     utdut += ut[c] * dut[c];
   }
   const double mL = qL[0] * unL, mR = qR[0] * unR;
@@ -1619,9 +1620,11 @@ cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* gra
     FaceParams P = dgk_face_params_for(m, q, surf);
     P.grad = grad;
     const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+    Prof pr(m, DG_KERNEL_FACE_FLUX);
     if ((err = dispatch_face(m, P, 0, grid))) return err;
   }
   if (m->n_mbatches) {
+    Prof pr(m, DG_KERNEL_MORTAR);
     MortarParams M;
     M.m = view(m);
     M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
@@ -1703,7 +1706,6 @@ static FaceParams face_params(dg_mesh_impl* m, const double* q, const double* gr
 
 cudaError_t face_flux(dg_mesh_impl* m, const double* q, const double* grad, bool isolated) {
   (void)isolated;
-  Prof pr(m, DG_KERNEL_FACE_FLUX, (m->n_faces ? 1 : 0) + (m->n_mbatches ? 1 : 0));
   return launch_all_faces(m, q, grad, m->d_surf);
 }
 
@@ -1980,7 +1982,7 @@ extern "C" dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double*
   size_t vsmem = 0;
   int vgrid = 0;
   if (dispatch_volume(mesh, V, vsmem, vgrid) != cudaSuccess) return DG_ERR_CUDA;
-  mesh->launches += (int64_t)mesh->vol_classes.size() + (mesh->n_faces ? 1 : 0) + (mesh->n_mbatches ? 1 : 0);
+  mesh->launches += (int64_t)mesh->vol_classes.size();   // the face launches count themselves
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
 }
 

@@ -25,7 +25,7 @@ DG_EXTRAP_DECOUPLED = 0x1
 DG_EXTRAP_ACCUM_MAX = 0x2
 DG_ADVANCE_EAGER = 0x1
 KERNELS = {"face_flux": 0, "face_qhat": 1, "gradient": 2, "volume": 3, "max_dt": 4, "tau": 5, "tau_combine": 6,
-           "project": 7, "select": 8, "extrap": 9}
+           "project": 7, "select": 8, "extrap": 9, "mortar": 10}
 STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_NOMEM", 3: "DG_ERR_CUDA", 4: "DG_ERR_UNSUPPORTED",
           5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_TIMEOUT"}
 
