@@ -122,8 +122,9 @@ ROE_FLOPS = 160   # one Roe flux through an axis-aligned unit normal, counted be
 def mortar_counts(mi):
     """Algorithmic FP64 flops and HBM bytes of one mortar-kernel launch.
 
-    For every interior face whose two sides differ in a tangential order
-    (la x lb and ra x rb nodes, mortar Ma x Mb = max per direction):
+    For every interior face in the launch (on straight-sided Euler meshes the
+    conforming faces too, with no interpolation) with la x lb and ra x rb
+    nodes and mortar Ma x Mb = max per direction:
     interpolation of the 5 trace variables up to the mortar, per side and
     tangential direction where the side is coarser (2 * 5 * taps flops per
     output node), Roe at the Ma*Mb mortar nodes (ROE_FLOPS each: velocities
@@ -140,8 +141,6 @@ def mortar_counts(mi):
         L = np.flatnonzero(nb[:, 2 * d + 1] >= 0)
         R = nb[L, 2 * d + 1]
         la, lb, ra, rb = o[L, t0], o[L, t1], o[R, t0], o[R, t1]
-        mort = (la != ra) | (lb != rb)
-        la, lb, ra, rb = la[mort], lb[mort], ra[mort], rb[mort]
         Ma, Mb = np.maximum(la, ra), np.maximum(lb, rb)
         for a, b in ((la, lb), (ra, rb)):
             up_a, up_b = a != Ma, b != Mb

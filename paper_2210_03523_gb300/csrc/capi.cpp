@@ -339,6 +339,28 @@ dg_status build(dg_mesh_impl* m) {
     }
   }
   m->n_mbatches = (int)mbatches.size() / 6;
+  // largest batches first: the kernel runs one CTA per batch, and the block
+  // scheduler then fills the tail with the small ones
+  {
+    auto cost = [&](int b) {
+      const int32_t* B = &mbatches[6 * b];
+      const long la = B[2], lb = B[3], ra = B[4], rb = B[5];
+      const long Ma = std::max(la, ra), Mb = std::max(lb, rb);
+      long c = Ma * Mb * 165;
+      for (int s = 0; s < 2; ++s) {
+        const long a = s ? ra : la, bb = s ? rb : lb;
+        c += 20 * a * Ma * bb * (a != Ma) + 20 * bb * Ma * Mb * (bb != Mb);
+      }
+      return c * B[1];
+    };
+    std::vector<int> order(m->n_mbatches);
+    for (int b = 0; b < m->n_mbatches; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<int32_t> sorted(mbatches.size());
+    for (int b = 0; b < m->n_mbatches; ++b)
+      std::copy(mbatches.begin() + 6 * order[b], mbatches.begin() + 6 * order[b] + 6, sorted.begin() + 6 * b);
+    mbatches.swap(sorted);
+  }
   // mortars are implemented for affine Euler meshes; elsewhere only the
   // element-local (isolated) operations are available
   m->faces_unsupported = m->n_face_mortar > 0 && (ns || !m->affine);
@@ -413,6 +435,14 @@ dg_status build(dg_mesh_impl* m) {
       if (tile <= 400) { vs.push_back(i); Ss = std::max(Ss, tile); }
       else { vl.push_back(i); Sl = std::max(Sl, tile); }
     }
+    // largest tiles first (one CTA per tile; see the mortar batches)
+    auto vcost = [&](int i) {
+      const WorkItem& w = items[i];
+      const long n = (long)(w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
+      return w.count * n * (134 + 10 * (w.n1 + w.n2 + w.n3 + 3));
+    };
+    for (auto* v : {&vs, &vl})
+      std::stable_sort(v->begin(), v->end(), [&](int a, int b) { return vcost(a) > vcost(b); });
     for (int k = 0; k < 2; ++k) {
       auto& v = k ? vl : vs;
       if (v.empty()) continue;

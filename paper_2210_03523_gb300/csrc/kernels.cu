@@ -1634,7 +1634,7 @@ cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* gra
     M.surf = surf;
     M.basis = m->basis64;
     const size_t smem = sizeof(double) * m->mortar_smem;
-    const int grid = grid_for(m->n_mbatches, 8);
+    const int grid = m->n_mbatches;   // one CTA per batch, largest first
     if (m->axis) {
       if ((err = allow_smem(mortar_kernel<true>, smem))) return err;
       mortar_kernel<true><<<grid, kVolThreads, smem, m->stream>>>(M);
@@ -1662,7 +1662,7 @@ cudaError_t dispatch_volume(dg_mesh_impl* m, const VolParams& P0, size_t, int) {
     VolParams P = P0;
     P.ilist = c.d_list;
     P.n_items = c.n;
-    if ((err = dispatch_volume_one(m, P, sizeof(double) * 20 * c.S, grid_for(c.n, 8)))) return err;
+    if ((err = dispatch_volume_one(m, P, sizeof(double) * 20 * c.S, c.n))) return err;   // one CTA per tile
   }
   return cudaSuccess;
 }
