@@ -268,6 +268,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def fp32_tau_check(m, q, sweep):
+    """The FP32 sweep against the FP64 sweep on the same state (outside the
+    timed regions): the largest |tau32 - tau64|, the FP32 value where FP64 is
+    exactly zero (the FP32 noise floor), and the fraction of elements whose
+    selection (approach 2, no jump rule) changes at each tau_max of the
+    paper's range (Sec. 3.1)."""
+    from paper_2210_03523_gb300 import dg
+    try:
+        m64, _ = m.tau_estimate(q, sweep, isolated=True, fp32=False, want=(True, False))
+    except dg.DGError as e:       # FP64 tiles above the shared-memory limit (orders 8)
+        return {"unavailable": str(e)}
+    m32, _ = m.tau_estimate(q, sweep, isolated=True, fp32=True, want=(True, False))
+    a64, a32 = m64.cpu().numpy(), m32.double().cpu().numpy()
+    valid = a64 >= 0
+    err = np.abs(a32 - a64)[valid]
+    zero = valid & (a64 == 0.0)      # exact zeros in FP64 (elements the pulse has not reached)
+    changed = {}
+    for tm in (1e-3, 1e-2, 1e-1, 1.0):
+        s64 = m.select_orders(m64, sweep, tm, 1, 8, 0)
+        s32 = m.select_orders(m32, sweep, tm, 1, 8, 0)
+        changed[f"{tm:g}"] = float((s64 != s32).any(axis=1).mean())
+    return {"max_abs_err": float(err.max()), "map_max": float(a64[valid].max()),
+            "max_abs_err_over_map_max": float(err.max() / a64[valid].max()),
+            "fp32_noise_floor": float(a32[zero].max()) if zero.any() else None,
+            "selection_changed_fraction": changed, "eps32": 2.0 ** -23}
+
+
 # ------------------------------------------------------------ our arm
 def run_gb300(args, rank, world):
     import torch
@@ -390,6 +417,7 @@ def run_gb300(args, rank, world):
     t0 = time.perf_counter()
     sel = m.select_orders(map_new, sweep, 1.0, 1, 8, 2)
     select_ms = (time.perf_counter() - t0) * 1e3
+    fp32_check = fp32_tau_check(m, q, sweep)
 
     # roofline of the dominant kernel (by share of the profiled step) and of the volume kernel
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
@@ -453,6 +481,7 @@ def run_gb300(args, rank, world):
                          "frac": (tflops / (tau_k_ms / tau_k_n * 1e-3) / 1e12 / fp32_peak) if tau_k_n else None,
                          "peak_source": f"FP32: {N_SM} SMs x {FP32_FMA_PER_CLK_PER_SM} FFMA/clk x 2 x {sm_mhz:.0f} MHz"},
         "kernels": kernels_json,
+        "fp32_tau_check": fp32_check,
         "select_orders": {"ms": select_ms, "tau_max": 1.0, "jump_rule": "N_i >= N_j - 1",
                           "mean_order_after": float(np.mean(sel)), "synchronous_host_call": True},
         "e2e": {"value": job_value(world, ndof, res_per_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
