@@ -174,7 +174,12 @@ dg_status dg_rk_step(dg_mesh* mesh, double* q, double* g, const double* dt_dev);
  * infinity norm over the element's nodes and all five variables if
  * N_s <= P_e componentwise, else -1.
  *   q: device state (q^P); r_p: device state R^P or NULL (then R^P is the
- *      residual of the same variant as R^N, so tau at N = P is exactly 0);
+ *      residual of the same variant as R^N, so tau at N = P is exactly 0).
+ *      The full residual of the time stepper gives the literal variational
+ *      form; the physical time derivative delta_p/delta_t q^P of a dual
+ *      time-stepping integrator gives the dual time-stepping estimate
+ *      (Sec. 2.3 item 2): the time discretisation is linear, so
+ *      delta_p/delta_t (I q^P) = I (delta_p/delta_t q^P);
  *   sweep: host [n_sweep][3]; map_new / map_trad: device [n_elem][n_sweep],
  *      float if DG_TAU_FP32 else double; either may be NULL (not written).
  *   flags: DG_TAU_ISOLATED (element-local residuals; coarse geometry is the

@@ -195,3 +195,34 @@ def test_dynamic_driver_matches_oracle(torch_cuda, rule):
         assert np.array_equal(a, b)
     assert got["steps"] == ref["steps"]
     assert _close(got["q"].cpu().numpy(), ref["q"], got["orders"], 1e-11)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_dual_time_stepping_tau_matches_oracle(torch_cuda, fp32):
+    """The dual time-stepping estimate (Sec. 2.3, item 2) through the C ABI:
+    r_p = BDF2 time derivative of three states of an RK trajectory."""
+    torch = torch_cuda
+    import oracle
+    from paper_2210_03523_gb300 import dg
+    mi, om, q0 = _case(nx=2, lo=2, hi=4, seed=12, width=0.4)
+    m = dg.Mesh(mi)
+    dt = 2e-3
+    qs = [q0.copy()]
+    q, G = q0.copy(), np.zeros_like(q0)
+    for _ in range(2):
+        om.rk_step(q, G, dt)
+        qs.append(q.copy())
+    bdf2 = (3.0 * qs[2] - 4.0 * qs[1] + qs[0]) / (2.0 * dt)
+    sweep = I.full_sweep((4, 4, 4))
+    ref, _ = om.tau(qs[2], sweep, rP=bdf2)
+    got, _ = m.tau_estimate(torch.from_numpy(qs[2]).cuda(), sweep, fp32=fp32, r_p=torch.from_numpy(bdf2).cuda(),
+                            want=(True, False))
+    from test_gpu_parity import _fp32_scale, _tau_tol
+    g = got.double().cpu().numpy()
+    assert np.array_equal(g < 0, ref < 0)
+    ok = ref >= 0
+    if fp32:      # the FP32 bound of the sweep: 8 eps32 S_e per element
+        d = np.abs(g - ref) / _fp32_scale(om, qs[2], mi)[:, None]
+        assert (d[ok] <= 8 * np.finfo(np.float32).eps).all()
+    else:
+        assert np.abs(g - ref)[ok].max() <= _tau_tol(ref, mi, qs[2], om)

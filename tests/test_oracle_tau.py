@@ -197,3 +197,32 @@ def test_non_isolated_tau(orc):
     for e in interior:
         assert abs(tn[e, 1]) < 1e-11 and abs(tn[e, 2]) < 1e-11
         assert tn[e, 3] > 1e-3 and tn[e, 4] > 1e-3
+
+
+def test_dual_time_stepping_form_converges_to_the_variational_form(orc):
+    """Dual time-stepping estimate (Sec. 2.3, item 2): the steady operator
+    dQ/dt-discretisation + M^{-1} F (new form) gives
+    tau~ = delta_p/delta_t (I q^P) - R^N(I q^P) = I (delta_p/delta_t q^P) - R^N(I q^P)
+    (the time discretisation is linear, so it commutes with I): the tau call
+    with r_p = delta_p/delta_t q^P.  With BDF2 over an RK trajectory of step
+    dt it differs from the variational form with the full R^P (the time
+    stepper's residual) by O(dt^2)."""
+    ph = I.pulse_physics(mach=0.4)
+    mi = I.box_mesh(2, orders=(4, 3, 3), phys=ph)
+    m = orc.Mesh(mi)
+    q0 = I.pulse_state(m.coords(), m.orders, ph, width=0.4, center=(-0.2, 0.1, 0.0))
+    sweep = I.full_sweep((4, 3, 3))
+    diffs = []
+    for dt in (4e-3, 2e-3, 1e-3):
+        qs = [q0.copy()]
+        q, G = q0.copy(), np.zeros_like(q0)
+        for _ in range(2):
+            m.rk_step(q, G, dt)
+            qs.append(q.copy())
+        bdf2 = (3.0 * qs[2] - 4.0 * qs[1] + qs[0]) / (2.0 * dt)
+        dual = m.tau(qs[2], sweep, rP=bdf2)[0]
+        var = m.tau(qs[2], sweep, rP=m.residual(qs[2]))[0]
+        ok = var >= 0
+        diffs.append(np.abs(dual - var)[ok].max() / np.abs(var[ok]).max())
+    rates = [diffs[k] / diffs[k + 1] for k in range(2)]
+    assert all(3.0 < r < 5.0 for r in rates), (diffs, rates)
