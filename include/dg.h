@@ -268,6 +268,46 @@ dg_status dg_tau_extrapolate(dg_mesh* mesh, const void* map, int32_t map_fp32, c
 dg_status dg_advance(dg_mesh* mesh, double* q, double* g, double* t_dev, double t_end, double cfl, int64_t max_steps,
                      uint32_t flags, int64_t* steps_out);
 
+/* Tile shapes (Sec. 2.4: elements of mixed anisotropic orders run in one
+ * launch, bucketed by (N1,N2,N3)).  The volume kernels run one CTA per tile
+ * of same-order elements, at most vol_budget nodes per tile (one element at
+ * least) for the element-size class of the bucket: elements of <= 27, 125,
+ * 343 or more nodes.  The mortar kernel runs one CTA per batch of same-shape
+ * faces, at most mortar_budget mortar nodes per batch for the mortar-size
+ * class: <= 9, 25, 49 or more mortar nodes.  Tiling does not change any
+ * node's arithmetic: results are bitwise the same for every budget. */
+#define DG_SIZE_CLASSES 4
+#define DG_MAX_VOL_BUDGET 1024     /* 20 doubles of shared memory per node: 160 KB */
+#define DG_MAX_MORTAR_BUDGET 512   /* up to 30 doubles per mortar node: 120 KB */
+typedef struct {
+  int32_t vol_budget[DG_SIZE_CLASSES];
+  int32_t mortar_budget[DG_SIZE_CLASSES];
+  double vol_ms[DG_SIZE_CLASSES];             /* dg_autotune: launch time after class k was tuned (-1: empty) */
+  double vol_ms_default[DG_SIZE_CLASSES];     /* ... before */
+  double mortar_ms[DG_SIZE_CLASSES];
+  double mortar_ms_default[DG_SIZE_CLASSES];
+} dg_tiles;
+
+/* Autotuner of the tile shapes, by coordinate descent: for every size class
+ * in turn (volume tiles first, then mortar batches), each candidate budget
+ * (64, 128, 192, 256, 384, 512 nodes) with the other classes held is timed on
+ * the whole production launch (the volume residual, or the face fluxes) on
+ * this mesh and state: CUDA events on the mesh stream, the median of reps
+ * launches after one warm-up.  The fastest is kept and the work lists are
+ * rebuilt.  q: a device state of the mesh (physical, as for dg_residual);
+ * out (host, optional): the chosen budgets; vol_ms[k] / mortar_ms[k] the
+ * launch time after class k was tuned, *_default[k] before (-1: class
+ * empty).  Synchronous.  Cached dg_advance graphs are released.
+ * Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED (as dg_residual), DG_ERR_NOMEM,
+ * DG_ERR_CUDA. */
+dg_status dg_autotune(dg_mesh* mesh, const double* q, int32_t reps, dg_tiles* out);
+/* The budgets in use (times -1). */
+dg_status dg_get_tiles(const dg_mesh* mesh, dg_tiles* out);
+/* Sets the budgets (the times are ignored; volume budgets 1..DG_MAX_VOL_BUDGET,
+ * mortar budgets 1..DG_MAX_MORTAR_BUDGET nodes, else DG_ERR_ARG) and rebuilds
+ * the work lists; releases cached dg_advance graphs.  Synchronous. */
+dg_status dg_set_tiles(dg_mesh* mesh, const dg_tiles* in);
+
 /* Kernel kinds for dg_profile_read. */
 enum {
   DG_KERNEL_FACE_FLUX = 0,   /* Roe (+ BR1 viscous) numerical flux on conforming and boundary faces */

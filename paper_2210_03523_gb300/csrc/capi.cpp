@@ -164,7 +164,8 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 void free_device(dg_mesh_impl* m) {
   void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
                   m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
-                  m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv};
+                  m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv,
+                  m->d_vitems, m->d_velist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
@@ -173,6 +174,8 @@ void free_device(dg_mesh_impl* m) {
   m->d_taugeo = nullptr; m->d_taugeo32 = nullptr; m->d_taugeo_off = nullptr; m->d_rp = nullptr; m->d_qc = nullptr;
   m->d_rc = nullptr; m->d_sweep = nullptr; m->d_mfaces = nullptr; m->d_mbatches = nullptr; m->d_rp32 = nullptr;
   m->d_adv = nullptr;
+  m->d_vitems = nullptr;
+  m->d_velist = nullptr;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
@@ -208,6 +211,109 @@ void destroy_impl(dg_mesh_impl* m) {
   } while (0)
 
 constexpr int kTileNodes = 256;
+
+}  // namespace
+
+// Mortar batches from the shape groups: per group, batches of at most the
+// budget of its mortar-size class in mortar nodes (one face at least),
+// largest batches first (the kernel runs one CTA per batch, and the block
+// scheduler then fills the tail with the small ones).  Uploads the face list
+// and the batch records.
+dg_status build_mortar_batches(dg_mesh_impl* m) {
+  std::vector<int32_t> mfaces, mbatches;
+  m->mortar_smem = 0;
+  for (const auto& g : m->h_mgroups) {
+    const int nm = std::max(g.la, g.ra) * std::max(g.lb, g.rb);
+    const int per = std::max(1, m->mortar_budget[mortar_size_class(nm)] / nm);
+    const int nf = (int)g.faces.size() / 3;
+    for (int i = 0; i < nf; i += per) {
+      const int cnt = std::min(per, nf - i);
+      mbatches.insert(mbatches.end(), {(int32_t)(mfaces.size() / 3), cnt, g.la, g.lb, g.ra, g.rb});
+      mfaces.insert(mfaces.end(), g.faces.begin() + 3 * i, g.faces.begin() + 3 * (i + cnt));
+      m->mortar_smem = std::max(m->mortar_smem, dg_mortar_smem_doubles(cnt, g.la, g.lb, g.ra, g.rb));
+    }
+  }
+  m->n_mbatches = (int)mbatches.size() / 6;
+  auto cost = [&](int b) {
+    const int32_t* B = &mbatches[6 * b];
+    const long la = B[2], lb = B[3], ra = B[4], rb = B[5];
+    const long Ma = std::max(la, ra), Mb = std::max(lb, rb);
+    long c = Ma * Mb * 165;
+    for (int s = 0; s < 2; ++s) {
+      const long a = s ? ra : la, bb = s ? rb : lb;
+      c += 20 * a * Ma * bb * (a != Ma) + 20 * bb * Ma * Mb * (bb != Mb);
+    }
+    return c * B[1];
+  };
+  std::vector<int> order(m->n_mbatches);
+  for (int b = 0; b < m->n_mbatches; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  m->h_mbatches.assign(mbatches.size(), 0);
+  for (int b = 0; b < m->n_mbatches; ++b)
+    std::copy(mbatches.begin() + 6 * order[b], mbatches.begin() + 6 * order[b] + 6, m->h_mbatches.begin() + 6 * b);
+  if (m->d_mfaces) cudaFree(m->d_mfaces);
+  if (m->d_mbatches) cudaFree(m->d_mbatches);
+  m->d_mfaces = nullptr;
+  m->d_mbatches = nullptr;
+  DG_CUDA(upload(&m->d_mfaces, mfaces.data(), mfaces.size()));
+  DG_CUDA(upload(&m->d_mbatches, m->h_mbatches.data(), m->h_mbatches.size()));
+  return DG_OK;
+}
+
+// Volume tiles from the order buckets: per bucket, tiles of at most the budget
+// of its element-size class in nodes (one element at least).
+dg_status build_volume_items(dg_mesh_impl* m) {
+  std::vector<WorkItem> items;
+  std::vector<int32_t> elist;
+  for (size_t b = 0; b < m->h_buckets.size(); ++b) {
+    const int n1 = m->h_bucket_key[b][0], n2 = m->h_bucket_key[b][1], n3 = m->h_bucket_key[b][2];
+    const int n = (n1 + 1) * (n2 + 1) * (n3 + 1);
+    const int per = std::max(1, m->vol_budget[elem_size_class(n)] / n);
+    const auto& els = m->h_buckets[b];
+    for (size_t i = 0; i < els.size(); i += per) {
+      const int cnt = (int)std::min<size_t>(per, els.size() - i);
+      items.push_back({(int32_t)elist.size(), cnt, n1, n2, n3});
+      for (int c = 0; c < cnt; ++c) elist.push_back(els[i + c]);
+    }
+  }
+  m->n_vitems = (int)items.size();
+  m->h_vitems = items;
+  // two launches: tiles up to 400 nodes (<= 64 KB of FP64 shared memory,
+  // three CTAs per SM) and larger ones, so that a few 9^3 elements do not set
+  // the occupancy of all the others; in each, the largest tiles first
+  std::vector<std::vector<int32_t>> cl(2);
+  std::vector<int> cS(2, 0);
+  for (int i = 0; i < (int)items.size(); ++i) {
+    const WorkItem& w = items[i];
+    const int tile = w.count * (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
+    const int k = tile <= 400 ? 0 : 1;
+    cl[k].push_back(i);
+    cS[k] = std::max(cS[k], tile);
+  }
+  auto vcost = [&](int i) {
+    const WorkItem& w = items[i];
+    const long n = (long)(w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
+    return w.count * n * (134 + 10 * (w.n1 + w.n2 + w.n3 + 3));
+  };
+  for (auto& v : cl) std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return vcost(a) > vcost(b); });
+  for (auto& c : m->vol_classes) cudaFree(c.d_list);
+  m->vol_classes.clear();
+  if (m->d_vitems) cudaFree(m->d_vitems);
+  if (m->d_velist) cudaFree(m->d_velist);
+  m->d_vitems = nullptr;
+  m->d_velist = nullptr;
+  DG_CUDA(upload(&m->d_vitems, items.data(), items.size()));
+  DG_CUDA(upload(&m->d_velist, elist.data(), elist.size()));
+  for (int k = 0; k < 2; ++k) {
+    if (cl[k].empty()) continue;
+    dg_mesh_impl::TauClass c{nullptr, (int)cl[k].size(), cS[k]};
+    DG_CUDA(upload(&c.d_list, cl[k].data(), cl[k].size()));
+    m->vol_classes.push_back(c);
+  }
+  return DG_OK;
+}
+
+namespace {
 
 // Build every host and device structure of a mesh from its host arrays.
 dg_status build(dg_mesh_impl* m) {
@@ -312,54 +418,27 @@ dg_status build(dg_mesh_impl* m) {
   }
   faces.swap(wfaces);
   m->n_faces = (int)faces.size();
-  std::vector<int32_t> mfaces, mbatches;
-  m->mortar_smem = 0;
+  // the batched faces by shape, faces of one direction together: the
+  // axis-aligned Roe flux branches on the direction, so a warp that spans
+  // two directions runs both variants
+  m->h_mgroups.clear();
   for (auto& kv : msig) {
-    int la, lb, ra, rb;
-    std::tie(la, lb, ra, rb) = kv.first;
-    const int nm = std::max(la, ra) * std::max(lb, rb);
-    const int per = std::max(1, kTileNodes / nm);
+    dg_mesh_impl::MGroup g;
+    std::tie(g.la, g.lb, g.ra, g.rb) = kv.first;
     const int nf = (int)kv.second.size() / 3;
-    // faces of one direction together: the axis-aligned Roe flux branches on
-    // the direction, so a warp that spans two directions runs both variants
-    {
-      std::vector<std::array<int32_t, 3>> fs(nf);
-      for (int i = 0; i < nf; ++i) fs[i] = {kv.second[3 * i], kv.second[3 * i + 1], kv.second[3 * i + 2]};
-      std::stable_sort(fs.begin(), fs.end(), [](const std::array<int32_t, 3>& a, const std::array<int32_t, 3>& b) {
-        return a[2] < b[2];
-      });
-      for (int i = 0; i < nf; ++i)
-        for (int k = 0; k < 3; ++k) kv.second[3 * i + k] = fs[i][k];
-    }
-    for (int i = 0; i < nf; i += per) {
-      const int cnt = std::min(per, nf - i);
-      mbatches.insert(mbatches.end(), {(int32_t)(mfaces.size() / 3), cnt, la, lb, ra, rb});
-      mfaces.insert(mfaces.end(), kv.second.begin() + 3 * i, kv.second.begin() + 3 * (i + cnt));
-      m->mortar_smem = std::max(m->mortar_smem, dg_mortar_smem_doubles(cnt, la, lb, ra, rb));
-    }
+    std::vector<std::array<int32_t, 3>> fs(nf);
+    for (int i = 0; i < nf; ++i) fs[i] = {kv.second[3 * i], kv.second[3 * i + 1], kv.second[3 * i + 2]};
+    std::stable_sort(fs.begin(), fs.end(), [](const std::array<int32_t, 3>& a, const std::array<int32_t, 3>& b) {
+      return a[2] < b[2];
+    });
+    g.faces.resize(3 * (size_t)nf);
+    for (int i = 0; i < nf; ++i)
+      for (int k = 0; k < 3; ++k) g.faces[3 * i + k] = fs[i][k];
+    m->h_mgroups.push_back(std::move(g));
   }
-  m->n_mbatches = (int)mbatches.size() / 6;
-  // largest batches first: the kernel runs one CTA per batch, and the block
-  // scheduler then fills the tail with the small ones
   {
-    auto cost = [&](int b) {
-      const int32_t* B = &mbatches[6 * b];
-      const long la = B[2], lb = B[3], ra = B[4], rb = B[5];
-      const long Ma = std::max(la, ra), Mb = std::max(lb, rb);
-      long c = Ma * Mb * 165;
-      for (int s = 0; s < 2; ++s) {
-        const long a = s ? ra : la, bb = s ? rb : lb;
-        c += 20 * a * Ma * bb * (a != Ma) + 20 * bb * Ma * Mb * (bb != Mb);
-      }
-      return c * B[1];
-    };
-    std::vector<int> order(m->n_mbatches);
-    for (int b = 0; b < m->n_mbatches; ++b) order[b] = b;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    std::vector<int32_t> sorted(mbatches.size());
-    for (int b = 0; b < m->n_mbatches; ++b)
-      std::copy(mbatches.begin() + 6 * order[b], mbatches.begin() + 6 * order[b] + 6, sorted.begin() + 6 * b);
-    mbatches.swap(sorted);
+    dg_status st = build_mortar_batches(m);
+    if (st != DG_OK) return st;
   }
   // mortars are implemented for affine Euler meshes; elsewhere only the
   // element-local (isolated) operations are available
@@ -367,6 +446,12 @@ dg_status build(dg_mesh_impl* m) {
   // work items: elements bucketed by order triple
   std::map<std::tuple<int, int, int>, std::vector<int32_t>> buckets;
   for (int e = 0; e < ne; ++e) buckets[{m->h_ord[3 * e], m->h_ord[3 * e + 1], m->h_ord[3 * e + 2]}].push_back(e);
+  m->h_bucket_key.clear();
+  m->h_buckets.clear();
+  for (auto& kv : buckets) {
+    m->h_bucket_key.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first)});
+    m->h_buckets.push_back(kv.second);
+  }
   std::vector<WorkItem> items;
   std::vector<int32_t> elist;
   m->item_max_nodes = 1;
@@ -396,8 +481,6 @@ dg_status build(dg_mesh_impl* m) {
     DG_CUDA(upload(&m->d_metric32, m32.data(), m32.size()));
   }
   DG_CUDA(upload(&m->d_faces, faces.data(), faces.size()));
-  DG_CUDA(upload(&m->d_mfaces, mfaces.data(), mfaces.size()));
-  DG_CUDA(upload(&m->d_mbatches, mbatches.data(), mbatches.size()));
   DG_CUDA(upload(&m->d_items, items.data(), items.size()));
   DG_CUDA(upload(&m->d_elist, elist.data(), elist.size()));
   DG_CUDA(upload<double>(&m->d_surf, nullptr, 5 * (size_t)m->h_soff[ne]));
@@ -425,31 +508,10 @@ dg_status build(dg_mesh_impl* m) {
       DG_CUDA(upload(&c.d_list, cls[k].data(), cls[k].size()));
       m->tau_classes.push_back(c);
     }
-    // volume kernels: tiles up to 400 nodes (<= 64 KB of FP64 shared memory,
-    // three CTAs per SM) in one launch, larger tiles in a second one
-    std::vector<int32_t> vs, vl;
-    int Ss = 0, Sl = 0;
-    for (int i = 0; i < (int)items.size(); ++i) {
-      const WorkItem& w = items[i];
-      const int tile = w.count * (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
-      if (tile <= 400) { vs.push_back(i); Ss = std::max(Ss, tile); }
-      else { vl.push_back(i); Sl = std::max(Sl, tile); }
-    }
-    // largest tiles first (one CTA per tile; see the mortar batches)
-    auto vcost = [&](int i) {
-      const WorkItem& w = items[i];
-      const long n = (long)(w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
-      return w.count * n * (134 + 10 * (w.n1 + w.n2 + w.n3 + 3));
-    };
-    for (auto* v : {&vs, &vl})
-      std::stable_sort(v->begin(), v->end(), [&](int a, int b) { return vcost(a) > vcost(b); });
-    for (int k = 0; k < 2; ++k) {
-      auto& v = k ? vl : vs;
-      if (v.empty()) continue;
-      dg_mesh_impl::TauClass c{nullptr, (int)v.size(), k ? Sl : Ss};
-      DG_CUDA(upload(&c.d_list, v.data(), v.size()));
-      m->vol_classes.push_back(c);
-    }
+  }
+  {
+    dg_status st = build_volume_items(m);
+    if (st != DG_OK) return st;
   }
   DG_CUDA(upload<unsigned>(&m->d_err, nullptr, 1));
   DG_CUDA(cudaMemset(m->d_err, 0, sizeof(unsigned)));
@@ -571,6 +633,8 @@ dg_mesh_impl* make_child(const dg_mesh_impl* m, const std::vector<int32_t>& orde
   c->h_geom = m->h_geom;
   c->h_nbr = m->h_nbr;
   c->h_ord = orders;
+  std::copy(m->vol_budget, m->vol_budget + kSizeClasses, c->vol_budget);   // tuned budgets carry over
+  std::copy(m->mortar_budget, m->mortar_budget + kSizeClasses, c->mortar_budget);
   *st = build(c);
   if (*st != DG_OK) {
     destroy_impl(c);

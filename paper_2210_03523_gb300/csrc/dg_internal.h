@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <vector>
 
 #include "../../include/dg.h"
@@ -57,6 +58,12 @@ struct WorkItem {
 
 struct dg_mesh_impl;
 
+// size classes of the tuned tile budgets: elements by node count, mortars by
+// mortar nodes (<= 27 / 125 / 343 / more; <= 9 / 25 / 49 / more)
+constexpr int kSizeClasses = DG_SIZE_CLASSES;
+inline int elem_size_class(int n) { return n <= 27 ? 0 : n <= 125 ? 1 : n <= 343 ? 2 : 3; }
+inline int mortar_size_class(int nm) { return nm <= 9 ? 0 : nm <= 25 ? 1 : nm <= 49 ? 2 : 3; }
+
 // shared memory (doubles) of a batch of `count` mortar faces of one shape
 size_t dg_mortar_smem_doubles(int count, int la, int lb, int ra, int rb);
 
@@ -87,6 +94,10 @@ size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32);
 // (as the bit pattern of a non-negative double)
 cudaError_t max_dt_bits(dg_mesh_impl* m, const double* q, unsigned long long* bits);
 }  // namespace dgk
+
+// work-list (re)builders with the mesh's tile budgets (capi.cpp)
+dg_status build_volume_items(dg_mesh_impl* m);
+dg_status build_mortar_batches(dg_mesh_impl* m);
 
 // releases the dg_advance graphs and capture stream of a mesh
 void dg_advance_release(dg_mesh_impl* m);
@@ -128,9 +139,22 @@ struct dg_mesh_impl {
   int32_t* d_mbatches = nullptr;   // mortar batches [first, count, la, lb, ra, rb]
   int n_mbatches = 0;
   size_t mortar_smem = 0;          // doubles of shared memory of the largest batch
-  WorkItem* d_items = nullptr;
+  WorkItem* d_items = nullptr;     // tiles of <= 256 nodes (tau sweep)
   int32_t* d_elist = nullptr;
   int n_items = 0;
+  // volume / gradient / CFL tiles, with a node budget per element-size class
+  // (dg_autotune), and the mortar batches' budget per mortar-size class
+  int vol_budget[kSizeClasses] = {256, 256, 256, 256};
+  int mortar_budget[kSizeClasses] = {256, 256, 256, 256};
+  WorkItem* d_vitems = nullptr;
+  int32_t* d_velist = nullptr;
+  int n_vitems = 0;
+  std::vector<WorkItem> h_vitems;
+  std::vector<std::array<int, 3>> h_bucket_key;    // order triples
+  std::vector<std::vector<int32_t>> h_buckets;     // their elements
+  struct MGroup { int la, lb, ra, rb; std::vector<int32_t> faces; };
+  std::vector<MGroup> h_mgroups;                   // batched faces [L, R, dir] by shape, sorted by direction
+  std::vector<int32_t> h_mbatches;                 // [first, count, la, lb, ra, rb] per batch, as uploaded
   int item_max_nodes = 0;          // max count*n over items (smem sizing)
   unsigned* d_err = nullptr;       // sticky error word
   double* d_scratch = nullptr;     // dt reduction

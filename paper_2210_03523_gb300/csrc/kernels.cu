@@ -1568,9 +1568,9 @@ VolParams dgk_vol_params_for(dg_mesh_impl* m, const double* q, const double* sur
   VolParams P;
   memset(&P, 0, sizeof(P));
   P.m = view(m);
-  P.items = m->d_items;
-  P.n_items = m->n_items;
-  P.elist = m->d_elist;
+  P.items = m->d_vitems;
+  P.n_items = m->n_vitems;
+  P.elist = m->d_velist;
   P.q = q;
   P.surf = surf;
   P.basis = m->basis64;
@@ -1723,9 +1723,9 @@ static VolParams vol_params(dg_mesh_impl* m, const double* q) {
   VolParams P;
   memset(&P, 0, sizeof(P));
   P.m = view(m);
-  P.items = m->d_items;
-  P.n_items = m->n_items;
-  P.elist = m->d_elist;
+  P.items = m->d_vitems;
+  P.n_items = m->n_vitems;
+  P.elist = m->d_velist;
   P.q = q;
   P.grad = m->d_grad;
   P.surf = m->d_surf;
@@ -1783,7 +1783,7 @@ cudaError_t max_dt_bits(dg_mesh_impl* m, const double* q, unsigned long long* bi
   VolParams P = vol_params(m, q);
   cudaError_t err = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), m->stream);
   if (err) return err;
-  int grid = grid_for(m->n_items, 8);
+  int grid = grid_for(m->n_vitems, 8);
   Prof pr(m, DG_KERNEL_MAX_DT, 1);
   if (m->axis) dt_kernel<true, true><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
   else if (m->affine) dt_kernel<true, false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);

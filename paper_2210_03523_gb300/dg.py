@@ -46,6 +46,16 @@ class dg_mesh_desc(C.Structure):
                 ("neighbors", C.POINTER(C.c_int32)), ("orders", C.POINTER(C.c_int32)), ("phys", dg_physics)]
 
 
+class dg_tiles(C.Structure):
+    _fields_ = [("vol_budget", C.c_int32 * 4), ("mortar_budget", C.c_int32 * 4), ("vol_ms", C.c_double * 4),
+                ("vol_ms_default", C.c_double * 4), ("mortar_ms", C.c_double * 4),
+                ("mortar_ms_default", C.c_double * 4)]
+
+
+def _tiles_dict(t):
+    return {k: list(getattr(t, k)) for k, _ in dg_tiles._fields_}
+
+
 _L = None
 
 
@@ -72,6 +82,9 @@ def _lib():
             "dg_tau_extrapolate": [vp, vp, C.c_int32, i32p, C.c_int32, i32p, C.c_int32, C.c_int32, C.c_double,
                                    C.c_uint32, vp],
             "dg_advance": [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int64, C.c_uint32, i64p],
+            "dg_autotune": [vp, vp, C.c_int32, C.POINTER(dg_tiles)],
+            "dg_get_tiles": [vp, C.POINTER(dg_tiles)],
+            "dg_set_tiles": [vp, C.POINTER(dg_tiles)],
             "dg_max_dt": [vp, vp, C.c_double, vp],
             "dg_rk_step": [vp, vp, vp, vp],
             "dg_tau_estimate": [vp, vp, vp, i32p, C.c_int32, C.c_uint32, vp, vp],
@@ -93,7 +106,7 @@ def exported_symbols():
     return ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_count_nodes", "dg_set_stream", "dg_node_coords",
             "dg_residual", "dg_max_dt", "dg_rk_step", "dg_tau_estimate", "dg_set_orders", "dg_get_error",
             "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc",
-            "dg_select_orders", "dg_tau_extrapolate", "dg_advance"]
+            "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles"]
 
 
 def _check(st, where):
@@ -290,6 +303,25 @@ class Mesh:
         _check(_lib().dg_advance(self.h, _ptr(q), _ptr(g), _ptr(t), float(t_end), float(cfl), int(max_steps),
                                  DG_ADVANCE_EAGER if eager else 0, C.byref(n) if count else None), "dg_advance")
         return n.value if count else None
+
+    def autotune(self, q, reps=5):
+        """dg_autotune: time each tile budget per size class on this mesh and
+        state, keep the fastest; returns the report as a dict."""
+        self._check_state(q)
+        t = dg_tiles()
+        _check(_lib().dg_autotune(self.h, _ptr(q), int(reps), C.byref(t)), "dg_autotune")
+        return _tiles_dict(t)
+
+    def tiles(self):
+        t = dg_tiles()
+        _check(_lib().dg_get_tiles(self.h, C.byref(t)), "dg_get_tiles")
+        return _tiles_dict(t)
+
+    def set_tiles(self, vol_budget, mortar_budget):
+        t = dg_tiles()
+        t.vol_budget[:] = [int(x) for x in vol_budget]
+        t.mortar_budget[:] = [int(x) for x in mortar_budget]
+        _check(_lib().dg_set_tiles(self.h, C.byref(t)), "dg_set_tiles")
 
     def _check_state(self, *states):
         """State-layout device tensors: float64, contiguous, 5 * n_nodes values."""
