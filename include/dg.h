@@ -308,6 +308,28 @@ dg_status dg_get_tiles(const dg_mesh* mesh, dg_tiles* out);
  * the work lists; releases cached dg_advance graphs.  Synchronous. */
 dg_status dg_set_tiles(dg_mesh* mesh, const dg_tiles* in);
 
+/* Adjoint (vector-Jacobian product) of the residual: out = (dR/dq)^T v at the
+ * state q, for Euler on straight-sided (affine) elements with conforming,
+ * p-nonconforming (mortar) and boundary faces.  R = A Phi(q), Phi the
+ * pointwise fluxes (contravariant volume flux, Roe at face and mortar
+ * nodes) and A linear (GL derivative, surface lift, mortar interpolation and
+ * L2 projection, -1/J): the kernels apply A^T and then the flux Jacobians'
+ * transposes, taken exactly by forward-mode differentiation of the same
+ * flux code (Dual numbers).  q, v, out: device state-layout arrays; out may
+ * not alias q or v.  Asynchronous.
+ * Errors: DG_ERR_ARG; DG_ERR_UNSUPPORTED (Navier-Stokes, curved elements, or
+ * mortar batches whose adjoint exceeds shared memory); DG_ERR_CUDA. */
+dg_status dg_residual_vjp(dg_mesh* mesh, const double* q, const double* v, double* out);
+
+/* Adjoint of one Williamson RK3 step (dg_rk_step) from the state q0 at the
+ * step's start: lam <- (dq1/dq0)^T lam, with dt (the device scalar dt_dev)
+ * held fixed.  The stage states are recomputed from q0; then, with
+ * G_k = A_k G_{k-1} + dt R(Q_{k-1}) and Q_k = Q_{k-1} + B_k G_k reversed:
+ * LG = B3 lam, lam += dt J(Q2)^T LG; LG = A3 LG + B2 lam, lam += dt J(Q1)^T LG;
+ * LG = A2 LG + B1 lam, lam += dt J(q0)^T LG.  The mesh holds four states of
+ * workspace.  Same support and errors as dg_residual_vjp. */
+dg_status dg_rk_step_vjp(dg_mesh* mesh, const double* q0, const double* dt_dev, double* lam);
+
 /* Kernel kinds for dg_profile_read. */
 enum {
   DG_KERNEL_FACE_FLUX = 0,   /* Roe (+ BR1 viscous) numerical flux on conforming and boundary faces */
@@ -321,7 +343,8 @@ enum {
   DG_KERNEL_SELECT = 8,      /* order selection and degree-jump sweeps */
   DG_KERNEL_EXTRAP = 9,      /* truncation-error extrapolation */
   DG_KERNEL_MORTAR = 10,     /* p-nonconforming faces: mortar interpolation, Roe, L2 projection */
-  DG_KERNEL_KINDS = 11
+  DG_KERNEL_ADJOINT = 11,    /* residual / RK3 vector-Jacobian products */
+  DG_KERNEL_KINDS = 12
 };
 
 /* Per-kernel timing with CUDA events recorded on the mesh stream around

@@ -69,6 +69,8 @@ def lib():
                                         C.c_int, ip]
         L.orc_tau_extrapolate.argtypes = [C.c_int, ip, C.c_int, ip, dp, C.c_int, ip, C.c_int, C.c_double, C.c_int,
                                           C.c_int, dp]
+        L.orc_residual_vjp_fd.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_int, dp]
+        L.orc_rk_step_vjp_fd.argtypes = [C.c_void_p, dp, C.c_double, dp, C.c_double, dp]
         L.orc_advance.restype = C.c_int
         L.orc_advance.argtypes = [C.c_void_p, dp, dp, C.c_double, dp, C.c_double, C.c_int]
         _lib = L
@@ -223,6 +225,20 @@ class Mesh:
         rp = _d(_f64(rP)) if rP is not None else None
         lib().orc_tau(self.h, _d(q), rp, _i(sweep), ns, int(isolated), int(accumulate is not None), _d(tn), _d(tt))
         return tn, tt
+
+    def residual_vjp_fd(self, q, v, eps=1e-3, isolated=False):
+        """(dR/dq)^T v by fourth-order central differences of every Jacobian column."""
+        q, v = _f64(q), _f64(v)
+        out = np.empty_like(q)
+        lib().orc_residual_vjp_fd(self.h, _d(q), _d(v), float(eps), int(isolated), _d(out))
+        return out
+
+    def rk_step_vjp_fd(self, q, dt, lam, eps=1e-3):
+        """(d step(q)/dq)^T lam for one RK3 step of size dt, the same way."""
+        q, lam = _f64(q), _f64(lam)
+        out = np.empty_like(q)
+        lib().orc_rk_step_vjp_fd(self.h, _d(q), float(dt), _d(lam), float(eps), _d(out))
+        return out
 
     def isolated_residual_at(self, e, N, qN):
         N = _i32(N)

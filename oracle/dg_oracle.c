@@ -1326,3 +1326,79 @@ void orc_tau_extrapolate(int n_elem, const int* orders, int n_sweep, const int* 
     }
   }
 }
+
+/* ------------------------------------------------------------------------
+ * The discrete adjoint by brute force, the reference for the adjoint
+ * (vector-Jacobian product) kernels: every column of the Jacobian of the
+ * residual, or of one RK3 step with dt held fixed, by fourth-order central
+ * differences of this file's own functions,
+ *   J e_k = (-F(q + 2h e_k) + 8 F(q + h e_k) - 8 F(q - h e_k) + F(q - 2h e_k)) / (12 h),
+ * then out_k = v . J e_k.  Column k steps by h = eps * s, s the largest |q|
+ * of the column's variable over the mesh (a zero component still gets a
+ * sensible step).  The error is O(h^4) plus rounding of order 1e-16 / eps.
+ * ---------------------------------------------------------------------- */
+static void var_of_dof(const omesh* m, int* var, double s[NV], const double* q) {
+  for (int v = 0; v < NV; ++v) s[v] = 0.0;
+  for (int e = 0; e < m->n_elem; ++e) {
+    const long n = m->off[e + 1] - m->off[e];
+    for (int v = 0; v < NV; ++v)
+      for (long p = 0; p < n; ++p) {
+        const long k = NV * m->off[e] + v * n + p;
+        var[k] = v;
+        if (fabs(q[k]) > s[v]) s[v] = fabs(q[k]);
+      }
+  }
+  for (int v = 0; v < NV; ++v) if (s[v] == 0.0) s[v] = 1.0;
+}
+
+/* which: 0 residual, 1 isolated residual, 2 one RK3 step of size dt */
+static void fd_apply(void* h, int which, double dt, const double* x, double* y, double* G, long ns) {
+  if (which == 2) {
+    memcpy(y, x, sizeof(double) * ns);
+    memset(G, 0, sizeof(double) * ns);
+    orc_rk_step(h, y, G, dt);
+  } else {
+    orc_residual(h, x, y, which);
+  }
+}
+
+static void fd_vjp(void* h, int which, double dt, const double* q, const double* v, double eps, double* out) {
+  omesh* m = h;
+  const long ns = NV * m->off[m->n_elem];
+  int* var = malloc(sizeof(int) * ns);
+  double s[NV];
+  var_of_dof(m, var, s, q);
+  #pragma omp parallel
+  {
+    double* x = malloc(sizeof(double) * ns);
+    double* y = malloc(sizeof(double) * ns);
+    double* G = malloc(sizeof(double) * ns);
+    double* col = malloc(sizeof(double) * ns);
+    memcpy(x, q, sizeof(double) * ns);
+    #pragma omp for schedule(dynamic, 4)
+    for (long k = 0; k < ns; ++k) {
+      const double hk = eps * s[var[k]];
+      const double c[4] = {-1.0, 8.0, -8.0, 1.0}, d[4] = {2.0, 1.0, -1.0, -2.0};
+      for (long i = 0; i < ns; ++i) col[i] = 0.0;
+      for (int t = 0; t < 4; ++t) {
+        x[k] = q[k] + d[t] * hk;
+        fd_apply(h, which, dt, x, y, G, ns);
+        for (long i = 0; i < ns; ++i) col[i] += c[t] * y[i];
+      }
+      x[k] = q[k];
+      double a = 0.0;
+      for (long i = 0; i < ns; ++i) a += v[i] * col[i];
+      out[k] = a / (12.0 * hk);
+    }
+    free(x); free(y); free(G); free(col);
+  }
+  free(var);
+}
+
+void orc_residual_vjp_fd(void* h, const double* q, const double* v, double eps, int isolated, double* out) {
+  fd_vjp(h, isolated ? 1 : 0, 0.0, q, v, eps, out);
+}
+
+void orc_rk_step_vjp_fd(void* h, const double* q, double dt, const double* lam, double eps, double* out) {
+  fd_vjp(h, 2, dt, q, lam, eps, out);
+}

@@ -165,7 +165,7 @@ void free_device(dg_mesh_impl* m) {
   void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
                   m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
                   m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv,
-                  m->d_vitems, m->d_velist};
+                  m->d_vitems, m->d_velist, m->d_sadj, m->d_adjw};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
@@ -176,6 +176,8 @@ void free_device(dg_mesh_impl* m) {
   m->d_adv = nullptr;
   m->d_vitems = nullptr;
   m->d_velist = nullptr;
+  m->d_sadj = nullptr;
+  m->d_adjw = nullptr;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
@@ -919,6 +921,59 @@ dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_o
   std::swap(m->d_err, c->d_err);   // keep the sticky error word of the mesh
   (void)old_err;
   destroy_impl(c);
+  return DG_OK;
+}
+
+static dg_status adjoint_ready(dg_mesh* m) {
+  if (m->phys.eqs != DG_EULER || !m->affine) return DG_ERR_UNSUPPORTED;
+  if (m->faces_unsupported) return DG_ERR_UNSUPPORTED;
+  int limit = 0;
+  DG_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+  if (sizeof(double) * dgk::mortar_adj_smem_max(m) + 1024 > (size_t)limit) return DG_ERR_UNSUPPORTED;
+  if (!m->d_sadj) DG_CUDA(cudaMalloc(&m->d_sadj, sizeof(double) * 5 * (size_t)m->h_soff[m->n_elem]));
+  return DG_OK;
+}
+
+dg_status dg_residual_vjp(dg_mesh* m, const double* q, const double* v, double* out) {
+  if (!m || !q || !v || !out || out == q || out == v) return DG_ERR_ARG;
+  dg_status st = adjoint_ready(m);
+  if (st != DG_OK) return st;
+  return from_cuda(dgk::residual_vjp(m, q, v, out, nullptr, false));
+}
+
+dg_status dg_rk_step_vjp(dg_mesh* m, const double* q0, const double* dt_dev, double* lam) {
+  if (!m || !q0 || !dt_dev || !lam || lam == q0) return DG_ERR_ARG;
+  dg_status st = adjoint_ready(m);
+  if (st != DG_OK) return st;
+  const size_t ns = 5 * (size_t)m->n_nodes;
+  if (!m->d_adjw) DG_CUDA(cudaMalloc(&m->d_adjw, sizeof(double) * 4 * ns));
+  double* Q1 = m->d_adjw;
+  double* Q2 = Q1 + ns;
+  double* G = Q2 + ns;
+  double* LG = G + ns;
+  static const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+  static const double B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+  cudaError_t e;
+  // the stage states Q1, Q2 again, from q0 (the register starts at zero; the
+  // first stage does not read it)
+  if ((e = cudaMemcpyAsync(Q1, q0, sizeof(double) * ns, cudaMemcpyDeviceToDevice, m->stream))) return from_cuda(e);
+  for (int k = 0; k < 2; ++k) {
+    double* Qk = k ? Q2 : Q1;
+    if (k && (e = cudaMemcpyAsync(Q2, Q1, sizeof(double) * ns, cudaMemcpyDeviceToDevice, m->stream)))
+      return from_cuda(e);
+    if ((e = dgk::face_flux(m, Qk, nullptr, false))) return from_cuda(e);
+    if ((e = dgk::volume(m, Qk, nullptr, nullptr, false, k, Qk, G, dt_dev))) return from_cuda(e);
+  }
+  // reversed: with G_k = A_k G_{k-1} + dt R(Q_{k-1}) and Q_k = Q_{k-1} + B_k G_k,
+  //   LG = B3 lam;            lam += dt J(Q2)^T LG
+  //   LG = A3 LG + B2 lam;    lam += dt J(Q1)^T LG
+  //   LG = A2 LG + B1 lam;    lam += dt J(q0)^T LG
+  const double* Qs[3] = {q0, Q1, Q2};
+  for (int k = 2; k >= 0; --k) {
+    const double a = k == 2 ? 0.0 : A[k + 1], b = B[k];
+    if ((e = dgk::axpby(m, LG, lam, a, b, (int64_t)ns))) return from_cuda(e);
+    if ((e = dgk::residual_vjp(m, Qs[k], LG, lam, dt_dev, true))) return from_cuda(e);
+  }
   return DG_OK;
 }
 

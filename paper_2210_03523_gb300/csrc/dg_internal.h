@@ -93,6 +93,12 @@ size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32);
 // CFL reduction only: *bits = max over nodes of the inverse time-step scale
 // (as the bit pattern of a non-negative double)
 cudaError_t max_dt_bits(dg_mesh_impl* m, const double* q, unsigned long long* bits);
+// adjoint: out = J(q)^T v, or out += (*scale) J(q)^T v (Euler, straight-sided elements)
+cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, double* out, const double* scale,
+                         bool accumulate);
+size_t mortar_adj_smem_max(dg_mesh_impl* m);
+// y = a y + b x
+cudaError_t axpby(dg_mesh_impl* m, double* y, const double* x, double a, double b, int64_t n);
 }  // namespace dgk
 
 // work-list (re)builders with the mesh's tile budgets (capi.cpp)
@@ -199,6 +205,10 @@ struct dg_mesh_impl {
   // dg_advance: device block {cfl, t_end, dt, steps}, the capture stream and
   // the instantiated step batches, keyed by the caller's buffers
   double* d_adv = nullptr;
+  // adjoint: trace cotangents per element face node (face-buffer layout) and
+  // the RK3 step's workspace (stage states Q1, Q2 and the register's cotangent)
+  double* d_sadj = nullptr;
+  double* d_adjw = nullptr;
   cudaStream_t cap_stream = nullptr;
   bool adv_warm = false;             // one eager step taken (kernel attributes set)
   struct AdvGraph { const void *q, *g, *t; int steps; cudaGraphExec_t exec; int64_t launches; };

@@ -17,6 +17,7 @@
 //                      entries that share N3 / (N2,N3)), coarse isolated
 //                      residual, both tau forms, block max-reduction.
 // FP64 throughout, except tau_kernel<float>.
+#include <algorithm>
 #include <cfloat>
 #include <cstdio>
 #include <cstring>
@@ -88,39 +89,81 @@ __device__ __forceinline__ Prim primitive(double gm1, const double q[5]) {
   return s;
 }
 
+// Forward-mode dual number (value, derivative along one seed direction): the
+// adjoint kernels differentiate the flux functions below exactly by running
+// them on Dual, one input component seeded at a time (Jacobian columns).
+struct Dual {
+  double v, d;
+};
+__device__ __forceinline__ Dual mkd(double v) { return {v, 0.0}; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.v * b.d + a.d * b.v}; }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+  const double r = 1.0 / b.v;
+  return {a.v * r, (a.d - a.v * r * b.d) * r};
+}
+__device__ __forceinline__ Dual operator+(Dual a, double b) { return {a.v + b, a.d}; }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return {a + b.v, b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, double b) { return {a.v - b, a.d}; }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return {a - b.v, -b.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, double b) { return {a.v * b, a.d * b}; }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
+__device__ __forceinline__ Dual operator/(Dual a, double b) { return {a.v / b, a.d / b}; }
+__device__ __forceinline__ Dual operator/(double a, Dual b) {
+  const double r = 1.0 / b.v;
+  return {a * r, -a * r * r * b.d};
+}
+__device__ __forceinline__ Dual& operator+=(Dual& a, Dual b) { return a = a + b; }
+__device__ __forceinline__ Dual& operator-=(Dual& a, Dual b) { return a = a - b; }
+__device__ __forceinline__ Dual& operator*=(Dual& a, double b) { return a = a * b; }
+__device__ __forceinline__ bool operator>(Dual a, double b) { return a.v > b; }
+// the two nonlinear primitives of the fluxes, on double and on Dual
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ Dual rsq(Dual x) {
+  const double r = rsqrt(x.v);
+  return {r, -0.5 * r * r * r * x.d};
+}
+__device__ __forceinline__ double absval(double x) { return fabs(x); }
+__device__ __forceinline__ Dual absval(Dual x) { return x.v < 0.0 ? Dual{-x.v, -x.d} : x; }
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ double val(Dual x) { return x.v; }
+
 // Roe's approximate Riemann solver: flux through the unit normal n from qL
 // (behind) to qR (ahead).  AX >= 0: the normal is the unit vector e_AX (axis
 // aligned faces), n is not read.  sqrt(rho) and 1/rho come from one rsqrt,
-// as do the Roe sound speed and its inverse square.
+// as do the Roe sound speed and its inverse square.  S: double, or Dual for
+// the adjoint's Jacobian columns.
 template <int AX>
 __device__ __forceinline__ double ncomp(const double n[3], int c) {
   return AX >= 0 ? (c == AX ? 1.0 : 0.0) : n[c];
 }
 
-template <int AX>
-__device__ void roe_t(double gamma, const double qL[5], const double qR[5], const double n[3], double f[5]) {
+template <int AX, typename S = double>
+__device__ void roe_t(double gamma, const S qL[5], const S qR[5], const double n[3], S f[5]) {
   const double gm1 = gamma - 1.0;
-  const double rsL = rsqrt(qL[0]), rsR = rsqrt(qR[0]);
-  const double sL = qL[0] * rsL, sR = qR[0] * rsR;      // sqrt(rho)
-  const double irL = rsL * rsL, irR = rsR * rsR;        // 1/rho
-  double uL[3], uR[3];
+  const S rsL = rsq(qL[0]), rsR = rsq(qR[0]);
+  const S sL = qL[0] * rsL, sR = qR[0] * rsR;      // sqrt(rho)
+  const S irL = rsL * rsL, irR = rsR * rsR;        // 1/rho
+  S uL[3], uR[3];
   for (int c = 0; c < 3; ++c) {
     uL[c] = qL[1 + c] * irL;
     uR[c] = qR[1 + c] * irR;
   }
-  const double pL = gm1 * (qL[4] - 0.5 * (qL[1] * uL[0] + qL[2] * uL[1] + qL[3] * uL[2]));
-  const double pR = gm1 * (qR[4] - 0.5 * (qR[1] * uR[0] + qR[2] * uR[1] + qR[3] * uR[2]));
-  const double HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
-  const double is = 1.0 / (sL + sR);
-  double ut[3];
+  const S pL = gm1 * (qL[4] - 0.5 * (qL[1] * uL[0] + qL[2] * uL[1] + qL[3] * uL[2]));
+  const S pR = gm1 * (qR[4] - 0.5 * (qR[1] * uR[0] + qR[2] * uR[1] + qR[3] * uR[2]));
+  const S HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
+  const S is = 1.0 / (sL + sR);
+  S ut[3];
   for (int c = 0; c < 3; ++c) ut[c] = (sL * uL[c] + sR * uR[c]) * is;
-  const double Ht = (sL * HL + sR * HR) * is;
-  const double rt = sL * sR;
-  const double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
-  const double c2 = gm1 * (Ht - 0.5 * q2);
-  const double rc = rsqrt(c2);
-  const double ct = c2 * rc, ic2 = rc * rc;
-  double unL, unR, utn;
+  const S Ht = (sL * HL + sR * HR) * is;
+  const S rt = sL * sR;
+  const S q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  const S c2 = gm1 * (Ht - 0.5 * q2);
+  const S rc = rsq(c2);
+  const S ct = c2 * rc, ic2 = rc * rc;
+  S unL, unR, utn;
   if (AX >= 0) {
     unL = uL[AX];
     unR = uR[AX];
@@ -130,32 +173,32 @@ __device__ void roe_t(double gamma, const double qL[5], const double qR[5], cons
     unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
     utn = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
   }
-  const double dun = unR - unL, dp = pR - pL, dr = qR[0] - qL[0];
-  const double rcd = rt * ct * dun;
-  const double a1 = 0.5 * (dp - rcd) * ic2;
-  const double a5 = 0.5 * (dp + rcd) * ic2;
-  const double a2 = dr - dp * ic2;
-  const double l1a1 = fabs(utn - ct) * a1, l5a5 = fabs(utn + ct) * a5, l2 = fabs(utn);
-  double dut[3], utdut = 0.0;
+  const S dun = unR - unL, dp = pR - pL, dr = qR[0] - qL[0];
+  const S rcd = rt * ct * dun;
+  const S a1 = 0.5 * (dp - rcd) * ic2;
+  const S a5 = 0.5 * (dp + rcd) * ic2;
+  const S a2 = dr - dp * ic2;
+  const S l1a1 = absval(utn - ct) * a1, l5a5 = absval(utn + ct) * a5, l2 = absval(utn);
+  S dut[3], utdut{};
   for (int c = 0; c < 3; ++c) {
     // tangential velocity jump; on an axis normal only component AX has a normal part
     dut[c] = (AX < 0 || c == AX) ? (uR[c] - uL[c]) - dun * ncomp<AX>(n, c) : uR[c] - uL[c];
     utdut += ut[c] * dut[c];
   }
-  const double mL = qL[0] * unL, mR = qR[0] * unR;
+  const S mL = qL[0] * unL, mR = qR[0] * unR;
   f[0] = 0.5 * (mL + mR) - 0.5 * (l1a1 + l5a5 + l2 * a2);
   for (int c = 0; c < 3; ++c) {
     const double nc = ncomp<AX>(n, c);
-    double phys = mL * uL[c] + mR * uR[c];
-    double diss = (l1a1 + l5a5) * ut[c] + l2 * (a2 * ut[c] + rt * dut[c]);
+    S phys = mL * uL[c] + mR * uR[c];
+    S diss = (l1a1 + l5a5) * ut[c] + l2 * (a2 * ut[c] + rt * dut[c]);
     if (AX < 0 || c == AX) {
       phys += (pL + pR) * nc;
       diss += (l5a5 - l1a1) * ct * nc;
     }
     f[1 + c] = 0.5 * (phys - diss);
   }
-  const double physE = unL * (qL[4] + pL) + unR * (qR[4] + pR);
-  const double dissE = (l1a1 + l5a5) * Ht + (l5a5 - l1a1) * utn * ct + l2 * (a2 * 0.5 * q2 + rt * utdut);
+  const S physE = unL * (qL[4] + pL) + unR * (qR[4] + pR);
+  const S dissE = (l1a1 + l5a5) * Ht + (l5a5 - l1a1) * utn * ct + l2 * (a2 * 0.5 * q2 + rt * utdut);
   f[4] = 0.5 * (physE - dissE);
 }
 
@@ -2105,3 +2148,575 @@ extern "C" dg_status dg_select_orders(dg_mesh* m, const void* map, int32_t map_f
   cudaFree(d_flag);
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// Adjoint (vector-Jacobian product) of the residual, Euler on straight-sided
+// elements.  R = A Phi(q): Phi the pointwise fluxes (contravariant volume
+// flux at the nodes, Roe at the face and mortar nodes), A linear (GL
+// derivative, surface lift, mortar interpolation and L2 projection, -1/J).
+// J^T v = (dPhi/dq)^T A^T v: the kernels apply the transposes of the linear
+// steps and take (dPhi/dq)^T from Jacobian columns computed by running the
+// same flux functions on Dual numbers, one input component seeded at a time.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename S>
+__device__ __forceinline__ void euler_flux3(double gm1, const S q[5], S f[3][5]) {
+  const S ir = 1.0 / q[0];
+  const S u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const S p = gm1 * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  for (int d = 0; d < 3; ++d) {
+    f[d][0] = q[1 + d];
+    f[d][1] = q[1] * u[d];
+    f[d][2] = q[2] * u[d];
+    f[d][3] = q[3] * u[d];
+    f[d][1 + d] += p;
+    f[d][4] = u[d] * (q[4] + p);
+  }
+}
+
+template <bool AXIS>
+__device__ __forceinline__ void roe_face_d(double gamma, int dir, const Dual qL[5], const Dual qR[5],
+                                           const double n[3], Dual f[5]) {
+  if (AXIS) {
+    if (dir == 0) roe_t<0, Dual>(gamma, qL, qR, n, f);
+    else if (dir == 1) roe_t<1, Dual>(gamma, qL, qR, n, f);
+    else roe_t<2, Dual>(gamma, qL, qR, n, f);
+  } else {
+    roe_t<-1, Dual>(gamma, qL, qR, n, f);
+  }
+}
+
+// gL[k] = sum_v dF_v/dqL_k lf_v, gR likewise: the Roe flux's Jacobian
+// transposes applied to lf, from ten Dual evaluations
+template <bool AXIS>
+__device__ void roe_vjp(double gamma, int dir, const double qL[5], const double qR[5], const double n[3],
+                        const double lf[5], double gL[5], double gR[5]) {
+  for (int k = 0; k < 10; ++k) {
+    Dual a[5], b[5], F[5];
+    for (int v = 0; v < 5; ++v) {
+      a[v] = {qL[v], k == v ? 1.0 : 0.0};
+      b[v] = {qR[v], k == 5 + v ? 1.0 : 0.0};
+    }
+    roe_face_d<AXIS>(gamma, dir, a, b, n, F);
+    double g = 0.0;
+    for (int v = 0; v < 5; ++v) g += F[v].d * lf[v];
+    if (k < 5) gL[k] = g;
+    else gR[k - 5] = g;
+  }
+}
+
+// 1 / w_0 = 1 / w_N of the order-N GL rule
+__device__ __forceinline__ double inv_wend(int N) { return 0.5 * N * (N + 1); }
+
+// Mortar batches, reversed.  Per batch: the traces and the face cotangents
+// lf_side = s_side (1/w_N) (-v/J) at each side's face nodes (s = +1 behind
+// the face, -1 ahead: the sign of the lift), the forward interpolation up
+// to the mortar (the Roe linearisation point), the transposes of the two
+// projection passes onto the mortar grid (both sides summed), the Roe
+// vector-Jacobian product at the mortar nodes, and the transposes of the two
+// interpolation passes back onto each side's face grid, into sadj.
+template <bool AXIS>
+__global__ void __launch_bounds__(kVolThreads) adj_mortar_kernel(MortarParams P, const double* __restrict__ vin,
+                                                                 double* __restrict__ sadj) {
+  extern __shared__ double smem[];
+  const MeshView& m = P.m;
+  const double gamma = m.ph.gamma;
+  for (int it = blockIdx.x; it < P.n_batches; it += gridDim.x) {
+    const MortarBatch B = P.batches[it];
+    const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb, cnt = B.count;
+    const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
+    const int nfl = la * lb, nfr = ra * rb, nm = Ma * Mb;
+    const bool upLa = la != Ma, upLb = lb != Mb, upRa = ra != Ma, upRb = rb != Mb;
+    const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+    double* TL = smem;
+    double* TR = TL + cnt * 5 * nfl;
+    double* UL = TR + cnt * 5 * nfr;
+    double* UR = UL + cnt * 5 * uL;
+    double* QL = UR + cnt * 5 * uR;
+    double* QR = QL + cnt * 5 * nm;
+    double* AL = QR + cnt * 5 * nm;   // face cotangents on each side's grid
+    double* AR = AL + cnt * 5 * nfl;
+    double* LM = AR + cnt * 5 * nfr;  // flux cotangent at the mortar nodes
+    double* NR = LM + cnt * 5 * nm;
+    // 1. traces, face cotangents, normals
+    for (int t = threadIdx.x; t < cnt * (nfl + nfr); t += blockDim.x) {
+      const bool isL = t < cnt * nfl;
+      const int tt = isL ? t : t - cnt * nfl;
+      const int nf = isL ? nfl : nfr, na = isL ? la : ra;
+      const int f = tt / nf, p = tt - f * nf;
+      const int* fr = P.faces + 3 * (B.first + f);
+      const int e = isL ? fr[0] : fr[1], dir = fr[2];
+      int n1, n2, n3;
+      orders_of(m, e, n1, n2, n3);
+      const int n = n1 * n2 * n3;
+      const int vi = face_vidx(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir, p % na, p / na);
+      const int64_t o = m.off[e];
+      const int Nd = (dir == 0 ? n1 : dir == 1 ? n2 : n3) - 1;
+      const double c = (isL ? -1.0 : 1.0) * inv_wend(Nd) * metric<true>(m.metric, e, 0, 0, 0, 10);
+      double* T = (isL ? TL + f * 5 * nfl : TR + f * 5 * nfr) + p;
+      double* A = (isL ? AL + f * 5 * nfl : AR + f * 5 * nfr) + p;
+      for (int v = 0; v < 5; ++v) {
+        T[v * nf] = P.q[5 * o + v * n + vi];
+        A[v * nf] = c * vin[5 * o + v * n + vi];
+      }
+    }
+    for (int f = threadIdx.x; f < cnt; f += blockDim.x) {
+      const int* fr = P.faces + 3 * (B.first + f);
+      double ja[3], nrm[3];
+      for (int c = 0; c < 3; ++c) ja[c] = metric<true>(m.metric, fr[0], 0, 0, 0, 3 * fr[2] + c);
+      const double area = unit_normal(ja, nrm);
+      NR[4 * f + 0] = nrm[0];
+      NR[4 * f + 1] = nrm[1];
+      NR[4 * f + 2] = nrm[2];
+      NR[4 * f + 3] = area;
+    }
+    __syncthreads();
+    // 2-3. interpolation up to the mortar, as in the forward kernel
+    const double* IaL = P.basis + c_boff.I[la - 1][Ma - 1];
+    const double* IaR = P.basis + c_boff.I[ra - 1][Ma - 1];
+    const double* IbL = P.basis + c_boff.I[lb - 1][Mb - 1];
+    const double* IbR = P.basis + c_boff.I[rb - 1][Mb - 1];
+    {
+      const int nL = upLa ? cnt * Ma * lb : 0, nR = upRa ? cnt * Ma * rb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int nb = isL ? lb : rb, na = isL ? la : ra, per = Ma * nb;
+        const int f = tt / per, x = tt - f * per, m0 = x % Ma, b = x / Ma;
+        const double* src = isL ? TL + f * 5 * nfl : TR + f * 5 * nfr;
+        const double* Ia = isL ? IaL : IaR;
+        double* dst = (isL ? UL + f * 5 * uL : UR + f * 5 * uR) + x;
+        const int nsrc = na * nb;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int a = 0; a < na; ++a) {
+          const double w = __ldg(Ia + m0 * na + a);
+          for (int v = 0; v < 5; ++v) acc[v] += w * src[v * nsrc + a + na * b];
+        }
+        for (int v = 0; v < 5; ++v) dst[v * per] = acc[v];
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * cnt * nm; t += blockDim.x) {
+      const bool isL = t < cnt * nm;
+      const int tt = isL ? t : t - cnt * nm;
+      const int f = tt / nm, x = tt - f * nm, m0 = x % Ma, m1 = x / Ma;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      const int nb = isL ? lb : rb;
+      const double* src = upa ? (isL ? UL + f * 5 * uL : UR + f * 5 * uR) : (isL ? TL + f * 5 * nfl : TR + f * 5 * nfr);
+      const int nsrc = Ma * nb;
+      double* dst = (isL ? QL : QR) + f * 5 * nm + x;
+      if (upb) {
+        const double* Ib = isL ? IbL : IbR;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int b = 0; b < nb; ++b) {
+          const double w = __ldg(Ib + m1 * nb + b);
+          for (int v = 0; v < 5; ++v) acc[v] += w * src[v * nsrc + m0 + Ma * b];
+        }
+        for (int v = 0; v < 5; ++v) dst[v * nm] = acc[v];
+      } else {
+        for (int v = 0; v < 5; ++v) dst[v * nm] = src[v * nsrc + m0 + Ma * m1];
+      }
+    }
+    __syncthreads();
+    // 4a. transpose of the xi_b projection pass: X(a, m1) = sum_b Pb(b, m1) A(a, b), into U
+    const double* PaL = P.basis + c_boff.P[Ma - 1][la - 1];
+    const double* PaR = P.basis + c_boff.P[Ma - 1][ra - 1];
+    const double* PbL = P.basis + c_boff.P[Mb - 1][lb - 1];
+    const double* PbR = P.basis + c_boff.P[Mb - 1][rb - 1];
+    {
+      const int nL = upLb ? cnt * la * Mb : 0, nR = upRb ? cnt * ra * Mb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int na = isL ? la : ra, nb = isL ? lb : rb, per = na * Mb;
+        const int f = tt / per, x = tt - f * per, a = x % na, m1 = x / na;
+        const double* Pb = isL ? PbL : PbR;
+        const double* src = isL ? AL + f * 5 * nfl : AR + f * 5 * nfr;
+        double* dst = (isL ? UL + f * 5 * uL : UR + f * 5 * uR) + x;
+        const int nsrc = na * nb;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int b = 0; b < nb; ++b) {
+          const double w = __ldg(Pb + b * Mb + m1);
+          for (int v = 0; v < 5; ++v) acc[v] += w * src[v * nsrc + a + na * b];
+        }
+        for (int v = 0; v < 5; ++v) dst[v * per] = acc[v];
+      }
+    }
+    __syncthreads();
+    // 4b. transpose of the xi_a projection pass, both sides summed onto the mortar grid
+    for (int t = threadIdx.x; t < cnt * nm; t += blockDim.x) {
+      const int f = t / nm, x = t - f * nm, m0 = x % Ma, m1 = x / Ma;
+      double acc[5] = {0, 0, 0, 0, 0};
+      for (int side = 0; side < 2; ++side) {
+        const bool isL = side == 0;
+        const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+        const int na = isL ? la : ra, nb = isL ? lb : rb;
+        // the side's cotangent on its (na x Mb) grid: pass 4a's result, or A itself
+        const double* src = upb ? (isL ? UL + f * 5 * uL : UR + f * 5 * uR) : (isL ? AL + f * 5 * nfl : AR + f * 5 * nfr);
+        const int nsrc = upb ? na * Mb : na * nb;
+        if (upa) {
+          const double* Pa = isL ? PaL : PaR;
+          for (int a = 0; a < na; ++a) {
+            const double w = __ldg(Pa + a * Ma + m0);
+            for (int v = 0; v < 5; ++v) acc[v] += w * src[v * nsrc + a + na * m1];
+          }
+        } else {
+          for (int v = 0; v < 5; ++v) acc[v] += src[v * nsrc + m0 + Ma * m1];
+        }
+      }
+      for (int v = 0; v < 5; ++v) LM[f * 5 * nm + v * nm + x] = acc[v];
+    }
+    __syncthreads();
+    // 5. Roe vector-Jacobian product at the mortar nodes (F* = area Roe), into QL / QR
+    for (int t = threadIdx.x; t < cnt * nm; t += blockDim.x) {
+      const int f = t / nm, x = t - f * nm;
+      double qa[5], qb[5], lf[5], ga[5], gb[5];
+      const double area = NR[4 * f + 3];
+      for (int v = 0; v < 5; ++v) {
+        qa[v] = QL[f * 5 * nm + v * nm + x];
+        qb[v] = QR[f * 5 * nm + v * nm + x];
+        lf[v] = LM[f * 5 * nm + v * nm + x] * area;
+      }
+      const double nrm[3] = {NR[4 * f], NR[4 * f + 1], NR[4 * f + 2]};
+      roe_vjp<AXIS>(gamma, P.faces[3 * (B.first + f) + 2], qa, qb, nrm, lf, ga, gb);
+      for (int v = 0; v < 5; ++v) {
+        QL[f * 5 * nm + v * nm + x] = ga[v];
+        QR[f * 5 * nm + v * nm + x] = gb[v];
+      }
+    }
+    __syncthreads();
+    // 6a. transpose of the xi_b interpolation pass: (Ma x Mb) -> (Ma x nb), into U
+    {
+      const int nL = upLb ? cnt * Ma * lb : 0, nR = upRb ? cnt * Ma * rb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int nb = isL ? lb : rb, per = Ma * nb;
+        const int f = tt / per, x = tt - f * per, m0 = x % Ma, b = x / Ma;
+        const double* Ib = isL ? IbL : IbR;
+        const double* src = (isL ? QL : QR) + f * 5 * nm;
+        double* dst = (isL ? UL + f * 5 * uL : UR + f * 5 * uR) + x;
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int m1 = 0; m1 < Mb; ++m1) {
+          const double w = __ldg(Ib + m1 * nb + b);
+          for (int v = 0; v < 5; ++v) acc[v] += w * src[v * nm + m0 + Ma * m1];
+        }
+        for (int v = 0; v < 5; ++v) dst[v * per] = acc[v];
+      }
+    }
+    __syncthreads();
+    // 6b. transpose of the xi_a interpolation pass onto each side's face grid, into sadj
+    for (int t = threadIdx.x; t < cnt * (nfl + nfr); t += blockDim.x) {
+      const bool isL = t < cnt * nfl;
+      const int tt = isL ? t : t - cnt * nfl;
+      const int nf = isL ? nfl : nfr, na = isL ? la : ra, nb = isL ? lb : rb;
+      const int f = tt / nf, x = tt - f * nf, a = x % na, b = x / na;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      // the cotangent on the (Ma x nb) grid: pass 6a's result, or the mortar's own
+      const double* src = upb ? (isL ? UL + f * 5 * uL : UR + f * 5 * uR) : (isL ? QL : QR) + f * 5 * nm;
+      const int nsrc = upb ? Ma * nb : nm;
+      double out[5];
+      if (upa) {
+        const double* Ia = isL ? IaL : IaR;
+        for (int v = 0; v < 5; ++v) out[v] = 0.0;
+        for (int m0 = 0; m0 < Ma; ++m0) {
+          const double w = __ldg(Ia + m0 * na + a);
+          for (int v = 0; v < 5; ++v) out[v] += w * src[v * nsrc + m0 + Ma * b];
+        }
+      } else {
+        for (int v = 0; v < 5; ++v) out[v] = src[v * nsrc + a + na * b];
+      }
+      const int* fr = P.faces + 3 * (B.first + f);
+      const int e = isL ? fr[0] : fr[1], dir = fr[2];
+      int n1, n2, n3;
+      orders_of(m, e, n1, n2, n3);
+      double* dst = sadj + 5 * (m.soff[e] + face_offset(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir)) + x;
+      for (int v = 0; v < 5; ++v) dst[v * nf] = out[v];
+    }
+    __syncthreads();
+  }
+}
+
+// Boundary faces, reversed (one warp per face): the Roe flux against the
+// ghost state, which itself depends on the interior trace at a wall.
+template <typename S>
+__device__ __forceinline__ void bc_ghost_t(const DevPhys& ph, int tag, const S qi[5], S qg[5]) {
+  if (tag == DG_BC_WALL) {
+    qg[0] = qi[0]; qg[1] = -qi[1]; qg[2] = -qi[2]; qg[3] = -qi[3]; qg[4] = qi[4];
+  } else {
+    for (int v = 0; v < 5; ++v) qg[v] = qi[v] * 0.0 + ph.qinf[v];
+  }
+}
+
+template <bool AXIS>
+__global__ void __launch_bounds__(32 * kFaceWarps) adj_face_bc_kernel(FaceParams P, const double* __restrict__ vin,
+                                                                       double* __restrict__ sadj) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int fidx = blockIdx.x * kFaceWarps + warp;
+  if (fidx >= P.n_faces) return;
+  const FaceRec fr = P.faces[fidx];
+  if (fr.kind != 2) return;   // interior faces of straight-sided Euler meshes are in the mortar batches
+  const MeshView& m = P.m;
+  const double gamma = m.ph.gamma;
+  const int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1, side = f & 1;
+  int n1, n2, n3;
+  orders_of(m, e, n1, n2, n3);
+  const int n = n1 * n2 * n3;
+  const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+  const int64_t o = m.off[e];
+  double ja[3], nrm[3];
+  face_metric<true>(m, e, n, 0, dir, ja);
+  const double area = unit_normal(ja, nrm);
+  const int Nd = (dir == 0 ? n1 : dir == 1 ? n2 : n3) - 1;
+  // d R / d F*(face node) = -(s / w_N) / J, s = +1 on a +xi face, -1 on a -xi face
+  const double c = (side ? -1.0 : 1.0) * inv_wend(Nd) * metric<true>(m.metric, e, 0, 0, 0, 10) * area;
+  double* out = sadj + 5 * (m.soff[e] + face_offset(n1, n2, n3, f));
+  for (int p = lane; p < nf; p += 32) {
+    const int vi = face_vidx(n1, n2, n3, f, p % na, p / na);
+    double lf[5], g[5];
+    for (int v = 0; v < 5; ++v) lf[v] = c * vin[5 * o + v * n + vi];
+    for (int k = 0; k < 5; ++k) {
+      Dual qi[5], qg[5], F[5];
+      for (int v = 0; v < 5; ++v) qi[v] = {P.q[5 * o + v * n + vi], k == v ? 1.0 : 0.0};
+      bc_ghost_t(m.ph, tag, qi, qg);
+      if (side) roe_face_d<AXIS>(gamma, dir, qi, qg, nrm, F);
+      else roe_face_d<AXIS>(gamma, dir, qg, qi, nrm, F);
+      double s = 0.0;
+      for (int v = 0; v < 5; ++v) s += F[v].d * lf[v];
+      g[k] = s;
+    }
+    for (int v = 0; v < 5; ++v) out[v * nf + p] = g[v];
+  }
+}
+
+struct AdjParams {
+  MeshView m;
+  const WorkItem* items;
+  const int32_t* elist;
+  const int32_t* ilist;
+  int n_items;
+  const double* q;
+  const double* v;         // cotangent of the residual (state layout)
+  const double* sadj;      // trace cotangents per element face node (face-buffer layout)
+  double* out;             // J^T v, or out += (*scale) J^T v
+  const double* scale;     // device scalar (accumulate mode)
+  int accumulate;
+  const double* basis;
+};
+
+// Volume part, reversed, one tile per CTA: u = -v/J; the transposed GL
+// derivatives lF_i = D_i^T u; the inner-flux part of the lift, lF_dir -=
+// s (1/w_N) u at each face's nodes; then per node mu_d = sum_i J a^i_d lF_i
+// and J^T v = sum_d (d f_d / d q)^T mu_d (five Dual evaluations of the
+// Euler flux), plus the trace cotangents of the node's faces.
+template <bool AXIS>
+__global__ void __launch_bounds__(kVolThreads) adj_volume_kernel(AdjParams P) {
+  extern __shared__ double smem[];
+  const MeshView& m = P.m;
+  const double gm1 = m.ph.gamma - 1.0;
+  for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
+    const int slots = w.count * n;
+    double* U = smem;                                 // [count][5][n]
+    double* LF = smem + (size_t)w.count * 5 * n;      // [count][3][5][n]
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int e = P.elist[w.first + el];
+      const int64_t o = m.off[e];
+      const double iJ = metric<true>(m.metric, e, o, n, p, 10);
+      for (int v = 0; v < 5; ++v) U[(size_t)el * 5 * n + v * n + p] = -P.v[5 * o + v * n + p] * iJ;
+    }
+    __syncthreads();
+    const double* D1 = P.basis + c_boff.D[w.n1];
+    const double* D2 = P.basis + c_boff.D[w.n2];
+    const double* D3 = P.basis + c_boff.D[w.n3];
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const double* Ue = U + (size_t)el * 5 * n;
+      double* L = LF + (size_t)el * 15 * n;
+      double acc[5];
+      for (int v = 0; v < 5; ++v) acc[v] = 0.0;
+      for (int mm = 0; mm < n1; ++mm) {
+        const double d = __ldg(D1 + mm * n1 + i);
+        for (int v = 0; v < 5; ++v) acc[v] += d * Ue[v * n + mm + n1 * (j + n2 * k)];
+      }
+      for (int v = 0; v < 5; ++v) L[v * n + p] = acc[v];
+      for (int v = 0; v < 5; ++v) acc[v] = 0.0;
+      for (int mm = 0; mm < n2; ++mm) {
+        const double d = __ldg(D2 + mm * n2 + j);
+        for (int v = 0; v < 5; ++v) acc[v] += d * Ue[v * n + i + n1 * (mm + n2 * k)];
+      }
+      for (int v = 0; v < 5; ++v) L[(5 + v) * n + p] = acc[v];
+      for (int v = 0; v < 5; ++v) acc[v] = 0.0;
+      for (int mm = 0; mm < n3; ++mm) {
+        const double d = __ldg(D3 + mm * n3 + k);
+        for (int v = 0; v < 5; ++v) acc[v] += d * Ue[v * n + i + n1 * (j + n2 * mm)];
+      }
+      for (int v = 0; v < 5; ++v) L[(10 + v) * n + p] = acc[v];
+    }
+    __syncthreads();
+    // the inner flux in the lift: the two faces of a direction touch
+    // disjoint nodes and each direction its own lF, so one pass has no races
+    for (int dir = 0; dir < 3; ++dir) {
+      const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, fsz = na * nb;
+      const int Nd = dir == 0 ? w.n1 : (dir == 1 ? w.n2 : w.n3);
+      const double iw = inv_wend(Nd);
+      const int per_el = 2 * fsz;
+      for (int s = threadIdx.x; s < w.count * per_el; s += blockDim.x) {
+        const int el = s / per_el, r = s - el * per_el;
+        const int side = r / fsz, fn = r - side * fsz;
+        const int p = face_vidx(n1, n2, n3, 2 * dir + side, fn % na, fn / na);
+        const double sg = side ? iw : -iw;
+        for (int v = 0; v < 5; ++v)
+          LF[(size_t)el * 15 * n + (dir * 5 + v) * n + p] -= sg * U[(size_t)el * 5 * n + v * n + p];
+      }
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int e = P.elist[w.first + el];
+      const int64_t o = m.off[e];
+      const double* L = LF + (size_t)el * 15 * n;
+      double mu[3][5];
+      for (int d = 0; d < 3; ++d)
+        for (int v = 0; v < 5; ++v) {
+          if (AXIS) {
+            mu[d][v] = metric<true>(m.metric, e, o, n, p, 4 * d) * L[(d * 5 + v) * n + p];
+          } else {
+            mu[d][v] = 0.0;
+            for (int i = 0; i < 3; ++i) mu[d][v] += metric<true>(m.metric, e, o, n, p, 3 * i + d) * L[(i * 5 + v) * n + p];
+          }
+        }
+      double q[5], lam[5];
+      for (int v = 0; v < 5; ++v) q[v] = P.q[5 * o + v * n + p];
+      for (int kk = 0; kk < 5; ++kk) {
+        Dual qd[5], fd[3][5];
+        for (int v = 0; v < 5; ++v) qd[v] = {q[v], kk == v ? 1.0 : 0.0};
+        euler_flux3(gm1, qd, fd);
+        double g = 0.0;
+        for (int d = 0; d < 3; ++d)
+          for (int v = 0; v < 5; ++v) g += fd[d][v].d * mu[d][v];
+        lam[kk] = g;
+      }
+      // trace cotangents of the faces through this node
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const double* sb = P.sadj + 5 * m.soff[e];
+      for (int f = 0; f < 6; ++f) {
+        const int dir = f >> 1, side = f & 1;
+        const int c = dir == 0 ? i : dir == 1 ? j : k, nd = dir == 0 ? n1 : dir == 1 ? n2 : n3;
+        if (c != (side ? nd - 1 : 0)) continue;
+        const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+        const int a = dir == 0 ? j : i, b = dir == 2 ? j : k;
+        const double* fb = sb + 5 * face_offset(n1, n2, n3, f) + a + na * b;
+        for (int v = 0; v < 5; ++v) lam[v] += fb[v * nf];
+      }
+      if (P.accumulate) {
+        const double sc = *P.scale;
+        for (int v = 0; v < 5; ++v) P.out[5 * o + v * n + p] += sc * lam[v];
+      } else {
+        for (int v = 0; v < 5; ++v) P.out[5 * o + v * n + p] = lam[v];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y = a y + b x over n values (a = 0: y is not read, so it may hold anything)
+__global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ x, double a, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (a == 0.0 ? 0.0 : a * y[i]) + b * x[i];
+}
+
+}  // namespace
+
+// shared memory (doubles) of one mortar batch in the adjoint kernel
+static size_t mortar_adj_smem_doubles(int count, int la, int lb, int ra, int rb) {
+  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
+  const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+  return (size_t)count * (5 * (2 * la * lb + 2 * ra * rb + uL + uR + 3 * Ma * Mb) + 4);
+}
+
+namespace dgk {
+
+cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, double* out, const double* scale,
+                         bool accumulate) {
+  cudaError_t err;
+  Prof pr(m, DG_KERNEL_ADJOINT, (m->n_faces ? 1 : 0) + (m->n_mbatches ? 1 : 0) + (int)m->vol_classes.size());
+  if (m->n_faces) {
+    FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
+    const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+    if (m->axis) adj_face_bc_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj);
+    else adj_face_bc_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj);
+    if ((err = cudaGetLastError())) return err;
+  }
+  if (m->n_mbatches) {
+    MortarParams M;
+    M.m = view(m);
+    M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
+    M.n_batches = m->n_mbatches;
+    M.faces = m->d_mfaces;
+    M.q = q;
+    M.surf = nullptr;
+    M.basis = m->basis64;
+    size_t sm = 0;
+    for (int b = 0; b < m->n_mbatches; ++b) {
+      const int32_t* B = &m->h_mbatches[6 * b];
+      sm = std::max(sm, mortar_adj_smem_doubles(B[1], B[2], B[3], B[4], B[5]));
+    }
+    const size_t smem = sizeof(double) * sm;
+    if (m->axis) {
+      if ((err = allow_smem(adj_mortar_kernel<true>, smem))) return err;
+      adj_mortar_kernel<true><<<m->n_mbatches, kVolThreads, smem, m->stream>>>(M, v, m->d_sadj);
+    } else {
+      if ((err = allow_smem(adj_mortar_kernel<false>, smem))) return err;
+      adj_mortar_kernel<false><<<m->n_mbatches, kVolThreads, smem, m->stream>>>(M, v, m->d_sadj);
+    }
+    if ((err = cudaGetLastError())) return err;
+  }
+  AdjParams A;
+  A.m = view(m);
+  A.items = m->d_vitems;
+  A.elist = m->d_velist;
+  A.q = q;
+  A.v = v;
+  A.sadj = m->d_sadj;
+  A.out = out;
+  A.scale = scale;
+  A.accumulate = accumulate;
+  A.basis = m->basis64;
+  for (auto& c : m->vol_classes) {
+    A.ilist = c.d_list;
+    A.n_items = c.n;
+    const size_t smem = sizeof(double) * 20 * c.S;
+    if (m->axis) {
+      if ((err = allow_smem(adj_volume_kernel<true>, smem))) return err;
+      adj_volume_kernel<true><<<c.n, kVolThreads, smem, m->stream>>>(A);
+    } else {
+      if ((err = allow_smem(adj_volume_kernel<false>, smem))) return err;
+      adj_volume_kernel<false><<<c.n, kVolThreads, smem, m->stream>>>(A);
+    }
+    if ((err = cudaGetLastError())) return err;
+  }
+  return cudaSuccess;
+}
+
+size_t mortar_adj_smem_max(dg_mesh_impl* m) {
+  size_t sm = 0;
+  for (int b = 0; b < m->n_mbatches; ++b) {
+    const int32_t* B = &m->h_mbatches[6 * b];
+    sm = std::max(sm, mortar_adj_smem_doubles(B[1], B[2], B[3], B[4], B[5]));
+  }
+  return sm;
+}
+
+cudaError_t axpby(dg_mesh_impl* m, double* y, const double* x, double a, double b, int64_t n) {
+  const int grid = grid_for((int)std::min<int64_t>((n + 255) / 256, 1 << 20), 8);
+  Prof pr(m, DG_KERNEL_ADJOINT);
+  axpby_kernel<<<grid, 256, 0, m->stream>>>(y, x, a, b, n);
+  return cudaGetLastError();
+}
+
+}  // namespace dgk

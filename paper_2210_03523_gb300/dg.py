@@ -25,7 +25,7 @@ DG_EXTRAP_DECOUPLED = 0x1
 DG_EXTRAP_ACCUM_MAX = 0x2
 DG_ADVANCE_EAGER = 0x1
 KERNELS = {"face_flux": 0, "face_qhat": 1, "gradient": 2, "volume": 3, "max_dt": 4, "tau": 5, "tau_combine": 6,
-           "project": 7, "select": 8, "extrap": 9, "mortar": 10}
+           "project": 7, "select": 8, "extrap": 9, "mortar": 10, "adjoint": 11}
 STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_NOMEM", 3: "DG_ERR_CUDA", 4: "DG_ERR_UNSUPPORTED",
           5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_TIMEOUT"}
 
@@ -83,6 +83,8 @@ def _lib():
                                    C.c_uint32, vp],
             "dg_advance": [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int64, C.c_uint32, i64p],
             "dg_autotune": [vp, vp, C.c_int32, C.POINTER(dg_tiles)],
+            "dg_residual_vjp": [vp, vp, vp, vp],
+            "dg_rk_step_vjp": [vp, vp, vp, vp],
             "dg_get_tiles": [vp, C.POINTER(dg_tiles)],
             "dg_set_tiles": [vp, C.POINTER(dg_tiles)],
             "dg_max_dt": [vp, vp, C.c_double, vp],
@@ -106,7 +108,8 @@ def exported_symbols():
     return ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_count_nodes", "dg_set_stream", "dg_node_coords",
             "dg_residual", "dg_max_dt", "dg_rk_step", "dg_tau_estimate", "dg_set_orders", "dg_get_error",
             "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc",
-            "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles"]
+            "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles",
+            "dg_residual_vjp", "dg_rk_step_vjp"]
 
 
 def _check(st, where):
@@ -303,6 +306,19 @@ class Mesh:
         _check(_lib().dg_advance(self.h, _ptr(q), _ptr(g), _ptr(t), float(t_end), float(cfl), int(max_steps),
                                  DG_ADVANCE_EAGER if eager else 0, C.byref(n) if count else None), "dg_advance")
         return n.value if count else None
+
+    def residual_vjp(self, q, v, out=None):
+        """dg_residual_vjp: (dR/dq)^T v at q."""
+        out = self.new_state() if out is None else out
+        self._check_state(q, v, out)
+        _check(_lib().dg_residual_vjp(self.h, _ptr(q), _ptr(v), _ptr(out)), "dg_residual_vjp")
+        return out
+
+    def rk_step_vjp(self, q0, dt, lam):
+        """dg_rk_step_vjp: lam <- (d step(q0) / d q0)^T lam in place, dt a device scalar."""
+        self._check_state(q0, lam)
+        _check(_lib().dg_rk_step_vjp(self.h, _ptr(q0), _ptr(dt), _ptr(lam)), "dg_rk_step_vjp")
+        return lam
 
     def autotune(self, q, reps=5):
         """dg_autotune: time each tile budget per size class on this mesh and

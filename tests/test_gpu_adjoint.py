@@ -1,0 +1,146 @@
+"""The adjoint kernels through the C ABI (dg_residual_vjp, dg_rk_step_vjp)
+against the oracle's brute-force discrete adjoint (every Jacobian column by
+fourth-order central differences of the oracle's own residual / RK3 step),
+a dot-product test against central differences of the GPU residual at scale,
+and gradients through the time integration (torch.autograd) against finite
+differences of a functional, for every checkpoint budget."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2210_03523_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+VEL = (0.9, -0.6, 0.3)    # no velocity component is zero: Roe's |u.n| stays away from its kink
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_03523_gb300 import build
+    build.build()
+    return torch
+
+
+def _case(name):
+    ph = I.pulse_physics(mach=0.4, velocity=VEL)
+    if name == "periodic_mortars":
+        mi = I.box_mesh(2, orders=I.random_orders(8, 1, 4, 41), phys=ph)
+    elif name == "farfield_mortars":
+        mi = I.box_mesh(2, orders=I.random_orders(8, 1, 3, 42), phys=ph, periodic=(False, False, False))
+    elif name == "sheared":
+        A = [[1.0, 0.2, 0.0], [0.0, 1.0, -0.15], [0.1, 0.0, 1.0]]
+        mi = I.box_mesh(2, orders=I.random_orders(8, 2, 3, 43), phys=ph, mapping=I.affine_map(A))
+    elif name == "wall":
+        mi = I.box_mesh(2, orders=(2, 3, 2), phys=ph, periodic=(True, False, True),
+                        tags=(I.FAR_FIELD, I.FAR_FIELD, I.WALL, I.WALL, I.FAR_FIELD, I.FAR_FIELD))
+    else:
+        raise KeyError(name)
+    import oracle
+    om = oracle.Mesh(mi)
+    q = I.pulse_state(om.coords(), mi.orders, ph, width=0.5, center=(-0.2, 0.1, 0.0))
+    return mi, om, q
+
+
+@pytest.mark.parametrize("name", ["periodic_mortars", "farfield_mortars", "sheared", "wall"])
+def test_residual_vjp_matches_oracle(torch_cuda, name):
+    torch = torch_cuda
+    from paper_2210_03523_gb300 import dg
+    mi, om, q = _case(name)
+    v = np.random.default_rng(9).standard_normal(q.size)
+    ref = om.residual_vjp_fd(q, v)
+    m = dg.Mesh(mi)
+    got = m.residual_vjp(torch.from_numpy(q).cuda(), torch.from_numpy(v).cuda()).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+    assert m.get_error() == 0
+
+
+def test_rk_step_vjp_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2210_03523_gb300 import dg
+    mi, om, q = _case("periodic_mortars")
+    dt = 0.5 * om.max_dt(q, 1.0)
+    lam = np.random.default_rng(10).standard_normal(q.size)
+    ref = om.rk_step_vjp_fd(q, dt, lam)
+    m = dg.Mesh(mi)
+    lam_g = torch.from_numpy(lam).cuda()
+    m.rk_step_vjp(torch.from_numpy(q).cuda(), torch.tensor([dt], dtype=torch.float64, device="cuda"), lam_g)
+    got = lam_g.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
+def test_dot_product_at_scale(torch_cuda):
+    """<J^T v, w> = <v, J w> on 8^3 elements of orders 1..6 (every mortar shape),
+    J w by fourth-order central differences of the GPU residual."""
+    torch = torch_cuda
+    import oracle
+    from paper_2210_03523_gb300 import dg
+    ph = I.pulse_physics(mach=0.4, velocity=VEL)
+    mi = I.box_mesh(8, orders=I.random_orders(512, 1, 6, 44), phys=ph)
+    q = torch.from_numpy(I.pulse_state(oracle.Mesh(mi).coords(), mi.orders, ph, width=0.3)).cuda()
+    m = dg.Mesh(mi)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    v = torch.randn(q.shape, generator=g, device="cuda", dtype=torch.float64)
+    w = torch.randn(q.shape, generator=g, device="cuda", dtype=torch.float64) * q.abs().amax() * 1e-3
+    jtv = m.residual_vjp(q, v)
+    h = 1.0
+    R = lambda s: m.residual(q + s * h * w)
+    jw = (-R(2) + 8 * R(1) - 8 * R(-1) + R(-2)) / (12 * h)
+    lhs, rhs = float(jtv @ w), float(v @ jw)
+    assert abs(lhs - rhs) <= 1e-7 * (jtv.abs() @ w.abs()).item(), (lhs, rhs)
+
+
+def test_gradient_through_time_integration(torch_cuda):
+    """d/dq0 of a functional of the state after 12 RK3 steps, through RKSteps
+    (dg_rk_step_vjp under checkpointing), against central differences; every
+    checkpoint budget gives the same gradient bitwise."""
+    torch = torch_cuda
+    from paper_2210_03523_gb300 import autograd as AG, dg
+    mi, om, qh = _case("periodic_mortars")
+    m = dg.Mesh(mi)
+    q0 = torch.from_numpy(qh).cuda()
+    dt = torch.tensor([0.5 * om.max_dt(qh, 1.0)], dtype=torch.float64, device="cuda")
+    c = torch.from_numpy(np.random.default_rng(11).standard_normal(qh.size)).cuda()
+    n = 12
+
+    def functional(q):
+        return (c * AG.rk_steps(q, m, dt, n, snapshots)).sum()
+    grads = []
+    for snapshots in (0, 1, 2, 8):
+        x = q0.clone().requires_grad_(True)
+        functional(x).backward()
+        grads.append(x.grad.clone())
+    for gr in grads[1:]:
+        assert torch.equal(gr, grads[0])
+    w = torch.from_numpy(np.random.default_rng(12).standard_normal(qh.size)).cuda() * 1e-4 * q0.abs().amax()
+    with torch.no_grad():
+        snapshots = 0
+        f = lambda s: float(functional(q0 + s * w))
+        fd = (-f(2) + 8 * f(1) - 8 * f(-1) + f(-2)) / 12.0
+    ad = float(grads[0] @ w)
+    assert abs(ad - fd) <= 1e-7 * abs(fd) + 1e-12, (ad, fd)
+
+
+def test_residual_function_backward(torch_cuda):
+    torch = torch_cuda
+    from paper_2210_03523_gb300 import autograd as AG, dg
+    mi, om, qh = _case("farfield_mortars")
+    m = dg.Mesh(mi)
+    q = torch.from_numpy(qh).cuda().requires_grad_(True)
+    v = torch.from_numpy(np.random.default_rng(13).standard_normal(qh.size)).cuda()
+    (AG.residual(q, m) * v).sum().backward()
+    assert torch.equal(q.grad, m.residual_vjp(q.detach(), v))
+
+
+def test_unsupported_meshes_refuse(torch_cuda):
+    torch = torch_cuda
+    from paper_2210_03523_gb300 import dg
+    mi = I.workload("cylinder")
+    m = dg.Mesh(mi)
+    q = m.new_state() + 1.0
+    with pytest.raises(dg.DGError):
+        m.residual_vjp(q, q.clone())
