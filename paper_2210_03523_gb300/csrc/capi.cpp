@@ -165,7 +165,7 @@ void free_device(dg_mesh_impl* m) {
   void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
                   m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
                   m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv,
-                  m->d_vitems, m->d_velist, m->d_sadj, m->d_adjw};
+                  m->d_vitems, m->d_velist, m->d_sadj, m->d_adjw, m->d_gadj, m->d_lG, m->d_lS, m->d_adjt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
@@ -178,6 +178,10 @@ void free_device(dg_mesh_impl* m) {
   m->d_velist = nullptr;
   m->d_sadj = nullptr;
   m->d_adjw = nullptr;
+  m->d_gadj = nullptr;
+  m->d_lG = nullptr;
+  m->d_lS = nullptr;
+  m->d_adjt = nullptr;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
@@ -925,12 +929,18 @@ dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_o
 }
 
 static dg_status adjoint_ready(dg_mesh* m) {
-  if (m->phys.eqs != DG_EULER || !m->affine) return DG_ERR_UNSUPPORTED;
   if (m->faces_unsupported) return DG_ERR_UNSUPPORTED;
   int limit = 0;
   DG_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
   if (sizeof(double) * dgk::mortar_adj_smem_max(m) + 1024 > (size_t)limit) return DG_ERR_UNSUPPORTED;
-  if (!m->d_sadj) DG_CUDA(cudaMalloc(&m->d_sadj, sizeof(double) * 5 * (size_t)m->h_soff[m->n_elem]));
+  const size_t sf = (size_t)m->h_soff[m->n_elem];
+  if (!m->d_sadj) DG_CUDA(cudaMalloc(&m->d_sadj, sizeof(double) * 5 * sf));
+  if (m->phys.eqs == DG_NAVIER_STOKES) {
+    if (!m->d_gadj) DG_CUDA(cudaMalloc(&m->d_gadj, sizeof(double) * 15 * sf));
+    if (!m->d_lS) DG_CUDA(cudaMalloc(&m->d_lS, sizeof(double) * 15 * sf));
+    if (!m->d_lG) DG_CUDA(cudaMalloc(&m->d_lG, sizeof(double) * 15 * (size_t)m->n_nodes));
+    if (!m->d_adjt) DG_CUDA(cudaMalloc(&m->d_adjt, sizeof(double) * 5 * (size_t)m->n_nodes));
+  }
   return DG_OK;
 }
 
@@ -961,8 +971,12 @@ dg_status dg_rk_step_vjp(dg_mesh* m, const double* q0, const double* dt_dev, dou
     double* Qk = k ? Q2 : Q1;
     if (k && (e = cudaMemcpyAsync(Q2, Q1, sizeof(double) * ns, cudaMemcpyDeviceToDevice, m->stream)))
       return from_cuda(e);
-    if ((e = dgk::face_flux(m, Qk, nullptr, false))) return from_cuda(e);
-    if ((e = dgk::volume(m, Qk, nullptr, nullptr, false, k, Qk, G, dt_dev))) return from_cuda(e);
+    if (m->phys.eqs == DG_NAVIER_STOKES) {   // BR1 gradient of the stage state, as in dg_rk_step
+      if ((e = dgk::face_qhat(m, Qk))) return from_cuda(e);
+      if ((e = dgk::gradient(m, Qk, m->d_grad, false))) return from_cuda(e);
+    }
+    if ((e = dgk::face_flux(m, Qk, m->d_grad, false))) return from_cuda(e);
+    if ((e = dgk::volume(m, Qk, m->d_grad, nullptr, false, k, Qk, G, dt_dev))) return from_cuda(e);
   }
   // reversed: with G_k = A_k G_{k-1} + dt R(Q_{k-1}) and Q_k = Q_{k-1} + B_k G_k,
   //   LG = B3 lam;            lam += dt J(Q2)^T LG

@@ -209,6 +209,12 @@ struct dg_mesh_impl {
   // the RK3 step's workspace (stage states Q1, Q2 and the register's cotangent)
   double* d_sadj = nullptr;
   double* d_adjw = nullptr;
+  // Navier-Stokes adjoint: gradient cotangents per element face node and per
+  // node, the lifted q-hat's cotangent per element face node, a state scratch
+  double* d_gadj = nullptr;
+  double* d_lG = nullptr;
+  double* d_lS = nullptr;
+  double* d_adjt = nullptr;
   cudaStream_t cap_stream = nullptr;
   bool adv_warm = false;             // one eager step taken (kernel attributes set)
   struct AdvGraph { const void *q, *g, *t; int steps; cudaGraphExec_t exec; int64_t launches; };

@@ -2438,8 +2438,37 @@ __global__ void __launch_bounds__(kVolThreads) adj_mortar_kernel(MortarParams P,
   }
 }
 
-// Boundary faces, reversed (one warp per face): the Roe flux against the
-// ghost state, which itself depends on the interior trace at a wall.
+// The viscous flux of viscous() on any scalar type (Dual for Jacobian
+// columns in q or in the gradient g = [v][c]).
+template <typename S>
+__device__ void viscous_s(const DevPhys& ph, const S q[5], const S g[15], S fv[3][5]) {
+  const double gm1 = ph.gamma - 1.0;
+  const S ir = 1.0 / q[0];
+  const S u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const S p = gm1 * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  const S T = p * ir / ph.Rgas;
+  S du[3][3], dT[3];
+  const S half_u2 = 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  for (int c = 0; c < 3; ++c) {
+    for (int i = 0; i < 3; ++i) du[i][c] = (g[(1 + i) * 3 + c] - u[i] * g[c]) * ir;
+    const S dpc = gm1 * (g[12 + c] - (u[0] * g[3 + c] + u[1] * g[6 + c] + u[2] * g[9 + c]) + half_u2 * g[c]);
+    dT[c] = (dpc - ph.Rgas * T * g[c]) * ir / ph.Rgas;
+  }
+  const S div = du[0][0] + du[1][1] + du[2][2];
+  for (int d = 0; d < 3; ++d) {
+    S tau[3];
+    for (int i = 0; i < 3; ++i) {
+      tau[i] = ph.mu * (du[i][d] + du[d][i]);
+      if (i == d) tau[i] -= (2.0 / 3.0) * ph.mu * div;
+    }
+    fv[d][0] = q[0] * 0.0;
+    fv[d][1] = tau[0];
+    fv[d][2] = tau[1];
+    fv[d][3] = tau[2];
+    fv[d][4] = u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2] + ph.kappa * dT[d];
+  }
+}
+
 template <typename S>
 __device__ __forceinline__ void bc_ghost_t(const DevPhys& ph, int tag, const S qi[5], S qg[5]) {
   if (tag == DG_BC_WALL) {
@@ -2449,44 +2478,212 @@ __device__ __forceinline__ void bc_ghost_t(const DevPhys& ph, int tag, const S q
   }
 }
 
-template <bool AXIS>
-__global__ void __launch_bounds__(32 * kFaceWarps) adj_face_bc_kernel(FaceParams P, const double* __restrict__ vin,
-                                                                       double* __restrict__ sadj) {
+template <typename S>
+__device__ __forceinline__ void bc_qhat_t(const DevPhys& ph, int tag, const S qi[5], S qh[5]) {
+  if (tag == DG_BC_WALL) {
+    qh[0] = qi[0]; qh[1] = qi[0] * 0.0; qh[2] = qh[1]; qh[3] = qh[1];
+    qh[4] = qi[4] - 0.5 * (qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]) / qi[0];
+  } else {
+    for (int v = 0; v < 5; ++v) qh[v] = qi[v] * 0.0 + ph.qinf[v];
+  }
+}
+
+// (d fv/d q)^T lf -> gq[5] and (d fv/d g)^T lf -> gg[15] at one node, for
+// the viscous flux contracted as sum_d sum_v lf[d][v] fv[d][v]
+__device__ void viscous_vjp(const DevPhys& ph, const double q[5], const double g[15], const double lf[3][5],
+                            double gq[5], double gg[15]) {
+  for (int k = 0; k < 20; ++k) {
+    Dual qd[5], gd[15], fd[3][5];
+    for (int v = 0; v < 5; ++v) qd[v] = {q[v], k == v ? 1.0 : 0.0};
+    for (int c = 0; c < 15; ++c) gd[c] = {g[c], k == 5 + c ? 1.0 : 0.0};
+    viscous_s(ph, qd, gd, fd);
+    double a = 0.0;
+    for (int d = 0; d < 3; ++d)
+      for (int v = 0; v < 5; ++v) a += fd[d][v].d * lf[d][v];
+    if (k < 5) gq[k] = a;
+    else gg[k - 5] = a;
+  }
+}
+
+// Faces of the warp-per-face list, reversed (one warp per face): conforming
+// interior faces (Navier-Stokes or curved meshes) and boundary faces.  The
+// numerical flux F* = |J a| Roe - sum_c {{fv_c}} (J a)_c (BR1 average; a
+// boundary uses the interior fv, without its energy part at a wall) takes
+// the cotangent lf = sum over the sides of -s (1/w_N) v / J; its Jacobian
+// transposes go to the traces (sadj) and, for Navier-Stokes, to the face
+// nodes' gradients (gadj, [v][c] per element face node).
+template <bool AFFINE, bool AXIS, bool NS>
+__global__ void __launch_bounds__(32 * kFaceWarps) adj_face_kernel(FaceParams P, const double* __restrict__ vin,
+                                                                    double* __restrict__ sadj,
+                                                                    double* __restrict__ gadj) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
   const FaceRec fr = P.faces[fidx];
-  if (fr.kind != 2) return;   // interior faces of straight-sided Euler meshes are in the mortar batches
   const MeshView& m = P.m;
   const double gamma = m.ph.gamma;
-  const int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1, side = f & 1;
-  int n1, n2, n3;
-  orders_of(m, e, n1, n2, n3);
-  const int n = n1 * n2 * n3;
-  const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
-  const int64_t o = m.off[e];
-  double ja[3], nrm[3];
-  face_metric<true>(m, e, n, 0, dir, ja);
-  const double area = unit_normal(ja, nrm);
-  const int Nd = (dir == 0 ? n1 : dir == 1 ? n2 : n3) - 1;
-  // d R / d F*(face node) = -(s / w_N) / J, s = +1 on a +xi face, -1 on a -xi face
-  const double c = (side ? -1.0 : 1.0) * inv_wend(Nd) * metric<true>(m.metric, e, 0, 0, 0, 10) * area;
-  double* out = sadj + 5 * (m.soff[e] + face_offset(n1, n2, n3, f));
-  for (int p = lane; p < nf; p += 32) {
-    const int vi = face_vidx(n1, n2, n3, f, p % na, p / na);
-    double lf[5], g[5];
-    for (int v = 0; v < 5; ++v) lf[v] = c * vin[5 * o + v * n + vi];
-    for (int k = 0; k < 5; ++k) {
-      Dual qi[5], qg[5], F[5];
-      for (int v = 0; v < 5; ++v) qi[v] = {P.q[5 * o + v * n + vi], k == v ? 1.0 : 0.0};
-      bc_ghost_t(m.ph, tag, qi, qg);
-      if (side) roe_face_d<AXIS>(gamma, dir, qi, qg, nrm, F);
-      else roe_face_d<AXIS>(gamma, dir, qg, qi, nrm, F);
-      double s = 0.0;
-      for (int v = 0; v < 5; ++v) s += F[v].d * lf[v];
-      g[k] = s;
+  if (fr.kind == 2) {
+    const int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1, side = f & 1;
+    int n1, n2, n3;
+    orders_of(m, e, n1, n2, n3);
+    const int n = n1 * n2 * n3;
+    const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+    const int64_t o = m.off[e];
+    const int Nd = (dir == 0 ? n1 : dir == 1 ? n2 : n3) - 1;
+    double* out = sadj + 5 * (m.soff[e] + face_offset(n1, n2, n3, f));
+    double* gout = NS ? gadj + 15 * (m.soff[e] + face_offset(n1, n2, n3, f)) : nullptr;
+    for (int p = lane; p < nf; p += 32) {
+      const int vi = face_vidx(n1, n2, n3, f, p % na, p / na);
+      double ja[3], nrm[3];
+      face_metric<AFFINE>(m, e, n, vi, dir, ja);
+      const double area = unit_normal(ja, nrm);
+      const double iJ = metric<AFFINE>(m.metric, e, o, n, vi, 10);
+      double qi[5], lf[5], gq[5];
+      for (int v = 0; v < 5; ++v) {
+        qi[v] = P.q[5 * o + v * n + vi];
+        lf[v] = (side ? -1.0 : 1.0) * inv_wend(Nd) * iJ * vin[5 * o + v * n + vi];
+      }
+      for (int k = 0; k < 5; ++k) {   // Roe against the ghost (which depends on qi at a wall)
+        Dual a[5], b[5], F[5];
+        for (int v = 0; v < 5; ++v) a[v] = {qi[v], k == v ? 1.0 : 0.0};
+        bc_ghost_t(m.ph, tag, a, b);
+        if (side) roe_face_d<AXIS>(gamma, dir, a, b, nrm, F);
+        else roe_face_d<AXIS>(gamma, dir, b, a, nrm, F);
+        double s = 0.0;
+        for (int v = 0; v < 5; ++v) s += F[v].d * lf[v];
+        gq[k] = area * s;
+      }
+      if (NS) {
+        double g[15], lv[3][5], vq[5], vg[15];
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + vi];
+        for (int d = 0; d < 3; ++d)
+          for (int v = 0; v < 5; ++v) lv[d][v] = (v >= 1 && (v < 4 || tag != DG_BC_WALL)) ? -ja[d] * lf[v] : 0.0;
+        viscous_vjp(m.ph, qi, g, lv, vq, vg);
+        for (int v = 0; v < 5; ++v) gq[v] += vq[v];
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) gout[(v * 3 + c) * nf + p] = vg[v * 3 + c];
+      }
+      for (int v = 0; v < 5; ++v) out[v * nf + p] = gq[v];
     }
-    for (int v = 0; v < 5; ++v) out[v * nf + p] = g[v];
+    return;
+  }
+  if (fr.kind != 0) return;   // p-nonconforming faces run in the mortar batches
+  const int L = fr.L, R = fr.R, dir = fr.face;
+  int l1, l2, l3, r1, r2, r3;
+  orders_of(m, L, l1, l2, l3);
+  orders_of(m, R, r1, r2, r3);
+  const int nL = l1 * l2 * l3, nR = r1 * r2 * r3;
+  const int64_t oL = m.off[L], oR = m.off[R];
+  const int fL = 2 * dir + 1, fR = 2 * dir;
+  const int la = dir == 0 ? l2 : l1, lb = dir == 2 ? l2 : l3, nf = la * lb;
+  const int NdL = (dir == 0 ? l1 : dir == 1 ? l2 : l3) - 1, NdR = (dir == 0 ? r1 : dir == 1 ? r2 : r3) - 1;
+  double* outL = sadj + 5 * (m.soff[L] + face_offset(l1, l2, l3, fL));
+  double* outR = sadj + 5 * (m.soff[R] + face_offset(r1, r2, r3, fR));
+  for (int p = lane; p < nf; p += 32) {
+    const int a = p % la, b = p / la;
+    const int iL = face_vidx(l1, l2, l3, fL, a, b), iR = face_vidx(r1, r2, r3, fR, a, b);
+    double ja[3], nrm[3];
+    face_metric<AFFINE>(m, L, nL, iL, dir, ja);
+    const double area = unit_normal(ja, nrm);
+    const double iJL = metric<AFFINE>(m.metric, L, oL, nL, iL, 10), iJR = metric<AFFINE>(m.metric, R, oR, nR, iR, 10);
+    double qL[5], qR[5], lf[5], gL[5], gR[5];
+    for (int v = 0; v < 5; ++v) {
+      qL[v] = P.q[5 * oL + v * nL + iL];
+      qR[v] = P.q[5 * oR + v * nR + iR];
+      lf[v] = -inv_wend(NdL) * iJL * vin[5 * oL + v * nL + iL] + inv_wend(NdR) * iJR * vin[5 * oR + v * nR + iR];
+    }
+    double lfa[5];
+    for (int v = 0; v < 5; ++v) lfa[v] = area * lf[v];
+    roe_vjp<AXIS>(gamma, dir, qL, qR, nrm, lfa, gL, gR);
+    if (NS) {
+      double gg[15], lv[3][5], vq[5], vg[15];
+      for (int d = 0; d < 3; ++d)
+        for (int v = 0; v < 5; ++v) lv[d][v] = v >= 1 ? -0.5 * ja[d] * lf[v] : 0.0;
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int e = s2 ? R : L, vi = s2 ? iR : iL, ne = s2 ? nR : nL;
+        const int64_t oe = s2 ? oR : oL;
+        const double* qe = s2 ? qR : qL;
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) gg[v * 3 + c] = P.grad[15 * oe + (c * 5 + v) * ne + vi];
+        viscous_vjp(m.ph, qe, gg, lv, vq, vg);
+        double* gq = s2 ? gR : gL;
+        for (int v = 0; v < 5; ++v) gq[v] += vq[v];
+        int e1, e2, e3;
+        orders_of(m, e, e1, e2, e3);
+        double* go = gadj + 15 * (m.soff[e] + face_offset(e1, e2, e3, s2 ? fR : fL));
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) go[(v * 3 + c) * nf + p] = vg[v * 3 + c];
+      }
+    }
+    for (int v = 0; v < 5; ++v) {
+      outL[v * nf + p] = gL[v];
+      outR[v * nf + p] = gR[v];
+    }
+  }
+}
+
+// q-hat of BR1, reversed (one warp per face): the cotangent of each side's
+// lifted q-hat J a^dir (lS, [v][c] per element face node) becomes that of
+// q-hat, then of the traces: half to each side of an interior face, through
+// q-hat(q_in) at a wall, nothing at the far field (q-hat = q_inf).  Added to
+// sadj.
+template <bool AFFINE>
+__global__ void __launch_bounds__(32 * kFaceWarps) adj_qhat_kernel(FaceParams P, const double* __restrict__ lS,
+                                                                    double* __restrict__ sadj) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int fidx = blockIdx.x * kFaceWarps + warp;
+  if (fidx >= P.n_faces) return;
+  const FaceRec fr = P.faces[fidx];
+  const MeshView& m = P.m;
+  if (fr.kind == 2) {
+    const int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1;
+    if (tag != DG_BC_WALL) return;
+    int n1, n2, n3;
+    orders_of(m, e, n1, n2, n3);
+    const int n = n1 * n2 * n3;
+    const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+    const int64_t o = m.off[e];
+    const int64_t fo = m.soff[e] + face_offset(n1, n2, n3, f);
+    for (int p = lane; p < nf; p += 32) {
+      const int vi = face_vidx(n1, n2, n3, f, p % na, p / na);
+      double ja[3], lh[5];
+      face_metric<AFFINE>(m, e, n, vi, dir, ja);
+      for (int v = 0; v < 5; ++v) {
+        lh[v] = 0.0;
+        for (int c = 0; c < 3; ++c) lh[v] += ja[c] * lS[15 * fo + (v * 3 + c) * nf + p];
+      }
+      for (int k = 0; k < 5; ++k) {
+        Dual qi[5], qh[5];
+        for (int v = 0; v < 5; ++v) qi[v] = {P.q[5 * o + v * n + vi], k == v ? 1.0 : 0.0};
+        bc_qhat_t(m.ph, tag, qi, qh);
+        double s = 0.0;
+        for (int v = 0; v < 5; ++v) s += qh[v].d * lh[v];
+        sadj[5 * fo + k * nf + p] += s;
+      }
+    }
+    return;
+  }
+  if (fr.kind != 0) return;
+  const int L = fr.L, R = fr.R, dir = fr.face;
+  int l1, l2, l3, r1, r2, r3;
+  orders_of(m, L, l1, l2, l3);
+  orders_of(m, R, r1, r2, r3);
+  const int nL = l1 * l2 * l3;
+  const int la = dir == 0 ? l2 : l1, lb = dir == 2 ? l2 : l3, nf = la * lb;
+  const int64_t foL = m.soff[L] + face_offset(l1, l2, l3, 2 * dir + 1);
+  const int64_t foR = m.soff[R] + face_offset(r1, r2, r3, 2 * dir);
+  for (int p = lane; p < nf; p += 32) {
+    const int iL = face_vidx(l1, l2, l3, 2 * dir + 1, p % la, p / la);
+    double ja[3];
+    face_metric<AFFINE>(m, L, nL, iL, dir, ja);   // both sides lift q-hat J a^dir with L's metric
+    for (int v = 0; v < 5; ++v) {
+      double lh = 0.0;
+      for (int c = 0; c < 3; ++c)
+        lh += ja[c] * (lS[15 * foL + (v * 3 + c) * nf + p] + lS[15 * foR + (v * 3 + c) * nf + p]);
+      sadj[5 * foL + v * nf + p] += 0.5 * lh;
+      sadj[5 * foR + v * nf + p] += 0.5 * lh;
+    }
   }
 }
 
@@ -2497,8 +2694,12 @@ struct AdjParams {
   const int32_t* ilist;
   int n_items;
   const double* q;
+  const double* grad;      // BR1 gradient of q (Navier-Stokes)
   const double* v;         // cotangent of the residual (state layout)
-  const double* sadj;      // trace cotangents per element face node (face-buffer layout)
+  const double* sadj;      // trace cotangents per element face node (face-buffer layout), or null
+  const double* gadj;      // gradient cotangents per element face node [v][c] (Navier-Stokes)
+  double* gout;            // the gradient's cotangent, gradient layout (Navier-Stokes)
+  double* lS;              // cotangent of the lifted q-hat J a^dir per element face node [v][c]
   double* out;             // J^T v, or out += (*scale) J^T v
   const double* scale;     // device scalar (accumulate mode)
   int accumulate;
@@ -2508,9 +2709,11 @@ struct AdjParams {
 // Volume part, reversed, one tile per CTA: u = -v/J; the transposed GL
 // derivatives lF_i = D_i^T u; the inner-flux part of the lift, lF_dir -=
 // s (1/w_N) u at each face's nodes; then per node mu_d = sum_i J a^i_d lF_i
-// and J^T v = sum_d (d f_d / d q)^T mu_d (five Dual evaluations of the
-// Euler flux), plus the trace cotangents of the node's faces.
-template <bool AXIS>
+// and J^T v = sum_d (d phi_d / d q)^T mu_d with phi_d = f_d - fv_d (five Dual
+// evaluations of the Euler flux; Navier-Stokes adds the viscous flux's
+// columns in q and, into gout, in the gradient).  With sadj, the trace
+// cotangents of the node's faces are added here.
+template <bool AFFINE, bool AXIS, bool NS>
 __global__ void __launch_bounds__(kVolThreads) adj_volume_kernel(AdjParams P) {
   extern __shared__ double smem[];
   const MeshView& m = P.m;
@@ -2525,7 +2728,7 @@ __global__ void __launch_bounds__(kVolThreads) adj_volume_kernel(AdjParams P) {
       const int el = s / n, p = s - el * n;
       const int e = P.elist[w.first + el];
       const int64_t o = m.off[e];
-      const double iJ = metric<true>(m.metric, e, o, n, p, 10);
+      const double iJ = metric<AFFINE>(m.metric, e, o, n, p, 10);
       for (int v = 0; v < 5; ++v) U[(size_t)el * 5 * n + v * n + p] = -P.v[5 * o + v * n + p] * iJ;
     }
     __syncthreads();
@@ -2584,10 +2787,11 @@ __global__ void __launch_bounds__(kVolThreads) adj_volume_kernel(AdjParams P) {
       for (int d = 0; d < 3; ++d)
         for (int v = 0; v < 5; ++v) {
           if (AXIS) {
-            mu[d][v] = metric<true>(m.metric, e, o, n, p, 4 * d) * L[(d * 5 + v) * n + p];
+            mu[d][v] = metric<AFFINE>(m.metric, e, o, n, p, 4 * d) * L[(d * 5 + v) * n + p];
           } else {
             mu[d][v] = 0.0;
-            for (int i = 0; i < 3; ++i) mu[d][v] += metric<true>(m.metric, e, o, n, p, 3 * i + d) * L[(i * 5 + v) * n + p];
+            for (int i = 0; i < 3; ++i)
+              mu[d][v] += metric<AFFINE>(m.metric, e, o, n, p, 3 * i + d) * L[(i * 5 + v) * n + p];
           }
         }
       double q[5], lam[5];
@@ -2601,17 +2805,29 @@ __global__ void __launch_bounds__(kVolThreads) adj_volume_kernel(AdjParams P) {
           for (int v = 0; v < 5; ++v) g += fd[d][v].d * mu[d][v];
         lam[kk] = g;
       }
-      // trace cotangents of the faces through this node
-      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
-      const double* sb = P.sadj + 5 * m.soff[e];
-      for (int f = 0; f < 6; ++f) {
-        const int dir = f >> 1, side = f & 1;
-        const int c = dir == 0 ? i : dir == 1 ? j : k, nd = dir == 0 ? n1 : dir == 1 ? n2 : n3;
-        if (c != (side ? nd - 1 : 0)) continue;
-        const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
-        const int a = dir == 0 ? j : i, b = dir == 2 ? j : k;
-        const double* fb = sb + 5 * face_offset(n1, n2, n3, f) + a + na * b;
-        for (int v = 0; v < 5; ++v) lam[v] += fb[v * nf];
+      if (NS) {   // phi = f - fv: the viscous columns with the opposite sign
+        double g[15], lv[3][5], vq[5], vg[15];
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + p];
+        for (int d = 0; d < 3; ++d)
+          for (int v = 0; v < 5; ++v) lv[d][v] = -mu[d][v];
+        viscous_vjp(m.ph, q, g, lv, vq, vg);
+        for (int v = 0; v < 5; ++v) lam[v] += vq[v];
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) P.gout[15 * o + (c * 5 + v) * n + p] = vg[v * 3 + c];
+      }
+      if (P.sadj) {   // trace cotangents of the faces through this node
+        const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+        const double* sb = P.sadj + 5 * m.soff[e];
+        for (int f = 0; f < 6; ++f) {
+          const int dir = f >> 1, side = f & 1;
+          const int c = dir == 0 ? i : dir == 1 ? j : k, nd = dir == 0 ? n1 : dir == 1 ? n2 : n3;
+          if (c != (side ? nd - 1 : 0)) continue;
+          const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+          const int a = dir == 0 ? j : i, b = dir == 2 ? j : k;
+          const double* fb = sb + 5 * face_offset(n1, n2, n3, f) + a + na * b;
+          for (int v = 0; v < 5; ++v) lam[v] += fb[v * nf];
+        }
       }
       if (P.accumulate) {
         const double sc = *P.scale;
@@ -2622,6 +2838,129 @@ __global__ void __launch_bounds__(kVolThreads) adj_volume_kernel(AdjParams P) {
     }
     __syncthreads();
   }
+}
+
+// The BR1 gradient, reversed, one tile per CTA.  Forward, per component c:
+// g_c = (1/J) [sum_i D_i (J a^i_c q) + sum over the node's faces s (1/w_N)
+// (qhat J a^dir_c - J a^dir_c q)].  With gamma_c = (gout_c + the node's
+// face cotangents gadj) / J: out += sum_c sum_i J a^i_c D_i^T gamma_c - the
+// lift's inner part, and lS (the cotangent of each face node's lifted
+// q-hat J a^dir) = s (1/w_N) gamma.
+template <bool AFFINE>
+__global__ void __launch_bounds__(kVolThreads) adj_gradient_kernel(AdjParams P) {
+  extern __shared__ double smem[];
+  const MeshView& m = P.m;
+  for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
+    const int slots = w.count * n;
+    double* Gm = smem;   // [count][3][5][n]: gamma_c[v]
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int e = P.elist[w.first + el];
+      const int64_t o = m.off[e];
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      double gm[15];
+      for (int c = 0; c < 3; ++c)
+        for (int v = 0; v < 5; ++v) gm[c * 5 + v] = P.gout[15 * o + (c * 5 + v) * n + p];
+      const double* gb = P.gadj + 15 * m.soff[e];
+      for (int f = 0; f < 6; ++f) {
+        const int dir = f >> 1, side = f & 1;
+        const int cc = dir == 0 ? i : dir == 1 ? j : k, nd = dir == 0 ? n1 : dir == 1 ? n2 : n3;
+        if (cc != (side ? nd - 1 : 0)) continue;
+        const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+        const int a = dir == 0 ? j : i, b = dir == 2 ? j : k;
+        const double* fb = gb + 15 * face_offset(n1, n2, n3, f) + a + na * b;
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) gm[c * 5 + v] += fb[(v * 3 + c) * nf];
+      }
+      const double iJ = metric<AFFINE>(m.metric, e, o, n, p, 10);
+      for (int c = 0; c < 15; ++c) Gm[(size_t)el * 15 * n + c * n + p] = gm[c] * iJ;
+    }
+    __syncthreads();
+    const double* D1 = P.basis + c_boff.D[w.n1];
+    const double* D2 = P.basis + c_boff.D[w.n2];
+    const double* D3 = P.basis + c_boff.D[w.n3];
+    for (int s = threadIdx.x; s < slots; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int e = P.elist[w.first + el];
+      const int64_t o = m.off[e];
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const double* G = Gm + (size_t)el * 15 * n;
+      double lam[5] = {0, 0, 0, 0, 0};
+      for (int c = 0; c < 3; ++c) {
+        double a1[5] = {0, 0, 0, 0, 0}, a2[5] = {0, 0, 0, 0, 0}, a3[5] = {0, 0, 0, 0, 0};
+        for (int mm = 0; mm < n1; ++mm) {
+          const double d = __ldg(D1 + mm * n1 + i);
+          for (int v = 0; v < 5; ++v) a1[v] += d * G[(c * 5 + v) * n + mm + n1 * (j + n2 * k)];
+        }
+        for (int mm = 0; mm < n2; ++mm) {
+          const double d = __ldg(D2 + mm * n2 + j);
+          for (int v = 0; v < 5; ++v) a2[v] += d * G[(c * 5 + v) * n + i + n1 * (mm + n2 * k)];
+        }
+        for (int mm = 0; mm < n3; ++mm) {
+          const double d = __ldg(D3 + mm * n3 + k);
+          for (int v = 0; v < 5; ++v) a3[v] += d * G[(c * 5 + v) * n + i + n1 * (j + n2 * mm)];
+        }
+        const double j1 = metric<AFFINE>(m.metric, e, o, n, p, c), j2 = metric<AFFINE>(m.metric, e, o, n, p, 3 + c),
+                     j3 = metric<AFFINE>(m.metric, e, o, n, p, 6 + c);
+        for (int v = 0; v < 5; ++v) lam[v] += j1 * a1[v] + j2 * a2[v] + j3 * a3[v];
+      }
+      // the lift: inner part on q, face part on the lifted q-hat
+      double* lb_ = P.lS + 15 * m.soff[e];
+      for (int f = 0; f < 6; ++f) {
+        const int dir = f >> 1, side = f & 1;
+        const int cc = dir == 0 ? i : dir == 1 ? j : k, nd = dir == 0 ? n1 : dir == 1 ? n2 : n3;
+        if (cc != (side ? nd - 1 : 0)) continue;
+        const int Nd = nd - 1;
+        const double sg = (side ? 1.0 : -1.0) * inv_wend(Nd);
+        const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+        const int a = dir == 0 ? j : i, b = dir == 2 ? j : k;
+        double* fb = lb_ + 15 * face_offset(n1, n2, n3, f) + a + na * b;
+        for (int c = 0; c < 3; ++c) {
+          const double jd = metric<AFFINE>(m.metric, e, o, n, p, 3 * dir + c);
+          for (int v = 0; v < 5; ++v) {
+            lam[v] -= sg * jd * G[(c * 5 + v) * n + p];
+            fb[(v * 3 + c) * nf] = sg * G[(c * 5 + v) * n + p];
+          }
+        }
+      }
+      for (int v = 0; v < 5; ++v) P.out[5 * o + v * n + p] += lam[v];
+    }
+    __syncthreads();
+  }
+}
+
+// out += the trace cotangents of each node's faces (sadj), one tile per CTA
+__global__ void __launch_bounds__(kVolThreads) adj_gather_kernel(AdjParams P) {
+  const MeshView& m = P.m;
+  for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
+    for (int s = threadIdx.x; s < w.count * n; s += blockDim.x) {
+      const int el = s / n, p = s - el * n;
+      const int e = P.elist[w.first + el];
+      const int64_t o = m.off[e];
+      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const double* sb = P.sadj + 5 * m.soff[e];
+      for (int f = 0; f < 6; ++f) {
+        const int dir = f >> 1, side = f & 1;
+        const int c = dir == 0 ? i : dir == 1 ? j : k, nd = dir == 0 ? n1 : dir == 1 ? n2 : n3;
+        if (c != (side ? nd - 1 : 0)) continue;
+        const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+        const int a = dir == 0 ? j : i, b = dir == 2 ? j : k;
+        const double* fb = sb + 5 * face_offset(n1, n2, n3, f) + a + na * b;
+        for (int v = 0; v < 5; ++v) P.out[5 * o + v * n + p] += fb[v * nf];
+      }
+    }
+  }
+}
+
+// y += (*scale) x
+__global__ void axpy_dev_kernel(double* __restrict__ y, const double* __restrict__ x, const double* scale, int64_t n) {
+  const double a = *scale;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
 }
 
 // y = a y + b x over n values (a = 0: y is not read, so it may hold anything)
@@ -2641,15 +2980,46 @@ static size_t mortar_adj_smem_doubles(int count, int la, int lb, int ra, int rb)
 
 namespace dgk {
 
+template <bool AFF, bool AX, bool NSV>
+static cudaError_t launch_adj_volume(dg_mesh_impl* m, AdjParams A) {
+  cudaError_t err;
+  for (auto& c : m->vol_classes) {
+    A.ilist = c.d_list;
+    A.n_items = c.n;
+    const size_t smem = sizeof(double) * 20 * c.S;
+    if ((err = allow_smem(adj_volume_kernel<AFF, AX, NSV>, smem))) return err;
+    adj_volume_kernel<AFF, AX, NSV><<<c.n, kVolThreads, smem, m->stream>>>(A);
+    if ((err = cudaGetLastError())) return err;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, double* out, const double* scale,
                          bool accumulate) {
   cudaError_t err;
-  Prof pr(m, DG_KERNEL_ADJOINT, (m->n_faces ? 1 : 0) + (m->n_mbatches ? 1 : 0) + (int)m->vol_classes.size());
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  if (ns) {   // the BR1 gradient of q, as in the forward residual
+    if ((err = face_qhat(m, q)) || (err = gradient(m, q, m->d_grad, false))) return err;
+  }
+  const int nvc = (int)m->vol_classes.size();
+  Prof pr(m, DG_KERNEL_ADJOINT,
+          (m->n_faces ? 1 : 0) + (m->n_mbatches ? 1 : 0) + nvc +
+              (ns ? 2 * nvc + (m->n_faces ? 1 : 0) + (accumulate ? 1 : 0) : 0));
+  // 1. faces: warp-per-face list (conforming on curved / Navier-Stokes meshes, boundaries) and mortar batches
   if (m->n_faces) {
     FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
+    F.grad = m->d_grad;
     const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
-    if (m->axis) adj_face_bc_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj);
-    else adj_face_bc_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj);
+    if (ns) {
+      if (m->affine) adj_face_kernel<true, false, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, m->d_gadj);
+      else adj_face_kernel<false, false, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, m->d_gadj);
+    } else if (m->axis) {
+      adj_face_kernel<true, true, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr);
+    } else if (m->affine) {
+      adj_face_kernel<true, false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr);
+    } else {
+      adj_face_kernel<false, false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr);
+    }
     if ((err = cudaGetLastError())) return err;
   }
   if (m->n_mbatches) {
@@ -2661,12 +3031,7 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
     M.q = q;
     M.surf = nullptr;
     M.basis = m->basis64;
-    size_t sm = 0;
-    for (int b = 0; b < m->n_mbatches; ++b) {
-      const int32_t* B = &m->h_mbatches[6 * b];
-      sm = std::max(sm, mortar_adj_smem_doubles(B[1], B[2], B[3], B[4], B[5]));
-    }
-    const size_t smem = sizeof(double) * sm;
+    const size_t smem = sizeof(double) * mortar_adj_smem_max(m);
     if (m->axis) {
       if ((err = allow_smem(adj_mortar_kernel<true>, smem))) return err;
       adj_mortar_kernel<true><<<m->n_mbatches, kVolThreads, smem, m->stream>>>(M, v, m->d_sadj);
@@ -2677,30 +3042,66 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
     if ((err = cudaGetLastError())) return err;
   }
   AdjParams A;
+  memset(&A, 0, sizeof(A));
   A.m = view(m);
   A.items = m->d_vitems;
   A.elist = m->d_velist;
   A.q = q;
+  A.grad = m->d_grad;
   A.v = v;
-  A.sadj = m->d_sadj;
-  A.out = out;
-  A.scale = scale;
-  A.accumulate = accumulate;
   A.basis = m->basis64;
+  if (!ns) {   // 2. volume, with the face cotangents gathered, straight into out
+    A.sadj = m->d_sadj;
+    A.out = out;
+    A.scale = scale;
+    A.accumulate = accumulate;
+    if (m->axis) return launch_adj_volume<true, true, false>(m, A);
+    if (m->affine) return launch_adj_volume<true, false, false>(m, A);
+    return launch_adj_volume<false, false, false>(m, A);
+  }
+  // Navier-Stokes: volume (into the scratch state, and the gradient's
+  // cotangent), BR1 gradient reversed, q-hat reversed, the face cotangents
+  // gathered, then into out
+  double* tmp = m->d_adjt;
+  A.sadj = nullptr;
+  A.out = tmp;
+  A.gout = m->d_lG;
+  A.gadj = m->d_gadj;
+  A.lS = m->d_lS;
+  if ((err = m->affine ? launch_adj_volume<true, false, true>(m, A) : launch_adj_volume<false, false, true>(m, A)))
+    return err;
   for (auto& c : m->vol_classes) {
     A.ilist = c.d_list;
     A.n_items = c.n;
-    const size_t smem = sizeof(double) * 20 * c.S;
-    if (m->axis) {
-      if ((err = allow_smem(adj_volume_kernel<true>, smem))) return err;
-      adj_volume_kernel<true><<<c.n, kVolThreads, smem, m->stream>>>(A);
+    const size_t smem = sizeof(double) * 15 * c.S;
+    if (m->affine) {
+      if ((err = allow_smem(adj_gradient_kernel<true>, smem))) return err;
+      adj_gradient_kernel<true><<<c.n, kVolThreads, smem, m->stream>>>(A);
     } else {
-      if ((err = allow_smem(adj_volume_kernel<false>, smem))) return err;
-      adj_volume_kernel<false><<<c.n, kVolThreads, smem, m->stream>>>(A);
+      if ((err = allow_smem(adj_gradient_kernel<false>, smem))) return err;
+      adj_gradient_kernel<false><<<c.n, kVolThreads, smem, m->stream>>>(A);
     }
     if ((err = cudaGetLastError())) return err;
   }
-  return cudaSuccess;
+  if (m->n_faces) {
+    FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
+    const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+    if (m->affine) adj_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj);
+    else adj_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj);
+    if ((err = cudaGetLastError())) return err;
+  }
+  A.sadj = m->d_sadj;
+  for (auto& c : m->vol_classes) {
+    A.ilist = c.d_list;
+    A.n_items = c.n;
+    adj_gather_kernel<<<c.n, kVolThreads, 0, m->stream>>>(A);
+    if ((err = cudaGetLastError())) return err;
+  }
+  const int64_t ns5 = 5 * m->n_nodes;
+  if (!accumulate) return cudaMemcpyAsync(out, tmp, sizeof(double) * ns5, cudaMemcpyDeviceToDevice, m->stream);
+  const int grid = grid_for((int)std::min<int64_t>((ns5 + 255) / 256, 1 << 20), 8);
+  axpy_dev_kernel<<<grid, 256, 0, m->stream>>>(out, tmp, scale, ns5);
+  return cudaGetLastError();
 }
 
 size_t mortar_adj_smem_max(dg_mesh_impl* m) {

@@ -38,15 +38,39 @@ def _case(name):
     elif name == "wall":
         mi = I.box_mesh(2, orders=(2, 3, 2), phys=ph, periodic=(True, False, True),
                         tags=(I.FAR_FIELD, I.FAR_FIELD, I.WALL, I.WALL, I.FAR_FIELD, I.FAR_FIELD))
+    elif name == "curved_euler":
+        mi = I.box_mesh(2, orders=(2, 3, 2), phys=ph, geom_order=2, mapping=I.wavy_map(0.05))
+    elif name in ("ns_box", "ns_box_farfield"):
+        ph = I.Physics(1, 1.4, 0.05, 0.72, 2.0, (1.0, 0.4, -0.3, 0.2, 8.0))
+        kw = {} if name == "ns_box" else dict(periodic=(False, False, False))
+        mi = I.box_mesh(2, orders=(2, 2, 3), phys=ph, **kw)
+    elif name == "ns_ogrid":
+        p0 = 10.0
+        ph = I.Physics(1, 1.4, 0.05, 0.72, p0, (1.0, 0.5, 0.1, 0.05, p0 / 0.4 + 0.5 * (0.25 + 0.01 + 0.0025)))
+        mi = I.ogrid_mesh(n_theta=8, n_r=2, ratio=4.0, orders=(2, 2, 1), phys=ph)
     else:
         raise KeyError(name)
     import oracle
     om = oracle.Mesh(mi)
-    q = I.pulse_state(om.coords(), mi.orders, ph, width=0.5, center=(-0.2, 0.1, 0.0))
+    if ph.eqs == 1:   # the free stream with a smooth perturbation
+        qi = np.asarray(ph.qinf)
+        u0 = qi[1:4] / qi[0]
+        p0 = (ph.gamma - 1) * (qi[4] - 0.5 * qi[0] * u0 @ u0)
+
+        def fn(x, y, z):
+            rho = qi[0] * (1.0 + 0.05 * np.sin(1.3 * x + 0.2) * np.cos(0.9 * y))
+            u = [u0[0] + 0.05 * np.cos(y + 0.4 * z), u0[1] + 0.04 * np.sin(0.7 * x), u0[2] + 0.03 * np.cos(x - y)]
+            p = p0 * (1.0 + 0.02 * np.cos(x + 0.5 * y))
+            return np.stack([rho, rho * u[0], rho * u[1], rho * u[2],
+                             p / (ph.gamma - 1) + 0.5 * rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)])
+        q = I.pointwise_state(om.coords(), mi.orders, fn)
+    else:
+        q = I.pulse_state(om.coords(), mi.orders, ph, width=0.5, center=(-0.2, 0.1, 0.0))
     return mi, om, q
 
 
-@pytest.mark.parametrize("name", ["periodic_mortars", "farfield_mortars", "sheared", "wall"])
+@pytest.mark.parametrize("name", ["periodic_mortars", "farfield_mortars", "sheared", "wall", "curved_euler", "ns_box",
+                                  "ns_box_farfield", "ns_ogrid"])
 def test_residual_vjp_matches_oracle(torch_cuda, name):
     torch = torch_cuda
     from paper_2210_03523_gb300 import dg
@@ -59,10 +83,11 @@ def test_residual_vjp_matches_oracle(torch_cuda, name):
     assert m.get_error() == 0
 
 
-def test_rk_step_vjp_matches_oracle(torch_cuda):
+@pytest.mark.parametrize("name", ["periodic_mortars", "ns_ogrid"])
+def test_rk_step_vjp_matches_oracle(torch_cuda, name):
     torch = torch_cuda
     from paper_2210_03523_gb300 import dg
-    mi, om, q = _case("periodic_mortars")
+    mi, om, q = _case(name)
     dt = 0.5 * om.max_dt(q, 1.0)
     lam = np.random.default_rng(10).standard_normal(q.size)
     ref = om.rk_step_vjp_fd(q, dt, lam)
@@ -137,9 +162,11 @@ def test_residual_function_backward(torch_cuda):
 
 
 def test_unsupported_meshes_refuse(torch_cuda):
+    """Mortars on curved or Navier-Stokes meshes have no forward kernel, so no adjoint either."""
     torch = torch_cuda
     from paper_2210_03523_gb300 import dg
-    mi = I.workload("cylinder")
+    ph = I.Physics(1, 1.4, 0.05, 0.72, 2.0, (1.0, 0.4, -0.3, 0.2, 8.0))
+    mi = I.box_mesh(2, orders=I.random_orders(8, 1, 3, 45), phys=ph)
     m = dg.Mesh(mi)
     q = m.new_state() + 1.0
     with pytest.raises(dg.DGError):
