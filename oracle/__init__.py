@@ -71,6 +71,7 @@ def lib():
                                           C.c_int, dp]
         L.orc_residual_vjp_fd.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_int, dp]
         L.orc_rk_step_vjp_fd.argtypes = [C.c_void_p, dp, C.c_double, dp, C.c_double, dp]
+        L.orc_wall_force.argtypes = [C.c_void_p, dp, C.c_int, dp]
         L.orc_advance.restype = C.c_int
         L.orc_advance.argtypes = [C.c_void_p, dp, dp, C.c_double, dp, C.c_double, C.c_int]
         _lib = L
@@ -239,6 +240,12 @@ class Mesh:
         out = np.empty_like(q)
         lib().orc_rk_step_vjp_fd(self.h, _d(q), float(dt), _d(lam), float(eps), _d(out))
         return out
+
+    def wall_force(self, q, tag=-2):
+        """Force of the fluid on the boundary faces with this tag (3 values)."""
+        F = np.empty(3)
+        lib().orc_wall_force(self.h, _d(_f64(q)), int(tag), _d(F))
+        return F
 
     def isolated_residual_at(self, e, N, qN):
         N = _i32(N)

@@ -1402,3 +1402,57 @@ void orc_residual_vjp_fd(void* h, const double* q, const double* v, double eps, 
 void orc_rk_step_vjp_fd(void* h, const double* q, double dt, const double* lam, double eps, double* out) {
   fd_vjp(h, 2, dt, q, lam, eps, out);
 }
+
+/* ------------------------------------------------------------------------
+ * Force of the fluid on the boundary faces with tag `tag` (the wall of the
+ * cylinder case, Sec. 3.3: drag and lift):
+ *   F = sum over those faces and their GL nodes of w_a w_b |J a^dir| (p n - tau n),
+ * n the unit outward normal of the fluid element (pointing into the body),
+ * p the pressure and tau the viscous stress of the node's state and BR1
+ * gradient (Navier-Stokes; zero for Euler).  The face's own GL rule.
+ * ---------------------------------------------------------------------- */
+void orc_wall_force(void* h, const double* q, int tag, double* F) {
+  omesh* m = h;
+  const ophys* ph = &m->ph;
+  double* g = NULL;
+  if (ph->eqs == 1) {
+    g = malloc(sizeof(double) * 3 * NV * m->off[m->n_elem]);
+    orc_gradient(h, q, g, 0);
+  }
+  F[0] = F[1] = F[2] = 0.0;
+  for (int e = 0; e < m->n_elem; ++e)
+    for (int f = 0; f < 6; ++f) {
+      if (m->nbr[6 * e + f] != tag) continue;
+      const int* N = m->ord + 3 * e;
+      const egeo* geo = &m->geo[e];
+      const int n = geo->n, dir = f / 2, side = f % 2;
+      int t0, t1;
+      tangential(dir, &t0, &t1);
+      double xa[NMAX], wa[NMAX], xb[NMAX], wb[NMAX];
+      orc_gl(N[t0], xa, wa);
+      orc_gl(N[t1], xb, wb);
+      for (int b = 0; b <= N[t1]; ++b)
+        for (int a = 0; a <= N[t0]; ++a) {
+          const int p = face_vol_index(N, f, a, b);
+          double ja[3], nv[3], qn[NV];
+          for (int c = 0; c < 3; ++c) ja[c] = geo->Ja[dir][c][p];
+          const double area = sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+          for (int c = 0; c < 3; ++c) nv[c] = (side ? 1.0 : -1.0) * ja[c] / area;
+          for (int v = 0; v < NV; ++v) qn[v] = q[NV * m->off[e] + v * n + p];
+          const double pr = (ph->gamma - 1.0) * (qn[4] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]) / qn[0]);
+          double tn[3] = {0.0, 0.0, 0.0};
+          if (g) {
+            double gq[3 * NV], fv[NV];
+            for (int v = 0; v < NV; ++v)
+              for (int c = 0; c < 3; ++c) gq[v * 3 + c] = g[3 * NV * m->off[e] + (c * NV + v) * n + p];
+            for (int d = 0; d < 3; ++d) {
+              visc_flux(ph, qn, gq, d, fv);   /* fv[1 + i] = tau_{i d} */
+              for (int i = 0; i < 3; ++i) tn[i] += fv[1 + i] * nv[d];
+            }
+          }
+          const double wgt = wa[a] * wb[b] * area;
+          for (int i = 0; i < 3; ++i) F[i] += wgt * (pr * nv[i] - tn[i]);
+        }
+    }
+  free(g);
+}
