@@ -317,9 +317,28 @@ dg_status dg_set_tiles(dg_mesh* mesh, const dg_tiles* in);
  * transposes, taken exactly by forward-mode differentiation of the same
  * flux code (Dual numbers).  q, v, out: device state-layout arrays; out may
  * not alias q or v.  Asynchronous.
- * Errors: DG_ERR_ARG; DG_ERR_UNSUPPORTED (Navier-Stokes, curved elements, or
- * mortar batches whose adjoint exceeds shared memory); DG_ERR_CUDA. */
-dg_status dg_residual_vjp(dg_mesh* mesh, const double* q, const double* v, double* out);
+ * Navier-Stokes adds the BR1 terms: the viscous flux's Jacobians in q and
+ * in the gradient, the gradient's own transpose (GL derivative and lift) and
+ * q-hat's (the interior average, the wall's q-hat(q_in)).
+ * qinf_adj (device, 5 doubles, optional): accumulates the cotangent of the
+ * far-field state q_inf (the Roe ghost and BR1's q-hat at far-field faces).
+ * Errors: DG_ERR_ARG; DG_ERR_UNSUPPORTED (mortars on curved or Navier-Stokes
+ * meshes, which have no forward kernel either, or mortar batches whose
+ * adjoint exceeds shared memory); DG_ERR_CUDA. */
+dg_status dg_residual_vjp(dg_mesh* mesh, const double* q, const double* v, double* out, double* qinf_adj);
+
+/* Force of the fluid on the boundary faces with tag `tag` (DG_BC_WALL: the
+ * cylinder's drag and lift, Sec. 3.3):
+ *   F = sum over those faces and their GL nodes of w_a w_b |J a^dir| (p n - tau n),
+ * n the unit outward normal of the fluid element (into the body), p and tau
+ * the pressure and viscous stress of the node's state and BR1 gradient
+ * (tau = 0 for Euler).  force_dev: device double[3], written on the mesh
+ * stream; the sum runs in face order (deterministic). */
+dg_status dg_wall_force(dg_mesh* mesh, const double* q, int32_t tag, double* force_dev);
+/* out = (dF/dq)^T lam (lam_dev: device double[3]), through the BR1 gradient
+ * for Navier-Stokes; with scale_dev (device scalar) out += (*scale_dev) ... */
+dg_status dg_wall_force_vjp(dg_mesh* mesh, const double* q, int32_t tag, const double* lam_dev, double* out,
+                            const double* scale_dev);
 
 /* Adjoint of one Williamson RK3 step (dg_rk_step) from the state q0 at the
  * step's start: lam <- (dq1/dq0)^T lam, with dt (the device scalar dt_dev)
@@ -327,8 +346,9 @@ dg_status dg_residual_vjp(dg_mesh* mesh, const double* q, const double* v, doubl
  * G_k = A_k G_{k-1} + dt R(Q_{k-1}) and Q_k = Q_{k-1} + B_k G_k reversed:
  * LG = B3 lam, lam += dt J(Q2)^T LG; LG = A3 LG + B2 lam, lam += dt J(Q1)^T LG;
  * LG = A2 LG + B1 lam, lam += dt J(q0)^T LG.  The mesh holds four states of
- * workspace.  Same support and errors as dg_residual_vjp. */
-dg_status dg_rk_step_vjp(dg_mesh* mesh, const double* q0, const double* dt_dev, double* lam);
+ * workspace.  qinf_adj (optional): accumulates the far-field state's
+ * cotangent of the step.  Same support and errors as dg_residual_vjp. */
+dg_status dg_rk_step_vjp(dg_mesh* mesh, const double* q0, const double* dt_dev, double* lam, double* qinf_adj);
 
 /* Kernel kinds for dg_profile_read. */
 enum {

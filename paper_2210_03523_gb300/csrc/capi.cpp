@@ -165,7 +165,8 @@ void free_device(dg_mesh_impl* m) {
   void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
                   m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
                   m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv,
-                  m->d_vitems, m->d_velist, m->d_sadj, m->d_adjw, m->d_gadj, m->d_lG, m->d_lS, m->d_adjt};
+                  m->d_vitems, m->d_velist, m->d_sadj, m->d_adjw, m->d_gadj, m->d_lG, m->d_lS, m->d_adjt,
+                  m->d_force};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
@@ -182,6 +183,7 @@ void free_device(dg_mesh_impl* m) {
   m->d_lG = nullptr;
   m->d_lS = nullptr;
   m->d_adjt = nullptr;
+  m->d_force = nullptr;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
@@ -935,23 +937,39 @@ static dg_status adjoint_ready(dg_mesh* m) {
   if (sizeof(double) * dgk::mortar_adj_smem_max(m) + 1024 > (size_t)limit) return DG_ERR_UNSUPPORTED;
   const size_t sf = (size_t)m->h_soff[m->n_elem];
   if (!m->d_sadj) DG_CUDA(cudaMalloc(&m->d_sadj, sizeof(double) * 5 * sf));
+  if (!m->d_adjt) DG_CUDA(cudaMalloc(&m->d_adjt, sizeof(double) * 5 * (size_t)m->n_nodes));
+  if (!m->d_force) DG_CUDA(cudaMalloc(&m->d_force, sizeof(double) * 3 * (size_t)std::max(m->n_faces, 1)));
   if (m->phys.eqs == DG_NAVIER_STOKES) {
     if (!m->d_gadj) DG_CUDA(cudaMalloc(&m->d_gadj, sizeof(double) * 15 * sf));
     if (!m->d_lS) DG_CUDA(cudaMalloc(&m->d_lS, sizeof(double) * 15 * sf));
     if (!m->d_lG) DG_CUDA(cudaMalloc(&m->d_lG, sizeof(double) * 15 * (size_t)m->n_nodes));
-    if (!m->d_adjt) DG_CUDA(cudaMalloc(&m->d_adjt, sizeof(double) * 5 * (size_t)m->n_nodes));
   }
   return DG_OK;
 }
 
-dg_status dg_residual_vjp(dg_mesh* m, const double* q, const double* v, double* out) {
+dg_status dg_residual_vjp(dg_mesh* m, const double* q, const double* v, double* out, double* qinf_adj) {
   if (!m || !q || !v || !out || out == q || out == v) return DG_ERR_ARG;
   dg_status st = adjoint_ready(m);
   if (st != DG_OK) return st;
-  return from_cuda(dgk::residual_vjp(m, q, v, out, nullptr, false));
+  return from_cuda(dgk::residual_vjp(m, q, v, out, nullptr, false, qinf_adj));
 }
 
-dg_status dg_rk_step_vjp(dg_mesh* m, const double* q0, const double* dt_dev, double* lam) {
+dg_status dg_wall_force(dg_mesh* m, const double* q, int32_t tag, double* force_dev) {
+  if (!m || !q || !force_dev || tag >= 0) return DG_ERR_ARG;
+  dg_status st = adjoint_ready(m);
+  if (st != DG_OK) return st;
+  return from_cuda(dgk::wall_force(m, q, tag, force_dev));
+}
+
+dg_status dg_wall_force_vjp(dg_mesh* m, const double* q, int32_t tag, const double* lam_dev, double* out,
+                            const double* scale_dev) {
+  if (!m || !q || !lam_dev || !out || out == q || tag >= 0) return DG_ERR_ARG;
+  dg_status st = adjoint_ready(m);
+  if (st != DG_OK) return st;
+  return from_cuda(dgk::wall_force_vjp(m, q, tag, lam_dev, out, scale_dev));
+}
+
+dg_status dg_rk_step_vjp(dg_mesh* m, const double* q0, const double* dt_dev, double* lam, double* qinf_adj) {
   if (!m || !q0 || !dt_dev || !lam || lam == q0) return DG_ERR_ARG;
   dg_status st = adjoint_ready(m);
   if (st != DG_OK) return st;
@@ -986,7 +1004,7 @@ dg_status dg_rk_step_vjp(dg_mesh* m, const double* q0, const double* dt_dev, dou
   for (int k = 2; k >= 0; --k) {
     const double a = k == 2 ? 0.0 : A[k + 1], b = B[k];
     if ((e = dgk::axpby(m, LG, lam, a, b, (int64_t)ns))) return from_cuda(e);
-    if ((e = dgk::residual_vjp(m, Qs[k], LG, lam, dt_dev, true))) return from_cuda(e);
+    if ((e = dgk::residual_vjp(m, Qs[k], LG, lam, dt_dev, true, qinf_adj))) return from_cuda(e);
   }
   return DG_OK;
 }

@@ -95,7 +95,12 @@ size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32);
 cudaError_t max_dt_bits(dg_mesh_impl* m, const double* q, unsigned long long* bits);
 // adjoint: out = J(q)^T v, or out += (*scale) J(q)^T v (Euler, straight-sided elements)
 cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, double* out, const double* scale,
-                         bool accumulate);
+                         bool accumulate, double* qinf_adj);
+// force of the fluid on the boundary faces of a tag (device F[3]) and its
+// vector-Jacobian product: out = (dF/dq)^T lam, or out += (*scale) ... (scale non-null)
+cudaError_t wall_force(dg_mesh_impl* m, const double* q, int tag, double* F);
+cudaError_t wall_force_vjp(dg_mesh_impl* m, const double* q, int tag, const double* lam, double* out,
+                           const double* scale);
 size_t mortar_adj_smem_max(dg_mesh_impl* m);
 // y = a y + b x
 cudaError_t axpby(dg_mesh_impl* m, double* y, const double* x, double a, double b, int64_t n);
@@ -215,6 +220,7 @@ struct dg_mesh_impl {
   double* d_lG = nullptr;
   double* d_lS = nullptr;
   double* d_adjt = nullptr;
+  double* d_force = nullptr;   // wall force: one partial per warp-list face
   cudaStream_t cap_stream = nullptr;
   bool adv_warm = false;             // one eager step taken (kernel attributes set)
   struct AdvGraph { const void *q, *g, *t; int steps; cudaGraphExec_t exec; int64_t launches; };

@@ -2515,7 +2515,8 @@ __device__ void viscous_vjp(const DevPhys& ph, const double q[5], const double g
 template <bool AFFINE, bool AXIS, bool NS>
 __global__ void __launch_bounds__(32 * kFaceWarps) adj_face_kernel(FaceParams P, const double* __restrict__ vin,
                                                                     double* __restrict__ sadj,
-                                                                    double* __restrict__ gadj) {
+                                                                    double* __restrict__ gadj, double* qinf_adj,
+                                                                    const double* scale) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
@@ -2552,6 +2553,21 @@ __global__ void __launch_bounds__(32 * kFaceWarps) adj_face_kernel(FaceParams P,
         double s = 0.0;
         for (int v = 0; v < 5; ++v) s += F[v].d * lf[v];
         gq[k] = area * s;
+      }
+      if (qinf_adj && tag != DG_BC_WALL) {   // the far-field state is the ghost: its cotangent too
+        const double sc = scale ? *scale : 1.0;
+        for (int k = 0; k < 5; ++k) {
+          Dual a[5], b[5], F[5];
+          for (int v = 0; v < 5; ++v) {
+            a[v] = {qi[v], 0.0};
+            b[v] = {m.ph.qinf[v], k == v ? 1.0 : 0.0};
+          }
+          if (side) roe_face_d<AXIS>(gamma, dir, a, b, nrm, F);
+          else roe_face_d<AXIS>(gamma, dir, b, a, nrm, F);
+          double s = 0.0;
+          for (int v = 0; v < 5; ++v) s += F[v].d * lf[v];
+          atomicAdd(qinf_adj + k, sc * area * s);
+        }
       }
       if (NS) {
         double g[15], lv[3][5], vq[5], vg[15];
@@ -2630,7 +2646,8 @@ __global__ void __launch_bounds__(32 * kFaceWarps) adj_face_kernel(FaceParams P,
 // sadj.
 template <bool AFFINE>
 __global__ void __launch_bounds__(32 * kFaceWarps) adj_qhat_kernel(FaceParams P, const double* __restrict__ lS,
-                                                                    double* __restrict__ sadj) {
+                                                                    double* __restrict__ sadj, double* qinf_adj,
+                                                                    const double* scale) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
@@ -2638,7 +2655,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) adj_qhat_kernel(FaceParams P,
   const MeshView& m = P.m;
   if (fr.kind == 2) {
     const int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1;
-    if (tag != DG_BC_WALL) return;
+    if (tag != DG_BC_WALL && !qinf_adj) return;
     int n1, n2, n3;
     orders_of(m, e, n1, n2, n3);
     const int n = n1 * n2 * n3;
@@ -2652,6 +2669,11 @@ __global__ void __launch_bounds__(32 * kFaceWarps) adj_qhat_kernel(FaceParams P,
       for (int v = 0; v < 5; ++v) {
         lh[v] = 0.0;
         for (int c = 0; c < 3; ++c) lh[v] += ja[c] * lS[15 * fo + (v * 3 + c) * nf + p];
+      }
+      if (tag != DG_BC_WALL) {   // far field: q-hat = q_inf
+        const double sc = scale ? *scale : 1.0;
+        for (int v = 0; v < 5; ++v) atomicAdd(qinf_adj + v, sc * lh[v]);
+        continue;
       }
       for (int k = 0; k < 5; ++k) {
         Dual qi[5], qh[5];
@@ -2995,7 +3017,7 @@ static cudaError_t launch_adj_volume(dg_mesh_impl* m, AdjParams A) {
 }
 
 cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, double* out, const double* scale,
-                         bool accumulate) {
+                         bool accumulate, double* qinf_adj) {
   cudaError_t err;
   const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
   if (ns) {   // the BR1 gradient of q, as in the forward residual
@@ -3011,14 +3033,17 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
     F.grad = m->d_grad;
     const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
     if (ns) {
-      if (m->affine) adj_face_kernel<true, false, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, m->d_gadj);
-      else adj_face_kernel<false, false, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, m->d_gadj);
+      if (m->affine) adj_face_kernel<true, false, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, m->d_gadj, qinf_adj, scale);
+      else adj_face_kernel<false, false, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, m->d_gadj, qinf_adj,
+                                                                                     scale);
     } else if (m->axis) {
-      adj_face_kernel<true, true, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr);
+      adj_face_kernel<true, true, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr, qinf_adj, scale);
     } else if (m->affine) {
-      adj_face_kernel<true, false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr);
+      adj_face_kernel<true, false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr, qinf_adj,
+                                                                                   scale);
     } else {
-      adj_face_kernel<false, false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr);
+      adj_face_kernel<false, false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, v, m->d_sadj, nullptr, qinf_adj,
+                                                                                    scale);
     }
     if ((err = cudaGetLastError())) return err;
   }
@@ -3086,8 +3111,8 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
   if (m->n_faces) {
     FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
     const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
-    if (m->affine) adj_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj);
-    else adj_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj);
+    if (m->affine) adj_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, qinf_adj, scale);
+    else adj_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, qinf_adj, scale);
     if ((err = cudaGetLastError())) return err;
   }
   A.sadj = m->d_sadj;
@@ -3117,6 +3142,224 @@ cudaError_t axpby(dg_mesh_impl* m, double* y, const double* x, double a, double 
   const int grid = grid_for((int)std::min<int64_t>((n + 255) / 256, 1 << 20), 8);
   Prof pr(m, DG_KERNEL_ADJOINT);
   axpby_kernel<<<grid, 256, 0, m->stream>>>(y, x, a, b, n);
+  return cudaGetLastError();
+}
+
+}  // namespace dgk
+
+// ---------------------------------------------------------------------------
+// Force of the fluid on the boundary faces of one tag (the cylinder's wall,
+// Sec. 3.3: drag and lift): F = sum over the faces and their GL nodes of
+// w_a w_b |J a^dir| (p n - tau n), n the unit outward normal of the fluid
+// element (into the body), tau the viscous stress of the node's state and
+// BR1 gradient.  One warp per face, a partial per face, then a sum in face
+// order (deterministic); and its vector-Jacobian product.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename S>
+__device__ __forceinline__ void wall_traction(const DevPhys& ph, const S q[5], const S* g, bool ns, const double nv[3],
+                                              S t[3]) {
+  const double gm1 = ph.gamma - 1.0;
+  const S p = gm1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+  for (int i = 0; i < 3; ++i) t[i] = p * nv[i];
+  if (ns) {
+    S fv[3][5];
+    viscous_s(ph, q, g, fv);
+    for (int i = 0; i < 3; ++i)
+      for (int d = 0; d < 3; ++d) t[i] -= fv[d][1 + i] * nv[d];
+  }
+}
+
+template <bool AFFINE, bool NS>
+__global__ void __launch_bounds__(32 * kFaceWarps) wall_force_kernel(FaceParams P, int tag, double* partial) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int fidx = blockIdx.x * kFaceWarps + warp;
+  if (fidx >= P.n_faces) return;
+  const FaceRec fr = P.faces[fidx];
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (fr.kind == 2 && fr.R == tag) {
+    const MeshView& m = P.m;
+    const int e = fr.L, f = fr.face, dir = f >> 1, side = f & 1;
+    int n1, n2, n3;
+    orders_of(m, e, n1, n2, n3);
+    const int n = n1 * n2 * n3;
+    const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+    const int64_t o = m.off[e];
+    const double* wa = P.basis + c_boff.W[na - 1];
+    const double* wb = P.basis + c_boff.W[nb - 1];
+    for (int p = lane; p < nf; p += 32) {
+      const int a = p % na, b = p / na;
+      const int vi = face_vidx(n1, n2, n3, f, a, b);
+      double ja[3], nv[3], q[5], g[15], t[3];
+      face_metric<AFFINE>(m, e, n, vi, dir, ja);
+      const double area = unit_normal(ja, nv);
+      for (int c = 0; c < 3; ++c) nv[c] *= side ? 1.0 : -1.0;
+      for (int v = 0; v < 5; ++v) q[v] = P.q[5 * o + v * n + vi];
+      if (NS)
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + vi];
+      wall_traction(m.ph, q, g, NS, nv, t);
+      const double wgt = __ldg(wa + a) * __ldg(wb + b) * area;
+      for (int i = 0; i < 3; ++i) acc[i] += wgt * t[i];
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off);
+  if (lane == 0)
+    for (int i = 0; i < 3; ++i) partial[3 * fidx + i] = acc[i];
+}
+
+__global__ void force_sum_kernel(const double* partial, int n_faces, double* F) {
+  if (threadIdx.x >= 3) return;
+  double s = 0.0;
+  for (int f = 0; f < n_faces; ++f) s += partial[3 * f + threadIdx.x];
+  F[threadIdx.x] = s;
+}
+
+// the force's cotangent lam (3, device) onto the wall nodes' traces (sadj)
+// and, for Navier-Stokes, gradients (gadj)
+template <bool AFFINE, bool NS>
+__global__ void __launch_bounds__(32 * kFaceWarps) wall_force_vjp_kernel(FaceParams P, int tag, const double* lam,
+                                                                          double* sadj, double* gadj) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int fidx = blockIdx.x * kFaceWarps + warp;
+  if (fidx >= P.n_faces) return;
+  const FaceRec fr = P.faces[fidx];
+  if (fr.kind != 2 || fr.R != tag) return;
+  const MeshView& m = P.m;
+  const int e = fr.L, f = fr.face, dir = f >> 1, side = f & 1;
+  int n1, n2, n3;
+  orders_of(m, e, n1, n2, n3);
+  const int n = n1 * n2 * n3;
+  const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+  const int64_t o = m.off[e];
+  const int64_t fo = m.soff[e] + face_offset(n1, n2, n3, f);
+  const double* wa = P.basis + c_boff.W[na - 1];
+  const double* wb = P.basis + c_boff.W[nb - 1];
+  const double l0 = lam[0], l1 = lam[1], l2 = lam[2];
+  for (int p = lane; p < nf; p += 32) {
+    const int a = p % na, b = p / na;
+    const int vi = face_vidx(n1, n2, n3, f, a, b);
+    double ja[3], nv[3], q[5], g[15];
+    face_metric<AFFINE>(m, e, n, vi, dir, ja);
+    const double area = unit_normal(ja, nv);
+    for (int c = 0; c < 3; ++c) nv[c] *= side ? 1.0 : -1.0;
+    for (int v = 0; v < 5; ++v) q[v] = P.q[5 * o + v * n + vi];
+    if (NS)
+      for (int v = 0; v < 5; ++v)
+        for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + vi];
+    const double wgt = __ldg(wa + a) * __ldg(wb + b) * area;
+    const int nk = NS ? 20 : 5;
+    for (int k = 0; k < nk; ++k) {
+      Dual qd[5], gd[15], t[3];
+      for (int v = 0; v < 5; ++v) qd[v] = {q[v], k == v ? 1.0 : 0.0};
+      if (NS)
+        for (int c = 0; c < 15; ++c) gd[c] = {g[c], k == 5 + c ? 1.0 : 0.0};
+      wall_traction(m.ph, qd, gd, NS, nv, t);
+      const double s = wgt * (l0 * t[0].d + l1 * t[1].d + l2 * t[2].d);
+      if (k < 5) sadj[5 * fo + k * nf + p] = s;
+      else gadj[15 * fo + (k - 5) * nf + p] = s;   // g index v*3+c: the gadj layout [v][c]
+    }
+  }
+}
+
+}  // namespace
+
+namespace dgk {
+
+cudaError_t wall_force(dg_mesh_impl* m, const double* q, int tag, double* F) {
+  cudaError_t err;
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  if (ns && ((err = face_qhat(m, q)) || (err = gradient(m, q, m->d_grad, false)))) return err;
+  FaceParams P = dgk_face_params_for(m, q, nullptr);
+  P.grad = m->d_grad;
+  const int nfc = std::max(m->n_faces, 1);
+  const int grid = (nfc + kFaceWarps - 1) / kFaceWarps;
+  Prof pr(m, DG_KERNEL_ADJOINT, m->n_faces ? 2 : 1);
+  if (!m->n_faces) return cudaMemsetAsync(F, 0, 3 * sizeof(double), m->stream);
+  if (ns) {
+    if (m->affine) wall_force_kernel<true, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, m->d_force);
+    else wall_force_kernel<false, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, m->d_force);
+  } else {
+    if (m->affine) wall_force_kernel<true, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, m->d_force);
+    else wall_force_kernel<false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, m->d_force);
+  }
+  if ((err = cudaGetLastError())) return err;
+  force_sum_kernel<<<1, 32, 0, m->stream>>>(m->d_force, m->n_faces, F);
+  return cudaGetLastError();
+}
+
+// out = (dF/dq)^T lam, or out += (*scale) (dF/dq)^T lam
+cudaError_t wall_force_vjp(dg_mesh_impl* m, const double* q, int tag, const double* lam, double* out,
+                           const double* scale) {
+  cudaError_t err;
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  if (ns && ((err = face_qhat(m, q)) || (err = gradient(m, q, m->d_grad, false)))) return err;
+  const size_t sf = (size_t)m->h_soff[m->n_elem];
+  const int64_t ns5 = 5 * m->n_nodes;
+  if ((err = cudaMemsetAsync(m->d_sadj, 0, sizeof(double) * 5 * sf, m->stream))) return err;
+  if ((err = cudaMemsetAsync(m->d_adjt, 0, sizeof(double) * ns5, m->stream))) return err;
+  if (ns) {
+    if ((err = cudaMemsetAsync(m->d_gadj, 0, sizeof(double) * 15 * sf, m->stream))) return err;
+    if ((err = cudaMemsetAsync(m->d_lG, 0, sizeof(double) * 15 * m->n_nodes, m->stream))) return err;
+  }
+  Prof pr(m, DG_KERNEL_ADJOINT, 1);
+  if (m->n_faces) {
+    FaceParams P = dgk_face_params_for(m, q, nullptr);
+    P.grad = m->d_grad;
+    const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+    if (ns) {
+      if (m->affine) wall_force_vjp_kernel<true, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, lam, m->d_sadj, m->d_gadj);
+      else wall_force_vjp_kernel<false, true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, lam, m->d_sadj, m->d_gadj);
+    } else {
+      if (m->affine) wall_force_vjp_kernel<true, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, lam, m->d_sadj, nullptr);
+      else wall_force_vjp_kernel<false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, lam, m->d_sadj, nullptr);
+    }
+    if ((err = cudaGetLastError())) return err;
+  }
+  AdjParams A;
+  memset(&A, 0, sizeof(A));
+  A.m = view(m);
+  A.items = m->d_vitems;
+  A.elist = m->d_velist;
+  A.q = q;
+  A.grad = m->d_grad;
+  A.basis = m->basis64;
+  A.out = m->d_adjt;
+  if (ns) {   // the gradients' cotangents through BR1, then q-hat
+    A.gout = m->d_lG;
+    A.gadj = m->d_gadj;
+    A.lS = m->d_lS;
+    for (auto& c : m->vol_classes) {
+      A.ilist = c.d_list;
+      A.n_items = c.n;
+      const size_t smem = sizeof(double) * 15 * c.S;
+      if (m->affine) {
+        if ((err = allow_smem(adj_gradient_kernel<true>, smem))) return err;
+        adj_gradient_kernel<true><<<c.n, kVolThreads, smem, m->stream>>>(A);
+      } else {
+        if ((err = allow_smem(adj_gradient_kernel<false>, smem))) return err;
+        adj_gradient_kernel<false><<<c.n, kVolThreads, smem, m->stream>>>(A);
+      }
+      if ((err = cudaGetLastError())) return err;
+    }
+    FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
+    const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+    if (m->affine) adj_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, nullptr, nullptr);
+    else adj_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, nullptr, nullptr);
+    if ((err = cudaGetLastError())) return err;
+  }
+  A.sadj = m->d_sadj;
+  for (auto& c : m->vol_classes) {
+    A.ilist = c.d_list;
+    A.n_items = c.n;
+    adj_gather_kernel<<<c.n, kVolThreads, 0, m->stream>>>(A);
+    if ((err = cudaGetLastError())) return err;
+  }
+  if (!scale) return cudaMemcpyAsync(out, m->d_adjt, sizeof(double) * ns5, cudaMemcpyDeviceToDevice, m->stream);
+  const int grid = grid_for((int)std::min<int64_t>((ns5 + 255) / 256, 1 << 20), 8);
+  axpy_dev_kernel<<<grid, 256, 0, m->stream>>>(out, m->d_adjt, scale, ns5);
   return cudaGetLastError();
 }
 

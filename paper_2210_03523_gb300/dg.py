@@ -83,8 +83,10 @@ def _lib():
                                    C.c_uint32, vp],
             "dg_advance": [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int64, C.c_uint32, i64p],
             "dg_autotune": [vp, vp, C.c_int32, C.POINTER(dg_tiles)],
-            "dg_residual_vjp": [vp, vp, vp, vp],
-            "dg_rk_step_vjp": [vp, vp, vp, vp],
+            "dg_residual_vjp": [vp, vp, vp, vp, vp],
+            "dg_rk_step_vjp": [vp, vp, vp, vp, vp],
+            "dg_wall_force": [vp, vp, C.c_int32, vp],
+            "dg_wall_force_vjp": [vp, vp, C.c_int32, vp, vp, vp],
             "dg_get_tiles": [vp, C.POINTER(dg_tiles)],
             "dg_set_tiles": [vp, C.POINTER(dg_tiles)],
             "dg_max_dt": [vp, vp, C.c_double, vp],
@@ -109,7 +111,7 @@ def exported_symbols():
             "dg_residual", "dg_max_dt", "dg_rk_step", "dg_tau_estimate", "dg_set_orders", "dg_get_error",
             "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc",
             "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles",
-            "dg_residual_vjp", "dg_rk_step_vjp"]
+            "dg_residual_vjp", "dg_rk_step_vjp", "dg_wall_force", "dg_wall_force_vjp"]
 
 
 def _check(st, where):
@@ -307,18 +309,36 @@ class Mesh:
                                  DG_ADVANCE_EAGER if eager else 0, C.byref(n) if count else None), "dg_advance")
         return n.value if count else None
 
-    def residual_vjp(self, q, v, out=None):
-        """dg_residual_vjp: (dR/dq)^T v at q."""
+    def residual_vjp(self, q, v, out=None, qinf_adj=None):
+        """dg_residual_vjp: (dR/dq)^T v at q; qinf_adj (5 doubles, device) accumulates
+        the far-field state's cotangent."""
         out = self.new_state() if out is None else out
         self._check_state(q, v, out)
-        _check(_lib().dg_residual_vjp(self.h, _ptr(q), _ptr(v), _ptr(out)), "dg_residual_vjp")
+        _check(_lib().dg_residual_vjp(self.h, _ptr(q), _ptr(v), _ptr(out), _ptr(qinf_adj)), "dg_residual_vjp")
         return out
 
-    def rk_step_vjp(self, q0, dt, lam):
+    def rk_step_vjp(self, q0, dt, lam, qinf_adj=None):
         """dg_rk_step_vjp: lam <- (d step(q0) / d q0)^T lam in place, dt a device scalar."""
         self._check_state(q0, lam)
-        _check(_lib().dg_rk_step_vjp(self.h, _ptr(q0), _ptr(dt), _ptr(lam)), "dg_rk_step_vjp")
+        _check(_lib().dg_rk_step_vjp(self.h, _ptr(q0), _ptr(dt), _ptr(lam), _ptr(qinf_adj)), "dg_rk_step_vjp")
         return lam
+
+    def wall_force(self, q, tag=-2, out=None):
+        """dg_wall_force: the force of the fluid on the boundary faces of this tag (3, device)."""
+        import torch
+        self._check_state(q)
+        out = torch.empty(3, dtype=torch.float64, device=self.device) if out is None else out
+        _check(_lib().dg_wall_force(self.h, _ptr(q), int(tag), _ptr(out)), "dg_wall_force")
+        return out
+
+    def wall_force_vjp(self, q, lam, tag=-2, out=None, scale=None):
+        """dg_wall_force_vjp: (dF/dq)^T lam (lam: 3 doubles on the device); with
+        scale (device scalar) out += scale * ... instead."""
+        out = self.new_state() if out is None else out
+        self._check_state(q, out)
+        _check(_lib().dg_wall_force_vjp(self.h, _ptr(q), int(tag), _ptr(lam), _ptr(out), _ptr(scale)),
+               "dg_wall_force_vjp")
+        return out
 
     def autotune(self, q, reps=5):
         """dg_autotune: time each tile budget per size class on this mesh and

@@ -92,7 +92,8 @@ def test_mesh_create_rejects_bad_input_on_the_host(lib):
     assert lib.dg_mesh_create(C.byref(d), None, C.byref(h)) == 1
     for fn in ("dg_residual", "dg_rk_step", "dg_max_dt", "dg_set_orders", "dg_get_error", "dg_mesh_destroy",
                "dg_tau_estimate", "dg_node_coords", "dg_advance", "dg_tau_extrapolate", "dg_select_orders",
-               "dg_autotune", "dg_get_tiles", "dg_set_tiles"):
+               "dg_autotune", "dg_get_tiles", "dg_set_tiles", "dg_residual_vjp", "dg_rk_step_vjp",
+               "dg_wall_force", "dg_wall_force_vjp"):
         f = getattr(lib, fn)
         args = [0 if t in (C.c_uint32, C.c_int32, C.c_int64) else (1.0 if t is C.c_double else None)
                 for t in f.argtypes]
