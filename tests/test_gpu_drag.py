@@ -46,7 +46,7 @@ def _state(mi, om):
         damp = 1.0 - np.exp(-(r2 - 0.25) * 4.0)
         rho = qi[0] * (1.0 + 0.05 * np.sin(1.3 * x + 0.2) * np.cos(0.9 * y))
         u = [damp * (u0[0] + 0.05 * np.cos(y)), damp * (u0[1] + 0.04 * np.sin(0.7 * x)), damp * u0[2]]
-        p = p0 * (1.0 + 0.02 * np.cos(x + 0.5 * y))
+        p = p0 * (1.0 + 0.02 * np.cos(x + 0.5 * y + 0.7))   # the phase: a net pressure force on the body
         return np.stack([rho, rho * u[0], rho * u[1], rho * u[2],
                          p / (ph.gamma - 1) + 0.5 * rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)])
     return I.pointwise_state(om.coords(), mi.orders, fn)
