@@ -28,6 +28,22 @@
 
 __constant__ BasisOffsets c_boff;
 
+// Division by a small runtime divisor (1..kFdivMax) as a multiply-high and
+// two shifts (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, the round-up method for full 32-bit dividends): the
+// multiplier and shift of every divisor in constant memory, read by a warp
+// whose divisor is uniform as one broadcast.  The tau sweep's index
+// arithmetic spends its integer pipe on these divisions otherwise.
+constexpr int kFdivMax = 1024;
+__constant__ uint2 c_fdiv[kFdivMax + 1];
+
+__device__ __forceinline__ int fdiv(int n, int d) {
+  if (d > kFdivMax) return n / d;
+  const uint2 c = c_fdiv[d];
+  const uint32_t un = (uint32_t)n, t1 = __umulhi(c.x, un);
+  return (int)((t1 + ((un - t1) >> (c.y ? 1u : 0u))) >> (c.y ? c.y - 1u : 0u));
+}
+
 namespace {
 
 constexpr int kFaceWarps = 4;          // faces per CTA in the face kernels
@@ -1046,7 +1062,7 @@ __device__ __forceinline__ T met_at(const T* met, bool affine, int n, int p, int
 template <typename T>
 __device__ __forceinline__ void div5(const T* basis, const T* F, int n1, int n2, int n3, int p, T acc[5]) {
   const int n = n1 * n2 * n3;
-  const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+  const int pj = fdiv(p, n1), k = fdiv(pj, n2), i = p - pj * n1, j = pj - k * n2;
   const T* D1 = basis + c_boff.D[n1 - 1];
   const T* D2 = basis + c_boff.D[n2 - 1];
   const T* D3 = basis + c_boff.D[n3 - 1];
@@ -1123,7 +1139,7 @@ __device__ void tau_residual(const TauParams<T>& P, bool affine, const T* met, c
     const T J = met_at(met, affine, n, p, 9);
     const T iJ = -(T)1 / J;
     if (IR) {
-      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const int pj = fdiv(p, n1), k = fdiv(pj, n2), i = p - pj * n1, j = pj - k * n2;
       const T Jw = J * w1[i] * w2[j] * w3[k];
       for (int v = 0; v < 5; ++v) {
         const T t = IR[v * qs + p] - acc[v] * iJ;   // tau~ = I R^P - R^N(I q^P)
@@ -1149,7 +1165,7 @@ __device__ void apply_dir_tile(const T* A, int t, int f, int dir, int e0, int e1
   if (dir == 0) o0 = t; else if (dir == 1) o1 = t; else o2 = t;
   const int no = o0 * o1 * o2;
   for (int p = threadIdx.x; p < no; p += blockDim.x) {
-    int i = p % o0, j = (p / o0) % o1, k = p / (o0 * o1);
+    const int pj = fdiv(p, o0), k = fdiv(pj, o1), i = p - pj * o0, j = pj - k * o1;
     int r, base, stride;
     if (dir == 0) { r = i; base = e0 * (j + e1 * k); stride = 1; }
     else if (dir == 1) { r = j; base = i + e0 * e1 * k; stride = e0; }
@@ -1236,7 +1252,7 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
   if (NS) {
     for (int c = 0; c < 3; ++c) {
       for (int t = threadIdx.x; t < pts; t += blockDim.x) {
-        const int el = t / n, p = t - el * n;
+        const int el = fdiv(t, n), p = t - el * n;
         const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
         for (int i = 0; i < 3; ++i) {
           T ja = met_at(met, AFFINE, n, p, 3 * i + c);
@@ -1245,7 +1261,7 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
       }
       __syncthreads();
       for (int t = threadIdx.x; t < pts; t += blockDim.x) {
-        const int el = t / n, p = t - el * n;
+        const int el = fdiv(t, n), p = t - el * n;
         const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
         T acc[5];
         div5(P.basis, Ft + el * 15 * n, n1, n2, n3, p, acc);
@@ -1256,7 +1272,7 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
     }
   }
   for (int t = threadIdx.x; t < pts; t += blockDim.x) {
-    const int el = t / n, p = t - el * n;
+    const int el = fdiv(t, n), p = t - el * n;
     const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
     T q[5], f[3][5];
     for (int v = 0; v < 5; ++v) q[v] = X[el * xs + v * n + p];
@@ -1284,7 +1300,7 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
   const T* w2 = P.basis + c_boff.W[N2];
   const T* w3 = P.basis + c_boff.W[N3];
   for (int t = threadIdx.x; t < pts; t += blockDim.x) {
-    const int el = t / n, p = t - el * n;
+    const int el = fdiv(t, n), p = t - el * n;
     const int e = els[el];
     const T* met = tile_met<T, AFFINE>(P, e, P1, P2, N1, N2, N3);
     T acc[5];
@@ -1293,7 +1309,7 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
     const T iJ = -(T)1 / J;
     if (na) {
       // R rounded exactly as when stored, so that tau at N = P is exactly 0
-      const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
+      const int pj = fdiv(p, n1), k = fdiv(pj, n2), i = p - pj * n1, j = pj - k * n2;
       const T Jw = J * w1[i] * w2[j] * w3[k];
       T a = 0, b = 0;
       for (int v = 0; v < 5; ++v) {
@@ -1330,7 +1346,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
     const int cnt = w.count;
     const int P1 = w.n1, P2 = w.n2, P3 = w.n3, nP = (P1 + 1) * (P2 + 1) * (P3 + 1);
     for (int t = threadIdx.x; t < cnt * P.n_sweep; t += blockDim.x) {
-      const int el = t / P.n_sweep, s = t - el * P.n_sweep;
+      const int el = fdiv(t, P.n_sweep), s = t - el * P.n_sweep;
       if (P.sweep[3 * s] > P1 || P.sweep[3 * s + 1] > P2 || P.sweep[3 * s + 2] > P3) {
         const int64_t idx = (int64_t)els[el] * P.n_sweep + s;
         if (P.map_new) P.map_new[idx] = (T)-1;
@@ -1339,7 +1355,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
     }
     if (P.rp) continue;
     for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
-      const int el = t / nP, p = t - el * nP;
+      const int el = fdiv(t, nP), p = t - el * nP;
       const int64_t o = m.off[els[el]];
       for (int v = 0; v < 5; ++v) A1[el * 10 * nP + v * nP + p] = (T)P.q[5 * o + v * nP + p];
     }
@@ -1379,7 +1395,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
       const T* I3 = P.basis + c_boff.I[P3][N3];
       const int per = n12 * c3;
       for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
-        const int el = t / per, x = t - el * per, ij = x % n12, k = x / n12;
+        const int el = fdiv(t, per), x = t - el * per, k = fdiv(x, n12), ij = x - k * n12;
         const int64_t o = m.off[els[el]];
         T acc[10];
         for (int c = 0; c < 10; ++c) acc[c] = 0;
@@ -1400,7 +1416,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
       const T* I2 = P.basis + c_boff.I[P2][N2];
       const int pin = n12 * c3, per = n1 * c2 * c3;
       for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
-        const int el = t / per, x = t - el * per, i = x % n1, j = (x / n1) % c2, k = x / (n1 * c2);
+        const int el = fdiv(t, per), x = t - el * per, xj = fdiv(x, n1), k = fdiv(xj, c2), i = x - xj * n1, j = xj - k * c2;
         const T* src = A3 + el * 10 * pin + i + n12 * k;
         T acc[10];
         for (int c = 0; c < 10; ++c) acc[c] = 0;
@@ -1421,7 +1437,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
         const T* I1 = P.basis + c_boff.I[P1][N1];
         const int pin = n1 * c2 * c3;
         for (int t = threadIdx.x; t < cnt * nN; t += blockDim.x) {
-          const int el = t / nN, x = t - el * nN, i = x % c1, jk = x / c1;
+          const int el = fdiv(t, nN), x = t - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
           const T* src = A2 + el * 10 * pin + n1 * jk;
           T acc[10];
           for (int c = 0; c < 10; ++c) acc[c] = 0;
@@ -1722,6 +1738,14 @@ void upload_basis(int device, const BasisOffsets& off, const std::vector<double>
                   const float** d32) {
   (void)device;
   cudaMemcpyToSymbol(c_boff, &off, sizeof(off));
+  std::vector<uint2> fd(kFdivMax + 1, make_uint2(0u, 0u));
+  for (int d = 1; d <= kFdivMax; ++d) {
+    uint32_t l = 0;
+    while ((1u << l) < (uint32_t)d) ++l;
+    const uint64_t mm = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - (uint64_t)d)) / (uint64_t)d + 1;
+    fd[d] = make_uint2((uint32_t)mm, l);
+  }
+  cudaMemcpyToSymbol(c_fdiv, fd.data(), sizeof(uint2) * fd.size());
   double* a = nullptr;
   float* b = nullptr;
   cudaMalloc(&a, sizeof(double) * data.size());
