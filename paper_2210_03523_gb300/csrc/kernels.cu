@@ -1236,13 +1236,33 @@ __device__ __forceinline__ const T* tile_met(const TauParams<T>& P, int e, int P
   return P.metric + P.bank_off[e] + 10 * bank_combo_offset(P1, P2, N1, N2, N3);
 }
 
+// Contravariant Euler fluxes Ft^i = J a^i . f at one node into F (stride n):
+// the tau sweep's one flux routine, shared by R^P and every coarse residual so
+// that R^N at N = P reproduces R^P bit for bit (tau at N = P is then exactly
+// 0).  AXIS: J a^i = (J a^i_i) e_i.
+template <typename T, bool AFFINE, bool AXIS>
+__device__ __forceinline__ void tau_flux(T gm1, const T* met, int n, int p, const T q[5], T* F) {
+  T f[3][5];
+  euler_fluxes(gm1, q, f);
+  for (int i = 0; i < 3; ++i) {
+    if (AXIS) {
+      const T a = met_at(met, AFFINE, n, p, 4 * i);
+      for (int v = 0; v < 5; ++v) F[(i * 5 + v) * n] = a * f[i][v];
+    } else {
+      const T ja0 = met_at(met, AFFINE, n, p, 3 * i), ja1 = met_at(met, AFFINE, n, p, 3 * i + 1),
+              ja2 = met_at(met, AFFINE, n, p, 3 * i + 2);
+      for (int v = 0; v < 5; ++v) F[(i * 5 + v) * n] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
+    }
+  }
+}
+
 // Isolated residual of a tile of cnt same-order elements, state X[el][5][n]
 // (element stride xs) at orders (n1,n2,n3): R = -(1/J) sum_i D^(i) Ft^i, with
 // the element-local BR1 gradient and viscous flux for Navier-Stokes.  Either
 // writes R to Rout (element e's R at Rout + 5*off_e, [5][n]), or folds it into
 // the tau norms: t = IR - R with IR = X + 5*n (the restricted I R^P), per
 // element max |t| and max |J w t| into the shared slots na[el], nb[el].
-template <typename T, bool AFFINE, bool NS>
+template <typename T, bool AFFINE, bool NS, bool AXIS>
 __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int cnt, int P1, int P2, int N1, int N2,
                                   int N3, const T* X, int xs, T* Ft, T* Gs, T* Rout,
                                   typename Bits<T>::type* na, typename Bits<T>::type* nb) {
@@ -1274,8 +1294,13 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
   for (int t = threadIdx.x; t < pts; t += blockDim.x) {
     const int el = fdiv(t, n), p = t - el * n;
     const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
-    T q[5], f[3][5];
+    T q[5];
     for (int v = 0; v < 5; ++v) q[v] = X[el * xs + v * n + p];
+    if (!NS) {
+      tau_flux<T, AFFINE, AXIS>(gm1, met, n, p, q, Ft + el * 15 * n + p);
+      continue;
+    }
+    T f[3][5];
     euler_fluxes(gm1, q, f);
     if (NS) {
       T g[15], fv[3][5];
@@ -1331,7 +1356,7 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
 // Prologue of the isolated sweep, one tile per CTA iteration: the isolated
 // R^P of every element (into the scratch, unless the caller gave R^P), and
 // -1 in the maps for every sweep entry the element's orders cannot reach.
-template <typename T, bool AFFINE, bool NS>
+template <typename T, bool AFFINE, bool NS, bool AXIS>
 __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -1360,7 +1385,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
       for (int v = 0; v < 5; ++v) A1[el * 10 * nP + v * nP + p] = (T)P.q[5 * o + v * nP + p];
     }
     __syncthreads();
-    tau_tile_residual<T, AFFINE, NS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, Ft, Gs, P.rp_scratch, nullptr,
+    tau_tile_residual<T, AFFINE, NS, AXIS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, Ft, Gs, P.rp_scratch, nullptr,
                                      nullptr);
   }
 }
@@ -1369,12 +1394,14 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
 // sweep entries sharing (N2, N3).  The unit restricts q^P and R^P in xi3 and
 // xi2 once, then runs every entry of the group: restriction in xi1, coarse
 // isolated residual fused with both tau norms, map store.
-template <typename T, bool AFFINE, bool NS>
+template <typename T, bool AFFINE, bool NS, bool AXIS>
 __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   typedef typename Bits<T>::type B;
-  __shared__ B na[kVolThreads], nb[kVolThreads];
+  __shared__ B na2[2][kVolThreads], nb2[2][kVolThreads];   // per-element norms, two entries in flight
+  B* na = na2[0];
+  B* nb = nb2[0];
   const int S = P.S;     // tile capacity in nodes (max count * n_P of the class)
   T* A3 = sm;            // [el][10][pts3]  q^P, R^P restricted in xi3
   T* A2 = A3 + 10 * S;   // [el][10][pts2]  ... in xi2, xi3
@@ -1428,6 +1455,76 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
       }
       __syncthreads();
     }
+    if (!NS) {
+      // Euler, two barriers per entry: (1) store the previous entry's norms,
+      // clear this entry's slots, restrict in xi1 and take the fluxes at once;
+      // (2) derivative, tau and both norms
+      const T gm1 = P.gamma - (T)1;
+      const T* w2 = P.basis + c_boff.W[N2];
+      const T* w3 = P.basis + c_boff.W[N3];
+      int prev_s = -1, buf = 0;
+      for (int ge = 0; ge < g.w; ++ge) {
+        const int2 ent = P.gentries[g.z + ge];   // sweep index, N1
+        const int s = ent.x, N1 = ent.y;
+        if (N1 > P1) continue;
+        const int c1 = N1 + 1, nN = c1 * c2 * c3;
+        const T* I1 = P.basis + c_boff.I[P1][N1];
+        const int pin = n1 * c2 * c3;
+        for (int el = threadIdx.x; el < cnt; el += blockDim.x) {
+          if (prev_s >= 0) {
+            const int64_t idx = (int64_t)els[el] * P.n_sweep + prev_s;
+            map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][el]));
+            map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][el]));
+          }
+          na2[buf][el] = 0;
+          nb2[buf][el] = 0;
+        }
+        for (int t = threadIdx.x; t < cnt * nN; t += blockDim.x) {
+          const int el = fdiv(t, nN), x = t - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
+          const T* src = A2 + el * 10 * pin + n1 * jk;
+          T acc[10];
+          for (int c = 0; c < 10; ++c) acc[c] = 0;
+          for (int mm = 0; mm < n1; ++mm) {
+            const T wi = I1[i * n1 + mm];
+            for (int c = 0; c < 10; ++c) acc[c] += wi * src[c * pin + mm];
+          }
+          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
+          tau_flux<T, AFFINE, AXIS>(gm1, met, nN, x, acc, Ft + el * 15 * nN + x);
+          for (int v = 0; v < 5; ++v) A1[el * 10 * nN + (5 + v) * nN + x] = acc[5 + v];   // I R^P
+        }
+        __syncthreads();
+        const T* w1 = P.basis + c_boff.W[N1];
+        for (int t = threadIdx.x; t < cnt * nN; t += blockDim.x) {
+          const int el = fdiv(t, nN), p = t - el * nN;
+          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
+          T acc[5];
+          div5(P.basis, Ft + el * 15 * nN, c1, c2, c3, p, acc);
+          const T J = met_at(met, AFFINE, nN, p, 9);
+          const T iJ = -(T)1 / J;
+          const int pj = fdiv(p, c1), k = fdiv(pj, c2), i = p - pj * c1, j = pj - k * c2;
+          const T Jw = J * w1[i] * w2[j] * w3[k];
+          T a = 0, b = 0;
+          for (int v = 0; v < 5; ++v) {
+            const T r = mul_rn(acc[v], iJ);   // rounded as R^P was, so that tau at N = P is exactly 0
+            const T tt = A1[el * 10 * nN + (5 + v) * nN + p] - r;
+            a = tmax(a, (T)fabs(tt));
+            b = tmax(b, (T)fabs(Jw * tt));
+          }
+          smax_bits(na2[buf] + el, a);
+          smax_bits(nb2[buf] + el, b);
+        }
+        __syncthreads();
+        prev_s = s;
+        buf ^= 1;
+      }
+      for (int el = threadIdx.x; el < cnt && prev_s >= 0; el += blockDim.x) {
+        const int64_t idx = (int64_t)els[el] * P.n_sweep + prev_s;
+        map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][el]));
+        map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][el]));
+      }
+      __syncthreads();
+      continue;
+    }
     for (int ge = 0; ge < g.w; ++ge) {
       const int2 ent = P.gentries[g.z + ge];   // sweep index, N1
       const int s = ent.x, N1 = ent.y;
@@ -1449,7 +1546,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
         }
         __syncthreads();
       }
-      tau_tile_residual<T, AFFINE, NS>(P, els, cnt, P1, P2, N1, N2, N3, A1, 10 * nN, Ft, Gs, nullptr, na, nb);
+      tau_tile_residual<T, AFFINE, NS, AXIS>(P, els, cnt, P1, P2, N1, N2, N3, A1, 10 * nN, Ft, Gs, nullptr, na, nb);
       for (int el = threadIdx.x; el < cnt; el += blockDim.x) {
         const int64_t idx = (int64_t)els[el] * P.n_sweep + s;
         map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na[el]));
@@ -1900,18 +1997,19 @@ static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
       if (P.n_list == 0) continue;
       const size_t smem = tau_smem_for(c.S, ns, fp32);
       const int grid = grid_for(P.n_list, 16);
-#define DG_TAU_CASE(AFF, NSV)                                                                  \
+#define DG_TAU_CASE(AFF, NSV, AXV)                                                             \
   if (phase == 0) {                                                                             \
-    if ((err = allow_smem(tau_prologue_kernel<T, AFF, NSV>, smem))) return err;                 \
-    tau_prologue_kernel<T, AFF, NSV><<<grid, kVolThreads, smem, m->stream>>>(P);                \
+    if ((err = allow_smem(tau_prologue_kernel<T, AFF, NSV, AXV>, smem))) return err;            \
+    tau_prologue_kernel<T, AFF, NSV, AXV><<<grid, kVolThreads, smem, m->stream>>>(P);           \
   } else {                                                                                      \
-    if ((err = allow_smem(tau_kernel<T, AFF, NSV>, smem))) return err;                          \
-    tau_kernel<T, AFF, NSV><<<grid, kVolThreads, smem, m->stream>>>(P);                         \
+    if ((err = allow_smem(tau_kernel<T, AFF, NSV, AXV>, smem))) return err;                     \
+    tau_kernel<T, AFF, NSV, AXV><<<grid, kVolThreads, smem, m->stream>>>(P);                    \
   }
-      if (m->affine && !ns) { DG_TAU_CASE(true, false) }
-      else if (m->affine) { DG_TAU_CASE(true, true) }
-      else if (!ns) { DG_TAU_CASE(false, false) }
-      else { DG_TAU_CASE(false, true) }
+      if (m->axis && !ns) { DG_TAU_CASE(true, false, true) }
+      else if (m->affine && !ns) { DG_TAU_CASE(true, false, false) }
+      else if (m->affine) { DG_TAU_CASE(true, true, false) }
+      else if (!ns) { DG_TAU_CASE(false, false, false) }
+      else { DG_TAU_CASE(false, true, false) }
 #undef DG_TAU_CASE
       if ((err = cudaGetLastError())) return err;
     }
