@@ -295,6 +295,39 @@ def fp32_tau_check(m, q, sweep):
             "selection_changed_fraction": changed, "eps32": 2.0 ** -23}
 
 
+def adjoint_timing(m, q, dt_adj, reps=10):
+    """The adjoint on the bench mesh (outside the timed regions): one residual
+    VJP and one RK3-step VJP (which recomputes the stage states), CUDA events
+    over reps calls each, against the forward residual."""
+    import torch
+    from paper_2210_03523_gb300 import dg
+    v = torch.randn(q.shape, dtype=torch.float64, device=q.device, generator=torch.Generator(q.device).manual_seed(1))
+    out = torch.empty_like(q)
+    lam = v.clone()
+    r = torch.empty_like(q)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    try:
+        fwd = timed(lambda: m.residual(q, r))
+        vjp = timed(lambda: m.residual_vjp(q, v, out))
+        step = timed(lambda: m.rk_step_vjp(q, dt_adj, lam))
+    except dg.DGError as e:
+        return {"unavailable": str(e)}
+    ndof = m.n_nodes
+    return {"residual_ms": fwd, "residual_vjp_ms": vjp, "rk_step_vjp_ms": step,
+            "vjp_over_residual": vjp / fwd, "vjp_dof_per_s": ndof / (vjp * 1e-3),
+            "note": "dg_residual_vjp and dg_rk_step_vjp (FP64; Roe by a hand-written reverse sweep, the volume fluxes by Dual numbers)"}
+
+
 # ------------------------------------------------------------ our arm
 def run_gb300(args, rank, world):
     import torch
@@ -422,6 +455,7 @@ def run_gb300(args, rank, world):
     sel = m.select_orders(map_new, sweep, 1.0, 1, 8, 2)
     select_ms = (time.perf_counter() - t0) * 1e3
     fp32_check = fp32_tau_check(m, q, sweep)
+    adjoint = adjoint_timing(m, q, dt_adj=m.max_dt(q, CFL))
 
     # roofline of the dominant kernel (by share of the profiled step) and of the volume kernel
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
@@ -489,6 +523,7 @@ def run_gb300(args, rank, world):
                          "peak_source": f"FP32: {N_SM} SMs x {FP32_FMA_PER_CLK_PER_SM} FFMA/clk x 2 x {sm_mhz:.0f} MHz"},
         "kernels": kernels_json,
         "fp32_tau_check": fp32_check,
+        "adjoint": adjoint,
         "autotune": {"enabled": not args.no_autotune, "seconds": tune_s, "vol_budget": tiles["vol_budget"],
                      "mortar_budget": tiles["mortar_budget"], "volume_launch_ms_after_class": tiles["vol_ms"],
                      "volume_launch_ms_before_class": tiles["vol_ms_default"],

@@ -2309,22 +2309,196 @@ __device__ __forceinline__ void roe_face_d(double gamma, int dir, const Dual qL[
   }
 }
 
+// The Roe flux's vector-Jacobian product by a reverse (adjoint) sweep: the
+// forward quantities of roe_t, then their cotangents in reverse order, each
+// step the transpose of one forward line.  gL = (dF/dqL)^T lf, gR likewise;
+// the same derivative the Dual evaluations give (|x| at x = 0 takes the
+// derivative of +x, as absval does), at a few times the cost of one flux.
+template <int AX>
+__device__ void roe_vjp_rev(double gamma, const double qL[5], const double qR[5], const double n[3],
+                            const double lf[5], double gL[5], double gR[5]) {
+  const double gm1 = gamma - 1.0;
+  // forward
+  const double rsL = rsqrt(qL[0]), rsR = rsqrt(qR[0]);
+  const double sL = qL[0] * rsL, sR = qR[0] * rsR;
+  const double irL = rsL * rsL, irR = rsR * rsR;
+  double uL[3], uR[3], nc[3];
+  for (int c = 0; c < 3; ++c) {
+    uL[c] = qL[1 + c] * irL;
+    uR[c] = qR[1 + c] * irR;
+    nc[c] = ncomp<AX>(n, c);
+  }
+  const double pL = gm1 * (qL[4] - 0.5 * (qL[1] * uL[0] + qL[2] * uL[1] + qL[3] * uL[2]));
+  const double pR = gm1 * (qR[4] - 0.5 * (qR[1] * uR[0] + qR[2] * uR[1] + qR[3] * uR[2]));
+  const double HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
+  const double is = 1.0 / (sL + sR);
+  double ut[3];
+  for (int c = 0; c < 3; ++c) ut[c] = (sL * uL[c] + sR * uR[c]) * is;
+  const double Ht = (sL * HL + sR * HR) * is;
+  const double rt = sL * sR;
+  const double q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+  const double c2 = gm1 * (Ht - 0.5 * q2);
+  const double rc = rsqrt(c2);
+  const double ct = c2 * rc, ic2 = rc * rc;
+  const double unL = uL[0] * nc[0] + uL[1] * nc[1] + uL[2] * nc[2];
+  const double unR = uR[0] * nc[0] + uR[1] * nc[1] + uR[2] * nc[2];
+  const double utn = ut[0] * nc[0] + ut[1] * nc[1] + ut[2] * nc[2];
+  const double dun = unR - unL, dp = pR - pL;
+  const double rcd = rt * ct * dun;
+  const double a1 = 0.5 * (dp - rcd) * ic2, a5 = 0.5 * (dp + rcd) * ic2;
+  const double a2 = (qR[0] - qL[0]) - dp * ic2;
+  const double s1 = (utn - ct) < 0.0 ? -1.0 : 1.0, s5 = (utn + ct) < 0.0 ? -1.0 : 1.0, s2 = utn < 0.0 ? -1.0 : 1.0;
+  const double l1 = s1 * (utn - ct), l5 = s5 * (utn + ct), l2 = s2 * utn;
+  const double l1a1 = l1 * a1, l5a5 = l5 * a5;
+  double dut[3], utdut = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    dut[c] = (uR[c] - uL[c]) - dun * nc[c];
+    utdut += ut[c] * dut[c];
+  }
+  const double mL = qL[0] * unL, mR = qR[0] * unR;
+  // reverse
+  double mL_b = 0.5 * lf[0], mR_b = 0.5 * lf[0];
+  double l1a1_b = -0.5 * lf[0], l5a5_b = -0.5 * lf[0];
+  double l2_b = -0.5 * lf[0] * a2, a2_b = -0.5 * lf[0] * l2;
+  double uL_b[3] = {0, 0, 0}, uR_b[3] = {0, 0, 0}, ut_b[3] = {0, 0, 0}, dut_b[3] = {0, 0, 0};
+  double pL_b = 0.0, pR_b = 0.0, ct_b = 0.0, rt_b = 0.0, Ht_b = 0.0, utn_b = 0.0, q2_b = 0.0, utdut_b = 0.0;
+  double unL_b = 0.0, unR_b = 0.0, qL4_b = 0.0, qR4_b = 0.0;
+  {  // f4 = 0.5 (physE - dissE)
+    const double pe = 0.5 * lf[4], de = -0.5 * lf[4];
+    unL_b += pe * (qL[4] + pL);
+    qL4_b += pe * unL;
+    pL_b += pe * unL;
+    unR_b += pe * (qR[4] + pR);
+    qR4_b += pe * unR;
+    pR_b += pe * unR;
+    l1a1_b += de * (Ht - utn * ct);
+    l5a5_b += de * (Ht + utn * ct);
+    Ht_b += de * (l1a1 + l5a5);
+    utn_b += de * (l5a5 - l1a1) * ct;
+    ct_b += de * (l5a5 - l1a1) * utn;
+    l2_b += de * (a2 * 0.5 * q2 + rt * utdut);
+    a2_b += de * l2 * 0.5 * q2;
+    q2_b += de * l2 * 0.5 * a2;
+    rt_b += de * l2 * utdut;
+    utdut_b += de * l2 * rt;
+  }
+  for (int c = 0; c < 3; ++c) {  // f[1+c] = 0.5 (phys_c - diss_c)
+    const double ph = 0.5 * lf[1 + c], di = -0.5 * lf[1 + c];
+    mL_b += ph * uL[c];
+    uL_b[c] += ph * mL;
+    mR_b += ph * uR[c];
+    uR_b[c] += ph * mR;
+    pL_b += ph * nc[c];
+    pR_b += ph * nc[c];
+    l1a1_b += di * (ut[c] - ct * nc[c]);
+    l5a5_b += di * (ut[c] + ct * nc[c]);
+    ut_b[c] += di * (l1a1 + l5a5 + l2 * a2);
+    l2_b += di * (a2 * ut[c] + rt * dut[c]);
+    a2_b += di * l2 * ut[c];
+    rt_b += di * l2 * dut[c];
+    dut_b[c] += di * l2 * rt;
+    ct_b += di * (l5a5 - l1a1) * nc[c];
+  }
+  double qL0_b = mL_b * unL, qR0_b = mR_b * unR;
+  unL_b += mL_b * qL[0];
+  unR_b += mR_b * qR[0];
+  double dun_b = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    ut_b[c] += utdut_b * dut[c];
+    dut_b[c] += utdut_b * ut[c];
+    uR_b[c] += dut_b[c];
+    uL_b[c] -= dut_b[c];
+    dun_b -= dut_b[c] * nc[c];
+  }
+  const double l1_b = l1a1_b * a1, l5_b = l5a5_b * a5;
+  double a1_b = l1a1_b * l1, a5_b = l5a5_b * l5;
+  utn_b += l1_b * s1 + l5_b * s5 + l2_b * s2;
+  ct_b += -l1_b * s1 + l5_b * s5;
+  double dp_b = -a2_b * ic2, ic2_b = -a2_b * dp;
+  qR0_b += a2_b;
+  qL0_b -= a2_b;
+  dp_b += 0.5 * ic2 * (a1_b + a5_b);
+  double rcd_b = 0.5 * ic2 * (a5_b - a1_b);
+  ic2_b += 0.5 * (a1_b * (dp - rcd) + a5_b * (dp + rcd));
+  rt_b += rcd_b * ct * dun;
+  ct_b += rcd_b * rt * dun;
+  dun_b += rcd_b * rt * ct;
+  unR_b += dun_b;
+  unL_b -= dun_b;
+  pR_b += dp_b;
+  pL_b -= dp_b;
+  for (int c = 0; c < 3; ++c) {
+    ut_b[c] += utn_b * nc[c];
+    uL_b[c] += unL_b * nc[c];
+    uR_b[c] += unR_b * nc[c];
+  }
+  double rc_b = ct_b * c2 + ic2_b * 2.0 * rc;
+  double c2_b = ct_b * rc - 0.5 * rc_b * rc * rc * rc;
+  Ht_b += c2_b * gm1;
+  q2_b -= c2_b * 0.5 * gm1;
+  for (int c = 0; c < 3; ++c) ut_b[c] += q2_b * 2.0 * ut[c];
+  double sL_b = rt_b * sR, sR_b = rt_b * sL;
+  double is_b = Ht_b * (sL * HL + sR * HR);
+  sL_b += Ht_b * HL * is;
+  sR_b += Ht_b * HR * is;
+  const double HL_b = Ht_b * sL * is, HR_b = Ht_b * sR * is;
+  for (int c = 0; c < 3; ++c) {
+    sL_b += ut_b[c] * uL[c] * is;
+    uL_b[c] += ut_b[c] * sL * is;
+    sR_b += ut_b[c] * uR[c] * is;
+    uR_b[c] += ut_b[c] * sR * is;
+    is_b += ut_b[c] * (sL * uL[c] + sR * uR[c]);
+  }
+  const double ss_b = -is_b * is * is;
+  sL_b += ss_b;
+  sR_b += ss_b;
+  // HL = (qL4 + pL) irL
+  qL4_b += HL_b * irL;
+  pL_b += HL_b * irL;
+  double irL_b = HL_b * (qL[4] + pL);
+  qR4_b += HR_b * irR;
+  pR_b += HR_b * irR;
+  double irR_b = HR_b * (qR[4] + pR);
+  // p = gm1 (q4 - 0.5 sum_c q[1+c] u[c])
+  double qLm_b[3], qRm_b[3];
+  qL4_b += pL_b * gm1;
+  qR4_b += pR_b * gm1;
+  for (int c = 0; c < 3; ++c) {
+    qLm_b[c] = -pL_b * gm1 * 0.5 * uL[c];
+    uL_b[c] -= pL_b * gm1 * 0.5 * qL[1 + c];
+    qRm_b[c] = -pR_b * gm1 * 0.5 * uR[c];
+    uR_b[c] -= pR_b * gm1 * 0.5 * qR[1 + c];
+    // u = q[1+c] ir
+    qLm_b[c] += uL_b[c] * irL;
+    irL_b += uL_b[c] * qL[1 + c];
+    qRm_b[c] += uR_b[c] * irR;
+    irR_b += uR_b[c] * qR[1 + c];
+  }
+  // ir = rs^2, s = q0 rs, rs = q0^(-1/2)
+  double rsL_b = irL_b * 2.0 * rsL + sL_b * qL[0], rsR_b = irR_b * 2.0 * rsR + sR_b * qR[0];
+  qL0_b += sL_b * rsL - 0.5 * rsL_b * rsL * rsL * rsL;
+  qR0_b += sR_b * rsR - 0.5 * rsR_b * rsR * rsR * rsR;
+  gL[0] = qL0_b;
+  gR[0] = qR0_b;
+  for (int c = 0; c < 3; ++c) {
+    gL[1 + c] = qLm_b[c];
+    gR[1 + c] = qRm_b[c];
+  }
+  gL[4] = qL4_b;
+  gR[4] = qR4_b;
+}
+
 // gL[k] = sum_v dF_v/dqL_k lf_v, gR likewise: the Roe flux's Jacobian
-// transposes applied to lf, from ten Dual evaluations
+// transposes applied to lf (the reverse sweep above)
 template <bool AXIS>
 __device__ void roe_vjp(double gamma, int dir, const double qL[5], const double qR[5], const double n[3],
                         const double lf[5], double gL[5], double gR[5]) {
-  for (int k = 0; k < 10; ++k) {
-    Dual a[5], b[5], F[5];
-    for (int v = 0; v < 5; ++v) {
-      a[v] = {qL[v], k == v ? 1.0 : 0.0};
-      b[v] = {qR[v], k == 5 + v ? 1.0 : 0.0};
-    }
-    roe_face_d<AXIS>(gamma, dir, a, b, n, F);
-    double g = 0.0;
-    for (int v = 0; v < 5; ++v) g += F[v].d * lf[v];
-    if (k < 5) gL[k] = g;
-    else gR[k - 5] = g;
+  if (AXIS) {
+    if (dir == 0) roe_vjp_rev<0>(gamma, qL, qR, n, lf, gL, gR);
+    else if (dir == 1) roe_vjp_rev<1>(gamma, qL, qR, n, lf, gL, gR);
+    else roe_vjp_rev<2>(gamma, qL, qR, n, lf, gL, gR);
+  } else {
+    roe_vjp_rev<-1>(gamma, qL, qR, n, lf, gL, gR);
   }
 }
 
