@@ -74,8 +74,6 @@ __device__ __forceinline__ int face_vidx(int n1, int n2, int n3, int f, int a, i
   return i + n1 * (j + n2 * k);
 }
 
-template <typename T>
-__device__ __forceinline__ const T* btab(const T* base, int off) { return base + off; }
 
 // Metric record: field m of element e at node p.  Fields 0..8: J a^i_d
 // (index 3i+d); 9: J; 10: 1/J; affine records also 11..13: |J a^i|.
@@ -1080,81 +1078,6 @@ __device__ __forceinline__ void div5(const T* basis, const T* F, int n1, int n2,
     T d = D3[k * n3 + mm];
     for (int v = 0; v < 5; ++v) acc[v] += d * F[(2 * 5 + v) * n + b3 + n1 * n2 * mm];
   }
-}
-
-// Isolated residual of a [5][n] state tile Qs (stride qs) at orders
-// (n1,n2,n3) with metrics met: R = -(1/J) sum_i D^(i) Ft^i (Euler) or, for
-// Navier-Stokes, with the element-local BR1 gradient and the viscous flux.
-// Ft: [15][n] scratch; Gs: [15][n] scratch (NS).  Either writes R to
-// Rout[5][rs], or (IR != null) folds it into the tau norms: per node
-// t = IR - R (IR = I R^P, stride of the tile), a = max |t|,
-// b = max |J w_i w_j w_k t| (w1, w2, the GL weights in xi1, xi2; xi3 from
-// the basis table), accumulated into *na, *nb.
-template <typename T, bool NS>
-__device__ void tau_residual(const TauParams<T>& P, bool affine, const T* met, const T* Qs, int qs, int n1, int n2,
-                             int n3, T* Ft, T* Gs, T* Rout, int rs, const T* IR, const T* w1, const T* w2, T* na,
-                             T* nb) {
-  const int n = n1 * n2 * n3;
-  const T gm1 = P.gamma - (T)1;
-  if (NS) {
-    for (int c = 0; c < 3; ++c) {
-      for (int p = threadIdx.x; p < n; p += blockDim.x)
-        for (int i = 0; i < 3; ++i) {
-          T ja = met_at(met, affine, n, p, 3 * i + c);
-          for (int v = 0; v < 5; ++v) Ft[(i * 5 + v) * n + p] = ja * Qs[v * qs + p];
-        }
-      __syncthreads();
-      for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        T acc[5];
-        div5(P.basis, Ft, n1, n2, n3, p, acc);
-        T iJ = (T)1 / met_at(met, affine, n, p, 9);
-        for (int v = 0; v < 5; ++v) Gs[(v * 3 + c) * n + p] = acc[v] * iJ;
-      }
-      __syncthreads();
-    }
-  }
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    T q[5], f[3][5];
-    for (int v = 0; v < 5; ++v) q[v] = Qs[v * qs + p];
-    euler_fluxes(gm1, q, f);
-    if (NS) {
-      T g[15], fv[3][5];
-      for (int c = 0; c < 15; ++c) g[c] = Gs[c * n + p];
-      viscous_t(P, q, g, fv);
-      for (int d = 0; d < 3; ++d)
-        for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
-    }
-    for (int i = 0; i < 3; ++i) {
-      T ja0 = met_at(met, affine, n, p, 3 * i), ja1 = met_at(met, affine, n, p, 3 * i + 1),
-        ja2 = met_at(met, affine, n, p, 3 * i + 2);
-      for (int v = 0; v < 5; ++v) Ft[(i * 5 + v) * n + p] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
-    }
-  }
-  __syncthreads();
-  const T* w3 = P.basis + c_boff.W[n3 - 1];
-  T a = 0, b = 0;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    T acc[5];
-    div5(P.basis, Ft, n1, n2, n3, p, acc);
-    const T J = met_at(met, affine, n, p, 9);
-    const T iJ = -(T)1 / J;
-    if (IR) {
-      const int pj = fdiv(p, n1), k = fdiv(pj, n2), i = p - pj * n1, j = pj - k * n2;
-      const T Jw = J * w1[i] * w2[j] * w3[k];
-      for (int v = 0; v < 5; ++v) {
-        const T t = IR[v * qs + p] - acc[v] * iJ;   // tau~ = I R^P - R^N(I q^P)
-        a = tmax(a, (T)fabs(t));
-        b = tmax(b, (T)fabs(Jw * t));
-      }
-    } else {
-      for (int v = 0; v < 5; ++v) Rout[v * rs + p] = acc[v] * iJ;
-    }
-  }
-  if (IR) {
-    *na = a;
-    *nb = b;
-  }
-  __syncthreads();
 }
 
 // apply a (t x f) matrix along direction dir of an [nvar][e0 e1 e2] tile
