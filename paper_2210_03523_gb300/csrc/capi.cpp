@@ -462,7 +462,6 @@ dg_status build(dg_mesh_impl* m) {
   }
   std::vector<WorkItem> items;
   std::vector<int32_t> elist;
-  m->item_max_nodes = 1;
   for (auto& kv : buckets) {
     int n1, n2, n3;
     std::tie(n1, n2, n3) = kv.first;
@@ -473,7 +472,6 @@ dg_status build(dg_mesh_impl* m) {
       int cnt = (int)std::min<size_t>(per, els.size() - i);
       items.push_back({(int32_t)elist.size(), cnt, n1, n2, n3});
       for (int c = 0; c < cnt; ++c) elist.push_back(els[i + c]);
-      m->item_max_nodes = std::max(m->item_max_nodes, cnt * n);
     }
   }
   m->n_items = (int)items.size();

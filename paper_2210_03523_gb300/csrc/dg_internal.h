@@ -166,7 +166,6 @@ struct dg_mesh_impl {
   struct MGroup { int la, lb, ra, rb; std::vector<int32_t> faces; };
   std::vector<MGroup> h_mgroups;                   // batched faces [L, R, dir] by shape, sorted by direction
   std::vector<int32_t> h_mbatches;                 // [first, count, la, lb, ra, rb] per batch, as uploaded
-  int item_max_nodes = 0;          // max count*n over items (smem sizing)
   unsigned* d_err = nullptr;       // sticky error word
   double* d_scratch = nullptr;     // dt reduction
   // tau geometry bank (curved meshes): metrics at every coarse order N <= P
