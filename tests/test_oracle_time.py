@@ -125,3 +125,26 @@ def test_design_order_convergence(orc, N):
         errs.append(_l2_error(m, q, ph, T, width, center))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert rates[-1] > N + 1 - 0.6, (errs, rates)
+
+
+def test_rk3_temporal_convergence_order(orc):
+    """At a fixed spatial discretisation (N = 6), the time-integration error of
+    Williamson's RK3 falls by 2^3 per halving of dt (Sec. 3: a third-order
+    scheme); the reference is the same run at dt/16."""
+    ph = I.pulse_physics(mach=0.5, velocity=(0.6, 0.3, -0.2))
+    mi = I.box_mesh(2, orders=(6, 6, 6), phys=ph)
+    m = orc.Mesh(mi)
+    q0 = I.pulse_state(m.coords(), m.orders, ph, width=0.45, images=2)
+    T = 0.08
+    dt0 = m.max_dt(q0, 1.0)
+
+    def run(n):
+        q, G = q0.copy(), np.zeros_like(q0)
+        for _ in range(n):
+            m.rk_step(q, G, T / n)
+        return q
+    n0 = int(math.ceil(T / dt0))
+    ref = run(16 * n0)
+    err = [np.abs(run(k * n0) - ref).max() for k in (1, 2, 4)]
+    rates = [err[i] / err[i + 1] for i in range(2)]
+    assert all(6.5 < r < 9.5 for r in rates), (err, rates)
