@@ -350,6 +350,22 @@ dg_status dg_wall_force_vjp(dg_mesh* mesh, const double* q, int32_t tag, const d
  * cotangent of the step.  Same support and errors as dg_residual_vjp. */
 dg_status dg_rk_step_vjp(dg_mesh* mesh, const double* q0, const double* dt_dev, double* lam, double* qinf_adj);
 
+/* Checkpoint and resume (the paper's runs restart from saved solutions,
+ * Sec. 3.3): one host file with the element orders (they change with
+ * adaptation), the time and the state, and an FNV-1a checksum.  Host memory
+ * only, synchronous, no device involved.
+ * dg_state_write: orders [n_elem][3], q_host in the state layout of those
+ *   orders (dg_count_nodes nodes).
+ * dg_state_info: n_elem, n_nodes and t of a file (each output optional).
+ * dg_state_read: orders (host [n_elem][3]) and q_host (host, 5 n_nodes) of a
+ *   file holding n_elem elements; t optional.
+ * Errors: DG_ERR_ARG for bad arguments, an unreadable or unwritable path, a
+ * wrong magic or version, a size mismatch, a truncated or longer file, or a
+ * checksum mismatch. */
+dg_status dg_state_write(const char* path, int32_t n_elem, const int32_t* orders, const double* q_host, double t);
+dg_status dg_state_info(const char* path, int32_t* n_elem, int64_t* n_nodes, double* t);
+dg_status dg_state_read(const char* path, int32_t n_elem, int32_t* orders, double* q_host, double* t);
+
 /* Kernel kinds for dg_profile_read. */
 enum {
   DG_KERNEL_FACE_FLUX = 0,   /* Roe (+ BR1 viscous) numerical flux on conforming and boundary faces */

@@ -26,6 +26,13 @@ import numpy as np
 from . import Mesh, select_orders, tau_extrapolate
 
 
+def ndof(orders):
+    """degrees of freedom per variable of a discretisation: sum of the element
+    node counts (N1+1)(N2+1)(N3+1)"""
+    o = np.asarray(orders, dtype=np.int64).reshape(-1, 3)
+    return int(np.prod(o + 1, axis=1).sum())
+
+
 def _stage_map(m, q, sweep, form, isolated, targets, n_fit, decoupled, tau_floor):
     tn, tt = m.tau(q, sweep, isolated=isolated)
     mp = tn if form == "new" else tt
@@ -37,12 +44,14 @@ def _stage_map(m, q, sweep, form, isolated, targets, n_fit, decoupled, tau_floor
 def static_adaptation(mi, q0, *, t0, t_est, dt_e, t_final, cfl, sweep, tau_max, n_min, n_max, jump_rule=0,
                       form="new", isolated=True, targets=None, n_fit=0, decoupled=False, tau_floor=0.0):
     """Fig. 2.  Returns a dict: orders, q (final state), t, total (the F_max
-    map or None), n_estimates, steps (before, after adaptation)."""
+    map or None), n_estimates, steps (before, after adaptation), ndof (of the
+    adapted orders), ndof_dyn (the step-weighted mean over the whole run)."""
     m = Mesh(mi)
     q = np.array(q0, dtype=np.float64)
     G = np.zeros_like(q)
     t, total, n_est, steps, k = float(t0), None, 0, 0, 1
     lst = None
+    nd0 = ndof(m.orders)
     while True:
         t, n = m.advance(q, G, cfl, t, min(t0 + k * dt_e, t_est))
         steps += n
@@ -60,21 +69,25 @@ def static_adaptation(mi, q0, *, t0, t_est, dt_e, t_final, cfl, sweep, tau_max, 
     m2 = Mesh(mi.with_orders(orders))
     G = np.zeros_like(q)
     t, n2 = m2.advance(q, G, cfl, t, t_final)
-    return dict(orders=orders, q=q, t=t, total=total, n_estimates=n_est, steps=(steps, n2))
+    nd = ndof(orders)
+    ndyn = (steps * nd0 + n2 * nd) / (steps + n2) if steps + n2 else float(nd)
+    return dict(orders=orders, q=q, t=t, total=total, n_estimates=n_est, steps=(steps, n2), ndof=nd, ndof_dyn=ndyn)
 
 
 def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min, n_max, jump_rule=0,
                        max_decrease=-1, form="new", isolated=True, targets=None, n_fit=0, decoupled=False, tau_floor=0.0):
     """Fig. 1.  sweep: a fixed list, or a callable orders -> list (the orders
     change between stages).  Returns a dict: orders, q, t, history (orders
-    after every adaptation), steps."""
+    after every adaptation), steps, ndof (of the final orders), ndof_dyn
+    (the mean NDOF over the time steps)."""
     m = Mesh(mi)
     q = np.array(q0, dtype=np.float64)
     G = np.zeros_like(q)
-    t, steps, k, hist = float(t0), 0, 1, []
+    t, steps, k, hist, nd_sum = float(t0), 0, 1, [], 0
     while True:
         t, n = m.advance(q, G, cfl, t, min(t0 + k * dt_e, t_final))
         steps += n
+        nd_sum += n * ndof(m.orders)
         if t >= t_final:
             break
         sw = sweep(m.orders) if callable(sweep) else sweep
@@ -86,4 +99,6 @@ def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min,
         G = np.zeros_like(q)
         hist.append(orders)
         k += 1
-    return dict(orders=np.array(m.orders, dtype=np.int32), q=q, t=t, history=hist, steps=steps)
+    nd = ndof(m.orders)
+    return dict(orders=np.array(m.orders, dtype=np.int32), q=q, t=t, history=hist, steps=steps, ndof=nd,
+                ndof_dyn=nd_sum / steps if steps else float(nd))

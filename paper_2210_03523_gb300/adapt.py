@@ -15,7 +15,9 @@ follow only stages that did not reach the final (estimation) time; a stage's
 estimate is the map of the chosen form (new, Eq. TEtildedef, or traditional,
 Eq. TEdef) over the sweep, extrapolated to the target list when one is
 given (approach 2, Sec. 2.4); the static total map is their F_max; the RK
-register restarts at zero after an adaptation.
+register restarts at zero after an adaptation.  NDOF is the node count per
+variable (dg_count_nodes); NDOF_dyn, the mean NDOF over the time steps of
+the run (Sec. 3.3), weights each stage's NDOF by the steps it took.
 """
 from __future__ import annotations
 
@@ -60,7 +62,8 @@ def static_adaptation(mi, q0, *, t0, t_est, dt_e, t_final, cfl, sweep, tau_max, 
                       stream=None):
     """Fig. 2 on the GPU.  mi: a MeshInput; q0: the initial state (host or
     device).  Returns a dict: orders (host), q (device), t, total (device F_max
-    map or None), n_estimates, steps (before, after adaptation), mesh."""
+    map or None), n_estimates, steps (before, after adaptation), ndof (of the
+    adapted orders), ndof_dyn (the step-weighted mean over the run), mesh."""
     import torch
     m = dg.Mesh(mi, stream=stream)
     q = _to_device(q0, m.device)
@@ -68,6 +71,7 @@ def static_adaptation(mi, q0, *, t0, t_est, dt_e, t_final, cfl, sweep, tau_max, 
     t = torch.full((1,), float(t0), dtype=torch.float64, device=m.device)
     st = _Stage(form, isolated, fp32, targets, n_fit, decoupled, tau_floor)
     total, lst, n_est, steps, k = None, None, 0, 0, 1
+    nd0 = dg.dg_count_nodes(np.asarray(mi.orders, np.int32).reshape(-1, 3))
     while True:
         steps += m.advance(q, g, t, min(t0 + k * dt_e, t_est), cfl, count=True)
         if float(t.item()) >= t_est:
@@ -82,7 +86,10 @@ def static_adaptation(mi, q0, *, t0, t_est, dt_e, t_final, cfl, sweep, tau_max, 
     q = m.set_orders(orders, q)
     g = torch.zeros_like(q)
     n2 = m.advance(q, g, t, t_final, cfl, count=True)
-    return dict(orders=orders, q=q, t=float(t.item()), total=total, n_estimates=n_est, steps=(steps, n2), mesh=m)
+    nd = dg.dg_count_nodes(orders)
+    ndyn = (steps * nd0 + n2 * nd) / (steps + n2) if steps + n2 else float(nd)
+    return dict(orders=orders, q=q, t=float(t.item()), total=total, n_estimates=n_est, steps=(steps, n2), ndof=nd,
+                ndof_dyn=ndyn, mesh=m)
 
 
 def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min, n_max, jump_rule=0,
@@ -90,7 +97,8 @@ def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min,
                        decoupled=False, tau_floor=0.0, stream=None):
     """Fig. 1 on the GPU.  sweep: a fixed list, or a callable orders -> list.
     Returns a dict: orders, q, t, history (orders after every adaptation),
-    steps, mesh."""
+    steps, ndof (of the final orders), ndof_dyn (the mean NDOF over the time
+    steps), mesh."""
     import torch
     m = dg.Mesh(mi, stream=stream)
     q = _to_device(q0, m.device)
@@ -98,9 +106,11 @@ def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min,
     t = torch.full((1,), float(t0), dtype=torch.float64, device=m.device)
     st = _Stage(form, isolated, fp32, targets, n_fit, decoupled, tau_floor)
     orders = np.array(mi.orders, dtype=np.int32).reshape(-1, 3)
-    steps, k, hist = 0, 1, []
+    steps, k, hist, nd_sum = 0, 1, [], 0
     while True:
-        steps += m.advance(q, g, t, min(t0 + k * dt_e, t_final), cfl, count=True)
+        n = m.advance(q, g, t, min(t0 + k * dt_e, t_final), cfl, count=True)
+        steps += n
+        nd_sum += n * dg.dg_count_nodes(orders)
         if float(t.item()) >= t_final:
             break
         sw = sweep(orders) if callable(sweep) else sweep
@@ -110,4 +120,6 @@ def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min,
         g = torch.zeros_like(q)
         hist.append(orders)
         k += 1
-    return dict(orders=orders, q=q, t=float(t.item()), history=hist, steps=steps, mesh=m)
+    nd = dg.dg_count_nodes(orders)
+    return dict(orders=orders, q=q, t=float(t.item()), history=hist, steps=steps, ndof=nd,
+                ndof_dyn=nd_sum / steps if steps else float(nd), mesh=m)

@@ -86,6 +86,9 @@ def _lib():
             "dg_residual_vjp": [vp, vp, vp, vp, vp],
             "dg_rk_step_vjp": [vp, vp, vp, vp, vp],
             "dg_wall_force": [vp, vp, C.c_int32, vp],
+            "dg_state_write": [C.c_char_p, C.c_int32, i32p, C.POINTER(C.c_double), C.c_double],
+            "dg_state_info": [C.c_char_p, i32p, i64p, C.POINTER(C.c_double)],
+            "dg_state_read": [C.c_char_p, C.c_int32, i32p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
             "dg_wall_force_vjp": [vp, vp, C.c_int32, vp, vp, vp],
             "dg_get_tiles": [vp, C.POINTER(dg_tiles)],
             "dg_set_tiles": [vp, C.POINTER(dg_tiles)],
@@ -111,7 +114,8 @@ def exported_symbols():
             "dg_residual", "dg_max_dt", "dg_rk_step", "dg_tau_estimate", "dg_set_orders", "dg_get_error",
             "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc",
             "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles",
-            "dg_residual_vjp", "dg_rk_step_vjp", "dg_wall_force", "dg_wall_force_vjp"]
+            "dg_residual_vjp", "dg_rk_step_vjp", "dg_wall_force", "dg_wall_force_vjp", "dg_state_write",
+            "dg_state_info", "dg_state_read"]
 
 
 def _check(st, where):
@@ -152,6 +156,27 @@ def dg_count_nodes(orders) -> int:
     n = C.c_int64()
     _check(_lib().dg_count_nodes(o.shape[0], o.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)), "dg_count_nodes")
     return n.value
+
+
+def save_state(path, orders, q, t=0.0):
+    """dg_state_write: orders [n_elem, 3] and the state (a host array or a device
+    tensor, copied to the host) at time t."""
+    o = np.ascontiguousarray(np.asarray(orders, dtype=np.int32).reshape(-1, 3))
+    qh = q.detach().cpu().numpy() if hasattr(q, "detach") else q
+    qh = np.ascontiguousarray(qh, dtype=np.float64)
+    _check(_lib().dg_state_write(str(path).encode(), o.shape[0], o.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 qh.ctypes.data_as(C.POINTER(C.c_double)), float(t)), "dg_state_write")
+
+
+def load_state(path):
+    """dg_state_read: returns (orders [n_elem, 3], host state, t)."""
+    ne, nn, t = C.c_int32(), C.c_int64(), C.c_double()
+    _check(_lib().dg_state_info(str(path).encode(), C.byref(ne), C.byref(nn), C.byref(t)), "dg_state_info")
+    o = np.empty((ne.value, 3), dtype=np.int32)
+    q = np.empty(5 * nn.value)
+    _check(_lib().dg_state_read(str(path).encode(), ne.value, o.ctypes.data_as(C.POINTER(C.c_int32)),
+                                q.ctypes.data_as(C.POINTER(C.c_double)), C.byref(t)), "dg_state_read")
+    return o, q, t.value
 
 
 class Mesh:
@@ -266,6 +291,29 @@ class Mesh:
         self._ord = o
         self._refresh()
         return q_new
+
+    def orders(self):
+        """the current element orders, host [n_elem, 3] (a copy)"""
+        return self._ord.copy()
+
+    def save_state(self, path, q, t=0.0):
+        """Checkpoint: this mesh's orders, the device state q and the time t
+        (a float or a device scalar) to a dg_state_write file."""
+        self._check_state(q)
+        save_state(path, self._ord, q, float(t))
+
+    def load_state(self, path):
+        """Resume from a dg_state_write file of this mesh's elements: adopts the
+        file's orders (dg_set_orders when they differ) and returns the state on
+        the device and the time as a 1-element float64 device tensor."""
+        import torch
+        o, qh, t = load_state(path)
+        if o.shape[0] != self.n_elem:
+            raise ValueError(f"{path}: {o.shape[0]} elements, the mesh has {self.n_elem}")
+        if not np.array_equal(o, self._ord):
+            self.set_orders(o, self.new_state())
+        q = torch.from_numpy(qh).to(self.device)
+        return q, torch.tensor([t], dtype=torch.float64, device=self.device)
 
     def select_orders(self, map_, sweep, tau_max, n_min=1, n_max=DG_MAX_ORDER, jump_rule=0, max_decrease=-1):
         """p-adaptation order selection (approach 2) from a device tau map over

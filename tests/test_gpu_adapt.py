@@ -177,6 +177,7 @@ def test_static_driver_matches_oracle(torch_cuda):
     fin = ref["total"][np.isfinite(ref["total"])]
     np.testing.assert_allclose(got["total"].cpu().numpy(), ref["total"], rtol=0, atol=1e-11 * np.abs(fin).max())
     assert np.array_equal(got["orders"], ref["orders"])
+    assert got["ndof"] == ref["ndof"] and got["ndof_dyn"] == ref["ndof_dyn"]
     assert _close(got["q"].cpu().numpy(), ref["q"], got["orders"], 1e-11)
 
 
@@ -194,6 +195,7 @@ def test_dynamic_driver_matches_oracle(torch_cuda, rule):
     for a, b in zip(got["history"], ref["history"]):
         assert np.array_equal(a, b)
     assert got["steps"] == ref["steps"]
+    assert got["ndof"] == ref["ndof"] and got["ndof_dyn"] == ref["ndof_dyn"]
     assert _close(got["q"].cpu().numpy(), ref["q"], got["orders"], 1e-11)
 
 
@@ -226,3 +228,34 @@ def test_dual_time_stepping_tau_matches_oracle(torch_cuda, fp32):
         assert (d[ok] <= 8 * np.finfo(np.float32).eps).all()
     else:
         assert np.abs(g - ref)[ok].max() <= _tau_tol(ref, mi, qs[2], om)
+
+
+def test_resume_from_checkpoint_is_bitwise(torch_cuda, tmp_path):
+    """A run checkpointed half way (after an order change) and resumed on a
+    fresh mesh ends bitwise where the uninterrupted run ends: the low-storage
+    RK3 register restarts at zero every step, so the state, the orders and
+    the time are the whole solution."""
+    torch = torch_cuda
+    from paper_2210_03523_gb300 import dg
+    mi, om, q0 = _case()
+    new_orders = I.random_orders(mi.n_elem, 1, 6, 77)
+
+    def run(m, q, t, n):
+        g = torch.zeros_like(q)
+        assert m.advance(q, g, t, math.inf, 0.5, max_steps=n, count=True) == n
+        return q
+
+    m = dg.Mesh(mi)
+    q = torch.from_numpy(q0).cuda()
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    run(m, q, t, 10)
+    q = m.set_orders(new_orders, q)
+    run(m, q, t, 5)
+    m.save_state(tmp_path / "half.dgs", q, t.item())
+    run(m, q, t, 12)
+    m2 = dg.Mesh(mi)                   # the original orders: load_state switches them
+    q2, t2 = m2.load_state(tmp_path / "half.dgs")
+    assert np.array_equal(m2.orders(), new_orders)
+    run(m2, q2, t2, 12)
+    assert torch.equal(q, q2) and t.item() == t2.item()
+    assert m.get_error() == 0 and m2.get_error() == 0

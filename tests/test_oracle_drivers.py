@@ -134,3 +134,41 @@ def test_static_adaptation_follows_the_pulse(orc):
                     for e in range(mi.n_elem)])
     near = np.abs(cen[:, 2]) < 0.5
     assert nd[near].mean() > 1.5 * nd[~near].mean(), (nd[near].mean(), nd[~near].mean())
+
+
+def test_ndof_counts_the_nodes(orc):
+    """NDOF = sum over elements of (N1+1)(N2+1)(N3+1): the number of nodes the
+    oracle mesh places (three coordinates each), for mixed anisotropic orders."""
+    from oracle import drivers
+    mi = I.box_mesh(3, orders=I.random_orders(27, 1, 7, 19), phys=I.pulse_physics())
+    assert drivers.ndof(mi.orders) * 3 == orc.Mesh(mi).coords().size
+    assert drivers.ndof([(3, 3, 1)]) == 32 and drivers.ndof([(1, 3, 1), (3, 1, 1)]) == 32
+
+
+def test_ndof_dyn_weights_each_step(orc):
+    """NDOF_dyn is the mean NDOF over the time steps (Sec. 3.3).  With a huge
+    tau_max every element drops to N_min at the first adaptation and stays
+    there (max_decrease off), so NDOF_dyn = (n1 NDOF_0 + (S - n1) NDOF_min) / S
+    with n1 the steps of the first stage, counted by a separate advance."""
+    from oracle import drivers
+    mi, q0 = _pulse_case(nx=2, P=4, width=0.3)
+    res = drivers.dynamic_adaptation(mi, q0, t0=0.0, dt_e=0.02, t_final=0.07, cfl=0.5,
+                                     sweep=I.full_sweep((4, 4, 4)), tau_max=1e30, n_min=2, n_max=4)
+    assert len(res["history"]) == 3
+    assert all(np.array_equal(h, np.full((8, 3), 2)) for h in res["history"])
+    m = orc.Mesh(mi)
+    q, G = q0.copy(), np.zeros_like(q0)
+    _, n1 = m.advance(q, G, 0.5, 0.0, 0.02)
+    S = res["steps"]
+    nd0, ndmin = 8 * 125, 8 * 27
+    assert 0 < n1 < S and res["ndof"] == ndmin
+    assert res["ndof_dyn"] == pytest.approx((n1 * nd0 + (S - n1) * ndmin) / S, rel=1e-15)
+    # without an adaptation stage the mean is the constant NDOF
+    res0 = drivers.dynamic_adaptation(mi, q0, t0=0.0, dt_e=0.05, t_final=0.02, cfl=0.5,
+                                      sweep=I.full_sweep((4, 4, 4)), tau_max=1e30, n_min=2, n_max=4)
+    assert res0["history"] == [] and res0["ndof_dyn"] == nd0 == res0["ndof"]
+    # static: the estimation phase at the initial orders, the rest at the adapted ones
+    st = drivers.static_adaptation(mi, q0, t0=0.0, t_est=0.03, dt_e=0.02, t_final=0.05, cfl=0.5,
+                                   sweep=I.full_sweep((4, 4, 4)), tau_max=1e30, n_min=2, n_max=4)
+    a, b = st["steps"]
+    assert st["ndof"] == ndmin and st["ndof_dyn"] == pytest.approx((a * nd0 + b * ndmin) / (a + b), rel=1e-15)
