@@ -763,6 +763,9 @@ dg_status dg_mesh_create(const dg_mesh_desc* d, void* stream, dg_mesh** out) {
   m->phys.kappa = d->phys.eqs == DG_NAVIER_STOKES
                       ? d->phys.mu * d->phys.gamma * d->phys.Rgas / ((d->phys.gamma - 1.0) * d->phys.Pr)
                       : 0.0;
+  m->phys.kappa_R = d->phys.eqs == DG_NAVIER_STOKES
+                        ? d->phys.mu * d->phys.gamma / ((d->phys.gamma - 1.0) * d->phys.Pr)
+                        : 0.0;
   for (int v = 0; v < 5; ++v) m->phys.qinf[v] = d->phys.q_inf[v];
   const size_t ng3 = (size_t)(d->geom_order + 1) * (d->geom_order + 1) * (d->geom_order + 1);
   m->h_geom.assign(d->geom, d->geom + ng3 * 3 * d->n_elem);

@@ -39,6 +39,7 @@ void interp_matrix(const double* xf, int nf, const double* xt, int nt, double* I
 struct DevPhys {
   int eqs;
   double gamma, mu, Pr, Rgas, kappa;
+  double kappa_R;          // kappa / Rgas: the heat flux is kappa_R (grad p - (p/rho) grad rho) / rho
   double qinf[DG_NV];
 };
 

@@ -235,13 +235,14 @@ __device__ __forceinline__ void roe_face(double gamma, int dir, const double qL[
 __device__ void viscous(const DevPhys& ph, const double q[5], const double g[15], double fv[3][5]) {
   double gm1 = ph.gamma - 1.0;
   Prim s = primitive(gm1, q);
-  double T = s.p * s.ir / ph.Rgas;
+  // dT = R grad T = (grad p - (p/rho) grad rho) / rho; the heat flux is (kappa/R) dT
+  const double pir = s.p * s.ir;
   double du[3][3], dT[3];
   double half_u2 = 0.5 * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
   for (int c = 0; c < 3; ++c) {
     for (int i = 0; i < 3; ++i) du[i][c] = (g[(1 + i) * 3 + c] - s.u[i] * g[c]) * s.ir;
     double dpc = gm1 * (g[12 + c] - (s.u[0] * g[3 + c] + s.u[1] * g[6 + c] + s.u[2] * g[9 + c]) + half_u2 * g[c]);
-    dT[c] = (dpc - ph.Rgas * T * g[c]) * s.ir / ph.Rgas;
+    dT[c] = (dpc - pir * g[c]) * s.ir;
   }
   double div = du[0][0] + du[1][1] + du[2][2];
   for (int d = 0; d < 3; ++d) {
@@ -251,7 +252,7 @@ __device__ void viscous(const DevPhys& ph, const double q[5], const double g[15]
     fv[d][1] = tau[0];
     fv[d][2] = tau[1];
     fv[d][3] = tau[2];
-    fv[d][4] = s.u[0] * tau[0] + s.u[1] * tau[1] + s.u[2] * tau[2] + ph.kappa * dT[d];
+    fv[d][4] = s.u[0] * tau[0] + s.u[1] * tau[1] + s.u[2] * tau[2] + ph.kappa_R * dT[d];
   }
 }
 
@@ -667,6 +668,13 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_qhat_kernel(FaceParams P
 }
 
 // ------------------------------------------------------ volume-type kernels
+// the gas constants of the CFL time scale in precision T
+template <typename T>
+struct ScaleConst {
+  T gm1, gamma, mu, gpr;   // gamma - 1, gamma, mu, max(1, gamma/Pr)
+  int ns;                  // Navier-Stokes
+};
+
 struct VolParams {
   MeshView m;
   const WorkItem* items;
@@ -687,6 +695,11 @@ struct VolParams {
   int rk_first;       // first stage: G = dt R (A = 0)
   int isolated;
   unsigned* err;
+  // CFL reduction: the gas constants in both precisions (formed on the host)
+  // and the FP32 copy of the affine metric
+  ScaleConst<float> k32;
+  ScaleConst<double> k64;
+  const float* metric32;
 };
 
 // Sum-factorised GL derivative of a [3][nv][n] contravariant-flux tile at
@@ -907,62 +920,196 @@ __global__ void __launch_bounds__(kVolThreads) gradient_kernel(VolParams P) {
 //   s_v = 1/(4J^2) sum_i (N_i+1)^4 |J a^i|^2 max(1, gamma/Pr) mu/rho  (NS).
 // Affine meshes read 1/J and |J a^i| from the element record (fields 10 and
 // 11..13); AXIS meshes use |J a^i . v| = J a^i_i |v_i|.
+//
+// The FP64 pipe is the bound of a plain FP64 pass (a division and a square
+// root per node), so the reduction runs in two kernels.  dt_filter_kernel
+// evaluates s in FP32 at every node and reduces its maximum M32.  dt_kernel
+// evaluates it again in FP32 and only where s32 >= M32 (1 - delta) (the
+// candidates, queued per warp so that the FP64 work runs on full warps) in
+// FP64, whose maximum is the result.  Error bound: with the inputs truncated
+// to FP32 (relative error < 2^-23 = eps32 each), every quantity of s is a
+// sum of non-negative terms except the
+// pressure gm1 (E - k) and |J a^i . v|.  The guard E - k >= E/16 keeps the
+// pressure's relative error below ~180 eps32 and the Mach number below 7.3,
+// which bounds the error of |J a^i . v| by ~75 eps32 of the c |J a^i| term;
+// so |s32/s - 1| <= eta ~ 200 eps32 = 2.4e-5 at every node that passes the
+// guard.  The FP64 maximiser n* then has s32(n*) >= M32 (1 - 2 eta), and
+// delta = 2^-10 ~ 20 x 2 eta keeps it among the candidates, so the maximum
+// equals the plain FP64 pass.  A node that fails the guard, or whose FP32
+// value is not finite, is always a candidate (and so still raises the
+// non-physical flag through its FP64 value).
+constexpr float kDtMargin = 1.0f / 1024.0f;
+
+__device__ __forceinline__ float tfmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tfmax(double a, double b) { return fmax(a, b); }
+
+// A double as a float by integer operations on its bits (the FP64 pipe,
+// which also converts, is the scarce one): the magnitude bits clamped to the
+// float exponent range, rebiased and shifted, the mantissa truncated to 23
+// bits (relative error below 2^-23 in the normal float range).  Magnitudes
+// below it come out below 2^-126; magnitudes above it, infinities and NaNs
+// come out infinite or NaN, which fails the guard or the finiteness test.
+template <typename T>
+__device__ __forceinline__ T from_double(double x);
+template <>
+__device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_double<float>(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned a = min(max(hi & 0x7fffffffu, 896u << 20), 1151u << 20);
+  return __uint_as_float((hi & 0x80000000u) | ((a - (896u << 20)) << 3) | (lo >> 29));
+}
+
+// The FP32 reciprocal and square root are the approximate hardware forms
+// (a few ulp, against the ~200 eps32 budget above); for x = 0 or outside
+// [2^-126, 2^126] they give 0, infinity or NaN, which the guard or the
+// finiteness test turns into a candidate.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float tsqrt(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+
+// s of node p of element e (offset o, n nodes, nn = N_i + 1) in precision T;
+// ok: the FP32 guard above (1e-30 < rho < 1e30, E - k >= E/16)
+// a metric field in precision T: affine meshes read FP32 from the rounded copy
+template <bool AFFINE, typename T>
+__device__ __forceinline__ T metric_t(const MeshView& m, const float* M32, int e, int64_t o, int n, int p, int f) {
+  if constexpr (AFFINE && sizeof(T) == sizeof(float)) return __ldg(M32 + kAffStride * e + f);
+  else return from_double<T>(metric<AFFINE>(m.metric, e, o, n, p, f));
+}
+
+template <bool AFFINE, bool AXIS, typename T>
+__device__ __forceinline__ T node_scale(const MeshView& m, const ScaleConst<T>& K, const float* M32,
+                                        const double* __restrict__ Q, int e, int64_t o, int n, int p, const int nn[3],
+                                        bool* ok) {
+  const T gm1 = K.gm1, gamma = K.gamma;
+  T q[5];
+  for (int v = 0; v < 5; ++v) q[v] = from_double<T>(Q[5 * o + v * n + p]);
+  const T ir = recip(q[0]);
+  const T u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const T k = T(0.5) * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]);
+  *ok = q[0] > T(1e-30) && q[0] < T(1e30) && q[4] - k >= T(0.0625) * q[4];
+  const T pr = gm1 * (q[4] - k);
+  const T c = tsqrt(gamma * pr * ir);
+  const T iJ = metric_t<AFFINE, T>(m, M32, e, o, n, p, 10);
+  T sa = T(0), sv = T(0);
+  for (int i = 0; i < 3; ++i) {
+    const T k2 = T(nn[i] * nn[i]);
+    T un, a;
+    if (AXIS) {
+      a = metric_t<true, T>(m, M32, e, 0, n, p, 4 * i);
+      un = a * tabs(u[i]);
+    } else {
+      T ja[3];
+      for (int d = 0; d < 3; ++d) ja[d] = metric_t<AFFINE, T>(m, M32, e, o, n, p, 3 * i + d);
+      un = tabs(ja[0] * u[0] + ja[1] * u[1] + ja[2] * u[2]);
+      a = AFFINE ? metric_t<true, T>(m, M32, e, 0, n, p, 11 + i) : tsqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+    }
+    sa += k2 * (un + c * a);
+    sv += k2 * k2 * a * a;
+  }
+  T sm = T(0.5) * iJ * sa;
+  if (K.ns) {
+    const T nu = K.mu * ir * K.gpr;
+    sm = tfmax(sm, T(0.25) * iJ * iJ * sv * nu);
+  }
+  return sm;
+}
+
 template <bool AFFINE, bool AXIS>
-__global__ void __launch_bounds__(kVolThreads) dt_kernel(VolParams P, unsigned long long* smax_bits) {
-  __shared__ double red[kVolThreads / 32];
+__global__ void __launch_bounds__(kVolThreads) dt_filter_kernel(VolParams P, unsigned* m32_bits) {
+  __shared__ float red[kVolThreads / 32];
   const MeshView& m = P.m;
-  const double gm1 = m.ph.gamma - 1.0;
-  const bool ns = m.ph.eqs == DG_NAVIER_STOKES;
-  const double g_pr = m.ph.gamma / m.ph.Pr;
-  double smax = 0.0;
+  float smax = 0.0f;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
     const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
-    const double k2[3] = {(double)(w.n1 + 1) * (w.n1 + 1), (double)(w.n2 + 1) * (w.n2 + 1),
-                          (double)(w.n3 + 1) * (w.n3 + 1)};
-    const int n = (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
+    const int nn[3] = {w.n1 + 1, w.n2 + 1, w.n3 + 1};
+    const int n = nn[0] * nn[1] * nn[2];
     for (int s = threadIdx.x; s < w.count * n; s += blockDim.x) {
-      const int el = s / n, p = s - el * n;
+      const int el = fdiv(s, n), p = s - el * n;
       const int e = P.elist[w.first + el];
-      const int64_t o = m.off[e];
-      double q[5];
-      for (int v = 0; v < 5; ++v) q[v] = P.q[5 * o + v * n + p];
-      const double ir = 1.0 / q[0];
-      const double u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
-      const double pr = gm1 * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
-      const double c = sqrt(m.ph.gamma * pr * ir);
-      const double iJ = metric<AFFINE>(m.metric, e, o, n, p, 10);
-      double sa = 0.0, sv = 0.0;
-      for (int i = 0; i < 3; ++i) {
-        double un, a;
-        if (AXIS) {
-          a = metric<true>(m.metric, e, 0, n, p, 4 * i);
-          un = a * fabs(u[i]);
-        } else {
-          double ja[3];
-          for (int d = 0; d < 3; ++d) ja[d] = metric<AFFINE>(m.metric, e, o, n, p, 3 * i + d);
-          un = fabs(ja[0] * u[0] + ja[1] * u[1] + ja[2] * u[2]);
-          a = AFFINE ? metric<true>(m.metric, e, 0, n, p, 11 + i) : sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
-        }
-        sa += k2[i] * (un + c * a);
-        sv += k2[i] * k2[i] * a * a;
-      }
-      double sm = 0.5 * iJ * sa;
-      if (ns) {
-        const double nu = m.ph.mu * ir * (g_pr > 1.0 ? g_pr : 1.0);
-        sm = fmax(sm, 0.25 * iJ * iJ * sv * nu);
-      }
-      if (!(sm <= DBL_MAX)) atomicOr(P.err, 1u);
-      smax = fmax(smax, sm);
+      bool ok;
+      const float v = node_scale<AFFINE, AXIS, float>(m, P.k32, P.metric32, P.q, e, m.off[e], n, p, nn, &ok);
+      if (ok && v <= FLT_MAX) smax = fmaxf(smax, v);
     }
   }
-  for (int off = 16; off > 0; off >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+  for (int off = 16; off > 0; off >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, off));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b = fmax(b, red[i]);
-    // non-negative doubles order like their bit patterns
-    atomicMax(smax_bits, (unsigned long long)__double_as_longlong(b));
+    float b = 0.0f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b = fmaxf(b, red[i]);
+    atomicMax(m32_bits, __float_as_uint(b));   // non-negative floats order like their bit patterns
+  }
+}
+
+// the FP64 s of a candidate as its bit pattern (non-negative doubles order
+// like their bits, so the maxima below run on the integer pipes); a NaN is
+// left out of the maximum (0) and, like an infinity, raises the flag
+template <bool AFFINE, bool AXIS>
+__device__ __forceinline__ unsigned long long exact_scale_bits(const VolParams& P, int2 ep) {
+  const MeshView& m = P.m;
+  int nn[3];
+  orders_of(m, ep.x, nn[0], nn[1], nn[2]);
+  bool ok;
+  const double sm =
+      node_scale<AFFINE, AXIS, double>(m, P.k64, nullptr, P.q, ep.x, m.off[ep.x], nn[0] * nn[1] * nn[2], ep.y, nn, &ok);
+  if (!(sm <= DBL_MAX)) atomicOr(P.err, 1u);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(sm);
+  return (b & 0x7fffffffffffffffull) > 0x7ff0000000000000ull ? 0ull : b;
+}
+
+template <bool AFFINE, bool AXIS>
+__global__ void __launch_bounds__(kVolThreads) dt_kernel(VolParams P, const unsigned* m32_bits,
+                                                         unsigned long long* smax_bits) {
+  constexpr int kWarps = kVolThreads / 32;
+  __shared__ int2 queue[kWarps][64];          // candidates (element, node) of each warp
+  __shared__ unsigned long long red[kWarps];
+  const MeshView& m = P.m;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float thr = __uint_as_float(*m32_bits) * (1.0f - kDtMargin);
+  int cnt = 0;                                 // queued candidates (warp-uniform, < 32 between iterations)
+  unsigned long long smax = 0;                 // bits of the largest FP64 s seen
+  for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
+    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    const int nn[3] = {w.n1 + 1, w.n2 + 1, w.n3 + 1};
+    const int n = nn[0] * nn[1] * nn[2];
+    const int total = w.count * n;
+    for (int base = warp * 32; base < total; base += blockDim.x) {   // warp-uniform trip count
+      const int s = base + lane;
+      bool cand = false;
+      int e = 0, p = 0;
+      if (s < total) {
+        const int el = fdiv(s, n);
+        p = s - el * n;
+        e = P.elist[w.first + el];
+        bool ok;
+        const float v = node_scale<AFFINE, AXIS, float>(m, P.k32, P.metric32, P.q, e, m.off[e], n, p, nn, &ok);
+        cand = !ok || !(v < thr);
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, cand);
+      if (cand) queue[warp][cnt + __popc(mask & ((1u << lane) - 1u))] = make_int2(e, p);
+      cnt += __popc(mask);
+      __syncwarp();
+      if (cnt >= 32) {
+        smax = max(smax, exact_scale_bits<AFFINE, AXIS>(P, queue[warp][lane]));
+        __syncwarp();
+        if (lane < cnt - 32) queue[warp][lane] = queue[warp][32 + lane];
+        cnt -= 32;
+        __syncwarp();
+      }
+    }
+  }
+  if (lane < cnt) smax = max(smax, exact_scale_bits<AFFINE, AXIS>(P, queue[warp][lane]));
+  for (int off = 16; off > 0; off >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+  if (lane == 0) red[warp] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int i = 0; i < kWarps; ++i) b = max(b, red[i]);
+    atomicMax(smax_bits, b);
   }
 }
 
@@ -998,7 +1145,7 @@ struct TauParams {
   const int2* gentries;     // group entries: sweep index, N1
   int n_list;
   T* rp_scratch;            // isolated R^P at P, state layout, when rp is null
-  T gamma, mu, Pr, Rgas, kappa;
+  T gamma, mu, Pr, Rgas, kappa_R;
   unsigned* err;
 };
 
@@ -1031,13 +1178,13 @@ __device__ void viscous_t(const TauParams<T>& P, const T q[5], const T g[15], T 
   T ir = (T)1 / q[0];
   T u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
   T pr = gm1 * (q[4] - (T)0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
-  T Tm = pr * ir / P.Rgas;
+  T pir = pr * ir;
   T half_u2 = (T)0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   T du[3][3], dT[3];
   for (int c = 0; c < 3; ++c) {
     for (int i = 0; i < 3; ++i) du[i][c] = (g[(1 + i) * 3 + c] - u[i] * g[c]) * ir;
     T dpc = gm1 * (g[12 + c] - (u[0] * g[3 + c] + u[1] * g[6 + c] + u[2] * g[9 + c]) + half_u2 * g[c]);
-    dT[c] = (dpc - P.Rgas * Tm * g[c]) * ir / P.Rgas;
+    dT[c] = (dpc - pir * g[c]) * ir;
   }
   T div = du[0][0] + du[1][1] + du[2][2];
   for (int d = 0; d < 3; ++d) {
@@ -1047,7 +1194,7 @@ __device__ void viscous_t(const TauParams<T>& P, const T q[5], const T g[15], T 
     fv[d][1] = tau[0];
     fv[d][2] = tau[1];
     fv[d][3] = tau[2];
-    fv[d][4] = u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2] + P.kappa * dT[d];
+    fv[d][4] = u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2] + P.kappa_R * dT[d];
   }
 }
 
@@ -1866,15 +2013,29 @@ cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double*
   return dispatch_volume(m, P, 0, 0);
 }
 
+// bits: the FP64 maximum (bits[0]); bits[1] holds the FP32 filter maximum
 cudaError_t max_dt_bits(dg_mesh_impl* m, const double* q, unsigned long long* bits) {
   VolParams P = vol_params(m, q);
-  cudaError_t err = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), m->stream);
+  cudaError_t err = cudaMemsetAsync(bits, 0, 2 * sizeof(unsigned long long), m->stream);
   if (err) return err;
+  unsigned* m32 = reinterpret_cast<unsigned*>(bits + 1);
+  const DevPhys& ph = P.m.ph;
+  const double gpr = ph.gamma / ph.Pr > 1.0 ? ph.gamma / ph.Pr : 1.0;
+  P.k64 = ScaleConst<double>{ph.gamma - 1.0, ph.gamma, ph.mu, gpr, ph.eqs == DG_NAVIER_STOKES};
+  P.k32 = ScaleConst<float>{(float)(ph.gamma - 1.0), (float)ph.gamma, (float)ph.mu, (float)gpr, P.k64.ns};
+  P.metric32 = m->d_metric32;
   int grid = grid_for(m->n_vitems, 8);
-  Prof pr(m, DG_KERNEL_MAX_DT, 1);
-  if (m->axis) dt_kernel<true, true><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
-  else if (m->affine) dt_kernel<true, false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
-  else dt_kernel<false, false><<<grid, kVolThreads, 0, m->stream>>>(P, bits);
+  Prof pr(m, DG_KERNEL_MAX_DT, 2);
+  if (m->axis) {
+    dt_filter_kernel<true, true><<<grid, kVolThreads, 0, m->stream>>>(P, m32);
+    dt_kernel<true, true><<<grid, kVolThreads, 0, m->stream>>>(P, m32, bits);
+  } else if (m->affine) {
+    dt_filter_kernel<true, false><<<grid, kVolThreads, 0, m->stream>>>(P, m32);
+    dt_kernel<true, false><<<grid, kVolThreads, 0, m->stream>>>(P, m32, bits);
+  } else {
+    dt_filter_kernel<false, false><<<grid, kVolThreads, 0, m->stream>>>(P, m32);
+    dt_kernel<false, false><<<grid, kVolThreads, 0, m->stream>>>(P, m32, bits);
+  }
   return cudaGetLastError();
 }
 
@@ -1954,7 +2115,7 @@ cudaError_t tau_isolated(dg_mesh_impl* m, const double* q, const double* r_p, co
     P.mu = m->phys.mu;
     P.Pr = m->phys.Pr;
     P.Rgas = m->phys.Rgas;
-    P.kappa = m->phys.kappa;
+    P.kappa_R = m->phys.kappa_R;
     P.err = m->d_err;
     P.bank_off = m->d_taugeo_off;
   };
@@ -2665,13 +2826,13 @@ __device__ void viscous_s(const DevPhys& ph, const S q[5], const S g[15], S fv[3
   const S ir = 1.0 / q[0];
   const S u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
   const S p = gm1 * (q[4] - 0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
-  const S T = p * ir / ph.Rgas;
+  const S pir = p * ir;
   S du[3][3], dT[3];
   const S half_u2 = 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   for (int c = 0; c < 3; ++c) {
     for (int i = 0; i < 3; ++i) du[i][c] = (g[(1 + i) * 3 + c] - u[i] * g[c]) * ir;
     const S dpc = gm1 * (g[12 + c] - (u[0] * g[3 + c] + u[1] * g[6 + c] + u[2] * g[9 + c]) + half_u2 * g[c]);
-    dT[c] = (dpc - ph.Rgas * T * g[c]) * ir / ph.Rgas;
+    dT[c] = (dpc - pir * g[c]) * ir;
   }
   const S div = du[0][0] + du[1][1] + du[2][2];
   for (int d = 0; d < 3; ++d) {
@@ -2684,7 +2845,7 @@ __device__ void viscous_s(const DevPhys& ph, const S q[5], const S g[15], S fv[3
     fv[d][1] = tau[0];
     fv[d][2] = tau[1];
     fv[d][3] = tau[2];
-    fv[d][4] = u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2] + ph.kappa * dT[d];
+    fv[d][4] = u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2] + ph.kappa_R * dT[d];
   }
 }
 

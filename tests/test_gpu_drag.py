@@ -139,10 +139,14 @@ def test_averaged_drag_gradient_small(torch_cuda):
 
 def test_cylinder_drag_gradient_400_steps(torch_cuda):
     """The cylinder case (40 x 24 curved elements, geometry order 3, P = (6,6,1),
-    Re 100, Ma 0.2): the drag averaged over 400 RK3 steps, its gradient with
-    respect to the initial field (a seeded random perturbation, seed 2211,
-    amplitude 1e-3 rho_inf) and to the inflow momentum, against central
-    differences of the forward run."""
+    Re 100, Ma 0.2): the drag averaged over 400 RK3 steps and its gradient
+    with respect to the initial field (a seeded random perturbation, seed
+    2211, amplitude 1e-3 rho_inf), against central differences of the
+    forward run.  The far-field state enters only through the outer ghost
+    states, 24 element layers from the adiabatic wall; over these 400 steps
+    (t ~ 0.015, a sound wave travels ~0.08) no signal from it reaches the
+    wall, so d(drag)/d(q_inf) is zero up to the exponentially small tails of
+    the discrete stencil, and its central difference is rounding noise."""
     torch = torch_cuda
     import oracle
     import bench
@@ -166,5 +170,6 @@ def test_cylinder_drag_gradient_400_steps(torch_cuda):
                                  dataclasses.replace(mi.phys, qinf=tuple(qi))))
         return _averaged_force(mk, q0, dtv, n, (1.0, 0.0, 0.0))
     fdk = _fd4(J_at) / 1e-4
-    assert float(dqinf[1]) == pytest.approx(fdk, rel=1e-5), (float(dqinf[1]), fdk)
+    assert abs(float(dqinf[1])) < 1e-40, float(dqinf[1])
+    assert abs(fdk) <= 1e-10 * max(abs(J), 1.0), (fdk, J)      # rounding of J over the 1e-4 step
     assert m.get_error() == 0
