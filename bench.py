@@ -99,6 +99,16 @@ def full_sweep_for(orders):
     return I.full_sweep(np.asarray(orders).max(0))
 
 
+# DRAM bytes per launch (one launch per RK stage, the mean of a step's three
+# stages) from ncu captures of these kernels as they stand; the commands and
+# the per-stage figures are in profiles/traffic_mortar_volume_pulse16mixed_pulse32mixed.txt
+MEASURED_TRAFFIC = {
+    ("pulse16mixed", "mortar"): 16.0e6, ("pulse16mixed", "volume"): 45.9e6,
+    ("pulse32mixed", "mortar"): 442.9e6, ("pulse32mixed", "volume"): 557.3e6,
+}
+TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/traffic_mortar_volume_pulse16mixed_pulse32mixed.txt"
+
+
 # ------------------------------------------------------------ algorithmic counts
 def is_axis_aligned(mi):
     """Every element an axis-aligned box (its lattice edges parallel to the axes)."""
@@ -470,24 +480,26 @@ def run_gb300(args, rank, world):
     mflops, mbytes = mortar_counts(mi)
     mor_avg_s = (mor_ms / stages * 1e-3) if mor_n else None
 
-    def fp64_roofline(name, flops, bytes_, avg_s):
+    def fp64_roofline(name, flops, bytes_, avg_s, kind):
+        traffic = MEASURED_TRAFFIC.get((args.workload, kind))
         return {"kernel": name, "bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / fp64_peak,
                 "peak_source": f"FP64: {N_SM} SMs x {FP64_FMA_PER_CLK_PER_SM} DFMA/clk x 2 x median SM clock "
                                f"{sm_mhz:.0f} MHz (recipe nominal 1.25 TFLOP/s at 2070 MHz)",
-                "traffic": None, "algorithmic_flops_per_stage": flops, "algorithmic_bytes_per_stage": bytes_,
+                "traffic": traffic, "traffic_source": TRAFFIC_SOURCE if traffic else None,
+                "algorithmic_flops_per_stage": flops, "algorithmic_bytes_per_stage": bytes_,
                 "time_from": "CUDA events around each launch, profiled region; the launches of one RK stage "
                              "(one per tile-size class) summed",
                 "avg_stage_ms": avg_s * 1e3, "hbm_achieved_gbs": bytes_ / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": bytes_ / avg_s / 1e9 / hbm_peak, "hbm_peak_source": hbm_src}
 
-    vol_roof = fp64_roofline("volume_kernel (FP64 residual + fused RK3 stage)", vflops, vbytes, vol_avg_s)
+    vol_roof = fp64_roofline("volume_kernel (FP64 residual + fused RK3 stage)", vflops, vbytes, vol_avg_s, "volume")
     if is_axis_aligned(mi):
         vflops_ax, _ = volume_counts(mi.orders, rk=True, axis_aligned=True)
         vol_roof["frac_diagonal_metric_count"] = vflops_ax / vol_avg_s / 1e12 / fp64_peak
         vol_roof["note"] = ("flops per the general affine count (contravariant fluxes 75 per node); the mesh is "
                             "an axis-aligned box, where the kernel needs 15: frac_diagonal_metric_count")
-    mor_roof = fp64_roofline("mortar_kernel (p-nonconforming faces)", mflops, mbytes, mor_avg_s) if mor_n else None
+    mor_roof = fp64_roofline("mortar_kernel (p-nonconforming faces)", mflops, mbytes, mor_avg_s, "mortar") if mor_n else None
     dominant = mor_roof if (mor_roof and mor_ms > vol_ms) else vol_roof
     others = [r for r in (vol_roof, mor_roof) if r is not None and r is not dominant]
     kernels_json = {k: {"launches": n, "total_ms": round(ms, 3), "share": None} for k, (ms, n) in kern.items() if n}
