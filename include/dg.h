@@ -41,7 +41,9 @@ typedef enum {
   DG_ERR_CUDA = 3,         /* a CUDA runtime call failed */
   DG_ERR_UNSUPPORTED = 4,  /* valid input outside what the library implements */
   DG_ERR_NONPHYSICAL = 5,  /* sticky device error: rho <= 0, p <= 0 or NaN met */
-  DG_ERR_TIMEOUT = 6       /* reserved: a bounded device wait gave up */
+  DG_ERR_TIMEOUT = 6,      /* reserved: a bounded device wait gave up */
+  DG_ERR_INDEX = 7         /* sticky device error of the bounds-checking build: a kernel met an index out of
+                              range in a work list and skipped that unit of work */
 } dg_status;
 
 enum { DG_EULER = 0, DG_NAVIER_STOKES = 1 };
@@ -365,6 +367,24 @@ dg_status dg_rk_step_vjp(dg_mesh* mesh, const double* q0, const double* dt_dev, 
 dg_status dg_state_write(const char* path, int32_t n_elem, const int32_t* orders, const double* q_host, double t);
 dg_status dg_state_info(const char* path, int32_t* n_elem, int64_t* n_nodes, double* t);
 dg_status dg_state_read(const char* path, int32_t n_elem, int32_t* orders, double* q_host, double* t);
+
+/* Bounds-checking build (libdg compiled with -DDG_BOUNDS_CHECK; the
+ * release build returns DG_ERR_UNSUPPORTED here).  Every kernel checks the
+ * indices it reads from the mesh's work lists before it uses them (work items
+ * and their element lists, face records, mortar batches and their faces, tau
+ * sweep groups) and skips a unit whose indices are out of range, setting the
+ * sticky DG_ERR_INDEX that dg_get_error reports (it takes precedence over
+ * DG_ERR_NONPHYSICAL).
+ * dg_debug_set_index overwrites one entry of a work list on the device, so
+ * that tests can plant a bad index: list DG_LIST_VOLUME_ELEMENTS (element list
+ * of the volume tiles, n_elem entries), DG_LIST_TAU_ELEMENTS (element list of
+ * the tau tiles, n_elem), DG_LIST_FACE_LEFT (the left element of face record
+ * i) or DG_LIST_MORTAR_FACES (entry i of the mortar faces' [L, R, dir]
+ * triples).  old_value (optional) receives the entry's previous value.
+ * Synchronous.  Errors: DG_ERR_ARG (null mesh, unknown list, i out of range),
+ * DG_ERR_UNSUPPORTED (release build), DG_ERR_CUDA. */
+enum { DG_LIST_VOLUME_ELEMENTS = 0, DG_LIST_TAU_ELEMENTS = 1, DG_LIST_FACE_LEFT = 2, DG_LIST_MORTAR_FACES = 3 };
+dg_status dg_debug_set_index(dg_mesh* mesh, int32_t list, int64_t i, int32_t value, int32_t* old_value);
 
 /* Kernel kinds for dg_profile_read. */
 enum {

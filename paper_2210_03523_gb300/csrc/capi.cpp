@@ -263,6 +263,7 @@ dg_status build_mortar_batches(dg_mesh_impl* m) {
   if (m->d_mbatches) cudaFree(m->d_mbatches);
   m->d_mfaces = nullptr;
   m->d_mbatches = nullptr;
+  m->n_mfaces = (int)mfaces.size() / 3;
   DG_CUDA(upload(&m->d_mfaces, mfaces.data(), mfaces.size()));
   DG_CUDA(upload(&m->d_mbatches, m->h_mbatches.data(), m->h_mbatches.size()));
   return DG_OK;
@@ -593,6 +594,8 @@ dg_status build_tau_units(dg_mesh_impl* m) {
   if (m->d_tgroups) cudaFree(m->d_tgroups);
   if (m->d_tgentries) cudaFree(m->d_tgentries);
   m->d_tgroups = m->d_tgentries = nullptr;
+  m->n_tgroups = (int)groups.size() / 4;
+  m->n_tgentries = (int)gentries.size() / 2;
   DG_CUDA(upload(&m->d_tgroups, groups.data(), groups.size()));
   DG_CUDA(upload(&m->d_tgentries, gentries.data(), gentries.size()));
   for (size_t k = 0; k < m->tau_classes.size(); ++k) {
@@ -727,6 +730,7 @@ const char* dg_status_str(dg_status s) {
     case DG_ERR_UNSUPPORTED: return "unsupported configuration";
     case DG_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
     case DG_ERR_TIMEOUT: return "device wait timed out";
+    case DG_ERR_INDEX: return "index out of range in a work list (bounds-checking build)";
   }
   return "unknown status";
 }
@@ -1017,7 +1021,41 @@ dg_status dg_get_error(dg_mesh* m) {
   unsigned w = 0;
   DG_CUDA(cudaMemcpy(&w, m->d_err, sizeof(w), cudaMemcpyDeviceToHost));
   DG_CUDA(cudaMemset(m->d_err, 0, sizeof(unsigned)));
+  if (w & 2u) return DG_ERR_INDEX;
   return w ? DG_ERR_NONPHYSICAL : DG_OK;
+}
+
+dg_status dg_debug_set_index(dg_mesh* m, int32_t list, int64_t i, int32_t value, int32_t* old_value) {
+#ifdef DG_BOUNDS_CHECK
+  if (!m || i < 0) return DG_ERR_ARG;
+  int32_t* base = nullptr;
+  int64_t len = 0;
+  switch (list) {
+    case DG_LIST_VOLUME_ELEMENTS: base = m->d_velist; len = m->n_elem; break;
+    case DG_LIST_TAU_ELEMENTS: base = m->d_elist; len = m->n_elem; break;
+    case DG_LIST_FACE_LEFT: {   // the L field (the first) of face record i
+      constexpr int64_t words = sizeof(FaceRec) / sizeof(int32_t);
+      if (i >= m->n_faces) return DG_ERR_ARG;
+      base = reinterpret_cast<int32_t*>(m->d_faces);
+      len = (int64_t)m->n_faces * words;
+      i *= words;
+      break;
+    }
+    case DG_LIST_MORTAR_FACES: base = m->d_mfaces; len = 3 * (int64_t)m->n_mfaces; break;
+    default: return DG_ERR_ARG;
+  }
+  if (!base || i >= len) return DG_ERR_ARG;
+  DG_CUDA(m->stream ? cudaStreamSynchronize(m->stream) : cudaDeviceSynchronize());
+  if (old_value) DG_CUDA(cudaMemcpy(old_value, base + i, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  DG_CUDA(cudaMemcpy(base + i, &value, sizeof(int32_t), cudaMemcpyHostToDevice));
+  return DG_OK;
+#else
+  (void)list;
+  (void)i;
+  (void)value;
+  (void)old_value;
+  return m ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
+#endif
 }
 
 }  // extern "C"

@@ -148,6 +148,7 @@ struct dg_mesh_impl {
   FaceRec* d_faces = nullptr;      // conforming and boundary faces (one warp each)
   int n_faces = 0, n_face_conf = 0, n_face_mortar = 0, n_face_bnd = 0;
   int32_t* d_mfaces = nullptr;     // p-nonconforming faces [L, R, dir], grouped by shape signature
+  int n_mfaces = 0;
   int32_t* d_mbatches = nullptr;   // mortar batches [first, count, la, lb, ra, rb]
   int n_mbatches = 0;
   size_t mortar_smem = 0;          // doubles of shared memory of the largest batch
@@ -191,6 +192,7 @@ struct dg_mesh_impl {
   std::vector<int> tau_n_units;
   int32_t* d_tgroups = nullptr;
   int32_t* d_tgentries = nullptr;
+  int n_tgroups = 0, n_tgentries = 0;
   std::vector<WorkItem> h_items;
   double* d_qc = nullptr;              // coarse mesh: restricted state scratch
   double* d_rc = nullptr;              // coarse mesh: coarse residual scratch

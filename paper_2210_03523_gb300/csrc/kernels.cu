@@ -279,7 +279,84 @@ struct MeshView {
   const int64_t* soff;
   const double* metric;
   DevPhys ph;
+  int n_elem;
+  int64_t n_nodes;
+  int64_t n_surf;    // element-face nodes (the face buffers' length)
+  unsigned* err;     // the sticky error word
 };
+
+// ------------------------------------------------ bounds-checking build
+// Built with -DDG_BOUNDS_CHECK, every kernel checks the indices it reads from
+// the mesh's work lists before it uses them: work items and their element
+// lists, face records and mortar batches.  A failed check sets bit 1 of the
+// sticky error word (dg_get_error: DG_ERR_INDEX) and the kernel skips that
+// unit of work; nothing out of range is read or written.  The release build
+// compiles the checks away.
+__device__ __forceinline__ void flag_index(const MeshView& m) { atomicOr(m.err, 2u); }
+
+// element e exists, has orders (N1,N2,N3) and its nodes lie inside the state
+__device__ __forceinline__ bool elem_fits(const MeshView& m, int e, int N1, int N2, int N3) {
+  if ((unsigned)e >= (unsigned)m.n_elem) return false;
+  if (m.ord[3 * e] != N1 || m.ord[3 * e + 1] != N2 || m.ord[3 * e + 2] != N3) return false;
+  const int n1 = N1 + 1, n2 = N2 + 1, n3 = N3 + 1;
+  const int64_t o = m.off[e], so = m.soff[e];
+  return o >= 0 && o + (int64_t)n1 * n2 * n3 <= m.n_nodes && so >= 0 &&
+         so + 2 * (int64_t)(n2 * n3 + n1 * n3 + n1 * n2) <= m.n_surf;
+}
+
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+  unsigned r;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+
+// Work item wi of a block-uniform loop into w; false: skip it.  In the
+// checking build every thread of the block must call it (a block-wide vote);
+// smem_per_node: the doubles of dynamic shared memory the kernel lays out per
+// tile node (0: none), checked against the launch's allocation.
+__device__ __forceinline__ bool take_item(const MeshView& m, const WorkItem* items, int wi, int n_items,
+                                          const int32_t* elist, int smem_per_node, WorkItem& w) {
+#ifdef DG_BOUNDS_CHECK
+  bool bad = (unsigned)wi >= (unsigned)n_items;
+  if (!bad) {
+    w = items[wi];
+    bad = w.count < 1 || w.first < 0 || w.first > m.n_elem - w.count || w.n1 < 1 || w.n1 > DG_MAX_ORDER ||
+          w.n2 < 1 || w.n2 > DG_MAX_ORDER || w.n3 < 1 || w.n3 > DG_MAX_ORDER;
+    if (!bad && smem_per_node > 0)
+      bad = (uint64_t)w.count * (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1) * smem_per_node * sizeof(double) >
+            dynamic_smem_bytes();
+    for (int el = threadIdx.x; !bad && el < w.count; el += blockDim.x)
+      bad = !elem_fits(m, elist[w.first + el], w.n1, w.n2, w.n3);
+  }
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) flag_index(m);
+  return !bad;
+#else
+  (void)n_items;
+  (void)elist;
+  (void)smem_per_node;
+  w = items[wi];
+  return true;
+#endif
+}
+
+// a face record's elements, tag and face number (warp-uniform)
+__device__ __forceinline__ bool bad_face(const MeshView& m, const FaceRec& f) {
+#ifdef DG_BOUNDS_CHECK
+  bool bad = (unsigned)f.L >= (unsigned)m.n_elem || f.kind < 0 || f.kind > 2;
+  if (!bad) bad = !elem_fits(m, f.L, m.ord[3 * f.L], m.ord[3 * f.L + 1], m.ord[3 * f.L + 2]);
+  if (!bad && f.kind == 2) bad = (f.R != DG_BC_FARFIELD && f.R != DG_BC_WALL) || (unsigned)f.face >= 6u;
+  else if (!bad)
+    bad = (unsigned)f.R >= (unsigned)m.n_elem || (unsigned)f.face >= 3u ||
+          !elem_fits(m, f.R, m.ord[3 * f.R], m.ord[3 * f.R + 1], m.ord[3 * f.R + 2]);
+  if (bad && (threadIdx.x & 31) == 0) flag_index(m);
+  return bad;
+#else
+  (void)m;
+  (void)f;
+  return false;
+#endif
+}
 
 __device__ __forceinline__ void orders_of(const MeshView& m, int e, int& n1, int& n2, int& n3) {
   n1 = __ldg(m.ord + 3 * e) + 1;
@@ -326,6 +403,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_flux_kernel(FaceParams P
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
   const FaceRec fr = P.faces[fidx];
+  if (bad_face(P.m, fr)) return;
   const MeshView& m = P.m;
   const double gamma = m.ph.gamma;
 
@@ -437,11 +515,63 @@ struct MortarParams {
   MeshView m;
   const MortarBatch* batches;
   int n_batches;
+  int n_mfaces;           // faces in the face list
   const int32_t* faces;   // [face][3]: L, R, dir
   const double* q;
   double* surf;
   const double* basis;
 };
+
+// shared memory (doubles) of one mortar batch
+__host__ __device__ inline size_t mortar_batch_smem(const MortarBatch& B) {
+  const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb;
+  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
+  const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+  return (size_t)B.count * (5 * (la * lb + ra * rb + uL + uR + 2 * Ma * Mb) + 4);
+}
+
+// the tangential node counts (a, b) of element e's faces of direction dir
+__device__ __forceinline__ void face_dims(const MeshView& m, int e, int dir, int& a, int& b) {
+  const int n1 = m.ord[3 * e] + 1, n2 = m.ord[3 * e + 1] + 1, n3 = m.ord[3 * e + 2] + 1;
+  a = dir == 0 ? n2 : n1;
+  b = dir == 2 ? n2 : n3;
+}
+
+// A mortar batch of a block-uniform loop: its faces inside the face list,
+// each face's elements in range with the batch's trace shapes, and the
+// batch's shared memory (need, in doubles) inside the launch's allocation.
+// In the checking build every thread of the block must call it.
+__device__ __forceinline__ bool bad_batch(const MortarParams& P, const MortarBatch& B, size_t need) {
+#ifdef DG_BOUNDS_CHECK
+  const MeshView& m = P.m;
+  bool bad = B.count < 1 || B.first < 0 || B.first > P.n_mfaces - B.count || B.la < 1 || B.lb < 1 || B.ra < 1 ||
+             B.rb < 1 || B.la > DG_NP1 || B.lb > DG_NP1 || B.ra > DG_NP1 || B.rb > DG_NP1 ||
+             need * sizeof(double) > dynamic_smem_bytes();
+  for (int f = threadIdx.x; !bad && f < B.count; f += blockDim.x) {
+    const int* fr = P.faces + 3 * (B.first + f);
+    const int L = fr[0], R = fr[1], dir = fr[2];
+    bad = (unsigned)L >= (unsigned)m.n_elem || (unsigned)R >= (unsigned)m.n_elem || (unsigned)dir >= 3u;
+    if (!bad)
+      bad = !elem_fits(m, L, m.ord[3 * L], m.ord[3 * L + 1], m.ord[3 * L + 2]) ||
+            !elem_fits(m, R, m.ord[3 * R], m.ord[3 * R + 1], m.ord[3 * R + 2]);
+    if (!bad) {
+      int a, b;
+      face_dims(m, L, dir, a, b);
+      bad = a != B.la || b != B.lb;
+      face_dims(m, R, dir, a, b);
+      bad = bad || a != B.ra || b != B.rb;
+    }
+  }
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) flag_index(m);
+  return bad;
+#else
+  (void)P;
+  (void)B;
+  (void)need;
+  return false;
+#endif
+}
 
 template <bool AXIS>
 __global__ void __launch_bounds__(kVolThreads) mortar_kernel(MortarParams P) {
@@ -450,6 +580,7 @@ __global__ void __launch_bounds__(kVolThreads) mortar_kernel(MortarParams P) {
   const double gamma = m.ph.gamma;
   for (int it = blockIdx.x; it < P.n_batches; it += gridDim.x) {
     const MortarBatch B = P.batches[it];
+    if (bad_batch(P, B, mortar_batch_smem(B))) continue;
     const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb, cnt = B.count;
     const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
     const int nfl = la * lb, nfr = ra * rb, nm = Ma * Mb;
@@ -608,13 +739,6 @@ __global__ void __launch_bounds__(kVolThreads) mortar_kernel(MortarParams P) {
   }
 }
 
-// shared memory (doubles) of one mortar batch
-__host__ __device__ inline size_t mortar_batch_smem(const MortarBatch& B) {
-  const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb;
-  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
-  const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
-  return (size_t)B.count * (5 * (la * lb + ra * rb + uL + uR + 2 * Ma * Mb) + 4);
-}
 
 // BR1 trace q-hat (J a^dir) on every face; conforming faces only.
 template <bool AFFINE>
@@ -623,6 +747,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) face_qhat_kernel(FaceParams P
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
   const FaceRec fr = P.faces[fidx];
+  if (bad_face(P.m, fr)) return;
   const MeshView& m = P.m;
   if (fr.kind == 2) {
     int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1;
@@ -700,6 +825,7 @@ struct VolParams {
   ScaleConst<float> k32;
   ScaleConst<double> k64;
   const float* metric32;
+  int n_items_all;    // length of items (the bound of an ilist entry)
 };
 
 // Sum-factorised GL derivative of a [3][nv][n] contravariant-flux tile at
@@ -743,7 +869,8 @@ __global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
   const MeshView& m = P.m;
   const double gm1 = m.ph.gamma - 1.0;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist ? P.ilist[it] : it, P.n_items_all, P.elist, 20, w)) continue;
     const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
     const int slots = w.count * n;
     double* Ft = smem;                                // [count][3][5][n]
@@ -864,7 +991,8 @@ __global__ void __launch_bounds__(kVolThreads) gradient_kernel(VolParams P) {
   extern __shared__ double smem[];
   const MeshView& m = P.m;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist ? P.ilist[it] : it, P.n_items_all, P.elist, 15, w)) continue;
     const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
     const int slots = w.count * n;
     const double* D1 = P.basis + c_boff.D[w.n1];
@@ -1024,7 +1152,8 @@ __global__ void __launch_bounds__(kVolThreads) dt_filter_kernel(VolParams P, uns
   const MeshView& m = P.m;
   float smax = 0.0f;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist ? P.ilist[it] : it, P.n_items_all, P.elist, 0, w)) continue;
     const int nn[3] = {w.n1 + 1, w.n2 + 1, w.n3 + 1};
     const int n = nn[0] * nn[1] * nn[2];
     for (int s = threadIdx.x; s < w.count * n; s += blockDim.x) {
@@ -1073,7 +1202,8 @@ __global__ void __launch_bounds__(kVolThreads) dt_kernel(VolParams P, const unsi
   int cnt = 0;                                 // queued candidates (warp-uniform, < 32 between iterations)
   unsigned long long smax = 0;                 // bits of the largest FP64 s seen
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist ? P.ilist[it] : it, P.n_items_all, P.elist, 0, w)) continue;
     const int nn[3] = {w.n1 + 1, w.n2 + 1, w.n3 + 1};
     const int n = nn[0] * nn[1] * nn[2];
     const int total = w.count * n;
@@ -1147,7 +1277,46 @@ struct TauParams {
   T* rp_scratch;            // isolated R^P at P, state layout, when rp is null
   T gamma, mu, Pr, Rgas, kappa_R;
   unsigned* err;
+  int n_items_all, n_groups, n_gentries;   // lengths of items, groups and gentries
 };
+
+// a tau tile inside its class's shared-memory capacity S (nodes at P)
+__device__ __forceinline__ bool bad_tile(const MeshView& m, const WorkItem& w, int S) {
+#ifdef DG_BOUNDS_CHECK
+  const bool bad = (int64_t)w.count * (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1) > S;
+  if (bad && threadIdx.x == 0) flag_index(m);
+  return bad;
+#else
+  (void)m;
+  (void)w;
+  (void)S;
+  return false;
+#endif
+}
+
+// a sweep group of a tile: coarse orders (N2, N3) within the tile's and
+// entries (sweep index, N1) inside the lists (block-uniform values)
+template <typename T>
+__device__ __forceinline__ bool bad_group(const TauParams<T>& P, const WorkItem& w, int gi) {
+#ifdef DG_BOUNDS_CHECK
+  bool bad = (unsigned)gi >= (unsigned)P.n_groups;
+  if (!bad) {
+    const int4 g = P.groups[gi];
+    bad = g.x < 1 || g.x > w.n2 || g.y < 1 || g.y > w.n3 || g.z < 0 || g.w < 0 || g.z > P.n_gentries - g.w;
+    for (int k = 0; !bad && k < g.w; ++k) {
+      const int2 ent = P.gentries[g.z + k];
+      bad = (unsigned)ent.x >= (unsigned)P.n_sweep || ent.y < 1 || ent.y > DG_MAX_ORDER;
+    }
+  }
+  if (bad && threadIdx.x == 0) flag_index(P.m);
+  return bad;
+#else
+  (void)P;
+  (void)w;
+  (void)gi;
+  return false;
+#endif
+}
 
 // offset (in nodes) of the metrics of coarse orders (N1,N2,N3) inside an
 // element's bank (all combos N <= P, N1 fastest, then N2, then N3)
@@ -1436,7 +1605,9 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
   T* Gs = Ft + 15 * S;
   const MeshView& m = P.m;
   for (int li = blockIdx.x; li < P.n_list; li += gridDim.x) {
-    const WorkItem w = P.items[P.ilist[li]];
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist[li], P.n_items_all, P.elist, 0, w)) continue;
+    if (bad_tile(P.m, w, P.S)) continue;
     const int32_t* els = P.elist + w.first;
     const int cnt = w.count;
     const int P1 = w.n1, P2 = w.n2, P3 = w.n3, nP = (P1 + 1) * (P2 + 1) * (P3 + 1);
@@ -1481,7 +1652,9 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   const MeshView& m = P.m;
   for (int ui = blockIdx.x; ui < P.n_list; ui += gridDim.x) {
     const int2 u = P.units[ui];
-    const WorkItem w = P.items[u.x];
+    WorkItem w;
+    if (!take_item(P.m, P.items, u.x, P.n_items_all, P.elist, 0, w)) continue;
+    if (bad_tile(P.m, w, P.S) || bad_group(P, w, u.y)) continue;
     const int4 g = P.groups[u.y];      // N2, N3, first entry, entry count
     const int32_t* els = P.elist + w.first;
     const int cnt = w.count;
@@ -1733,6 +1906,10 @@ MeshView view(const dg_mesh_impl* m) {
   v.soff = m->d_soff;
   v.metric = m->d_metric;
   v.ph = m->phys;
+  v.n_elem = m->n_elem;
+  v.n_nodes = m->n_nodes;
+  v.n_surf = m->h_soff.empty() ? 0 : m->h_soff[m->n_elem];
+  v.err = m->d_err;
   return v;
 }
 
@@ -1796,6 +1973,7 @@ VolParams dgk_vol_params_for(dg_mesh_impl* m, const double* q, const double* sur
   P.m = view(m);
   P.items = m->d_vitems;
   P.n_items = m->n_vitems;
+  P.n_items_all = m->n_vitems;
   P.elist = m->d_velist;
   P.q = q;
   P.surf = surf;
@@ -1855,6 +2033,7 @@ cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* gra
     M.m = view(m);
     M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
     M.n_batches = m->n_mbatches;
+    M.n_mfaces = m->n_mfaces;
     M.faces = m->d_mfaces;
     M.q = q;
     M.surf = surf;
@@ -1959,6 +2138,7 @@ static VolParams vol_params(dg_mesh_impl* m, const double* q) {
   P.m = view(m);
   P.items = m->d_vitems;
   P.n_items = m->n_vitems;
+  P.n_items_all = m->n_vitems;
   P.elist = m->d_velist;
   P.q = q;
   P.grad = m->d_grad;
@@ -2067,6 +2247,9 @@ static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
   cudaError_t err;
   Prof pr(m, DG_KERNEL_TAU, 2 * (int)m->tau_classes.size());
   P.items = m->d_items;
+  P.n_items_all = m->n_items;
+  P.n_groups = m->n_tgroups;
+  P.n_gentries = m->n_tgentries;
   P.elist = m->d_elist;
   P.groups = reinterpret_cast<const int4*>(m->d_tgroups);
   P.gentries = reinterpret_cast<const int2*>(m->d_tgentries);
@@ -2596,6 +2779,13 @@ __device__ __forceinline__ double inv_wend(int N) { return 0.5 * N * (N + 1); }
 // projection passes onto the mortar grid (both sides summed), the Roe
 // vector-Jacobian product at the mortar nodes, and the transposes of the two
 // interpolation passes back onto each side's face grid, into sadj.
+// shared memory (doubles) of an adjoint mortar batch
+__host__ __device__ inline size_t mortar_adj_smem_doubles(int count, int la, int lb, int ra, int rb) {
+  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
+  const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+  return (size_t)count * (5 * (2 * la * lb + 2 * ra * rb + uL + uR + 3 * Ma * Mb) + 4);
+}
+
 template <bool AXIS>
 __global__ void __launch_bounds__(kVolThreads) adj_mortar_kernel(MortarParams P, const double* __restrict__ vin,
                                                                  double* __restrict__ sadj) {
@@ -2604,6 +2794,7 @@ __global__ void __launch_bounds__(kVolThreads) adj_mortar_kernel(MortarParams P,
   const double gamma = m.ph.gamma;
   for (int it = blockIdx.x; it < P.n_batches; it += gridDim.x) {
     const MortarBatch B = P.batches[it];
+    if (bad_batch(P, B, mortar_adj_smem_doubles(B.count, B.la, B.lb, B.ra, B.rb))) continue;
     const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb, cnt = B.count;
     const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
     const int nfl = la * lb, nfr = ra * rb, nm = Ma * Mb;
@@ -2901,6 +3092,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) adj_face_kernel(FaceParams P,
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
   const FaceRec fr = P.faces[fidx];
+  if (bad_face(P.m, fr)) return;
   const MeshView& m = P.m;
   const double gamma = m.ph.gamma;
   if (fr.kind == 2) {
@@ -3032,6 +3224,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) adj_qhat_kernel(FaceParams P,
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
   const FaceRec fr = P.faces[fidx];
+  if (bad_face(P.m, fr)) return;
   const MeshView& m = P.m;
   if (fr.kind == 2) {
     const int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1;
@@ -3095,6 +3288,7 @@ struct AdjParams {
   const int32_t* elist;
   const int32_t* ilist;
   int n_items;
+  int n_items_all;         // length of items
   const double* q;
   const double* grad;      // BR1 gradient of q (Navier-Stokes)
   const double* v;         // cotangent of the residual (state layout)
@@ -3121,7 +3315,8 @@ __global__ void __launch_bounds__(kVolThreads) adj_volume_kernel(AdjParams P) {
   const MeshView& m = P.m;
   const double gm1 = m.ph.gamma - 1.0;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist ? P.ilist[it] : it, P.n_items_all, P.elist, 20, w)) continue;
     const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
     const int slots = w.count * n;
     double* U = smem;                                 // [count][5][n]
@@ -3253,7 +3448,8 @@ __global__ void __launch_bounds__(kVolThreads) adj_gradient_kernel(AdjParams P) 
   extern __shared__ double smem[];
   const MeshView& m = P.m;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist ? P.ilist[it] : it, P.n_items_all, P.elist, 15, w)) continue;
     const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
     const int slots = w.count * n;
     double* Gm = smem;   // [count][3][5][n]: gamma_c[v]
@@ -3337,7 +3533,8 @@ __global__ void __launch_bounds__(kVolThreads) adj_gradient_kernel(AdjParams P) 
 __global__ void __launch_bounds__(kVolThreads) adj_gather_kernel(AdjParams P) {
   const MeshView& m = P.m;
   for (int it = blockIdx.x; it < P.n_items; it += gridDim.x) {
-    const WorkItem w = P.items[P.ilist ? P.ilist[it] : it];
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist ? P.ilist[it] : it, P.n_items_all, P.elist, 0, w)) continue;
     const int n1 = w.n1 + 1, n2 = w.n2 + 1, n3 = w.n3 + 1, n = n1 * n2 * n3;
     for (int s = threadIdx.x; s < w.count * n; s += blockDim.x) {
       const int el = s / n, p = s - el * n;
@@ -3374,11 +3571,6 @@ __global__ void axpby_kernel(double* __restrict__ y, const double* __restrict__ 
 }  // namespace
 
 // shared memory (doubles) of one mortar batch in the adjoint kernel
-static size_t mortar_adj_smem_doubles(int count, int la, int lb, int ra, int rb) {
-  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
-  const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
-  return (size_t)count * (5 * (2 * la * lb + 2 * ra * rb + uL + uR + 3 * Ma * Mb) + 4);
-}
 
 namespace dgk {
 
@@ -3432,6 +3624,7 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
     M.m = view(m);
     M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
     M.n_batches = m->n_mbatches;
+    M.n_mfaces = m->n_mfaces;
     M.faces = m->d_mfaces;
     M.q = q;
     M.surf = nullptr;
@@ -3450,6 +3643,7 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
   memset(&A, 0, sizeof(A));
   A.m = view(m);
   A.items = m->d_vitems;
+  A.n_items_all = m->n_vitems;
   A.elist = m->d_velist;
   A.q = q;
   A.grad = m->d_grad;
@@ -3557,6 +3751,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) wall_force_kernel(FaceParams 
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
   const FaceRec fr = P.faces[fidx];
+  if (bad_face(P.m, fr)) return;
   double acc[3] = {0.0, 0.0, 0.0};
   if (fr.kind == 2 && fr.R == tag) {
     const MeshView& m = P.m;
@@ -3606,6 +3801,7 @@ __global__ void __launch_bounds__(32 * kFaceWarps) wall_force_vjp_kernel(FacePar
   const int fidx = blockIdx.x * kFaceWarps + warp;
   if (fidx >= P.n_faces) return;
   const FaceRec fr = P.faces[fidx];
+  if (bad_face(P.m, fr)) return;
   if (fr.kind != 2 || fr.R != tag) return;
   const MeshView& m = P.m;
   const int e = fr.L, f = fr.face, dir = f >> 1, side = f & 1;
@@ -3702,6 +3898,7 @@ cudaError_t wall_force_vjp(dg_mesh_impl* m, const double* q, int tag, const doub
   memset(&A, 0, sizeof(A));
   A.m = view(m);
   A.items = m->d_vitems;
+  A.n_items_all = m->n_vitems;
   A.elist = m->d_velist;
   A.q = q;
   A.grad = m->d_grad;

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libdg.so")
+# DG_LIBRARY=checked loads the bounds-checking build (build.build(checked=True))
+LIB_PATH = os.path.join(_HERE, "_build_checked" if os.environ.get("DG_LIBRARY") == "checked" else "_build",
+                        "libdg.so")
 
 DG_EULER, DG_NAVIER_STOKES = 0, 1
 DG_ISOLATED = 0x1
@@ -27,7 +29,8 @@ DG_ADVANCE_EAGER = 0x1
 KERNELS = {"face_flux": 0, "face_qhat": 1, "gradient": 2, "volume": 3, "max_dt": 4, "tau": 5, "tau_combine": 6,
            "project": 7, "select": 8, "extrap": 9, "mortar": 10, "adjoint": 11}
 STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_NOMEM", 3: "DG_ERR_CUDA", 4: "DG_ERR_UNSUPPORTED",
-          5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_TIMEOUT"}
+          5: "DG_ERR_NONPHYSICAL", 6: "DG_ERR_TIMEOUT", 7: "DG_ERR_INDEX"}
+DG_LIST_VOLUME_ELEMENTS, DG_LIST_TAU_ELEMENTS, DG_LIST_FACE_LEFT, DG_LIST_MORTAR_FACES = 0, 1, 2, 3
 
 
 class DGError(RuntimeError):
@@ -86,6 +89,7 @@ def _lib():
             "dg_residual_vjp": [vp, vp, vp, vp, vp],
             "dg_rk_step_vjp": [vp, vp, vp, vp, vp],
             "dg_wall_force": [vp, vp, C.c_int32, vp],
+            "dg_debug_set_index": [vp, C.c_int32, C.c_int64, C.c_int32, i32p],
             "dg_state_write": [C.c_char_p, C.c_int32, i32p, C.POINTER(C.c_double), C.c_double],
             "dg_state_info": [C.c_char_p, i32p, i64p, C.POINTER(C.c_double)],
             "dg_state_read": [C.c_char_p, C.c_int32, i32p, C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -115,7 +119,7 @@ def exported_symbols():
             "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc",
             "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles",
             "dg_residual_vjp", "dg_rk_step_vjp", "dg_wall_force", "dg_wall_force_vjp", "dg_state_write",
-            "dg_state_info", "dg_state_read"]
+            "dg_state_info", "dg_state_read", "dg_debug_set_index"]
 
 
 def _check(st, where):
@@ -291,6 +295,13 @@ class Mesh:
         self._ord = o
         self._refresh()
         return q_new
+
+    def debug_set_index(self, lst, i, value):
+        """dg_debug_set_index (bounds-checking build only): overwrite entry i of
+        a work list on the device; returns the previous value."""
+        old = C.c_int32()
+        _check(_lib().dg_debug_set_index(self.h, int(lst), int(i), int(value), C.byref(old)), "dg_debug_set_index")
+        return old.value
 
     def orders(self):
         """the current element orders, host [n_elem, 3] (a copy)"""

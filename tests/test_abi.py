@@ -34,8 +34,9 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for s in range(7):
+    for s in range(8):
         assert lib.dg_status_str(s)
+        assert b"unknown" not in lib.dg_status_str(s)
 
 
 def test_count_nodes(lib):
@@ -93,8 +94,21 @@ def test_mesh_create_rejects_bad_input_on_the_host(lib):
     for fn in ("dg_residual", "dg_rk_step", "dg_max_dt", "dg_set_orders", "dg_get_error", "dg_mesh_destroy",
                "dg_tau_estimate", "dg_node_coords", "dg_advance", "dg_tau_extrapolate", "dg_select_orders",
                "dg_autotune", "dg_get_tiles", "dg_set_tiles", "dg_residual_vjp", "dg_rk_step_vjp",
-               "dg_wall_force", "dg_wall_force_vjp"):
+               "dg_wall_force", "dg_wall_force_vjp", "dg_debug_set_index"):
         f = getattr(lib, fn)
         args = [0 if t in (C.c_uint32, C.c_int32, C.c_int64) else (1.0 if t is C.c_double else None)
                 for t in f.argtypes]
         assert f(*args) == 1, fn
+
+
+def test_bounds_checking_build_builds_and_exports():
+    """The -DDG_BOUNDS_CHECK variant compiles and exports the same symbols;
+    its debug hook validates arguments on the host."""
+    import ctypes as C
+    from paper_2210_03523_gb300 import build, dg
+    path = build.build(checked=True)
+    lib = C.CDLL(path)
+    for n in dg.exported_symbols():
+        assert hasattr(lib, n), n
+    lib.dg_debug_set_index.argtypes = [C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_int32)]
+    assert lib.dg_debug_set_index(None, 0, 0, 0, None) == 1
