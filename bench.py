@@ -305,6 +305,34 @@ def fp32_tau_check(m, q, sweep):
             "selection_changed_fraction": changed, "eps32": 2.0 ** -23}
 
 
+def tau_sweep_timing(m, q, P, reps=5):
+    """The isolated sweep over S = {N : 1 <= N_i <= P_i} and over the interior
+    set {1..P_i - 1}^3, each in FP32 and FP64 (outside the timed regions; CUDA
+    events over reps sweeps after one warm-up)."""
+    import torch
+    from paper_2210_03523_gb300 import dg, inputs as I
+    P = np.asarray(P)
+    out = {}
+    for name, sw in (("full", I.full_sweep(P)), ("interior", I.full_sweep(np.maximum(P - 1, 1)))):
+        for fp32 in (True, False):
+            key = f"{name}_{'fp32' if fp32 else 'fp64'}"
+            try:
+                mn, mt = m.tau_estimate(q, sw, isolated=True, fp32=fp32)
+            except dg.DGError as e:       # FP64 tiles above the shared-memory limit (orders 8)
+                out[key] = {"unavailable": str(e)}
+                continue
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                m.tau_estimate(q, sw, isolated=True, fp32=fp32, map_new=mn, map_trad=mt)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            out[key] = {"entries": int(len(sw)), "ms": ms, "elements_per_s": m.n_elem / (ms * 1e-3)}
+    return out
+
+
 def adjoint_timing(m, q, dt_adj, reps=10):
     """The adjoint on the bench mesh (outside the timed regions): one residual
     VJP and one RK3-step VJP (which recomputes the stage states), CUDA events
@@ -465,6 +493,7 @@ def run_gb300(args, rank, world):
     sel = m.select_orders(map_new, sweep, 1.0, 1, 8, 2)
     select_ms = (time.perf_counter() - t0) * 1e3
     fp32_check = fp32_tau_check(m, q, sweep)
+    sweeps = tau_sweep_timing(m, q, np.asarray(mi.orders).reshape(-1, 3).max(0))
     adjoint = adjoint_timing(m, q, dt_adj=m.max_dt(q, CFL))
 
     # roofline of the dominant kernel (by share of the profiled step) and of the volume kernel
@@ -535,6 +564,7 @@ def run_gb300(args, rank, world):
                          "peak_source": f"FP32: {N_SM} SMs x {FP32_FMA_PER_CLK_PER_SM} FFMA/clk x 2 x {sm_mhz:.0f} MHz"},
         "kernels": kernels_json,
         "fp32_tau_check": fp32_check,
+        "tau_sweep_timing": sweeps,
         "adjoint": adjoint,
         "autotune": {"enabled": not args.no_autotune, "seconds": tune_s, "vol_budget": tiles["vol_budget"],
                      "mortar_budget": tiles["mortar_budget"], "volume_launch_ms_after_class": tiles["vol_ms"],
