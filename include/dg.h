@@ -94,11 +94,12 @@ typedef struct dg_mesh dg_mesh;
 /* Builds geometry, Kopriva curl-form metric terms, face connectivity and
  * (N1,N2,N3) buckets, and uploads them.  stream: a cudaStream_t, or NULL
  * for the legacy default stream.  Synchronous.
- * Mortars (p-nonconforming faces) are implemented for affine Euler meshes;
- * on a curved or Navier-Stokes mesh with p-nonconforming faces the mesh is
- * created, the element-local operations (isolated residual, isolated tau,
- * CFL step, dg_set_orders) work, and every face-coupled call returns
- * DG_ERR_UNSUPPORTED.
+ * Mortars (p-nonconforming faces) of order max(N_L, N_R) per tangential
+ * direction: on affine Euler meshes one Roe flux per mortar node serves both
+ * sides; on curved or Navier-Stokes meshes each side takes the flux with its
+ * own J a^dir interpolated to the mortar (the two elements' metrics differ
+ * at a curved nonconforming face), with the BR1 averages of q and of the
+ * viscous flux formed on the mortar.
  * Errors: DG_ERR_ARG (null pointer, order outside 1..DG_MAX_ORDER,
  * neighbour index out of range or not reciprocal, unknown tag, J <= 0),
  * DG_ERR_NOMEM, DG_ERR_CUDA. */
@@ -121,8 +122,8 @@ dg_status dg_node_coords(dg_mesh* mesh, double* xyz);
  * max(N_L, N_R) per tangential direction.  flags: DG_ISOLATED gives the
  * isolated residual (surface numerical fluxes replaced by the inner flux,
  * end of Sec. 2.2).  q, r: device, state layout, FP64; r may not alias q.
- * Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED (face-coupled call on a mesh whose
- * mortars are not implemented, see dg_mesh_create), DG_ERR_CUDA. */
+ * Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED (a mortar batch above the device's
+ * shared memory, which no order up to DG_MAX_ORDER reaches), DG_ERR_CUDA. */
 dg_status dg_residual(dg_mesh* mesh, const double* q, double* r, uint32_t flags);
 
 /* Residual without any device allocation.  The paper has no counterpart:
@@ -325,8 +326,8 @@ dg_status dg_set_tiles(dg_mesh* mesh, const dg_tiles* in);
  * qinf_adj (device, 5 doubles, optional): accumulates the cotangent of the
  * far-field state q_inf (the Roe ghost and BR1's q-hat at far-field faces).
  * Errors: DG_ERR_ARG; DG_ERR_UNSUPPORTED (mortars on curved or Navier-Stokes
- * meshes, which have no forward kernel either, or mortar batches whose
- * adjoint exceeds shared memory); DG_ERR_CUDA. */
+ * meshes, whose transposed kernel is not implemented, or mortar batches
+ * whose adjoint exceeds shared memory); DG_ERR_CUDA. */
 dg_status dg_residual_vjp(dg_mesh* mesh, const double* q, const double* v, double* out, double* qinf_adj);
 
 /* Force of the fluid on the boundary faces with tag `tag` (DG_BC_WALL: the

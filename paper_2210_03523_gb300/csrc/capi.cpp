@@ -219,6 +219,7 @@ void destroy_impl(dg_mesh_impl* m) {
   } while (0)
 
 constexpr int kTileNodes = 256;
+constexpr size_t kGeneralMortarBytes = 96 * 1024;
 
 }  // namespace
 
@@ -230,15 +231,22 @@ constexpr int kTileNodes = 256;
 dg_status build_mortar_batches(dg_mesh_impl* m) {
   std::vector<int32_t> mfaces, mbatches;
   m->mortar_smem = 0;
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
   for (const auto& g : m->h_mgroups) {
     const int nm = std::max(g.la, g.ra) * std::max(g.lb, g.rb);
-    const int per = std::max(1, m->mortar_budget[mortar_size_class(nm)] / nm);
+    int per = std::max(1, m->mortar_budget[mortar_size_class(nm)] / nm);
+    if (m->general_mortars) {   // at most 96 KB of shared memory per batch: two CTAs per SM
+      const size_t one = dg_mortar_general_smem_doubles(1, g.la, g.lb, g.ra, g.rb, ns);
+      per = std::max(1, std::min(per, (int)(kGeneralMortarBytes / (sizeof(double) * one))));
+    }
     const int nf = (int)g.faces.size() / 3;
     for (int i = 0; i < nf; i += per) {
       const int cnt = std::min(per, nf - i);
       mbatches.insert(mbatches.end(), {(int32_t)(mfaces.size() / 3), cnt, g.la, g.lb, g.ra, g.rb});
       mfaces.insert(mfaces.end(), g.faces.begin() + 3 * i, g.faces.begin() + 3 * (i + cnt));
-      m->mortar_smem = std::max(m->mortar_smem, dg_mortar_smem_doubles(cnt, g.la, g.lb, g.ra, g.rb));
+      m->mortar_smem = std::max(m->mortar_smem, m->general_mortars
+                                                    ? dg_mortar_general_smem_doubles(cnt, g.la, g.lb, g.ra, g.rb, ns)
+                                                    : dg_mortar_smem_doubles(cnt, g.la, g.lb, g.ra, g.rb));
     }
   }
   m->n_mbatches = (int)mbatches.size() / 6;
@@ -445,13 +453,21 @@ dg_status build(dg_mesh_impl* m) {
       for (int k = 0; k < 3; ++k) g.faces[3 * i + k] = fs[i][k];
     m->h_mgroups.push_back(std::move(g));
   }
+  // mortars of curved or Navier-Stokes meshes take the general kernels (each
+  // side's flux with its own normal; BR1 gradients on the mortar)
+  m->general_mortars = m->n_face_mortar > 0 && (ns || !m->affine);
   {
     dg_status st = build_mortar_batches(m);
     if (st != DG_OK) return st;
   }
-  // mortars are implemented for affine Euler meshes; elsewhere only the
-  // element-local (isolated) operations are available
-  m->faces_unsupported = m->n_face_mortar > 0 && (ns || !m->affine);
+  // a mortar batch above the device's shared memory (one face of the largest
+  // shape always fits below DG_MAX_ORDER) would refuse face-coupled calls
+  {
+    int dev = 0, limit = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    DG_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    m->faces_unsupported = sizeof(double) * m->mortar_smem + 1024 > (size_t)limit;
+  }
   // work items: elements bucketed by order triple
   std::map<std::tuple<int, int, int>, std::vector<int32_t>> buckets;
   for (int e = 0; e < ne; ++e) buckets[{m->h_ord[3 * e], m->h_ord[3 * e + 1], m->h_ord[3 * e + 2]}].push_back(e);
@@ -936,7 +952,8 @@ dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_o
 }
 
 static dg_status adjoint_ready(dg_mesh* m) {
-  if (m->faces_unsupported) return DG_ERR_UNSUPPORTED;
+  // the transposed mortar kernel covers the affine Euler mortars only
+  if (m->faces_unsupported || m->general_mortars) return DG_ERR_UNSUPPORTED;
   int limit = 0;
   DG_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
   if (sizeof(double) * dgk::mortar_adj_smem_max(m) + 1024 > (size_t)limit) return DG_ERR_UNSUPPORTED;

@@ -65,8 +65,10 @@ constexpr int kSizeClasses = DG_SIZE_CLASSES;
 inline int elem_size_class(int n) { return n <= 27 ? 0 : n <= 125 ? 1 : n <= 343 ? 2 : 3; }
 inline int mortar_size_class(int nm) { return nm <= 9 ? 0 : nm <= 25 ? 1 : nm <= 49 ? 2 : 3; }
 
-// shared memory (doubles) of a batch of `count` mortar faces of one shape
+// shared memory (doubles) of a batch of `count` mortar faces of one shape:
+// the affine Euler kernel, and the general (curved or Navier-Stokes) kernels
 size_t dg_mortar_smem_doubles(int count, int la, int lb, int ra, int rb);
+size_t dg_mortar_general_smem_doubles(int count, int la, int lb, int ra, int rb, bool ns);
 
 // per-kernel timing / launch counting hooks (capi.cpp), called by the launchers
 void dg_prof_begin(dg_mesh_impl* m, int kernel_id, int n_launches);
@@ -126,7 +128,8 @@ struct dg_mesh_impl {
   bool affine = true;       // every element a parallelepiped: metrics per element
   bool axis = false;        // affine and every J a^i parallel to e_i (axis-aligned box)
   int max_order = 1;        // max over elements and directions
-  bool faces_unsupported = false;  // mortars on a curved or Navier-Stokes mesh
+  bool faces_unsupported = false;  // face-coupled calls refused (mortars whose shared memory exceeds the device's)
+  bool general_mortars = false;    // mortars on a curved or Navier-Stokes mesh (own-normal flux per side)
 
   // host copies (for rebuilds and coarse meshes)
   std::vector<double> h_geom;

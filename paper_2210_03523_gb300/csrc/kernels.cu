@@ -520,6 +520,7 @@ struct MortarParams {
   const double* q;
   double* surf;
   const double* basis;
+  const double* grad;     // general mortars, Navier-Stokes flux: the BR1 gradient
 };
 
 // shared memory (doubles) of one mortar batch
@@ -734,6 +735,241 @@ __global__ void __launch_bounds__(kVolThreads) mortar_kernel(MortarParams P) {
       orders_of(m, e, n1, n2, n3);
       double* dst = P.surf + 5 * (m.soff[e] + face_offset(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir)) + x;
       for (int v = 0; v < 5; ++v) dst[v * nf] = out[v];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------- general (curved, NS) mortars
+// p-nonconforming faces of curved or Navier-Stokes meshes, in the same shape
+// batches.  The two sides' J a^dir at a curved nonconforming face differ (each
+// element's metric comes from the geometry at its own order), so each side
+// takes the flux with its own normal, as a conforming face would, from both
+// traces on the mortar grid:
+//   gather each side's trace (q; the BR1 gradient for the Navier-Stokes flux)
+//   and its own J a^dir -> interpolate up to the mortar in two passes ->
+//   per side F* = |J a| Roe(q-, q+, n_side) - {{f_v}} . J a_side (BR1 average),
+//   or for the BR1 gradient pass S = {{q}} J a_side -> L2-project each side's
+//   output back to its own face grid in two passes -> store.
+// MODE 0: Euler flux, 1: Navier-Stokes flux, 2: BR1 q-hat (J a) into surfq.
+template <int MODE>
+struct GMortar {
+  static constexpr int nq = MODE == 1 ? 20 : 5;   // q and, for the NS flux, its gradient [v*3+c]
+  static constexpr int nin = nq + 3;              // ... and the side's own J a^dir
+  static constexpr int nout = MODE == 2 ? 15 : 5;
+  static constexpr int nmid = nin > nout ? nin : nout;
+};
+
+template <int MODE>
+__host__ __device__ inline size_t mortar_general_smem(const MortarBatch& B) {
+  const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb;
+  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb, nm = Ma * Mb;
+  const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+  return (size_t)B.count * ((size_t)GMortar<MODE>::nin * (la * lb + ra * rb + 2 * nm) +
+                            (size_t)GMortar<MODE>::nmid * (uL + uR) + 2 * (size_t)GMortar<MODE>::nout * nm);
+}
+
+template <bool AFFINE, int MODE>
+__global__ void __launch_bounds__(kVolThreads) mortar_general_kernel(MortarParams P) {
+  typedef GMortar<MODE> G;
+  constexpr int NIN = G::nin, NQ = G::nq, NOUT = G::nout, NMID = G::nmid;
+  extern __shared__ double smem[];
+  const MeshView& m = P.m;
+  const double gamma = m.ph.gamma;
+  for (int it = blockIdx.x; it < P.n_batches; it += gridDim.x) {
+    const MortarBatch B = P.batches[it];
+    if (bad_batch(P, B, mortar_general_smem<MODE>(B))) continue;
+    const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb, cnt = B.count;
+    const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
+    const int nfl = la * lb, nfr = ra * rb, nm = Ma * Mb;
+    const bool upLa = la != Ma, upLb = lb != Mb, upRa = ra != Ma, upRb = rb != Mb;
+    const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+    double* TL = smem;                          // [cnt][NIN][nfl] L trace and J a
+    double* TR = TL + cnt * NIN * nfl;          // [cnt][NIN][nfr]
+    double* UL = TR + cnt * NIN * nfr;          // [cnt][NMID][uL] pass temporaries
+    double* UR = UL + cnt * NMID * uL;          // [cnt][NMID][uR]
+    double* QL = UR + cnt * NMID * uR;          // [cnt][NIN][nm] on the mortar grid
+    double* QR = QL + cnt * NIN * nm;           // [cnt][NIN][nm]
+    double* OL = QR + cnt * NIN * nm;           // [cnt][NOUT][nm] each side's output
+    double* OR = OL + cnt * NOUT * nm;          // [cnt][NOUT][nm]
+    // 1. gather both traces and each side's own J a^dir
+    for (int t = threadIdx.x; t < cnt * (nfl + nfr); t += blockDim.x) {
+      const bool isL = t < cnt * nfl;
+      const int tt = isL ? t : t - cnt * nfl;
+      const int nf = isL ? nfl : nfr, na = isL ? la : ra;
+      const int f = tt / nf, p = tt - f * nf;
+      const int* fr = P.faces + 3 * (B.first + f);
+      const int e = isL ? fr[0] : fr[1], dir = fr[2];
+      int n1, n2, n3;
+      orders_of(m, e, n1, n2, n3);
+      const int n = n1 * n2 * n3;
+      const int vi = face_vidx(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir, p % na, p / na);
+      const int64_t o = m.off[e];
+      double* T = (isL ? TL + f * NIN * nfl : TR + f * NIN * nfr) + p;
+      for (int v = 0; v < 5; ++v) T[v * nf] = P.q[5 * o + v * n + vi];
+      if (MODE == 1)
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) T[(5 + v * 3 + c) * nf] = P.grad[15 * o + (c * 5 + v) * n + vi];
+      double ja[3];
+      face_metric<AFFINE>(m, e, n, vi, dir, ja);
+      for (int c = 0; c < 3; ++c) T[(NQ + c) * nf] = ja[c];
+    }
+    __syncthreads();
+    // 2. first interpolation pass (xi_a) for the sides that need it
+    const double* IaL = P.basis + c_boff.I[la - 1][Ma - 1];
+    const double* IaR = P.basis + c_boff.I[ra - 1][Ma - 1];
+    {
+      const int nL = upLa ? cnt * Ma * lb : 0, nR = upRa ? cnt * Ma * rb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int nb = isL ? lb : rb, na = isL ? la : ra, per = Ma * nb;
+        const int f = tt / per, x = tt - f * per, m0 = x % Ma, b = x / Ma;
+        const double* src = isL ? TL + f * NIN * nfl : TR + f * NIN * nfr;
+        const double* Ia = isL ? IaL : IaR;
+        double* dst = (isL ? UL + f * NMID * uL : UR + f * NMID * uR) + x;
+        const int nsrc = na * nb;
+        double acc[NIN];
+        for (int c = 0; c < NIN; ++c) acc[c] = 0.0;
+        for (int a = 0; a < na; ++a) {
+          const double w = __ldg(Ia + m0 * na + a);
+          for (int c = 0; c < NIN; ++c) acc[c] += w * src[c * nsrc + a + na * b];
+        }
+        for (int c = 0; c < NIN; ++c) dst[c * per] = acc[c];
+      }
+    }
+    __syncthreads();
+    // 3. second interpolation pass (xi_b), or a copy, onto the mortar grid
+    const double* IbL = P.basis + c_boff.I[lb - 1][Mb - 1];
+    const double* IbR = P.basis + c_boff.I[rb - 1][Mb - 1];
+    for (int t = threadIdx.x; t < 2 * cnt * nm; t += blockDim.x) {
+      const bool isL = t < cnt * nm;
+      const int tt = isL ? t : t - cnt * nm;
+      const int f = tt / nm, x = tt - f * nm, m0 = x % Ma, m1 = x / Ma;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      const int nb = isL ? lb : rb;
+      const double* src = upa ? (isL ? UL + f * NMID * uL : UR + f * NMID * uR)
+                              : (isL ? TL + f * NIN * nfl : TR + f * NIN * nfr);
+      const int nsrc = Ma * nb;
+      double* dst = (isL ? QL : QR) + f * NIN * nm + x;
+      if (upb) {
+        const double* Ib = isL ? IbL : IbR;
+        double acc[NIN];
+        for (int c = 0; c < NIN; ++c) acc[c] = 0.0;
+        for (int b = 0; b < nb; ++b) {
+          const double w = __ldg(Ib + m1 * nb + b);
+          for (int c = 0; c < NIN; ++c) acc[c] += w * src[c * nsrc + m0 + Ma * b];
+        }
+        for (int c = 0; c < NIN; ++c) dst[c * nm] = acc[c];
+      } else {
+        for (int c = 0; c < NIN; ++c) dst[c * nm] = src[c * nsrc + m0 + Ma * m1];
+      }
+    }
+    __syncthreads();
+    // 4. each side's output at the mortar nodes, with its own J a^dir
+    for (int t = threadIdx.x; t < cnt * nm; t += blockDim.x) {
+      const int f = t / nm, x = t - f * nm;
+      const double* ql = QL + f * NIN * nm + x;
+      const double* qr = QR + f * NIN * nm + x;
+      double qa[5], qb[5], jl[3], jr[3];
+      for (int v = 0; v < 5; ++v) {
+        qa[v] = ql[v * nm];
+        qb[v] = qr[v * nm];
+      }
+      for (int c = 0; c < 3; ++c) {
+        jl[c] = ql[(NQ + c) * nm];
+        jr[c] = qr[(NQ + c) * nm];
+      }
+      double* ol = OL + f * NOUT * nm + x;
+      double* orr = OR + f * NOUT * nm + x;
+      if (MODE == 2) {
+        for (int v = 0; v < 5; ++v) {
+          const double qh = 0.5 * (qa[v] + qb[v]);
+          for (int c = 0; c < 3; ++c) {
+            ol[(v * 3 + c) * nm] = qh * jl[c];
+            orr[(v * 3 + c) * nm] = qh * jr[c];
+          }
+        }
+        continue;
+      }
+      double nl[3], nr[3], FLv[5], FRv[5];
+      const double al = unit_normal(jl, nl), ar = unit_normal(jr, nr);
+      roe_face<false>(gamma, 0, qa, qb, nl, FLv);
+      roe_face<false>(gamma, 0, qa, qb, nr, FRv);
+      for (int v = 0; v < 5; ++v) {
+        FLv[v] *= al;
+        FRv[v] *= ar;
+      }
+      if (MODE == 1) {
+        double g[15], fa[3][5], fb[3][5];
+        for (int c = 0; c < 15; ++c) g[c] = ql[(5 + c) * nm];
+        viscous(m.ph, qa, g, fa);
+        for (int c = 0; c < 15; ++c) g[c] = qr[(5 + c) * nm];
+        viscous(m.ph, qb, g, fb);
+        for (int v = 1; v < 5; ++v) {
+          const double s0 = fa[0][v] + fb[0][v], s1 = fa[1][v] + fb[1][v], s2 = fa[2][v] + fb[2][v];
+          FLv[v] -= 0.5 * (s0 * jl[0] + s1 * jl[1] + s2 * jl[2]);
+          FRv[v] -= 0.5 * (s0 * jr[0] + s1 * jr[1] + s2 * jr[2]);
+        }
+      }
+      for (int v = 0; v < 5; ++v) {
+        ol[v * nm] = FLv[v];
+        orr[v * nm] = FRv[v];
+      }
+    }
+    __syncthreads();
+    // 5. first projection pass (xi_a) back to each side that needs it
+    const double* PaL = P.basis + c_boff.P[Ma - 1][la - 1];
+    const double* PaR = P.basis + c_boff.P[Ma - 1][ra - 1];
+    {
+      const int nL = upLa ? cnt * la * Mb : 0, nR = upRa ? cnt * ra * Mb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int na = isL ? la : ra, per = na * Mb;
+        const int f = tt / per, x = tt - f * per, a = x % na, m1 = x / na;
+        const double* Pa = isL ? PaL : PaR;
+        const double* src = (isL ? OL : OR) + f * NOUT * nm;
+        double* dst = (isL ? UL + f * NMID * uL : UR + f * NMID * uR) + x;
+        double acc[NOUT];
+        for (int c = 0; c < NOUT; ++c) acc[c] = 0.0;
+        for (int m0 = 0; m0 < Ma; ++m0) {
+          const double w = __ldg(Pa + a * Ma + m0);
+          for (int c = 0; c < NOUT; ++c) acc[c] += w * src[c * nm + m0 + Ma * m1];
+        }
+        for (int c = 0; c < NOUT; ++c) dst[c * per] = acc[c];
+      }
+    }
+    __syncthreads();
+    // 6. second projection pass (xi_b), or a copy, onto each side's face grid; store
+    const double* PbL = P.basis + c_boff.P[Mb - 1][lb - 1];
+    const double* PbR = P.basis + c_boff.P[Mb - 1][rb - 1];
+    for (int t = threadIdx.x; t < cnt * (nfl + nfr); t += blockDim.x) {
+      const bool isL = t < cnt * nfl;
+      const int tt = isL ? t : t - cnt * nfl;
+      const int nf = isL ? nfl : nfr, na = isL ? la : ra;
+      const int f = tt / nf, x = tt - f * nf, a = x % na, b = x / na;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      const double* src = upa ? (isL ? UL + f * NMID * uL : UR + f * NMID * uR) : (isL ? OL : OR) + f * NOUT * nm;
+      const int nsrc = na * Mb;
+      double out[NOUT];
+      if (upb) {
+        const double* Pb = isL ? PbL : PbR;
+        for (int c = 0; c < NOUT; ++c) out[c] = 0.0;
+        for (int m1 = 0; m1 < Mb; ++m1) {
+          const double w = __ldg(Pb + b * Mb + m1);
+          for (int c = 0; c < NOUT; ++c) out[c] += w * src[c * nsrc + a + na * m1];
+        }
+      } else {
+        for (int c = 0; c < NOUT; ++c) out[c] = src[c * nsrc + a + na * b];
+      }
+      const int* fr = P.faces + 3 * (B.first + f);
+      const int e = isL ? fr[0] : fr[1], dir = fr[2];
+      int n1, n2, n3;
+      orders_of(m, e, n1, n2, n3);
+      double* dst = (MODE == 2 ? P.surf + 15 * (m.soff[e] + face_offset(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir))
+                               : P.surf + 5 * (m.soff[e] + face_offset(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir)));
+      for (int c = 0; c < NOUT; ++c) dst[c * nf + x] = out[c];
     }
     __syncthreads();
   }
@@ -2038,9 +2274,22 @@ cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* gra
     M.q = q;
     M.surf = surf;
     M.basis = m->basis64;
+    M.grad = grad;
     const size_t smem = sizeof(double) * m->mortar_smem;
     const int grid = m->n_mbatches;   // one CTA per batch, largest first
-    if (m->axis) {
+    if (m->general_mortars) {
+      const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+#define DG_GMORTAR(AFF, MODE)                                                       \
+  {                                                                                 \
+    if ((err = allow_smem(mortar_general_kernel<AFF, MODE>, smem))) return err;     \
+    mortar_general_kernel<AFF, MODE><<<grid, kVolThreads, smem, m->stream>>>(M);    \
+  }
+      if (m->affine) {
+        if (ns) DG_GMORTAR(true, 1) else DG_GMORTAR(true, 0)
+      } else {
+        if (ns) DG_GMORTAR(false, 1) else DG_GMORTAR(false, 0)
+      }
+    } else if (m->axis) {
       if ((err = allow_smem(mortar_kernel<true>, smem))) return err;
       mortar_kernel<true><<<grid, kVolThreads, smem, m->stream>>>(M);
     } else {
@@ -2076,6 +2325,11 @@ cudaError_t dispatch_volume(dg_mesh_impl* m, const VolParams& P0, size_t, int) {
 
 size_t dg_mortar_smem_doubles(int count, int la, int lb, int ra, int rb) {
   return mortar_smem_doubles(count, la, lb, ra, rb);
+}
+
+size_t dg_mortar_general_smem_doubles(int count, int la, int lb, int ra, int rb, bool ns) {
+  const MortarBatch B{0, count, la, lb, ra, rb};
+  return ns ? std::max(mortar_general_smem<1>(B), mortar_general_smem<2>(B)) : mortar_general_smem<0>(B);
 }
 
 namespace dgk {
@@ -2123,14 +2377,34 @@ cudaError_t face_flux(dg_mesh_impl* m, const double* q, const double* grad, bool
 }
 
 cudaError_t face_qhat(dg_mesh_impl* m, const double* q) {
-  if (m->n_faces == 0) return cudaSuccess;
-  FaceParams P = face_params(m, q, nullptr);
-  int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+  cudaError_t err;
   Prof pr(m, DG_KERNEL_FACE_QHAT);
-  if (m->affine) face_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, m->d_surfq);
-  else face_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, m->d_surfq);
-  return cudaGetLastError();
+  if (m->n_faces) {
+    FaceParams P = face_params(m, q, nullptr);
+    int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+    if (m->affine) face_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, m->d_surfq);
+    else face_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, m->d_surfq);
+    if ((err = cudaGetLastError())) return err;
+  }
+  if (m->n_mbatches && m->general_mortars) {   // BR1 q-hat on the mortars
+    MortarParams M;
+    M.m = view(m);
+    M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
+    M.n_batches = m->n_mbatches;
+    M.n_mfaces = m->n_mfaces;
+    M.faces = m->d_mfaces;
+    M.q = q;
+    M.surf = m->d_surfq;
+    M.basis = m->basis64;
+    M.grad = nullptr;
+    const size_t smem = sizeof(double) * m->mortar_smem;
+    const int grid = m->n_mbatches;
+    if (m->affine) DG_GMORTAR(true, 2) else DG_GMORTAR(false, 2)
+    if ((err = cudaGetLastError())) return err;
+  }
+  return cudaSuccess;
 }
+#undef DG_GMORTAR
 
 static VolParams vol_params(dg_mesh_impl* m, const double* q) {
   VolParams P;

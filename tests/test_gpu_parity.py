@@ -65,12 +65,6 @@ def _h(mi):
 def test_residual_parity(torch_cuda, name, isolated):
     torch = torch_cuda
     mi, om, m, q = _setup(torch, name)
-    if name == "wavy_curved_mortar" and not isolated:
-        from paper_2210_03523_gb300 import dg
-        with pytest.raises(dg.DGError) as ei:
-            m.residual(torch.from_numpy(q).cuda())
-        assert ei.value.status == 4            # curved mortars: face-coupled calls unsupported
-        return
     r = m.residual(torch.from_numpy(q).cuda(), isolated=isolated).cpu().numpy()
     ro = om.residual(q, isolated=isolated)
     err = rel_err(r, ro, om.off, scale_per_var(q, mi.phys, _h(mi)))
