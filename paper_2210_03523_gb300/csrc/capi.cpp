@@ -978,8 +978,10 @@ dg_status dg_residual_vjp(dg_mesh* m, const double* q, const double* v, double* 
 
 dg_status dg_wall_force(dg_mesh* m, const double* q, int32_t tag, double* force_dev) {
   if (!m || !q || !force_dev || tag >= 0) return DG_ERR_ARG;
-  dg_status st = adjoint_ready(m);
-  if (st != DG_OK) return st;
+  // a forward quantity: the boundary faces and, for Navier-Stokes, the BR1
+  // gradient (its mortars included); only the per-face partial sums are needed
+  if (m->faces_unsupported) return DG_ERR_UNSUPPORTED;
+  if (!m->d_force) DG_CUDA(cudaMalloc(&m->d_force, sizeof(double) * 3 * (size_t)std::max(m->n_faces, 1)));
   return from_cuda(dgk::wall_force(m, q, tag, force_dev));
 }
 
