@@ -336,7 +336,7 @@ dg_status dg_residual_vjp(dg_mesh* mesh, const double* q, const double* v, doubl
  * n the unit outward normal of the fluid element (into the body), p and tau
  * the pressure and viscous stress of the node's state and BR1 gradient
  * (tau = 0 for Euler).  force_dev: device double[3], written on the mesh
- * stream; the sum runs in face order (deterministic).  Errors: DG_ERR_ARG
+ * stream; the sum over the faces runs in a fixed order (deterministic).  Errors: DG_ERR_ARG
  * (null pointers, tag >= 0), DG_ERR_UNSUPPORTED (as dg_residual),
  * DG_ERR_NOMEM, DG_ERR_CUDA. */
 dg_status dg_wall_force(dg_mesh* mesh, const double* q, int32_t tag, double* force_dev);

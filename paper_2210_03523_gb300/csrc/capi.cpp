@@ -163,7 +163,8 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 
 void free_device(dg_mesh_impl* m) {
   void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
-                  m->d_grad, m->d_xyz, m->d_faces, m->d_items, m->d_elist, m->d_err, m->d_scratch, m->d_taugeo,
+                  m->d_grad, m->d_xyz, m->d_faces, m->d_fnodes, m->d_items, m->d_elist, m->d_err, m->d_scratch,
+                  m->d_taugeo,
                   m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv,
                   m->d_vitems, m->d_velist, m->d_sadj, m->d_adjw, m->d_gadj, m->d_lG, m->d_lS, m->d_adjt,
                   m->d_force};
@@ -171,7 +172,7 @@ void free_device(dg_mesh_impl* m) {
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
   m->d_metric32 = nullptr; m->d_surf = nullptr; m->d_surfq = nullptr; m->d_grad = nullptr; m->d_xyz = nullptr;
-  m->d_faces = nullptr; m->d_items = nullptr; m->d_elist = nullptr; m->d_err = nullptr; m->d_scratch = nullptr;
+  m->d_faces = nullptr; m->d_fnodes = nullptr; m->d_items = nullptr; m->d_elist = nullptr; m->d_err = nullptr; m->d_scratch = nullptr;
   m->d_taugeo = nullptr; m->d_taugeo32 = nullptr; m->d_taugeo_off = nullptr; m->d_rp = nullptr; m->d_qc = nullptr;
   m->d_rc = nullptr; m->d_sweep = nullptr; m->d_mfaces = nullptr; m->d_mbatches = nullptr; m->d_rp32 = nullptr;
   m->d_adv = nullptr;
@@ -435,6 +436,19 @@ dg_status build(dg_mesh_impl* m) {
   }
   faces.swap(wfaces);
   m->n_faces = (int)faces.size();
+  // (face, node) of every node of the listed faces: the face kernel runs one
+  // thread per face node
+  std::vector<int32_t> fnodes;
+  for (int i = 0; i < m->n_faces; ++i) {
+    const FaceRec& f = faces[i];
+    const int e = f.L, d = f.kind == 2 ? f.face / 2 : f.face, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+    const int nf = (m->h_ord[3 * e + t0] + 1) * (m->h_ord[3 * e + t1] + 1);
+    for (int p = 0; p < nf; ++p) {
+      fnodes.push_back(i);
+      fnodes.push_back(p);
+    }
+  }
+  m->n_fnodes = (int)fnodes.size() / 2;
   // the batched faces by shape, faces of one direction together: the
   // axis-aligned Roe flux branches on the direction, so a warp that spans
   // two directions runs both variants
@@ -504,6 +518,7 @@ dg_status build(dg_mesh_impl* m) {
     DG_CUDA(upload(&m->d_metric32, m32.data(), m32.size()));
   }
   DG_CUDA(upload(&m->d_faces, faces.data(), faces.size()));
+  DG_CUDA(upload(&m->d_fnodes, fnodes.data(), fnodes.size()));
   DG_CUDA(upload(&m->d_items, items.data(), items.size()));
   DG_CUDA(upload(&m->d_elist, elist.data(), elist.size()));
   DG_CUDA(upload<double>(&m->d_surf, nullptr, 5 * (size_t)m->h_soff[ne]));

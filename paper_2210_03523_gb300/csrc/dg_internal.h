@@ -148,7 +148,9 @@ struct dg_mesh_impl {
   double* d_surfq = nullptr;       // NS: [15 * soff_total] BR1 q-hat * J a^dir
   double* d_grad = nullptr;        // NS: [15 * n_nodes] gradient [c][v][node]
   double* d_xyz = nullptr;         // lazily uploaded coordinates
-  FaceRec* d_faces = nullptr;      // conforming and boundary faces (one warp each)
+  FaceRec* d_faces = nullptr;      // conforming and boundary faces
+  int32_t* d_fnodes = nullptr;     // (face, node) pairs of those faces, one thread each
+  int n_fnodes = 0;
   int n_faces = 0, n_face_conf = 0, n_face_mortar = 0, n_face_bnd = 0;
   int32_t* d_mfaces = nullptr;     // p-nonconforming faces [L, R, dir], grouped by shape signature
   int n_mfaces = 0;

@@ -1,9 +1,9 @@
 // kernels.cu -- sm_103a kernels of libdg.
 //
 // Hot path (Sec. 2.1 DGSEM residual, Sec. 3 RK3, Sec. 2.3 tau sweep):
-//   face_flux_kernel   Roe (+ BR1 viscous average) numerical flux per face,
-//                      one warp per face; p-nonconforming faces through a
-//                      mortar staged in shared memory (interpolate both
+//   face_node_flux_kernel  Roe (+ BR1 viscous average) numerical flux, one
+//                      thread per face node; p-nonconforming faces through
+//                      mortars staged in shared memory (interpolate both
 //                      traces up, Roe at mortar nodes, L2-project back).
 //   face_qhat_kernel   BR1 q-hat * J a^dir on every face (Navier-Stokes).
 //   gradient_kernel    BR1 gradient, strong form (Navier-Stokes).
@@ -12,10 +12,10 @@
 //                      -(1/J) scaling, optionally the fused RK3 stage update.
 //                      Elements of one order triple are batched per CTA
 //                      (work items), all triples in one launch.
-//   tau_kernel<T>      isolated tau sweep, one CTA per element: restriction
-//                      by sum-factorised interpolation (reused across sweep
-//                      entries that share N3 / (N2,N3)), coarse isolated
-//                      residual, both tau forms, block max-reduction.
+//   tau_kernel<T>      isolated tau sweep, one CTA per (tile, group of sweep
+//                      entries sharing (N2,N3)): restriction by sum-factorised
+//                      interpolation (xi3 and xi2 once per group), coarse
+//                      isolated residual, both tau forms, per-element maxima.
 // FP64 throughout, except tau_kernel<float>.
 #include <algorithm>
 #include <cfloat>
@@ -349,7 +349,7 @@ __device__ __forceinline__ bool bad_face(const MeshView& m, const FaceRec& f) {
   else if (!bad)
     bad = (unsigned)f.R >= (unsigned)m.n_elem || (unsigned)f.face >= 3u ||
           !elem_fits(m, f.R, m.ord[3 * f.R], m.ord[3 * f.R + 1], m.ord[3 * f.R + 2]);
-  if (bad && (threadIdx.x & 31) == 0) flag_index(m);
+  if (bad) flag_index(m);
   return bad;
 #else
   (void)m;
@@ -375,6 +375,8 @@ struct FaceParams {
   const double* basis;
   int np_max;            // max order + 1 (mortar smem sizing)
   int warp_smem;         // doubles per warp
+  const int2* fnodes;    // (face, node) of every face node, faces in order
+  int n_fnodes;
 };
 
 template <bool AFFINE>
@@ -392,111 +394,114 @@ __device__ __forceinline__ double unit_normal(const double ja[3], double nrm[3])
   return a2 * ia;   // |J a|
 }
 
-// One warp per face.  AFFINE: the face's J a^dir (hence its normal and area)
-// is one constant read from the element record; AXIS: in addition it is
-// aligned with e_dir.  kind 0: conforming interior; 2: boundary.  Writes the contravariant numerical flux F* in
-// the +xi_dir direction onto each side's own face grid.
+
+// Numerical flux on the conforming interior (kind 0) and boundary (kind 2)
+// faces, one thread per face node over the (face, node) list, so that faces
+// of any size pack the warps (a warp per face left lanes idle on faces of
+// fewer than 32 nodes, e.g. 7 x 2 on a P = (6,6,1) mesh).  Writes the
+// contravariant numerical flux F* in the +xi_dir direction, |J a^dir| times
+// Roe (minus the BR1 viscous average for Navier-Stokes), onto each side's own
+// face grid.  AFFINE: J a^dir is the element record's constant; AXIS: it is
+// aligned with e_dir.
+constexpr int kFaceNodeThreads = 128;
 template <bool AFFINE, bool AXIS, bool NS>
-__global__ void __launch_bounds__(32 * kFaceWarps) face_flux_kernel(FaceParams P) {
-  extern __shared__ double smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int fidx = blockIdx.x * kFaceWarps + warp;
-  if (fidx >= P.n_faces) return;
-  const FaceRec fr = P.faces[fidx];
+__global__ void __launch_bounds__(kFaceNodeThreads, 4) face_node_flux_kernel(FaceParams P) {
+  const int g = blockIdx.x * kFaceNodeThreads + threadIdx.x;
+  if (g >= P.n_fnodes) return;
+  const int2 fp = P.fnodes[g];
+#ifdef DG_BOUNDS_CHECK
+  if ((unsigned)fp.x >= (unsigned)P.n_faces) {
+    flag_index(P.m);
+    return;
+  }
+#endif
+  const FaceRec fr = P.faces[fp.x];
   if (bad_face(P.m, fr)) return;
   const MeshView& m = P.m;
   const double gamma = m.ph.gamma;
-
+  const int p = fp.y;
   if (fr.kind == 2) {  // boundary face of element fr.L, face fr.face, tag fr.R
     const int e = fr.L, f = fr.face, tag = fr.R, dir = f >> 1, side = f & 1;
     int n1, n2, n3;
     orders_of(m, e, n1, n2, n3);
     const int n = n1 * n2 * n3;
     const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, nf = na * nb;
+#ifdef DG_BOUNDS_CHECK
+    if ((unsigned)p >= (unsigned)nf) {
+      flag_index(m);
+      return;
+    }
+#endif
     const int64_t o = m.off[e];
     double* out = P.surf + 5 * (m.soff[e] + face_offset(n1, n2, n3, f));
-    double ja[3], nrm[3], area = 0.0;
-    if (AFFINE) {
-      face_metric<true>(m, e, n, 0, dir, ja);
-      area = unit_normal(ja, nrm);
+    const int vi = face_vidx(n1, n2, n3, f, p % na, p / na);
+    double ja[3], nrm[3];
+    face_metric<AFFINE>(m, e, n, vi, dir, ja);
+    const double area = unit_normal(ja, nrm);
+    double qi[5], qg[5], F[5];
+    for (int v = 0; v < 5; ++v) qi[v] = P.q[5 * o + v * n + vi];
+    bc_ghost(m.ph, tag, qi, qg);
+    if (side) roe_face<AXIS>(gamma, dir, qi, qg, nrm, F);
+    else roe_face<AXIS>(gamma, dir, qg, qi, nrm, F);
+    for (int v = 0; v < 5; ++v) F[v] *= area;
+    if (NS) {
+      double gr[15], fv[3][5];
+      for (int v = 0; v < 5; ++v)
+        for (int c = 0; c < 3; ++c) gr[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + vi];
+      viscous(m.ph, qi, gr, fv);
+      for (int v = 1; v < 4; ++v) F[v] -= fv[0][v] * ja[0] + fv[1][v] * ja[1] + fv[2][v] * ja[2];
+      if (tag != DG_BC_WALL) F[4] -= fv[0][4] * ja[0] + fv[1][4] * ja[1] + fv[2][4] * ja[2];
     }
-    for (int p = lane; p < nf; p += 32) {
-      const int vi = face_vidx(n1, n2, n3, f, p % na, p / na);
-      double qi[5], qg[5], F[5];
-      for (int v = 0; v < 5; ++v) qi[v] = P.q[5 * o + v * n + vi];
-      if (!AFFINE) {
-        face_metric<false>(m, e, n, vi, dir, ja);
-        area = unit_normal(ja, nrm);
-      }
-      bc_ghost(m.ph, tag, qi, qg);
-      if (side) roe_face<AXIS>(gamma, dir, qi, qg, nrm, F);
-      else roe_face<AXIS>(gamma, dir, qg, qi, nrm, F);
-      for (int v = 0; v < 5; ++v) F[v] *= area;
-      if (NS) {
-        double g[15], fv[3][5];
-        for (int v = 0; v < 5; ++v)
-          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * o + (c * 5 + v) * n + vi];
-        viscous(m.ph, qi, g, fv);
-        for (int v = 1; v < 4; ++v) F[v] -= fv[0][v] * ja[0] + fv[1][v] * ja[1] + fv[2][v] * ja[2];
-        if (tag != DG_BC_WALL) F[4] -= fv[0][4] * ja[0] + fv[1][4] * ja[1] + fv[2][4] * ja[2];
-      }
-      for (int v = 0; v < 5; ++v) out[v * nf + p] = F[v];
-    }
+    for (int v = 0; v < 5; ++v) out[v * nf + p] = F[v];
     return;
   }
-
+  // conforming interior face (the list holds no other kind)
   const int L = fr.L, R = fr.R, dir = fr.face;
   int l1, l2, l3, r1, r2, r3;
   orders_of(m, L, l1, l2, l3);
   orders_of(m, R, r1, r2, r3);
   const int nL = l1 * l2 * l3, nR = r1 * r2 * r3;
-  const int64_t oL = m.off[L], oR = m.off[R];
   const int fL = 2 * dir + 1, fR = 2 * dir;
-  const int la = dir == 0 ? l2 : l1, lb = dir == 2 ? l2 : l3;   // == R's (conforming)
+  const int la = dir == 0 ? l2 : l1, lb = dir == 2 ? l2 : l3, nf = la * lb;
+#ifdef DG_BOUNDS_CHECK
+  {
+    const int ra = dir == 0 ? r2 : r1, rb = dir == 2 ? r2 : r3;
+    if (fr.kind != 0 || ra != la || rb != lb || (unsigned)p >= (unsigned)nf) {
+      flag_index(m);
+      return;
+    }
+  }
+#endif
+  const int64_t oL = m.off[L], oR = m.off[R];
   double* outL = P.surf + 5 * (m.soff[L] + face_offset(l1, l2, l3, fL));
   double* outR = P.surf + 5 * (m.soff[R] + face_offset(r1, r2, r3, fR));
-  double ja[3], nrm[3], area = 0.0;
-  if (AFFINE) {
-    face_metric<true>(m, L, nL, 0, dir, ja);
-    area = unit_normal(ja, nrm);
+  const int a = p % la, b = p / la;
+  const int iL = face_vidx(l1, l2, l3, fL, a, b), iR = face_vidx(r1, r2, r3, fR, a, b);
+  double ja[3], nrm[3];
+  face_metric<AFFINE>(m, L, nL, iL, dir, ja);
+  const double area = unit_normal(ja, nrm);
+  double qL[5], qR[5], F[5];
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = P.q[5 * oL + v * nL + iL];
+    qR[v] = P.q[5 * oR + v * nR + iR];
   }
-
-  if (fr.kind == 0) {  // conforming: la == ra, lb == rb
-    const int nf = la * lb;
-    for (int p = lane; p < nf; p += 32) {
-      const int a = p % la, b = p / la;
-      const int iL = face_vidx(l1, l2, l3, fL, a, b), iR = face_vidx(r1, r2, r3, fR, a, b);
-      double qL[5], qR[5], F[5];
-      for (int v = 0; v < 5; ++v) {
-        qL[v] = P.q[5 * oL + v * nL + iL];
-        qR[v] = P.q[5 * oR + v * nR + iR];
-      }
-      if (!AFFINE) {
-        face_metric<false>(m, L, nL, iL, dir, ja);
-        area = unit_normal(ja, nrm);
-      }
-      roe_face<AXIS>(gamma, dir, qL, qR, nrm, F);
-      for (int v = 0; v < 5; ++v) F[v] *= area;
-      if (NS) {
-        double g[15], fa[3][5], fb[3][5];
-        for (int v = 0; v < 5; ++v)
-          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * oL + (c * 5 + v) * nL + iL];
-        viscous(m.ph, qL, g, fa);
-        for (int v = 0; v < 5; ++v)
-          for (int c = 0; c < 3; ++c) g[v * 3 + c] = P.grad[15 * oR + (c * 5 + v) * nR + iR];
-        viscous(m.ph, qR, g, fb);
-        for (int v = 1; v < 5; ++v)
-          F[v] -= 0.5 * ((fa[0][v] + fb[0][v]) * ja[0] + (fa[1][v] + fb[1][v]) * ja[1] + (fa[2][v] + fb[2][v]) * ja[2]);
-      }
-      for (int v = 0; v < 5; ++v) {
-        outL[v * nf + p] = F[v];
-        outR[v * nf + p] = F[v];
-      }
-    }
-    return;
+  roe_face<AXIS>(gamma, dir, qL, qR, nrm, F);
+  for (int v = 0; v < 5; ++v) F[v] *= area;
+  if (NS) {
+    double gr[15], fa[3][5], fb[3][5];
+    for (int v = 0; v < 5; ++v)
+      for (int c = 0; c < 3; ++c) gr[v * 3 + c] = P.grad[15 * oL + (c * 5 + v) * nL + iL];
+    viscous(m.ph, qL, gr, fa);
+    for (int v = 0; v < 5; ++v)
+      for (int c = 0; c < 3; ++c) gr[v * 3 + c] = P.grad[15 * oR + (c * 5 + v) * nR + iR];
+    viscous(m.ph, qR, gr, fb);
+    for (int v = 1; v < 5; ++v)
+      F[v] -= 0.5 * ((fa[0][v] + fb[0][v]) * ja[0] + (fa[1][v] + fb[1][v]) * ja[1] + (fa[2][v] + fb[2][v]) * ja[2]);
   }
-
-  // p-nonconforming faces (kind 1) are handled by mortar_kernel in shape batches
+  for (int v = 0; v < 5; ++v) {
+    outL[v * nf + p] = F[v];
+    outR[v * nf + p] = F[v];
+  }
 }
 
 // ------------------------------------------------------------ batched mortars
@@ -2200,6 +2205,8 @@ FaceParams dgk_face_params_for(dg_mesh_impl* m, const double* q, double* surf) {
   P.basis = m->basis64;
   P.np_max = m->max_order + 1;
   P.warp_smem = 25 * P.np_max * P.np_max;
+  P.fnodes = reinterpret_cast<const int2*>(m->d_fnodes);
+  P.n_fnodes = m->n_fnodes;
   return P;
 }
 
@@ -2221,9 +2228,11 @@ VolParams dgk_vol_params_for(dg_mesh_impl* m, const double* q, const double* sur
 
 template <bool AFF, bool AX, bool NSV>
 cudaError_t launch_face(dg_mesh_impl* m, const FaceParams& P, size_t smem, int grid) {
-  cudaError_t err = allow_smem(face_flux_kernel<AFF, AX, NSV>, smem);
-  if (err) return err;
-  face_flux_kernel<AFF, AX, NSV><<<grid, 32 * kFaceWarps, smem, m->stream>>>(P);
+  (void)smem;
+  (void)grid;
+  if (P.n_fnodes == 0) return cudaSuccess;
+  const int blocks = (P.n_fnodes + kFaceNodeThreads - 1) / kFaceNodeThreads;
+  face_node_flux_kernel<AFF, AX, NSV><<<blocks, kFaceNodeThreads, 0, m->stream>>>(P);
   return cudaGetLastError();
 }
 
@@ -2368,6 +2377,8 @@ static FaceParams face_params(dg_mesh_impl* m, const double* q, const double* gr
   P.basis = m->basis64;
   P.np_max = m->max_order + 1;
   P.warp_smem = 25 * P.np_max * P.np_max;
+  P.fnodes = reinterpret_cast<const int2*>(m->d_fnodes);
+  P.n_fnodes = m->n_fnodes;
   return P;
 }
 
@@ -4059,11 +4070,22 @@ __global__ void __launch_bounds__(32 * kFaceWarps) wall_force_kernel(FaceParams 
     for (int i = 0; i < 3; ++i) partial[3 * fidx + i] = acc[i];
 }
 
-__global__ void force_sum_kernel(const double* partial, int n_faces, double* F) {
-  if (threadIdx.x >= 3) return;
-  double s = 0.0;
-  for (int f = 0; f < n_faces; ++f) s += partial[3 * f + threadIdx.x];
-  F[threadIdx.x] = s;
+// The three components summed over the per-face partials in a fixed order
+// (deterministic): each thread sums a strided subset, then a tree over the block.
+constexpr int kForceSumThreads = 256;
+__global__ void __launch_bounds__(kForceSumThreads) force_sum_kernel(const double* partial, int n_faces, double* F) {
+  __shared__ double red[3][kForceSumThreads];
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int f = threadIdx.x; f < n_faces; f += kForceSumThreads)
+    for (int c = 0; c < 3; ++c) s[c] += partial[3 * f + c];
+  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = s[c];
+  __syncthreads();
+  for (int h = kForceSumThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) F[threadIdx.x] = red[threadIdx.x][0];
 }
 
 // the force's cotangent lam (3, device) onto the wall nodes' traces (sadj)
@@ -4136,7 +4158,7 @@ cudaError_t wall_force(dg_mesh_impl* m, const double* q, int tag, double* F) {
     else wall_force_kernel<false, false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(P, tag, m->d_force);
   }
   if ((err = cudaGetLastError())) return err;
-  force_sum_kernel<<<1, 32, 0, m->stream>>>(m->d_force, m->n_faces, F);
+  force_sum_kernel<<<1, kForceSumThreads, 0, m->stream>>>(m->d_force, m->n_faces, F);
   return cudaGetLastError();
 }
 
