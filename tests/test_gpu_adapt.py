@@ -259,3 +259,47 @@ def test_resume_from_checkpoint_is_bitwise(torch_cuda, tmp_path):
     run(m2, q2, t2, 12)
     assert torch.equal(q, q2) and t.item() == t2.item()
     assert m.get_error() == 0 and m2.get_error() == 0
+
+
+def test_static_driver_on_a_curved_navier_stokes_ogrid_matches_oracle(torch_cuda):
+    """The static driver on a small curved O-grid around a cylinder
+    (Navier-Stokes, walls and far field, uniform P = (4,4,1)): estimation,
+    selection among N <= P and the run after adaptation, whose mixed orders put
+    p-nonconforming faces on a curved Navier-Stokes mesh.  tau_max sits midway
+    between two well separated values of the oracle's accumulated map, so that
+    no selection hinges on rounding."""
+    from oracle import drivers as od
+    from paper_2210_03523_gb300 import adapt
+    import oracle
+    p0 = 10.0
+    ph = I.Physics(1, 1.4, 0.05, 0.72, p0, (1.0, 0.5, 0.1, 0.0, p0 / 0.4 + 0.5 * 0.26))
+    mi = I.ogrid_mesh(n_theta=8, n_r=3, ratio=4.0, orders=(4, 4, 1), phys=ph)
+    om = oracle.Mesh(mi)
+
+    def fn(x, y, z):
+        r2 = x * x + y * y
+        damp = 1.0 - np.exp(-(r2 - 0.25) * 4.0)
+        rho = 1.0 + 0.05 * np.sin(1.3 * x + 0.2) * np.cos(0.9 * y)
+        u, v = damp * (0.5 + 0.05 * np.cos(y)), damp * (0.1 + 0.04 * np.sin(0.7 * x))
+        p = p0 * (1.0 + 0.02 * np.cos(x + 0.5 * y + 0.7))
+        return np.stack([rho, rho * u, rho * v, 0 * x, p / 0.4 + 0.5 * rho * (u * u + v * v)])
+    q0 = I.pointwise_state(om.coords(), mi.orders, fn)
+    dt = om.max_dt(q0, 0.5)
+    kw = dict(t0=0.0, t_est=3.5 * 4 * dt, dt_e=4 * dt, cfl=0.5, sweep=I.full_sweep((4, 4, 1)), n_min=1, n_max=4,
+              jump_rule=2)
+    est = od.static_adaptation(mi, q0, t_final=kw["t_est"], tau_max=1.0, **kw)
+    v = np.sort(est["total"][np.isfinite(est["total"]) & (est["total"] > 0)].ravel())
+    gaps = v[1:] / v[:-1]
+    mid = len(v) // 2
+    k = mid + int(np.argmax(gaps[mid: mid + len(v) // 4]))       # a wide gap above the median
+    tau_max = float(np.sqrt(v[k] * v[k + 1]))
+    kw.update(t_final=kw["t_est"] + 40 * dt, tau_max=tau_max)
+    ref = od.static_adaptation(mi, q0, **kw)
+    got = adapt.static_adaptation(mi, q0, **kw)
+    assert _margin_ok(ref["total"], tau_max)
+    assert len({tuple(o) for o in ref["orders"]}) > 1               # mixed orders after adaptation
+    assert got["n_estimates"] == ref["n_estimates"] == 3 and got["steps"] == ref["steps"]
+    assert np.array_equal(got["orders"], ref["orders"])
+    assert got["ndof"] == ref["ndof"] and got["ndof_dyn"] == ref["ndof_dyn"]
+    assert _close(got["q"].cpu().numpy(), ref["q"], got["orders"], 1e-11)
+    assert got["mesh"].get_error() == 0
