@@ -221,6 +221,7 @@ void destroy_impl(dg_mesh_impl* m) {
 
 constexpr int kTileNodes = 256;
 constexpr size_t kGeneralMortarBytes = 96 * 1024;
+constexpr int kMinTauUnits = 8 * 152;   // tau units of a size class below which groups are not shared
 
 }  // namespace
 
@@ -602,10 +603,12 @@ dg_status build_tau_bank(dg_mesh_impl* m) {
 // grouped by (N2, N3), and per shared-memory class the (item, group) pairs
 // whose group reaches at least one entry within the item's orders.
 dg_status build_tau_units(dg_mesh_impl* m) {
-  std::map<std::pair<int, int>, std::vector<int32_t>> grp;
+  // sweep entries grouped by (N2, N3), the groups ordered by N3 then N2: a
+  // unit is a tile and the groups of one N3 (the xi3 restriction is shared)
+  std::map<std::pair<int, int>, std::vector<int32_t>> grp;   // key (N3, N2)
   const int ns = (int)m->h_sweep.size() / 3;
   for (int s = 0; s < ns; ++s) {
-    auto& v = grp[{m->h_sweep[3 * s + 1], m->h_sweep[3 * s + 2]}];
+    auto& v = grp[{m->h_sweep[3 * s + 2], m->h_sweep[3 * s + 1]}];
     v.push_back(s);
     v.push_back(m->h_sweep[3 * s]);
   }
@@ -614,7 +617,7 @@ dg_status build_tau_units(dg_mesh_impl* m) {
   for (auto& kv : grp) {
     int mn = 1 << 30;
     for (size_t i = 1; i < kv.second.size(); i += 2) mn = std::min(mn, kv.second[i]);
-    groups.insert(groups.end(), {kv.first.first, kv.first.second, (int32_t)(gentries.size() / 2),
+    groups.insert(groups.end(), {kv.first.second, kv.first.first, (int32_t)(gentries.size() / 2),
                                  (int32_t)(kv.second.size() / 2)});
     gentries.insert(gentries.end(), kv.second.begin(), kv.second.end());
     gmin1.push_back(mn);
@@ -632,16 +635,32 @@ dg_status build_tau_units(dg_mesh_impl* m) {
   for (size_t k = 0; k < m->tau_classes.size(); ++k) {
     std::vector<int32_t> ilist(m->tau_classes[k].n);
     DG_CUDA(cudaMemcpy(ilist.data(), m->tau_classes[k].d_list, sizeof(int32_t) * ilist.size(), cudaMemcpyDeviceToHost));
-    std::vector<int32_t> units;
+    std::vector<int32_t> units;   // (item, first group, group count, 0)
+    const int ng = (int)groups.size() / 4;
     for (int it : ilist) {
       const WorkItem& w = m->h_items[it];
-      for (size_t g = 0; g < groups.size() / 4; ++g)
-        if (groups[4 * g] <= w.n2 && groups[4 * g + 1] <= w.n3 && gmin1[g] <= w.n1) {
-          units.push_back(it);
-          units.push_back((int32_t)g);
-        }
+      for (int g = 0; g < ng;) {
+        const int N3 = groups[4 * g + 1];
+        int h = g;
+        while (h < ng && groups[4 * h + 1] == N3) ++h;      // [g, h): the groups of this N3, N2 ascending
+        int last = g;                                        // the prefix with N2 <= P2
+        while (last < h && groups[4 * last] <= w.n2) ++last;
+        bool any = false;
+        for (int x = g; x < last; ++x) any = any || gmin1[x] <= w.n1;
+        if (N3 <= w.n3 && last > g && any) units.insert(units.end(), {it, g, last - g, 0});
+        g = h;
+      }
     }
-    m->tau_n_units[k] = (int)units.size() / 2;
+    // a small mesh keeps one group per unit: the shared xi3 restriction saves
+    // work, but too few units leave SMs idle
+    if ((int)units.size() / 4 < kMinTauUnits) {
+      std::vector<int32_t> split;
+      for (size_t u = 0; u < units.size(); u += 4)
+        for (int x = units[u + 1]; x < units[u + 1] + units[u + 2]; ++x)
+          if (gmin1[x] <= m->h_items[units[u]].n1) split.insert(split.end(), {units[u], x, 1, 0});
+      units.swap(split);
+    }
+    m->tau_n_units[k] = (int)units.size() / 4;
     DG_CUDA(upload(&m->tau_units[k], units.data(), units.size()));
   }
   return DG_OK;

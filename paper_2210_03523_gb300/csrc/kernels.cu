@@ -1511,7 +1511,7 @@ struct TauParams {
   const WorkItem* items;    // tiles of same-order elements (the volume work items)
   const int32_t* elist;     // their element list
   const int32_t* ilist;     // prologue: items of this launch (one shared-memory size class)
-  const int2* units;        // sweep: (item, group) units of this launch
+  const int4* units;        // sweep: (item, first group, group count) units of this launch: groups of one N3
   const int4* groups;       // sweep entries grouped by (N2, N3): N2, N3, first, count
   const int2* gentries;     // group entries: sweep index, N1
   int n_list;
@@ -1892,17 +1892,16 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   T* Gs = Ft + 15 * S;   // [el][15][nN]    (NS only: the Euler launch allocates 45 S)
   const MeshView& m = P.m;
   for (int ui = blockIdx.x; ui < P.n_list; ui += gridDim.x) {
-    const int2 u = P.units[ui];
+    const int4 u = P.units[ui];
     WorkItem w;
     if (!take_item(P.m, P.items, u.x, P.n_items_all, P.elist, 0, w)) continue;
     if (bad_tile(P.m, w, P.S) || bad_group(P, w, u.y)) continue;
-    const int4 g = P.groups[u.y];      // N2, N3, first entry, entry count
     const int32_t* els = P.elist + w.first;
     const int cnt = w.count;
     const int P1 = w.n1, P2 = w.n2, P3 = w.n3, n1 = P1 + 1, n2 = P2 + 1, n3 = P3 + 1, nP = n1 * n2 * n3;
-    const int N2 = g.x, N3 = g.y, c2 = N2 + 1, c3 = N3 + 1, n12 = n1 * n2;
+    const int N3 = P.groups[u.y].y, c3 = N3 + 1, n12 = n1 * n2;
     const T* rpS = P.rp_scratch;
-    {  // xi3 straight from q^P and R^P in global memory
+    {  // xi3 straight from q^P and R^P in global memory, once for the unit's groups
       const T* I3 = P.basis + c_boff.I[P3][N3];
       const int per = n12 * c3;
       for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
@@ -1923,6 +1922,16 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
       }
       __syncthreads();
     }
+    for (int gi = u.y; gi < u.y + u.z; ++gi) {   // the groups (N2, N3) of this N3, N2 ascending
+    if (gi > u.y && bad_group(P, w, gi)) continue;
+    const int4 g = P.groups[gi];      // N2, N3, first entry, entry count
+    const int N2 = g.x, c2 = N2 + 1;
+#ifdef DG_BOUNDS_CHECK
+    if (g.y != N3) {
+      if (threadIdx.x == 0) flag_index(m);
+      continue;
+    }
+#endif
     {  // xi2
       const T* I2 = P.basis + c_boff.I[P2][N2];
       const int pin = n12 * c3, per = n1 * c2 * c3;
@@ -2038,6 +2047,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
       }
       __syncthreads();
     }
+    }   // groups of the unit
   }
 }
 
@@ -2544,7 +2554,7 @@ static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
       const auto& c = m->tau_classes[k];
       P.S = c.S;
       P.ilist = c.d_list;
-      P.units = reinterpret_cast<const int2*>(m->tau_units[k]);
+      P.units = reinterpret_cast<const int4*>(m->tau_units[k]);
       P.n_list = phase == 0 ? c.n : m->tau_n_units[k];
       if (P.n_list == 0) continue;
       const size_t smem = tau_smem_for(c.S, ns, fp32);
