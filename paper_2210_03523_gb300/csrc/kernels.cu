@@ -156,7 +156,7 @@ __device__ __forceinline__ double ncomp(const double n[3], int c) {
 
 template <int AX, typename S = double>
 __device__ void roe_t(double gamma, const S qL[5], const S qR[5], const double n[3], S f[5]) {
-  const double gm1 = gamma - 1.0;
+  const double gm1 = gamma - 1.0, hgm1 = 0.5 * gm1;
   const S rsL = rsq(qL[0]), rsR = rsq(qR[0]);
   const S sL = qL[0] * rsL, sR = qR[0] * rsR;      // sqrt(rho)
   const S irL = rsL * rsL, irR = rsR * rsR;        // 1/rho
@@ -165,54 +165,69 @@ __device__ void roe_t(double gamma, const S qL[5], const S qR[5], const double n
     uL[c] = qL[1 + c] * irL;
     uR[c] = qR[1 + c] * irR;
   }
-  const S pL = gm1 * (qL[4] - 0.5 * (qL[1] * uL[0] + qL[2] * uL[1] + qL[3] * uL[2]));
-  const S pR = gm1 * (qR[4] - 0.5 * (qR[1] * uR[0] + qR[2] * uR[1] + qR[3] * uR[2]));
-  const S HL = (qL[4] + pL) * irL, HR = (qR[4] + pR) * irR;
+  // p = gm1 E - (gm1/2) m.u
+  const S pL = gm1 * qL[4] - hgm1 * (qL[1] * uL[0] + qL[2] * uL[1] + qL[3] * uL[2]);
+  const S pR = gm1 * qR[4] - hgm1 * (qR[1] * uR[0] + qR[2] * uR[1] + qR[3] * uR[2]);
+  const S eL = qL[4] + pL, eR = qR[4] + pR;        // rho H
+  const S HL = eL * irL, HR = eR * irR;
+  // Roe averages with the weights sqrt(rho_L,R) / (sqrt(rho_L) + sqrt(rho_R))
   const S is = 1.0 / (sL + sR);
+  const S wL = sL * is, wR = sR * is;
   S ut[3];
-  for (int c = 0; c < 3; ++c) ut[c] = (sL * uL[c] + sR * uR[c]) * is;
-  const S Ht = (sL * HL + sR * HR) * is;
+  for (int c = 0; c < 3; ++c) ut[c] = wL * uL[c] + wR * uR[c];
+  const S Ht = wL * HL + wR * HR;
   const S rt = sL * sR;
   const S q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
   const S c2 = gm1 * (Ht - 0.5 * q2);
   const S rc = rsq(c2);
-  const S ct = c2 * rc, ic2 = rc * rc;
-  S unL, unR, utn;
+  const S ct = c2 * rc, ic2 = rc * rc, hic2 = 0.5 * ic2;
+  S unL, unR, utn, mL, mR;
   if (AX >= 0) {
     unL = uL[AX];
     unR = uR[AX];
     utn = ut[AX];
+    mL = qL[1 + AX];   // rho u_n: the normal momentum itself
+    mR = qR[1 + AX];
   } else {
     unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
     unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
     utn = ut[0] * n[0] + ut[1] * n[1] + ut[2] * n[2];
+    mL = qL[0] * unL;
+    mR = qR[0] * unR;
   }
   const S dun = unR - unL, dp = pR - pL, dr = qR[0] - qL[0];
   const S rcd = rt * ct * dun;
-  const S a1 = 0.5 * (dp - rcd) * ic2;
-  const S a5 = 0.5 * (dp + rcd) * ic2;
+  const S a1 = (dp - rcd) * hic2;
+  const S a5 = (dp + rcd) * hic2;
   const S a2 = dr - dp * ic2;
   const S l1a1 = absval(utn - ct) * a1, l5a5 = absval(utn + ct) * a5, l2 = absval(utn);
+  const S s15 = l1a1 + l5a5, d15 = (l5a5 - l1a1) * ct;
+  // tangential velocity jump; on an axis normal its normal component is exactly zero
   S dut[3], utdut{};
   for (int c = 0; c < 3; ++c) {
-    // tangential velocity jump; on an axis normal only component AX has a normal part
-    dut[c] = (AX < 0 || c == AX) ? (uR[c] - uL[c]) - dun * ncomp<AX>(n, c) : uR[c] - uL[c];
-    utdut += ut[c] * dut[c];
+    if (AX >= 0) {
+      dut[c] = c == AX ? S{} : uR[c] - uL[c];
+      if (c != AX) utdut += ut[c] * dut[c];
+    } else {
+      dut[c] = (uR[c] - uL[c]) - dun * n[c];
+      utdut += ut[c] * dut[c];
+    }
   }
-  const S mL = qL[0] * unL, mR = qR[0] * unR;
-  f[0] = 0.5 * (mL + mR) - 0.5 * (l1a1 + l5a5 + l2 * a2);
+  f[0] = 0.5 * ((mL + mR) - (s15 + l2 * a2));
   for (int c = 0; c < 3; ++c) {
     const double nc = ncomp<AX>(n, c);
     S phys = mL * uL[c] + mR * uR[c];
-    S diss = (l1a1 + l5a5) * ut[c] + l2 * (a2 * ut[c] + rt * dut[c]);
+    S inner = a2 * ut[c];
+    if (AX < 0 || c != AX) inner += rt * dut[c];   // dut[AX] = 0 on an axis normal
+    S diss = s15 * ut[c] + l2 * inner;
     if (AX < 0 || c == AX) {
       phys += (pL + pR) * nc;
-      diss += (l5a5 - l1a1) * ct * nc;
+      diss += d15 * nc;
     }
     f[1 + c] = 0.5 * (phys - diss);
   }
-  const S physE = unL * (qL[4] + pL) + unR * (qR[4] + pR);
-  const S dissE = (l1a1 + l5a5) * Ht + (l5a5 - l1a1) * utn * ct + l2 * (a2 * 0.5 * q2 + rt * utdut);
+  const S physE = unL * eL + unR * eR;
+  const S dissE = s15 * Ht + d15 * utn + l2 * (a2 * 0.5 * q2 + rt * utdut);
   f[4] = 0.5 * (physE - dissE);
 }
 
