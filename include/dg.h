@@ -312,22 +312,24 @@ dg_status dg_get_tiles(const dg_mesh* mesh, dg_tiles* out);
 dg_status dg_set_tiles(dg_mesh* mesh, const dg_tiles* in);
 
 /* Adjoint (vector-Jacobian product) of the residual: out = (dR/dq)^T v at the
- * state q, for Euler on straight-sided (affine) elements with conforming,
- * p-nonconforming (mortar) and boundary faces.  R = A Phi(q), Phi the
- * pointwise fluxes (contravariant volume flux, Roe at face and mortar
- * nodes) and A linear (GL derivative, surface lift, mortar interpolation and
- * L2 projection, -1/J): the kernels apply A^T and then the flux Jacobians'
- * transposes, taken exactly by forward-mode differentiation of the same
- * flux code (Dual numbers).  q, v, out: device state-layout arrays; out may
- * not alias q or v.  Asynchronous.
+ * state q, on every mesh dg_residual accepts: affine or curved elements,
+ * conforming, p-nonconforming (mortar) and boundary faces.  R = A Phi(q),
+ * Phi the pointwise fluxes (contravariant volume flux, Roe at face and
+ * mortar nodes) and A linear (GL derivative, surface lift, mortar
+ * interpolation and L2 projection, -1/J): the kernels apply A^T and then
+ * the flux Jacobians' transposes, taken exactly by forward-mode
+ * differentiation of the same flux code (Dual numbers).  On curved or
+ * Navier-Stokes mortars each side's flux (its own J a^dir on the mortar)
+ * and the BR1 averages formed on the mortar are reversed the same way.
+ * q, v, out: device state-layout arrays; out may not alias q or v.
+ * Asynchronous.
  * Navier-Stokes adds the BR1 terms: the viscous flux's Jacobians in q and
  * in the gradient, the gradient's own transpose (GL derivative and lift) and
  * q-hat's (the interior average, the wall's q-hat(q_in)).
  * qinf_adj (device, 5 doubles, optional): accumulates the cotangent of the
  * far-field state q_inf (the Roe ghost and BR1's q-hat at far-field faces).
- * Errors: DG_ERR_ARG; DG_ERR_UNSUPPORTED (mortars on curved or Navier-Stokes
- * meshes, whose transposed kernel is not implemented, or mortar batches
- * whose adjoint exceeds shared memory); DG_ERR_CUDA. */
+ * Errors: DG_ERR_ARG; DG_ERR_UNSUPPORTED (mortar batches whose adjoint
+ * exceeds shared memory); DG_ERR_CUDA. */
 dg_status dg_residual_vjp(dg_mesh* mesh, const double* q, const double* v, double* out, double* qinf_adj);
 
 /* Force of the fluid on the boundary faces with tag `tag` (DG_BC_WALL: the

@@ -986,8 +986,7 @@ dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_o
 }
 
 static dg_status adjoint_ready(dg_mesh* m) {
-  // the transposed mortar kernel covers the affine Euler mortars only
-  if (m->faces_unsupported || m->general_mortars) return DG_ERR_UNSUPPORTED;
+  if (m->faces_unsupported) return DG_ERR_UNSUPPORTED;
   int limit = 0;
   DG_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
   if (sizeof(double) * dgk::mortar_adj_smem_max(m) + 1024 > (size_t)limit) return DG_ERR_UNSUPPORTED;

@@ -3319,6 +3319,312 @@ __global__ void __launch_bounds__(kVolThreads) adj_mortar_kernel(MortarParams P,
   }
 }
 
+// The general mortars (curved or Navier-Stokes) reversed.  MODE 0 / 1: the
+// flux pass; each side's face cotangent (the lift's -/+ (1/w_end)(1/J) v)
+// goes back through its own L2 projection to the mortar, then through the
+// side's Roe flux with its own normal and, for Navier-Stokes, through the
+// BR1 average of both viscous fluxes, to cotangents of both states (and
+// gradients) on the mortar grid, and through the transposed interpolation to
+// each side's trace nodes: written to sadj (and gadj).  MODE 2: the q-hat
+// pass; each side's cotangent of q-hat J a^dir (lS) back to the mortar, then
+// to q-hat and half to each trace: added to sadj.
+template <int MODE>
+struct GMortarAdj {
+  static constexpr int nin = GMortar<MODE == 2 ? 0 : MODE>::nin;       // traces (q [, gradient], J a)
+  static constexpr int nq = GMortar<MODE == 2 ? 0 : MODE>::nq;         // the cotangent fields sent back
+  static constexpr int nout = MODE == 2 ? 15 : 5;                      // the side's output cotangent
+  static constexpr int nmid = nin > nout ? nin : nout;
+};
+
+template <int MODE>
+__host__ __device__ inline size_t mortar_general_adj_smem(const MortarBatch& B) {
+  typedef GMortarAdj<MODE> G;
+  const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb;
+  const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb, nm = Ma * Mb;
+  const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+  return (size_t)B.count * ((size_t)(G::nin + G::nout) * (la * lb + ra * rb + 2 * nm) + (size_t)G::nmid * (uL + uR));
+}
+
+__device__ void viscous_vjp(const DevPhys& ph, const double q[5], const double g[15], const double lf[3][5],
+                            double gq[5], double gg[15]);
+
+template <bool AFFINE, int MODE>
+__global__ void __launch_bounds__(kVolThreads) adj_mortar_general_kernel(MortarParams P, const double* __restrict__ vin,
+                                                                         double* __restrict__ sadj,
+                                                                         double* __restrict__ gadj) {
+  typedef GMortarAdj<MODE> G;
+  constexpr int NIN = G::nin, NQ = G::nq, NOUT = G::nout, NMID = G::nmid;
+  extern __shared__ double smem[];
+  const MeshView& m = P.m;
+  const double gamma = m.ph.gamma;
+  for (int it = blockIdx.x; it < P.n_batches; it += gridDim.x) {
+    const MortarBatch B = P.batches[it];
+    if (bad_batch(P, B, mortar_general_adj_smem<MODE>(B))) continue;
+    const int la = B.la, lb = B.lb, ra = B.ra, rb = B.rb, cnt = B.count;
+    const int Ma = la > ra ? la : ra, Mb = lb > rb ? lb : rb;
+    const int nfl = la * lb, nfr = ra * rb, nm = Ma * Mb;
+    const bool upLa = la != Ma, upLb = lb != Mb, upRa = ra != Ma, upRb = rb != Mb;
+    const int uL = (Ma * lb > la * Mb ? Ma * lb : la * Mb), uR = (Ma * rb > ra * Mb ? Ma * rb : ra * Mb);
+    double* TL = smem;                          // [cnt][NIN][nfl] traces and J a
+    double* TR = TL + cnt * NIN * nfl;
+    double* AL = TR + cnt * NIN * nfr;          // [cnt][NOUT][nfl] each side's output cotangent
+    double* AR = AL + cnt * NOUT * nfl;
+    double* UL = AR + cnt * NOUT * nfr;         // [cnt][NMID][uL] pass temporaries
+    double* UR = UL + cnt * NMID * uL;
+    double* QL = UR + cnt * NMID * uR;          // [cnt][NIN][nm] traces on the mortar, then their cotangents
+    double* QR = QL + cnt * NIN * nm;
+    double* LL = QR + cnt * NIN * nm;           // [cnt][NOUT][nm] each side's output cotangent on the mortar
+    double* LR = LL + cnt * NOUT * nm;
+    // 1. traces, J a^dir and the output cotangents
+    for (int t = threadIdx.x; t < cnt * (nfl + nfr); t += blockDim.x) {
+      const bool isL = t < cnt * nfl;
+      const int tt = isL ? t : t - cnt * nfl;
+      const int nf = isL ? nfl : nfr, na = isL ? la : ra;
+      const int f = tt / nf, p = tt - f * nf;
+      const int* fr = P.faces + 3 * (B.first + f);
+      const int e = isL ? fr[0] : fr[1], dir = fr[2];
+      int n1, n2, n3;
+      orders_of(m, e, n1, n2, n3);
+      const int n = n1 * n2 * n3;
+      const int fe = isL ? 2 * dir + 1 : 2 * dir;
+      const int vi = face_vidx(n1, n2, n3, fe, p % na, p / na);
+      const int64_t o = m.off[e];
+      double* T = (isL ? TL + f * NIN * nfl : TR + f * NIN * nfr) + p;
+      double* A = (isL ? AL + f * NOUT * nfl : AR + f * NOUT * nfr) + p;
+      for (int v = 0; v < 5; ++v) T[v * nf] = P.q[5 * o + v * n + vi];
+      if (MODE == 1)
+        for (int v = 0; v < 5; ++v)
+          for (int c = 0; c < 3; ++c) T[(5 + v * 3 + c) * nf] = P.grad[15 * o + (c * 5 + v) * n + vi];
+      double ja[3];
+      face_metric<AFFINE>(m, e, n, vi, dir, ja);
+      for (int c = 0; c < 3; ++c) T[(NQ + c) * nf] = ja[c];
+      if (MODE == 2) {
+        const double* ls = vin + 15 * (m.soff[e] + face_offset(n1, n2, n3, fe));
+        for (int c = 0; c < 15; ++c) A[c * nf] = ls[c * nf + p];
+      } else {
+        const int Nd = (dir == 0 ? n1 : dir == 1 ? n2 : n3) - 1;
+        const double cf = (isL ? -1.0 : 1.0) * inv_wend(Nd) * metric<AFFINE>(m.metric, e, o, n, vi, 10);
+        for (int v = 0; v < 5; ++v) A[v * nf] = cf * vin[5 * o + v * n + vi];
+      }
+    }
+    __syncthreads();
+    // 2-3. the traces interpolated up to the mortar, as in the forward kernel
+    const double* IaL = P.basis + c_boff.I[la - 1][Ma - 1];
+    const double* IaR = P.basis + c_boff.I[ra - 1][Ma - 1];
+    const double* IbL = P.basis + c_boff.I[lb - 1][Mb - 1];
+    const double* IbR = P.basis + c_boff.I[rb - 1][Mb - 1];
+    {
+      const int nL = upLa ? cnt * Ma * lb : 0, nR = upRa ? cnt * Ma * rb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int nb = isL ? lb : rb, na = isL ? la : ra, per = Ma * nb;
+        const int f = tt / per, x = tt - f * per, m0 = x % Ma, b = x / Ma;
+        const double* src = isL ? TL + f * NIN * nfl : TR + f * NIN * nfr;
+        const double* Ia = isL ? IaL : IaR;
+        double* dst = (isL ? UL + f * NMID * uL : UR + f * NMID * uR) + x;
+        const int nsrc = na * nb;
+        double acc[NIN];
+        for (int c = 0; c < NIN; ++c) acc[c] = 0.0;
+        for (int a = 0; a < na; ++a) {
+          const double w = __ldg(Ia + m0 * na + a);
+          for (int c = 0; c < NIN; ++c) acc[c] += w * src[c * nsrc + a + na * b];
+        }
+        for (int c = 0; c < NIN; ++c) dst[c * per] = acc[c];
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * cnt * nm; t += blockDim.x) {
+      const bool isL = t < cnt * nm;
+      const int tt = isL ? t : t - cnt * nm;
+      const int f = tt / nm, x = tt - f * nm, m0 = x % Ma, m1 = x / Ma;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      const int nb = isL ? lb : rb;
+      const double* src = upa ? (isL ? UL + f * NMID * uL : UR + f * NMID * uR)
+                              : (isL ? TL + f * NIN * nfl : TR + f * NIN * nfr);
+      const int nsrc = Ma * nb;
+      double* dst = (isL ? QL : QR) + f * NIN * nm + x;
+      if (upb) {
+        const double* Ib = isL ? IbL : IbR;
+        double acc[NIN];
+        for (int c = 0; c < NIN; ++c) acc[c] = 0.0;
+        for (int b = 0; b < nb; ++b) {
+          const double w = __ldg(Ib + m1 * nb + b);
+          for (int c = 0; c < NIN; ++c) acc[c] += w * src[c * nsrc + m0 + Ma * b];
+        }
+        for (int c = 0; c < NIN; ++c) dst[c * nm] = acc[c];
+      } else {
+        for (int c = 0; c < NIN; ++c) dst[c * nm] = src[c * nsrc + m0 + Ma * m1];
+      }
+    }
+    __syncthreads();
+    // 4a. each side's cotangent: transpose of the xi_b projection pass, into U
+    const double* PaL = P.basis + c_boff.P[Ma - 1][la - 1];
+    const double* PaR = P.basis + c_boff.P[Ma - 1][ra - 1];
+    const double* PbL = P.basis + c_boff.P[Mb - 1][lb - 1];
+    const double* PbR = P.basis + c_boff.P[Mb - 1][rb - 1];
+    {
+      const int nL = upLb ? cnt * la * Mb : 0, nR = upRb ? cnt * ra * Mb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int na = isL ? la : ra, nb = isL ? lb : rb, per = na * Mb;
+        const int f = tt / per, x = tt - f * per, a = x % na, m1 = x / na;
+        const double* Pb = isL ? PbL : PbR;
+        const double* src = isL ? AL + f * NOUT * nfl : AR + f * NOUT * nfr;
+        double* dst = (isL ? UL + f * NMID * uL : UR + f * NMID * uR) + x;
+        const int nsrc = na * nb;
+        double acc[NOUT];
+        for (int c = 0; c < NOUT; ++c) acc[c] = 0.0;
+        for (int b = 0; b < nb; ++b) {
+          const double w = __ldg(Pb + b * Mb + m1);
+          for (int c = 0; c < NOUT; ++c) acc[c] += w * src[c * nsrc + a + na * b];
+        }
+        for (int c = 0; c < NOUT; ++c) dst[c * per] = acc[c];
+      }
+    }
+    __syncthreads();
+    // 4b. transpose of the xi_a projection pass, each side onto the mortar grid (not summed:
+    //     the two sides' outputs differ)
+    for (int t = threadIdx.x; t < 2 * cnt * nm; t += blockDim.x) {
+      const bool isL = t < cnt * nm;
+      const int tt = isL ? t : t - cnt * nm;
+      const int f = tt / nm, x = tt - f * nm, m0 = x % Ma, m1 = x / Ma;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      const int na = isL ? la : ra, nb = isL ? lb : rb;
+      const double* src = upb ? (isL ? UL + f * NMID * uL : UR + f * NMID * uR)
+                              : (isL ? AL + f * NOUT * nfl : AR + f * NOUT * nfr);
+      const int nsrc = upb ? na * Mb : na * nb;
+      double acc[NOUT];
+      if (upa) {
+        const double* Pa = isL ? PaL : PaR;
+        for (int c = 0; c < NOUT; ++c) acc[c] = 0.0;
+        for (int a = 0; a < na; ++a) {
+          const double w = __ldg(Pa + a * Ma + m0);
+          for (int c = 0; c < NOUT; ++c) acc[c] += w * src[c * nsrc + a + na * m1];
+        }
+      } else {
+        for (int c = 0; c < NOUT; ++c) acc[c] = src[c * nsrc + m0 + Ma * m1];
+      }
+      double* dst = (isL ? LL : LR) + f * NOUT * nm + x;
+      for (int c = 0; c < NOUT; ++c) dst[c * nm] = acc[c];
+    }
+    __syncthreads();
+    // 5. the mortar nodes: cotangents of both traces (and gradients), into QL / QR
+    for (int t = threadIdx.x; t < cnt * nm; t += blockDim.x) {
+      const int f = t / nm, x = t - f * nm;
+      double* ql = QL + f * NIN * nm + x;
+      double* qr = QR + f * NIN * nm + x;
+      const double* ll = LL + f * NOUT * nm + x;
+      const double* lr = LR + f * NOUT * nm + x;
+      double jl[3], jr[3], da[5], db[5];
+      for (int c = 0; c < 3; ++c) {
+        jl[c] = ql[(NQ + c) * nm];
+        jr[c] = qr[(NQ + c) * nm];
+      }
+      if (MODE == 2) {
+        for (int v = 0; v < 5; ++v) {
+          double dh = 0.0;
+          for (int c = 0; c < 3; ++c) dh += ll[(v * 3 + c) * nm] * jl[c] + lr[(v * 3 + c) * nm] * jr[c];
+          ql[v * nm] = 0.5 * dh;
+          qr[v * nm] = 0.5 * dh;
+        }
+        continue;
+      }
+      double qa[5], qb[5], lfl[5], lfr[5], ga[5], gb[5];
+      for (int v = 0; v < 5; ++v) {
+        qa[v] = ql[v * nm];
+        qb[v] = qr[v * nm];
+      }
+      double nl[3], nr[3];
+      const double al = unit_normal(jl, nl), ar = unit_normal(jr, nr);
+      for (int v = 0; v < 5; ++v) {
+        lfl[v] = al * ll[v * nm];
+        lfr[v] = ar * lr[v * nm];
+      }
+      roe_vjp<false>(gamma, 0, qa, qb, nl, lfl, da, db);
+      roe_vjp<false>(gamma, 0, qa, qb, nr, lfr, ga, gb);
+      for (int v = 0; v < 5; ++v) {
+        da[v] += ga[v];
+        db[v] += gb[v];
+      }
+      if (MODE == 1) {
+        double lv[3][5], g[15], vq[5], vg[15];
+        for (int d = 0; d < 3; ++d)
+          for (int v = 0; v < 5; ++v) lv[d][v] = v >= 1 ? -0.5 * (ll[v * nm] * jl[d] + lr[v * nm] * jr[d]) : 0.0;
+        for (int c = 0; c < 15; ++c) g[c] = ql[(5 + c) * nm];
+        viscous_vjp(m.ph, qa, g, lv, vq, vg);
+        for (int v = 0; v < 5; ++v) da[v] += vq[v];
+        for (int c = 0; c < 15; ++c) ql[(5 + c) * nm] = vg[c];
+        for (int c = 0; c < 15; ++c) g[c] = qr[(5 + c) * nm];
+        viscous_vjp(m.ph, qb, g, lv, vq, vg);
+        for (int v = 0; v < 5; ++v) db[v] += vq[v];
+        for (int c = 0; c < 15; ++c) qr[(5 + c) * nm] = vg[c];
+      }
+      for (int v = 0; v < 5; ++v) {
+        ql[v * nm] = da[v];
+        qr[v * nm] = db[v];
+      }
+    }
+    __syncthreads();
+    // 6a. transpose of the xi_b interpolation pass: (Ma x Mb) -> (Ma x nb), into U
+    {
+      const int nL = upLb ? cnt * Ma * lb : 0, nR = upRb ? cnt * Ma * rb : 0;
+      for (int t = threadIdx.x; t < nL + nR; t += blockDim.x) {
+        const bool isL = t < nL;
+        const int tt = isL ? t : t - nL;
+        const int nb = isL ? lb : rb, per = Ma * nb;
+        const int f = tt / per, x = tt - f * per, m0 = x % Ma, b = x / Ma;
+        const double* Ib = isL ? IbL : IbR;
+        const double* src = (isL ? QL : QR) + f * NIN * nm;
+        double* dst = (isL ? UL + f * NMID * uL : UR + f * NMID * uR) + x;
+        double acc[NQ];
+        for (int c = 0; c < NQ; ++c) acc[c] = 0.0;
+        for (int m1 = 0; m1 < Mb; ++m1) {
+          const double w = __ldg(Ib + m1 * nb + b);
+          for (int c = 0; c < NQ; ++c) acc[c] += w * src[c * nm + m0 + Ma * m1];
+        }
+        for (int c = 0; c < NQ; ++c) dst[c * per] = acc[c];
+      }
+    }
+    __syncthreads();
+    // 6b. transpose of the xi_a interpolation pass onto each side's face grid; store
+    for (int t = threadIdx.x; t < cnt * (nfl + nfr); t += blockDim.x) {
+      const bool isL = t < cnt * nfl;
+      const int tt = isL ? t : t - cnt * nfl;
+      const int nf = isL ? nfl : nfr, na = isL ? la : ra, nb = isL ? lb : rb;
+      const int f = tt / nf, x = tt - f * nf, a = x % na, b = x / na;
+      const bool upa = isL ? upLa : upRa, upb = isL ? upLb : upRb;
+      const double* src = upb ? (isL ? UL + f * NMID * uL : UR + f * NMID * uR) : (isL ? QL : QR) + f * NIN * nm;
+      const int nsrc = upb ? Ma * nb : nm;
+      double out[NQ];
+      if (upa) {
+        const double* Ia = isL ? IaL : IaR;
+        for (int c = 0; c < NQ; ++c) out[c] = 0.0;
+        for (int m0 = 0; m0 < Ma; ++m0) {
+          const double w = __ldg(Ia + m0 * na + a);
+          for (int c = 0; c < NQ; ++c) out[c] += w * src[c * nsrc + m0 + Ma * b];
+        }
+      } else {
+        for (int c = 0; c < NQ; ++c) out[c] = src[c * nsrc + a + na * b];
+      }
+      const int* fr = P.faces + 3 * (B.first + f);
+      const int e = isL ? fr[0] : fr[1], dir = fr[2];
+      int n1, n2, n3;
+      orders_of(m, e, n1, n2, n3);
+      const int64_t fo = m.soff[e] + face_offset(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir);
+      if (MODE == 2) {
+        for (int v = 0; v < 5; ++v) sadj[5 * fo + v * nf + x] += out[v];
+      } else {
+        for (int v = 0; v < 5; ++v) sadj[5 * fo + v * nf + x] = out[v];
+        if (MODE == 1)
+          for (int c = 0; c < 15; ++c) gadj[15 * fo + c * nf + x] = out[5 + c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // The viscous flux of viscous() on any scalar type (Dual for Jacobian
 // columns in q or in the gradient g = [v][c]).
 template <typename S>
@@ -3898,6 +4204,46 @@ static cudaError_t launch_adj_volume(dg_mesh_impl* m, AdjParams A) {
   return cudaSuccess;
 }
 
+static MortarParams mortar_params(dg_mesh_impl* m, const double* q) {
+  MortarParams M;
+  M.m = view(m);
+  M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
+  M.n_batches = m->n_mbatches;
+  M.n_mfaces = m->n_mfaces;
+  M.faces = m->d_mfaces;
+  M.q = q;
+  M.surf = nullptr;
+  M.basis = m->basis64;
+  M.grad = m->d_grad;
+  return M;
+}
+
+#define DG_ADJ_GMORTAR(AFF, MODE, VIN, GADJ)                                                                 \
+  {                                                                                                        \
+    if ((err = allow_smem(adj_mortar_general_kernel<AFF, MODE>, smem))) return err;                       \
+    adj_mortar_general_kernel<AFF, MODE><<<m->n_mbatches, kVolThreads, smem, m->stream>>>(M, VIN, m->d_sadj, \
+                                                                                           GADJ);          \
+  }
+
+// BR1 q-hat reversed on every face: the listed faces, then the general mortars
+static cudaError_t adj_qhat_all(dg_mesh_impl* m, const double* q, double* qinf_adj, const double* scale) {
+  cudaError_t err;
+  if (m->n_faces) {
+    FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
+    const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
+    if (m->affine) adj_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, qinf_adj, scale);
+    else adj_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, qinf_adj, scale);
+    if ((err = cudaGetLastError())) return err;
+  }
+  if (m->n_mbatches && m->general_mortars) {
+    MortarParams M = mortar_params(m, q);
+    const size_t smem = sizeof(double) * mortar_adj_smem_max(m);
+    if (m->affine) DG_ADJ_GMORTAR(true, 2, m->d_lS, nullptr) else DG_ADJ_GMORTAR(false, 2, m->d_lS, nullptr)
+    if ((err = cudaGetLastError())) return err;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, double* out, const double* scale,
                          bool accumulate, double* qinf_adj) {
   cudaError_t err;
@@ -3908,7 +4254,9 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
   const int nvc = (int)m->vol_classes.size();
   Prof pr(m, DG_KERNEL_ADJOINT,
           (m->n_faces ? 1 : 0) + (m->n_mbatches ? 1 : 0) + nvc +
-              (ns ? 2 * nvc + (m->n_faces ? 1 : 0) + (accumulate ? 1 : 0) : 0));
+              (ns ? 2 * nvc + (m->n_faces ? 1 : 0) + (m->n_mbatches && m->general_mortars ? 1 : 0) +
+                        (accumulate ? 1 : 0)
+                  : 0));
   // 1. faces: warp-per-face list (conforming on curved / Navier-Stokes meshes, boundaries) and mortar batches
   if (m->n_faces) {
     FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
@@ -3929,16 +4277,17 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
     }
     if ((err = cudaGetLastError())) return err;
   }
-  if (m->n_mbatches) {
-    MortarParams M;
-    M.m = view(m);
-    M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
-    M.n_batches = m->n_mbatches;
-    M.n_mfaces = m->n_mfaces;
-    M.faces = m->d_mfaces;
-    M.q = q;
-    M.surf = nullptr;
-    M.basis = m->basis64;
+  if (m->n_mbatches && m->general_mortars) {
+    MortarParams M = mortar_params(m, q);
+    const size_t smem = sizeof(double) * mortar_adj_smem_max(m);
+    if (m->affine) {
+      if (ns) { DG_ADJ_GMORTAR(true, 1, v, m->d_gadj) } else { DG_ADJ_GMORTAR(true, 0, v, nullptr) }
+    } else {
+      if (ns) { DG_ADJ_GMORTAR(false, 1, v, m->d_gadj) } else { DG_ADJ_GMORTAR(false, 0, v, nullptr) }
+    }
+    if ((err = cudaGetLastError())) return err;
+  } else if (m->n_mbatches) {
+    MortarParams M = mortar_params(m, q);
     const size_t smem = sizeof(double) * mortar_adj_smem_max(m);
     if (m->axis) {
       if ((err = allow_smem(adj_mortar_kernel<true>, smem))) return err;
@@ -3992,13 +4341,7 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
     }
     if ((err = cudaGetLastError())) return err;
   }
-  if (m->n_faces) {
-    FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
-    const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
-    if (m->affine) adj_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, qinf_adj, scale);
-    else adj_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, qinf_adj, scale);
-    if ((err = cudaGetLastError())) return err;
-  }
+  if ((err = adj_qhat_all(m, q, qinf_adj, scale))) return err;
   A.sadj = m->d_sadj;
   for (auto& c : m->vol_classes) {
     A.ilist = c.d_list;
@@ -4013,11 +4356,20 @@ cudaError_t residual_vjp(dg_mesh_impl* m, const double* q, const double* v, doub
   return cudaGetLastError();
 }
 
+#undef DG_ADJ_GMORTAR
+
 size_t mortar_adj_smem_max(dg_mesh_impl* m) {
   size_t sm = 0;
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
   for (int b = 0; b < m->n_mbatches; ++b) {
     const int32_t* B = &m->h_mbatches[6 * b];
-    sm = std::max(sm, mortar_adj_smem_doubles(B[1], B[2], B[3], B[4], B[5]));
+    if (m->general_mortars) {
+      const MortarBatch mb{B[0], B[1], B[2], B[3], B[4], B[5]};
+      sm = std::max(sm, ns ? std::max(mortar_general_adj_smem<1>(mb), mortar_general_adj_smem<2>(mb))
+                           : mortar_general_adj_smem<0>(mb));
+    } else {
+      sm = std::max(sm, mortar_adj_smem_doubles(B[1], B[2], B[3], B[4], B[5]));
+    }
   }
   return sm;
 }
@@ -4242,11 +4594,7 @@ cudaError_t wall_force_vjp(dg_mesh_impl* m, const double* q, int tag, const doub
       }
       if ((err = cudaGetLastError())) return err;
     }
-    FaceParams F = dgk_face_params_for(m, q, m->d_sadj);
-    const int grid = (m->n_faces + kFaceWarps - 1) / kFaceWarps;
-    if (m->affine) adj_qhat_kernel<true><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, nullptr, nullptr);
-    else adj_qhat_kernel<false><<<grid, 32 * kFaceWarps, 0, m->stream>>>(F, m->d_lS, m->d_sadj, nullptr, nullptr);
-    if ((err = cudaGetLastError())) return err;
+    if ((err = adj_qhat_all(m, q, nullptr, nullptr))) return err;
   }
   A.sadj = m->d_sadj;
   for (auto& c : m->vol_classes) {

@@ -137,6 +137,41 @@ def test_averaged_drag_gradient_small(torch_cuda):
         assert float(dqinf[k]) == pytest.approx(fdk, rel=1e-6, abs=1e-10), (k, float(dqinf[k]), fdk)
 
 
+def test_drag_gradient_through_general_mortars(torch_cuda):
+    """the curved Navier-Stokes O-grid with mixed orders, so that the force and
+    the time integration both cross the general mortar kernels: the force VJP
+    against central differences of the oracle's force, d(averaged drag)/dq0
+    against central differences of the GPU forward run.  Flow around the body
+    puts face nodes near u.n = 0 (Roe's kink), so the averaged drag is only
+    piecewise smooth in q0 and the difference step is small: at steps 1, 1/2,
+    1/4, 1/8 the oracle's differences approach the adjoint value as about
+    h^1.5 (9.5e-10, 3.2e-10, 1.1e-10, 3.9e-11 away)"""
+    torch = torch_cuda
+    import oracle
+    from paper_2210_03523_gb300 import autograd as AG, dg
+    mi = _ogrid()
+    orders = I.random_orders(mi.n_elem, 1, 3, 2212)
+    orders[:, 2] = 1
+    mi = mi.with_orders(orders)
+    om = oracle.Mesh(mi)
+    qh = _state(mi, om)
+    m = dg.Mesh(mi)
+    q0 = torch.from_numpy(qh).cuda()
+    w = np.random.default_rng(22).standard_normal(qh.size) * 1e-3
+    lam = np.asarray((0.6, -0.8, 0.1))
+    gv = m.wall_force_vjp(q0, torch.from_numpy(lam).cuda()).cpu().numpy()
+    fd = _fd4(lambda s: lam @ om.wall_force(qh + s * w))
+    assert abs(gv @ w - fd) <= 1e-8 * np.abs(gv * w).sum(), (gv @ w, fd)
+    dt = torch.tensor([0.5 * om.max_dt(qh, 1.0)], dtype=torch.float64, device="cuda")
+    n = 10
+    J, dq, _ = AG.time_averaged_force(m, q0, dt, n, snapshots=2)
+    assert J == pytest.approx(_averaged_force(m, q0, dt, n, (1.0, 0.0, 0.0)), rel=1e-13)
+    wd = _direction(torch, q0, mi, 2213, 1e-3)
+    fd = _fd4(lambda s: _averaged_force(m, q0 + s * wd, dt, n, (1.0, 0.0, 0.0)), h=0.125)
+    assert abs(float(dq @ wd) - fd) <= 1e-8 * float((dq * wd).abs().sum()), (float(dq @ wd), fd)
+    assert m.get_error() == 0
+
+
 def test_cylinder_drag_gradient_400_steps(torch_cuda):
     """The cylinder case (40 x 24 curved elements, geometry order 3, P = (6,6,1),
     Re 100, Ma 0.2): the drag averaged over 400 RK3 steps and its gradient

@@ -4,7 +4,8 @@ the mortar grid with its own J a^dir, BR1 q-hat and viscous-flux averages on
 the mortar, L2 projection back to each side.  Residuals (face-coupled), RK3
 steps and the non-isolated tau sweep, on curved Euler, affine and curved
 Navier-Stokes boxes with mixed orders, and on an O-grid around a cylinder
-with walls and far field; the adjoint still refuses these meshes."""
+with walls and far field.  The adjoint through these mortars is checked with
+the other adjoint kernels against the oracle's finite-difference Jacobian."""
 import numpy as np
 import pytest
 
@@ -129,14 +130,3 @@ def test_tau_non_isolated_parity(torch_cuda, name):
     Jmax = max(om.metrics(e)[2].max() for e in range(om.n_elem))
     assert np.abs(tn - on).max() <= RTOL * max(np.abs(on).max(), s)
     assert np.abs(tt - ot).max() <= RTOL * max(np.abs(ot).max(), s * Jmax)
-
-
-def test_adjoint_refuses_general_mortars(torch_cuda):
-    torch = torch_cuda
-    from paper_2210_03523_gb300 import dg
-    mi, om, q = _setup("ns_affine_periodic")
-    m = dg.Mesh(mi)
-    qg = torch.from_numpy(q).cuda()
-    with pytest.raises(dg.DGError) as ei:
-        m.residual_vjp(qg, qg.clone())
-    assert ei.value.status == 4
