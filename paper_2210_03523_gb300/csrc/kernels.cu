@@ -48,6 +48,7 @@ namespace {
 
 constexpr int kFaceWarps = 4;          // faces per CTA in the face kernels
 constexpr int kVolThreads = 256;
+constexpr int kTauChunk = 16;   // at most this many sweep entries share the two barriers of a tau chunk
 constexpr int kTauThreads = 128;
 
 // ------------------------------------------------------------------ helpers
@@ -1911,6 +1912,12 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
     WorkItem w;
     if (!take_item(P.m, P.items, u.x, P.n_items_all, P.elist, 0, w)) continue;
     if (bad_tile(P.m, w, P.S) || bad_group(P, w, u.y)) continue;
+#ifdef DG_BOUNDS_CHECK
+    if (w.count > kVolThreads) {   // one norm slot per element and chunk entry
+      if (threadIdx.x == 0) flag_index(P.m);
+      continue;
+    }
+#endif
     const int32_t* els = P.elist + w.first;
     const int cnt = w.count;
     const int P1 = w.n1, P2 = w.n2, P3 = w.n3, n1 = P1 + 1, n2 = P2 + 1, n3 = P3 + 1, nP = n1 * n2 * n3;
@@ -1964,31 +1971,53 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
       __syncthreads();
     }
     if (!NS) {
-      // Euler, two barriers per entry: (1) store the previous entry's norms,
-      // clear this entry's slots, restrict in xi1 and take the fluxes at once;
-      // (2) derivative, tau and both norms
+      // Euler: the group's entries in chunks of at most S coarse nodes (each
+      // entry alone fits: cnt nN <= cnt nP <= S), two barriers per chunk:
+      // (1) store the previous chunk's norms, clear this chunk's slots,
+      // restrict in xi1 and take the fluxes at once; (2) derivative, tau and
+      // both norms.  Entry j of a chunk owns cnt nN_j items from its base
+      // (none when N1 > P1) and the norm slots j cnt + el.
       const T gm1 = P.gamma - (T)1;
       const T* w2 = P.basis + c_boff.W[N2];
       const T* w3 = P.basis + c_boff.W[N3];
-      int prev_s = -1, buf = 0;
-      for (int ge = 0; ge < g.w; ++ge) {
-        const int2 ent = P.gentries[g.z + ge];   // sweep index, N1
-        const int s = ent.x, N1 = ent.y;
-        if (N1 > P1) continue;
-        const int c1 = N1 + 1, nN = c1 * c2 * c3;
-        const T* I1 = P.basis + c_boff.I[P1][N1];
-        const int pin = n1 * c2 * c3;
-        for (int el = threadIdx.x; el < cnt; el += blockDim.x) {
-          if (prev_s >= 0) {
-            const int64_t idx = (int64_t)els[el] * P.n_sweep + prev_s;
-            map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][el]));
-            map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][el]));
-          }
-          na2[buf][el] = 0;
-          nb2[buf][el] = 0;
+      const int pin = n1 * c2 * c3, c23 = c2 * c3;
+      const int2* gent = P.gentries + g.z;    // (sweep index, N1) per entry
+      int prev_first = 0, prev_k = 0, buf = 0;
+      for (int first = 0; first < g.w;) {
+        int k = 0, total = 0;                 // the chunk [first, first + k), the same in every thread
+        while (first + k < g.w && k < kTauChunk) {
+          const int M1 = gent[first + k].y;
+          const int sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
+          if (k > 0 && (total + sz > S || (k + 1) * cnt > kVolThreads)) break;
+          total += sz;
+          ++k;
         }
-        for (int t = threadIdx.x; t < cnt * nN; t += blockDim.x) {
-          const int el = fdiv(t, nN), x = t - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
+        const int nsl = (prev_k > k ? prev_k : k) * cnt;
+        for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) {
+          const int j = fdiv(sl, cnt), el = sl - j * cnt;
+          if (j < prev_k) {
+            const int2 pe = gent[prev_first + j];
+            if (pe.y <= P1) {
+              const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
+              map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
+              map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
+            }
+          }
+          if (j < k) {
+            na2[buf][sl] = 0;
+            nb2[buf][sl] = 0;
+          }
+        }
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+          int base = 0, M1 = gent[first].y, sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
+          for (int j = 1; t >= base + sz; ++j) {
+            base += sz;
+            M1 = gent[first + j].y;
+            sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
+          }
+          const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
+          const int el = fdiv(tt, nN), x = tt - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
+          const T* I1 = P.basis + c_boff.I[P1][M1];
           const T* src = A2 + el * 10 * pin + n1 * jk;
           T acc[10];
           for (int c = 0; c < 10; ++c) acc[c] = 0;
@@ -1996,39 +2025,52 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
             const T wi = I1[i * n1 + mm];
             for (int c = 0; c < 10; ++c) acc[c] += wi * src[c * pin + mm];
           }
-          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
-          tau_flux<T, AFFINE, AXIS>(gm1, met, nN, x, acc, Ft + el * 15 * nN + x);
-          for (int v = 0; v < 5; ++v) A1[el * 10 * nN + (5 + v) * nN + x] = acc[5 + v];   // I R^P
+          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
+          tau_flux<T, AFFINE, AXIS>(gm1, met, nN, x, acc, Ft + 15 * base + el * 15 * nN + x);
+          T* ir = A1 + 5 * base + el * 5 * nN + x;
+          for (int v = 0; v < 5; ++v) ir[v * nN] = acc[5 + v];   // I R^P
         }
         __syncthreads();
-        const T* w1 = P.basis + c_boff.W[N1];
-        for (int t = threadIdx.x; t < cnt * nN; t += blockDim.x) {
-          const int el = fdiv(t, nN), p = t - el * nN;
-          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+          int base = 0, j = 0, M1 = gent[first].y, sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
+          while (t >= base + sz) {
+            base += sz;
+            M1 = gent[first + ++j].y;
+            sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
+          }
+          const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
+          const int el = fdiv(tt, nN), p = tt - el * nN;
+          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
           T acc[5];
-          div5(P.basis, Ft + el * 15 * nN, c1, c2, c3, p, acc);
+          div5(P.basis, Ft + 15 * base + el * 15 * nN, c1, c2, c3, p, acc);
           const T J = met_at(met, AFFINE, nN, p, 9);
           const T iJ = -(T)1 / J;
-          const int pj = fdiv(p, c1), k = fdiv(pj, c2), i = p - pj * c1, j = pj - k * c2;
-          const T Jw = J * w1[i] * w2[j] * w3[k];
+          const int pj = fdiv(p, c1), pk = fdiv(pj, c2), pi = p - pj * c1, pjj = pj - pk * c2;
+          const T Jw = J * P.basis[c_boff.W[M1] + pi] * w2[pjj] * w3[pk];
+          const T* ir = A1 + 5 * base + el * 5 * nN + p;
           T a = 0, b = 0;
           for (int v = 0; v < 5; ++v) {
             const T r = mul_rn(acc[v], iJ);   // rounded as R^P was, so that tau at N = P is exactly 0
-            const T tt = A1[el * 10 * nN + (5 + v) * nN + p] - r;
-            a = tmax(a, (T)fabs(tt));
-            b = tmax(b, (T)fabs(Jw * tt));
+            const T d = ir[v * nN] - r;
+            a = tmax(a, (T)fabs(d));
+            b = tmax(b, (T)fabs(Jw * d));
           }
-          smax_bits(na2[buf] + el, a);
-          smax_bits(nb2[buf] + el, b);
+          smax_bits(na2[buf] + j * cnt + el, a);
+          smax_bits(nb2[buf] + j * cnt + el, b);
         }
         __syncthreads();
-        prev_s = s;
+        prev_first = first;
+        prev_k = k;
         buf ^= 1;
+        first += k;
       }
-      for (int el = threadIdx.x; el < cnt && prev_s >= 0; el += blockDim.x) {
-        const int64_t idx = (int64_t)els[el] * P.n_sweep + prev_s;
-        map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][el]));
-        map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][el]));
+      for (int sl = threadIdx.x; sl < prev_k * cnt; sl += blockDim.x) {
+        const int j = fdiv(sl, cnt), el = sl - j * cnt;
+        const int2 pe = gent[prev_first + j];
+        if (pe.y > P1) continue;
+        const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
+        map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
+        map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
       }
       __syncthreads();
       continue;
