@@ -1752,16 +1752,86 @@ __device__ __forceinline__ void tau_flux(T gm1, const T* met, int n, int p, cons
   }
 }
 
-// Isolated residual of a tile of cnt same-order elements, state X[el][5][n]
+// The per-node pieces of the isolated residual, shared by R^P and every
+// coarse residual of the sweep so that R^N at N = P reproduces R^P bit for
+// bit.  Element tiles are [field][n]; met is the element's metric block.
+// BR1 gradient, component c: the contravariant fluxes J a^i_c q of the state.
+template <typename T, bool AFFINE>
+__device__ __forceinline__ void tau_grad_flux(const T* met, int n, int p, int c, const T* X, T* F) {
+  for (int i = 0; i < 3; ++i) {
+    const T ja = met_at(met, AFFINE, n, p, 3 * i + c);
+    for (int v = 0; v < 5; ++v) F[(i * 5 + v) * n + p] = ja * X[v * n + p];
+  }
+}
+
+// ... their GL divergence over J: component c of the gradient, G[v*3+c]
+template <typename T, bool AFFINE>
+__device__ __forceinline__ void tau_grad_store(const T* basis, const T* met, int n1, int n2, int n3, int p, int c,
+                                               const T* F, T* G) {
+  const int n = n1 * n2 * n3;
+  T acc[5];
+  div5(basis, F, n1, n2, n3, p, acc);
+  const T iJ = (T)1 / met_at(met, AFFINE, n, p, 9);
+  for (int v = 0; v < 5; ++v) G[(v * 3 + c) * n + p] = acc[v] * iJ;
+}
+
+// Navier-Stokes contravariant fluxes J a^i . (f - f_v) at node p
+template <typename T, bool AFFINE>
+__device__ __forceinline__ void tau_ns_flux(const TauParams<T>& P, T gm1, const T* met, int n, int p, const T q[5],
+                                            const T* G, T* F) {
+  T f[3][5];
+  euler_fluxes(gm1, q, f);
+  T g[15], fv[3][5];
+  for (int c = 0; c < 15; ++c) g[c] = G[c * n + p];
+  viscous_t(P, q, g, fv);
+  for (int d = 0; d < 3; ++d)
+    for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
+  for (int i = 0; i < 3; ++i) {
+    const T ja0 = met_at(met, AFFINE, n, p, 3 * i), ja1 = met_at(met, AFFINE, n, p, 3 * i + 1),
+            ja2 = met_at(met, AFFINE, n, p, 3 * i + 2);
+    for (int v = 0; v < 5; ++v) F[(i * 5 + v) * n + p] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
+  }
+}
+
+// R = -(1/J) div F at node p, rounded as when stored
+template <typename T, bool AFFINE>
+__device__ __forceinline__ void tau_node_residual(const T* basis, const T* met, int n1, int n2, int n3, int p,
+                                                  const T* F, T r[5], T& J) {
+  const int n = n1 * n2 * n3;
+  T acc[5];
+  div5(basis, F, n1, n2, n3, p, acc);
+  J = met_at(met, AFFINE, n, p, 9);
+  const T iJ = -(T)1 / J;
+  for (int v = 0; v < 5; ++v) r[v] = mul_rn(acc[v], iJ);
+}
+
+// Both tau norms at node p of the coarse grid (c1, c2, c3): tau~ = I R^P - R^N
+// (IR: I R^P, [5][n]), max |tau~| and max |J w tau~| into a, b
+template <typename T, bool AFFINE>
+__device__ __forceinline__ void tau_node_norms(const T* basis, const T* met, int c1, int c2, int c3, int p,
+                                               const T* F, const T* IR, const T* w1, const T* w2, const T* w3,
+                                               T& a, T& b) {
+  const int n = c1 * c2 * c3;
+  T r[5], J;
+  tau_node_residual<T, AFFINE>(basis, met, c1, c2, c3, p, F, r, J);
+  const int pj = fdiv(p, c1), k = fdiv(pj, c2), i = p - pj * c1, j = pj - k * c2;
+  const T Jw = J * w1[i] * w2[j] * w3[k];
+  a = 0;
+  b = 0;
+  for (int v = 0; v < 5; ++v) {
+    const T d = IR[v * n + p] - r[v];   // tau~ = I R^P - R^N(I q^P)
+    a = tmax(a, (T)fabs(d));
+    b = tmax(b, (T)fabs(Jw * d));
+  }
+}
+
+// Isolated residual R^P of a tile of cnt same-order elements, state X[el][5][n]
 // (element stride xs) at orders (n1,n2,n3): R = -(1/J) sum_i D^(i) Ft^i, with
-// the element-local BR1 gradient and viscous flux for Navier-Stokes.  Either
-// writes R to Rout (element e's R at Rout + 5*off_e, [5][n]), or folds it into
-// the tau norms: t = IR - R with IR = X + 5*n (the restricted I R^P), per
-// element max |t| and max |J w t| into the shared slots na[el], nb[el].
+// the element-local BR1 gradient and viscous flux for Navier-Stokes; element
+// e's R to Rout + 5*off_e, [5][n].
 template <typename T, bool AFFINE, bool NS, bool AXIS>
 __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int cnt, int P1, int P2, int N1, int N2,
-                                  int N3, const T* X, int xs, T* Ft, T* Gs, T* Rout,
-                                  typename Bits<T>::type* na, typename Bits<T>::type* nb) {
+                                  int N3, const T* X, int xs, T* Ft, T* Gs, T* Rout) {
   const int n1 = N1 + 1, n2 = N2 + 1, n3 = N3 + 1, n = n1 * n2 * n3, pts = cnt * n;
   const T gm1 = P.gamma - (T)1;
   const MeshView& m = P.m;
@@ -1770,19 +1840,13 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
       for (int t = threadIdx.x; t < pts; t += blockDim.x) {
         const int el = fdiv(t, n), p = t - el * n;
         const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
-        for (int i = 0; i < 3; ++i) {
-          T ja = met_at(met, AFFINE, n, p, 3 * i + c);
-          for (int v = 0; v < 5; ++v) Ft[el * 15 * n + (i * 5 + v) * n + p] = ja * X[el * xs + v * n + p];
-        }
+        tau_grad_flux<T, AFFINE>(met, n, p, c, X + el * xs, Ft + el * 15 * n);
       }
       __syncthreads();
       for (int t = threadIdx.x; t < pts; t += blockDim.x) {
         const int el = fdiv(t, n), p = t - el * n;
         const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
-        T acc[5];
-        div5(P.basis, Ft + el * 15 * n, n1, n2, n3, p, acc);
-        T iJ = (T)1 / met_at(met, AFFINE, n, p, 9);
-        for (int v = 0; v < 5; ++v) Gs[el * 15 * n + (v * 3 + c) * n + p] = acc[v] * iJ;
+        tau_grad_store<T, AFFINE>(P.basis, met, n1, n2, n3, p, c, Ft + el * 15 * n, Gs + el * 15 * n);
       }
       __syncthreads();
     }
@@ -1792,61 +1856,52 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
     const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
     T q[5];
     for (int v = 0; v < 5; ++v) q[v] = X[el * xs + v * n + p];
-    if (!NS) {
-      tau_flux<T, AFFINE, AXIS>(gm1, met, n, p, q, Ft + el * 15 * n + p);
-      continue;
-    }
-    T f[3][5];
-    euler_fluxes(gm1, q, f);
-    if (NS) {
-      T g[15], fv[3][5];
-      for (int c = 0; c < 15; ++c) g[c] = Gs[el * 15 * n + c * n + p];
-      viscous_t(P, q, g, fv);
-      for (int d = 0; d < 3; ++d)
-        for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
-    }
-    for (int i = 0; i < 3; ++i) {
-      T ja0 = met_at(met, AFFINE, n, p, 3 * i), ja1 = met_at(met, AFFINE, n, p, 3 * i + 1),
-        ja2 = met_at(met, AFFINE, n, p, 3 * i + 2);
-      for (int v = 0; v < 5; ++v)
-        Ft[el * 15 * n + (i * 5 + v) * n + p] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
-    }
-  }
-  if (na && threadIdx.x < cnt) {
-    na[threadIdx.x] = 0;
-    nb[threadIdx.x] = 0;
+    if (NS) tau_ns_flux<T, AFFINE>(P, gm1, met, n, p, q, Gs + el * 15 * n, Ft + el * 15 * n);
+    else tau_flux<T, AFFINE, AXIS>(gm1, met, n, p, q, Ft + el * 15 * n + p);
   }
   __syncthreads();
-  const T* w1 = P.basis + c_boff.W[N1];
-  const T* w2 = P.basis + c_boff.W[N2];
-  const T* w3 = P.basis + c_boff.W[N3];
   for (int t = threadIdx.x; t < pts; t += blockDim.x) {
     const int el = fdiv(t, n), p = t - el * n;
     const int e = els[el];
     const T* met = tile_met<T, AFFINE>(P, e, P1, P2, N1, N2, N3);
-    T acc[5];
-    div5(P.basis, Ft + el * 15 * n, n1, n2, n3, p, acc);
-    const T J = met_at(met, AFFINE, n, p, 9);
-    const T iJ = -(T)1 / J;
-    if (na) {
-      // R rounded exactly as when stored, so that tau at N = P is exactly 0
-      const int pj = fdiv(p, n1), k = fdiv(pj, n2), i = p - pj * n1, j = pj - k * n2;
-      const T Jw = J * w1[i] * w2[j] * w3[k];
-      T a = 0, b = 0;
-      for (int v = 0; v < 5; ++v) {
-        const T r = mul_rn(acc[v], iJ);
-        const T tt = X[el * xs + (5 + v) * n + p] - r;   // tau~ = I R^P - R^N(I q^P)
-        a = tmax(a, (T)fabs(tt));
-        b = tmax(b, (T)fabs(Jw * tt));
-      }
-      smax_bits(na + el, a);
-      smax_bits(nb + el, b);
-    } else {
-      const int64_t o = m.off[e];
-      for (int v = 0; v < 5; ++v) Rout[5 * o + v * n + p] = mul_rn(acc[v], iJ);
-    }
+    T r[5], J;
+    tau_node_residual<T, AFFINE>(P.basis, met, n1, n2, n3, p, Ft + el * 15 * n, r, J);
+    const int64_t o = m.off[e];
+    for (int v = 0; v < 5; ++v) Rout[5 * o + v * n + p] = r[v];
   }
   __syncthreads();
+}
+
+// The chunk of sweep entries [first, first + k) of a group that starts at
+// entry first: entries while their items (cnt nN each, none when N1 > P1)
+// fit the tile capacity S and their norm slots (cnt each) fit kVolThreads;
+// one entry at least (cnt nN <= cnt nP <= S).  Returns k; total = the items.
+__device__ __forceinline__ int tau_chunk(const int2* gent, int first, int n_ent, int P1, int cnt, int c23, int S,
+                                         int& total) {
+  int k = 0;
+  total = 0;
+  while (first + k < n_ent && k < kTauChunk) {
+    const int M1 = gent[first + k].y;
+    const int sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
+    if (k > 0 && (total + sz > S || (k + 1) * cnt > kVolThreads)) break;
+    total += sz;
+    ++k;
+  }
+  return k;
+}
+
+// Item t of a chunk: its entry j, the entry's first item base and its N1.
+__device__ __forceinline__ void tau_chunk_item(const int2* gent, int first, int t, int P1, int cnt, int c23, int& base,
+                                               int& j, int& M1) {
+  base = 0;
+  j = 0;
+  M1 = gent[first].y;
+  int sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
+  while (t >= base + sz) {
+    base += sz;
+    M1 = gent[first + ++j].y;
+    sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
+  }
 }
 
 // Prologue of the isolated sweep, one tile per CTA iteration: the isolated
@@ -1883,8 +1938,7 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
       for (int v = 0; v < 5; ++v) A1[el * 10 * nP + v * nP + p] = (T)P.q[5 * o + v * nP + p];
     }
     __syncthreads();
-    tau_tile_residual<T, AFFINE, NS, AXIS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, Ft, Gs, P.rp_scratch, nullptr,
-                                     nullptr);
+    tau_tile_residual<T, AFFINE, NS, AXIS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, Ft, Gs, P.rp_scratch);
   }
 }
 
@@ -1898,8 +1952,6 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   T* sm = reinterpret_cast<T*>(smem_raw);
   typedef typename Bits<T>::type B;
   __shared__ B na2[2][kVolThreads], nb2[2][kVolThreads];   // per-element norms, two entries in flight
-  B* na = na2[0];
-  B* nb = nb2[0];
   const int S = P.S;     // tile capacity in nodes (max count * n_P of the class)
   T* A3 = sm;            // [el][10][pts3]  q^P, R^P restricted in xi3
   T* A2 = A3 + 10 * S;   // [el][10][pts2]  ... in xi2, xi3
@@ -1970,140 +2022,121 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
       }
       __syncthreads();
     }
-    if (!NS) {
-      // Euler: the group's entries in chunks of at most S coarse nodes (each
-      // entry alone fits: cnt nN <= cnt nP <= S), two barriers per chunk:
-      // (1) store the previous chunk's norms, clear this chunk's slots,
-      // restrict in xi1 and take the fluxes at once; (2) derivative, tau and
-      // both norms.  Entry j of a chunk owns cnt nN_j items from its base
-      // (none when N1 > P1) and the norm slots j cnt + el.
-      const T gm1 = P.gamma - (T)1;
-      const T* w2 = P.basis + c_boff.W[N2];
-      const T* w3 = P.basis + c_boff.W[N3];
-      const int pin = n1 * c2 * c3, c23 = c2 * c3;
-      const int2* gent = P.gentries + g.z;    // (sweep index, N1) per entry
-      int prev_first = 0, prev_k = 0, buf = 0;
-      for (int first = 0; first < g.w;) {
-        int k = 0, total = 0;                 // the chunk [first, first + k), the same in every thread
-        while (first + k < g.w && k < kTauChunk) {
-          const int M1 = gent[first + k].y;
-          const int sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
-          if (k > 0 && (total + sz > S || (k + 1) * cnt > kVolThreads)) break;
-          total += sz;
-          ++k;
-        }
-        const int nsl = (prev_k > k ? prev_k : k) * cnt;
-        for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) {
-          const int j = fdiv(sl, cnt), el = sl - j * cnt;
-          if (j < prev_k) {
-            const int2 pe = gent[prev_first + j];
-            if (pe.y <= P1) {
-              const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
-              map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
-              map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
-            }
-          }
-          if (j < k) {
-            na2[buf][sl] = 0;
-            nb2[buf][sl] = 0;
-          }
-        }
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-          int base = 0, M1 = gent[first].y, sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
-          for (int j = 1; t >= base + sz; ++j) {
-            base += sz;
-            M1 = gent[first + j].y;
-            sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
-          }
-          const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
-          const int el = fdiv(tt, nN), x = tt - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
-          const T* I1 = P.basis + c_boff.I[P1][M1];
-          const T* src = A2 + el * 10 * pin + n1 * jk;
-          T acc[10];
-          for (int c = 0; c < 10; ++c) acc[c] = 0;
-          for (int mm = 0; mm < n1; ++mm) {
-            const T wi = I1[i * n1 + mm];
-            for (int c = 0; c < 10; ++c) acc[c] += wi * src[c * pin + mm];
-          }
-          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
-          tau_flux<T, AFFINE, AXIS>(gm1, met, nN, x, acc, Ft + 15 * base + el * 15 * nN + x);
-          T* ir = A1 + 5 * base + el * 5 * nN + x;
-          for (int v = 0; v < 5; ++v) ir[v * nN] = acc[5 + v];   // I R^P
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-          int base = 0, j = 0, M1 = gent[first].y, sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
-          while (t >= base + sz) {
-            base += sz;
-            M1 = gent[first + ++j].y;
-            sz = M1 > P1 ? 0 : cnt * (M1 + 1) * c23;
-          }
-          const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
-          const int el = fdiv(tt, nN), p = tt - el * nN;
-          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
-          T acc[5];
-          div5(P.basis, Ft + 15 * base + el * 15 * nN, c1, c2, c3, p, acc);
-          const T J = met_at(met, AFFINE, nN, p, 9);
-          const T iJ = -(T)1 / J;
-          const int pj = fdiv(p, c1), pk = fdiv(pj, c2), pi = p - pj * c1, pjj = pj - pk * c2;
-          const T Jw = J * P.basis[c_boff.W[M1] + pi] * w2[pjj] * w3[pk];
-          const T* ir = A1 + 5 * base + el * 5 * nN + p;
-          T a = 0, b = 0;
-          for (int v = 0; v < 5; ++v) {
-            const T r = mul_rn(acc[v], iJ);   // rounded as R^P was, so that tau at N = P is exactly 0
-            const T d = ir[v * nN] - r;
-            a = tmax(a, (T)fabs(d));
-            b = tmax(b, (T)fabs(Jw * d));
-          }
-          smax_bits(na2[buf] + j * cnt + el, a);
-          smax_bits(nb2[buf] + j * cnt + el, b);
-        }
-        __syncthreads();
-        prev_first = first;
-        prev_k = k;
-        buf ^= 1;
-        first += k;
-      }
-      for (int sl = threadIdx.x; sl < prev_k * cnt; sl += blockDim.x) {
+    // The group's entries in chunks of at most S coarse nodes (tau_chunk),
+    // one pass per step for the whole chunk: (1) store the previous chunk's
+    // norms, clear this chunk's slots, restrict in xi1 (Euler: and take the
+    // fluxes); Navier-Stokes: (2-7) the BR1 gradient, (8) the fluxes; (last)
+    // derivative, tau and both norms.  Entry j of a chunk owns cnt nN_j items
+    // from its base and the norm slots j cnt + el; its elements' restricted
+    // fields are [el][XF][nN] from XF base in A1 (Euler: I R^P; Navier-Stokes:
+    // I q^P, then I R^P).
+    constexpr int XF = NS ? 10 : 5;
+    const T gm1 = P.gamma - (T)1;
+    const T* w2 = P.basis + c_boff.W[N2];
+    const T* w3 = P.basis + c_boff.W[N3];
+    const int pin = n1 * c2 * c3, c23 = c2 * c3;
+    const int2* gent = P.gentries + g.z;      // (sweep index, N1) per entry
+    int prev_first = 0, prev_k = 0, buf = 0;
+    for (int first = 0; first < g.w;) {
+      int total;
+      const int k = tau_chunk(gent, first, g.w, P1, cnt, c23, S, total);   // the same in every thread
+      const int nsl = (prev_k > k ? prev_k : k) * cnt;
+      for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) {
         const int j = fdiv(sl, cnt), el = sl - j * cnt;
-        const int2 pe = gent[prev_first + j];
-        if (pe.y > P1) continue;
-        const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
-        map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
-        map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
+        if (j < prev_k) {
+          const int2 pe = gent[prev_first + j];
+          if (pe.y <= P1) {
+            const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
+            map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
+            map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
+          }
+        }
+        if (j < k) {
+          na2[buf][sl] = 0;
+          nb2[buf][sl] = 0;
+        }
+      }
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int base, j, M1;
+        tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
+        const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
+        const int el = fdiv(tt, nN), x = tt - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
+        const T* I1 = P.basis + c_boff.I[P1][M1];
+        const T* src = A2 + el * 10 * pin + n1 * jk;
+        T acc[10];
+        for (int c = 0; c < 10; ++c) acc[c] = 0;
+        for (int mm = 0; mm < n1; ++mm) {
+          const T wi = I1[i * n1 + mm];
+          for (int c = 0; c < 10; ++c) acc[c] += wi * src[c * pin + mm];
+        }
+        T* X = A1 + XF * (base + el * nN) + x;
+        if (NS) {
+          for (int c = 0; c < 10; ++c) X[c * nN] = acc[c];
+        } else {
+          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
+          tau_flux<T, AFFINE, AXIS>(gm1, met, nN, x, acc, Ft + 15 * (base + el * nN) + x);
+          for (int v = 0; v < 5; ++v) X[v * nN] = acc[5 + v];   // I R^P
+        }
       }
       __syncthreads();
-      continue;
-    }
-    for (int ge = 0; ge < g.w; ++ge) {
-      const int2 ent = P.gentries[g.z + ge];   // sweep index, N1
-      const int s = ent.x, N1 = ent.y;
-      if (N1 > P1) continue;
-      const int c1 = N1 + 1, nN = c1 * c2 * c3;
-      {  // xi1
-        const T* I1 = P.basis + c_boff.I[P1][N1];
-        const int pin = n1 * c2 * c3;
-        for (int t = threadIdx.x; t < cnt * nN; t += blockDim.x) {
-          const int el = fdiv(t, nN), x = t - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
-          const T* src = A2 + el * 10 * pin + n1 * jk;
-          T acc[10];
-          for (int c = 0; c < 10; ++c) acc[c] = 0;
-          for (int mm = 0; mm < n1; ++mm) {
-            const T wi = I1[i * n1 + mm];
-            for (int c = 0; c < 10; ++c) acc[c] += wi * src[c * pin + mm];
+      if (NS) {
+        for (int c = 0; c < 3; ++c) {
+          for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int base, j, M1;
+            tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
+            const int nN = (M1 + 1) * c23, tt = t - base, el = fdiv(tt, nN), p = tt - el * nN;
+            const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
+            tau_grad_flux<T, AFFINE>(met, nN, p, c, A1 + XF * (base + el * nN), Ft + 15 * (base + el * nN));
           }
-          for (int c = 0; c < 10; ++c) A1[el * 10 * nN + c * nN + x] = acc[c];
+          __syncthreads();
+          for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int base, j, M1;
+            tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
+            const int nN = (M1 + 1) * c23, tt = t - base, el = fdiv(tt, nN), p = tt - el * nN;
+            const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
+            tau_grad_store<T, AFFINE>(P.basis, met, M1 + 1, c2, c3, p, c, Ft + 15 * (base + el * nN),
+                                      Gs + 15 * (base + el * nN));
+          }
+          __syncthreads();
+        }
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+          int base, j, M1;
+          tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
+          const int nN = (M1 + 1) * c23, tt = t - base, el = fdiv(tt, nN), p = tt - el * nN;
+          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
+          const T* X = A1 + XF * (base + el * nN);
+          T q[5];
+          for (int v = 0; v < 5; ++v) q[v] = X[v * nN + p];
+          tau_ns_flux<T, AFFINE>(P, gm1, met, nN, p, q, Gs + 15 * (base + el * nN), Ft + 15 * (base + el * nN));
         }
         __syncthreads();
       }
-      tau_tile_residual<T, AFFINE, NS, AXIS>(P, els, cnt, P1, P2, N1, N2, N3, A1, 10 * nN, Ft, Gs, nullptr, na, nb);
-      for (int el = threadIdx.x; el < cnt; el += blockDim.x) {
-        const int64_t idx = (int64_t)els[el] * P.n_sweep + s;
-        map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na[el]));
-        map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb[el]));
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int base, j, M1;
+        tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
+        const int c1 = M1 + 1, nN = c1 * c23, tt = t - base, el = fdiv(tt, nN), p = tt - el * nN;
+        const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
+        T a, b;
+        tau_node_norms<T, AFFINE>(P.basis, met, c1, c2, c3, p, Ft + 15 * (base + el * nN),
+                                  A1 + XF * (base + el * nN) + (XF - 5) * nN, P.basis + c_boff.W[M1], w2, w3, a, b);
+        smax_bits(na2[buf] + j * cnt + el, a);
+        smax_bits(nb2[buf] + j * cnt + el, b);
       }
       __syncthreads();
+      prev_first = first;
+      prev_k = k;
+      buf ^= 1;
+      first += k;
     }
+    for (int sl = threadIdx.x; sl < prev_k * cnt; sl += blockDim.x) {
+      const int j = fdiv(sl, cnt), el = sl - j * cnt;
+      const int2 pe = gent[prev_first + j];
+      if (pe.y > P1) continue;
+      const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
+      map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
+      map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
+    }
+    __syncthreads();
     }   // groups of the unit
   }
 }
