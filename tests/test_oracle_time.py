@@ -90,6 +90,49 @@ def test_max_dt_closed_form(orc):
     assert abs(m.max_dt(q, 0.5) - 0.5 / s) < 1e-14 * (0.5 / s)
 
 
+def _ns_rest(mu, Pr, p0=3.0, rho=1.7):
+    return I.Physics(1, 1.4, mu, Pr, 1.0, (rho, 0.0, 0.0, 0.0, p0 / 0.4))
+
+
+def _dt(orc, mi, cfl=0.5):
+    m = orc.Mesh(mi)
+    return m.max_dt(I.uniform_state(m.orders, mi.phys.qinf), cfl)
+
+
+def test_max_dt_viscous_term(orc):
+    """The viscous term of the CFL step (Navier-Stokes), pinned without its
+    formula: a fluid at rest (no advective speed but sound) with a large mu
+    is in the viscous regime, where the step must scale as h^2 (mesh scaled
+    by 2: dt x 4) and as 1/mu, take max(1, gamma/Pr) (Pr = 2.8 against 0.35:
+    ratio 4), and be invariant under a rotation of a sheared mesh (a
+    transposed metric index is not); at small mu the sound speed decides
+    (dt x 2 under the same scaling) and mu drops out."""
+    orders = (3, 2, 4)
+    A = np.array([[1.0, 0.3, 0.0], [0.0, 1.0, 0.2], [0.1, 0.0, 1.0]])
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    R = R @ np.array([[1.0, 0.0, 0.0], [0.0, math.cos(0.4), -math.sin(0.4)], [0.0, math.sin(0.4), math.cos(0.4)]])
+
+    def mesh(mu, Pr=2.8, M=A):
+        return I.box_mesh(2, orders=orders, phys=_ns_rest(mu, Pr), mapping=I.affine_map(M))
+    big, small = 50.0, 1e-6
+    dv = _dt(orc, mesh(big))
+    assert _dt(orc, mesh(big, M=2 * A)) == pytest.approx(4 * dv, rel=1e-13)
+    assert _dt(orc, mesh(2 * big)) == pytest.approx(dv / 2, rel=1e-13)
+    assert _dt(orc, mesh(big, Pr=0.35)) == pytest.approx(dv / 4, rel=1e-13)
+    assert _dt(orc, mesh(big, M=R @ A)) == pytest.approx(dv, rel=1e-12)
+    da = _dt(orc, mesh(small))
+    assert da < dv / 1e-3   # the sound speed now decides ...
+    assert _dt(orc, mesh(small, M=2 * A)) == pytest.approx(2 * da, rel=1e-13)
+    assert _dt(orc, mesh(2 * small)) == pytest.approx(da, rel=1e-13)
+    assert _dt(orc, mesh(small, M=R @ A)) == pytest.approx(da, rel=1e-12)
+    # ... and the axis-aligned closed form of the viscous term, h = 1 per element:
+    # |J a^i|^2 / (4 J^2) = 1 / h^2, nu = mu / rho
+    dbox = _dt(orc, I.box_mesh(2, orders=orders, phys=_ns_rest(big, 2.8)))
+    s_v = sum((N + 1) ** 4 for N in orders) * big / 1.7
+    assert dbox == pytest.approx(0.5 / s_v, rel=1e-14)
+
+
 def _l2_error(m, q, ph, t, width, center):
     xyz = m.coords()
     u = np.asarray(ph.qinf[1:4])
