@@ -133,6 +133,58 @@ def test_max_dt_viscous_term(orc):
     assert dbox == pytest.approx(0.5 / s_v, rel=1e-14)
 
 
+def test_pulse_centroid_moves_with_the_flow(orc):
+    """No dispersion of the pulse's position (Sec. 3.1, the advected pulse):
+    the discrete first moment M1 = sum w J x (rho - 1) of the density
+    perturbation obeys dM1/dt = u M0 exactly, because every face flux is
+    single-valued, x is continuous and linear (the mortars' L2 projection
+    keeps it) and the GL derivative is summation-by-parts.  So the residual's
+    first moment is u M0, and one RK3 step (linear in the moments) moves the
+    centroid by u dt, to roundoff, on mixed orders with mortars.  The identity
+    needs the perturbation to stay off the periodic seam, where x jumps: the
+    pulse family's Roe flux is pure upwinding (the acoustic waves vanish up to
+    roundoff), so the support grows by one element per stage downstream, and
+    the pulse starts four elements upstream of the seam."""
+    u = np.array([1.0, 0.5, -0.25])
+    ph = I.pulse_physics(mach=0.3, velocity=tuple(u))
+    mi = I.box_mesh(8, orders=I.random_orders(512, 2, 5, 31), phys=ph)
+    m = orc.Mesh(mi)
+    xyz = m.coords()
+    q = I.pulse_state(xyz, m.orders, ph, amp=4.0, width=0.05, center=(-0.6, -0.6, 0.6), images=0)
+
+    def last_layer_clean(q):   # the elements at the downstream seams hold rho = 1 to roundoff
+        dev = 0.0
+        for e in range(m.n_elem):
+            x = m.elem(xyz, e, 3)
+            if x[0].min() > 0.7 or x[1].min() > 0.7 or x[2].max() < -0.7:
+                dev = max(dev, np.abs(m.elem(q, e)[0] - 1.0).max())
+        return dev <= 1e-14
+
+    def moments(a, q0=True):   # M0, M1 and the size of their terms (the roundoff scale)
+        M0, M1, S = 0.0, np.zeros(3), 0.0
+        for e in range(m.n_elem):
+            _, _, J = m.metrics(e)
+            wr = tensor_weights(m.orders[e]) * J * (m.elem(a, e)[0] - (1.0 if q0 else 0.0))
+            M0 += wr.sum()
+            M1 += m.elem(xyz, e, 3) @ wr
+            S += np.abs(wr).sum()
+        return M0, M1, S
+    assert last_layer_clean(q)
+    M0, M1, _ = moments(q)
+    dM0, dM1, S = moments(m.residual(q), q0=False)
+    assert abs(dM0) <= 1e-13 * S
+    assert np.abs(dM1 - u * M0).max() <= 1e-13 * S, (dM1 / M0, u)
+    assert np.abs(u * M0).max() > 1e-3 * S        # ... which is not small against the terms
+    dt = m.max_dt(q, 0.5)
+    G = np.zeros_like(q)
+    m.rk_step(q, G, dt)
+    assert last_layer_clean(q)
+    M0t, M1t, _ = moments(q)
+    assert abs(M0t - M0) <= 1e-15 * 8.0             # roundoff of the nodal values over the box's volume
+    shift = M1t / M0t - M1 / M0
+    assert np.abs(shift - u * dt).max() <= 1e-10 * np.abs(u * dt).max(), (shift, u * dt)
+
+
 def _l2_error(m, q, ph, t, width, center):
     xyz = m.coords()
     u = np.asarray(ph.qinf[1:4])
