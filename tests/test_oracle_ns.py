@@ -41,12 +41,19 @@ def test_br1_gradient_exact_for_linear_state(orc):
             np.testing.assert_allclose(ge[c], np.repeat(C[:, 1 + c][:, None], n, 1), atol=1e-12)
 
 
-def test_shear_flow_viscous_residual(orc):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_shear_flow_viscous_residual(orc, mixed):
     """u = (a y, 0, 0), rho and p constant: the advective residual vanishes and
-    the viscous one is R_rhoE = mu a^2 (viscous heating), R_mom = 0."""
+    the viscous one is R_rhoE = mu a^2 (viscous heating), R_mom = 0.  Mixed:
+    orders 3..4 per element and direction, so that the BR1 and Roe fluxes
+    cross mortars; the energy flux (E + p) u is cubic in y, which every
+    order >= 3 holds exactly, so the mortar's projection changes nothing."""
     nx, a, mu = 4, 0.8, 0.07
     ph = _ns_phys(mu)
-    mi = I.box_mesh(nx, orders=(2, 3, 2), phys=ph)
+    mi = I.box_mesh(nx, orders=I.random_orders(nx ** 3, 3, 4, 33) if mixed else (2, 3, 2), phys=ph)
+    if mixed:   # p-nonconforming faces among the interior elements' faces
+        o = np.asarray(mi.orders).reshape(-1, 3)
+        assert len({tuple(o[e]) for e in _interior(nx)}) > 1
     m = orc.Mesh(mi)
     rho, p = 1.3, 5.0
     q = I.pointwise_state(m.coords(), m.orders, lambda x, y, z: np.stack(
