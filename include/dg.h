@@ -148,9 +148,10 @@ dg_status dg_residual(dg_mesh* mesh, const double* q, double* r, uint32_t flags)
  *   Every call rewrites the whole part of the array it reads, so nothing
  *   carries over from an earlier call.
  * Errors: DG_ERR_ARG (null or aliased pointers, mesh device not current),
- * DG_ERR_UNSUPPORTED (Navier-Stokes mesh, mortars not implemented, or a face
- * buffer of more than DG_NOALLOC_SURF_DOUBLES doubles: 5 per element-face
- * node, i.e. more than 838,860 element-face nodes), DG_ERR_CUDA. */
+ * DG_ERR_UNSUPPORTED (Navier-Stokes mesh, a mortar batch above the device's
+ * shared memory as for dg_residual, or a face buffer of more than
+ * DG_NOALLOC_SURF_DOUBLES doubles: 5 per element-face node, i.e. more than
+ * 838,860 element-face nodes), DG_ERR_CUDA. */
 #define DG_NOALLOC_SURF_DOUBLES 4194304
 dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double* r);
 
