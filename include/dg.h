@@ -189,7 +189,13 @@ dg_status dg_rk_step(dg_mesh* mesh, double* q, double* g, const double* dt_dev);
  *   flags: DG_TAU_ISOLATED (element-local residuals; coarse geometry is the
  *      element map interpolated to N), else non-isolated (full residual of
  *      the coarse discretisation with orders min(N_s, P_e) in every
- *      element); DG_TAU_FP32; DG_TAU_ACCUM_MAX. */
+ *      element); DG_TAU_FP32; DG_TAU_ACCUM_MAX.
+ * Asynchronous on the mesh stream.  Errors: DG_ERR_ARG (null q or sweep,
+ * n_sweep <= 0, both maps NULL, unknown flag bits, an order outside
+ * 1..DG_MAX_ORDER); DG_ERR_UNSUPPORTED (isolated: a tile class whose sweep
+ * needs more shared memory than the device offers, as FP64 does for
+ * elements of 9 x 9 x 9 nodes, where DG_TAU_FP32 serves; non-isolated: as
+ * dg_residual); DG_ERR_NOMEM; DG_ERR_CUDA. */
 dg_status dg_tau_estimate(dg_mesh* mesh, const double* q, const double* r_p, const int32_t* sweep, int32_t n_sweep,
                           uint32_t flags, void* map_new, void* map_trad);
 
