@@ -104,15 +104,24 @@ typedef struct dg_mesh dg_mesh;
  * neighbour index out of range or not reciprocal, unknown tag, J <= 0),
  * DG_ERR_NOMEM, DG_ERR_CUDA. */
 dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out);
+/* Synchronises the mesh stream and frees everything the mesh owns (its
+ * cached coarse meshes and CUDA graphs included).  Errors: DG_ERR_ARG (null). */
 dg_status dg_mesh_destroy(dg_mesh* mesh);
-/* Number of nodes and elements (host outputs; either may be NULL). */
+/* Number of nodes and elements (host outputs; either may be NULL).
+ * Errors: DG_ERR_ARG (null mesh). */
 dg_status dg_mesh_info(const dg_mesh* mesh, int64_t* n_nodes, int32_t* n_elem);
-/* Number of nodes of a layout with the given host orders [n_elem][3]. */
+/* Number of nodes sum_e prod_i (N_i+1) of a layout with the given host
+ * orders [n_elem][3]; host only.  Errors: DG_ERR_ARG (n_elem < 0, null
+ * orders with n_elem > 0, null n_nodes, an order outside 1..DG_MAX_ORDER). */
 dg_status dg_count_nodes(int32_t n_elem, const int32_t* orders, int64_t* n_nodes);
+/* Later calls on the mesh (and its cached coarse meshes) run on stream (a
+ * cudaStream_t, or NULL for the legacy default stream); ordering against
+ * work already queued on the previous stream is the caller's.
+ * Errors: DG_ERR_ARG (null mesh). */
 dg_status dg_set_stream(dg_mesh* mesh, void* stream);
 
 /* Node coordinates: device xyz[3*n_nodes], element e at 3*off_e as
- * [d][node].  Synchronous. */
+ * [d][node].  Synchronous.  Errors: DG_ERR_ARG (null pointer), DG_ERR_CUDA. */
 dg_status dg_node_coords(dg_mesh* mesh, double* xyz);
 
 /* Residual R(Q) = dQ/dt = -(M^N)^{-1} F^N(Q) of the DGSEM discretisation,
@@ -160,14 +169,19 @@ dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double* r);
  *   s_a = sum_i (N_i+1)^2 (|J a^i . v| + c |J a^i|) / (2J),
  *   s_v = sum_i (N_i+1)^4 |J a^i|^2/(4J^2) max(1, gamma/Pr) mu/rho (NS only).
  * q: device state; dt_dev: device double written on the stream, so that a
- * captured RK loop can consume it without a host round trip. */
+ * captured RK loop can consume it without a host round trip.
+ * Errors: DG_ERR_ARG (null pointer, cfl not > 0), DG_ERR_CUDA; a
+ * non-physical state sets the sticky error word. */
 dg_status dg_max_dt(dg_mesh* mesh, const double* q, double cfl, double* dt_dev);
 
 /* One step of Williamson's low-storage RK3 (Sec. 3), stages k = 1..3:
  *   G <- A_k G + dt R(Q),  Q <- Q + B_k G,
  * A = (0, -5/9, -153/128), B = (1/3, 15/16, 8/15).  q and g (the RK
  * register, zero before the first step) are device state-layout arrays
- * updated in place; dt_dev is a device double read by the kernels. */
+ * updated in place; dt_dev is a device double read by the kernels.
+ * Errors: DG_ERR_ARG (null pointer, q == g), DG_ERR_UNSUPPORTED (as
+ * dg_residual), DG_ERR_CUDA; a non-physical state sets the sticky error
+ * word. */
 dg_status dg_rk_step(dg_mesh* mesh, double* q, double* g, const double* dt_dev);
 
 /* Unsteady anisotropic tau-estimation, variational DG form (Sec. 2.3 item 1):
@@ -205,7 +219,9 @@ dg_status dg_tau_estimate(dg_mesh* mesh, const double* q, const double* r_p, con
  * interpolation when the order rises and L2 projection when it falls.
  * q_old: device, old layout; q_new: device, new layout of
  * dg_count_nodes(new_orders) nodes, caller-allocated, not aliasing q_old.
- * The mesh is rebuilt for the new orders (synchronous). */
+ * The mesh is rebuilt for the new orders (synchronous); on an error it is
+ * left as it was.  Errors: DG_ERR_ARG (null pointer, q_old == q_new, an
+ * order outside 1..DG_MAX_ORDER), DG_ERR_NOMEM, DG_ERR_CUDA. */
 dg_status dg_set_orders(dg_mesh* mesh, const int32_t* new_orders, const double* q_old, double* q_new);
 
 /* p-adaptation, order selection (Sec. 2.4, approach 2; with the degree-jump
@@ -311,11 +327,13 @@ typedef struct {
  * Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED (as dg_residual), DG_ERR_NOMEM,
  * DG_ERR_CUDA. */
 dg_status dg_autotune(dg_mesh* mesh, const double* q, int32_t reps, dg_tiles* out);
-/* The budgets in use (times -1). */
+/* The budgets in use (times -1).  Errors: DG_ERR_ARG (null pointer). */
 dg_status dg_get_tiles(const dg_mesh* mesh, dg_tiles* out);
 /* Sets the budgets (the times are ignored; volume budgets 1..DG_MAX_VOL_BUDGET,
  * mortar budgets 1..DG_MAX_MORTAR_BUDGET nodes, else DG_ERR_ARG) and rebuilds
- * the work lists; releases cached dg_advance graphs.  Synchronous. */
+ * the work lists; releases cached dg_advance graphs.  Synchronous.
+ * Errors: DG_ERR_ARG (null pointer, a budget out of range), DG_ERR_NOMEM,
+ * DG_ERR_CUDA. */
 dg_status dg_set_tiles(dg_mesh* mesh, const dg_tiles* in);
 
 /* Adjoint (vector-Jacobian product) of the residual: out = (dR/dq)^T v at the
@@ -417,18 +435,25 @@ enum {
 };
 
 /* Per-kernel timing with CUDA events recorded on the mesh stream around
- * every launch while enabled (on != 0 resets the totals).  Off by default. */
+ * every launch while enabled (on != 0 resets the totals).  Off by default.
+ * Errors: DG_ERR_ARG (null mesh). */
 dg_status dg_profile_enable(dg_mesh* mesh, int on);
 /* Synchronises the stream and returns, for one kernel kind, the summed
  * event-measured duration (ms) and the number of timed launches since
- * profiling was enabled. */
+ * profiling was enabled (host outputs; either may be NULL).
+ * Errors: DG_ERR_ARG (null mesh, kernel outside 0..DG_KERNEL_KINDS-1),
+ * DG_ERR_CUDA. */
 dg_status dg_profile_read(dg_mesh* mesh, int kernel, double* total_ms, int64_t* launches);
-/* Number of kernels the library has launched on this mesh since creation. */
+/* Number of kernels the library has launched on this mesh since creation
+ * (host output).  Errors: DG_ERR_ARG (null pointer). */
 dg_status dg_launch_count(const dg_mesh* mesh, int64_t* launches);
 
 /* Synchronises the mesh stream; returns and clears the sticky device error
- * (DG_OK if none). */
+ * (DG_OK if none): DG_ERR_NONPHYSICAL or, in the bounds-checking build,
+ * DG_ERR_INDEX; DG_ERR_ARG for a null mesh, DG_ERR_CUDA if the
+ * synchronisation fails. */
 dg_status dg_get_error(dg_mesh* mesh);
+/* A static description of a status code ("unknown status" for others). */
 const char* dg_status_str(dg_status s);
 
 #ifdef __cplusplus
