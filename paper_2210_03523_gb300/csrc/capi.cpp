@@ -975,12 +975,10 @@ dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_o
     return from_cuda(e);
   }
   // swap the rebuilt structures into m; the old ones leave with c
-  unsigned* old_err = m->d_err;
   cudaStream_t s = m->stream;
   std::swap(*static_cast<dg_mesh_impl*>(m), *c);
   m->stream = s;
   std::swap(m->d_err, c->d_err);   // keep the sticky error word of the mesh
-  (void)old_err;
   destroy_impl(c);
   return DG_OK;
 }
