@@ -12,10 +12,12 @@
 //                      -(1/J) scaling, optionally the fused RK3 stage update.
 //                      Elements of one order triple are batched per CTA
 //                      (work items), all triples in one launch.
-//   tau_kernel<T>      isolated tau sweep, one CTA per (tile, group of sweep
-//                      entries sharing (N2,N3)): restriction by sum-factorised
-//                      interpolation (xi3 and xi2 once per group), coarse
-//                      isolated residual, both tau forms, per-element maxima.
+//   tau_kernel<T>      isolated tau sweep, one CTA per unit (a tile and the
+//                      groups of sweep entries sharing (N2,N3) for one N3):
+//                      restriction by sum-factorised interpolation (xi3 once
+//                      per unit, xi2 once per group, xi1 per chunk of
+//                      entries), coarse isolated residual, both tau forms,
+//                      per-element maxima.
 // FP64 throughout, except tau_kernel<float>.
 #include <algorithm>
 #include <cfloat>
@@ -1939,10 +1941,11 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
   }
 }
 
-// The sweep proper, one (tile, group) unit per CTA iteration; a group is the
-// sweep entries sharing (N2, N3).  The unit restricts q^P and R^P in xi3 and
-// xi2 once, then runs every entry of the group: restriction in xi1, coarse
-// isolated residual fused with both tau norms, map store.
+// The sweep proper, one unit per CTA iteration: a tile and the groups of one
+// N3 (a group is the sweep entries sharing (N2, N3)).  The unit restricts
+// q^P and R^P in xi3 once, each group in xi2, then runs the group's entries
+// in chunks: restriction in xi1, coarse isolated residual fused with both
+// tau norms, map store.
 template <typename T, bool AFFINE, bool NS, bool AXIS>
 __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
