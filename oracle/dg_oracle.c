@@ -38,6 +38,28 @@
  *   - isolated tau uses the isolated residual in both terms unless the caller
  *     passes its own R^P.
  *
+ * Pins (each part checked against something other than itself, in the
+ * tests named test_oracle_*.py):
+ *   - GL tables: closed forms up to N = 4, numpy's Legendre roots, row sums
+ *     of D, the summation-by-parts identity (basis);
+ *   - residual: free-stream preservation (affine, sheared, curved, O-grid,
+ *     with mortars), polynomial exactness of the pulse family across mortars,
+ *     equality with an independent scalar upwind DGSEM, discrete
+ *     conservation, the curl-form metric identities (residual);
+ *   - Roe and viscous fluxes: consistency, upwinding, rotation invariance,
+ *     the contact-wave reduction, closed forms of shear and conduction
+ *     (fluxes); BR1 exact for linear states, viscous heating of a shear
+ *     flow on uniform and mixed orders, no mass flux through a wall (ns);
+ *   - RK3 and the CFL step: order conditions, the Taylor polynomial of a
+ *     linear operator, design-order convergence of the pulse, its centroid
+ *     moving with the flow, closed forms and invariants of both CFL terms
+ *     (time);
+ *   - tau: zero at N = P, closed forms of both forms, vanishing above the
+ *     state's degree, the exact truncation error of an analytic solution,
+ *     the scaling with element size, non-isolated tau (tau);
+ *   - order projection, selection (the paper's Table 1), extrapolation,
+ *     drivers, wall force and the finite-difference adjoint (their files).
+ *
  * Layout (the interface both implementations agree on): element e has
  * n_e = (N1+1)(N2+1)(N3+1) nodes; the state of element e starts at
  * 5 * sum_{e'<e} n_e' doubles and is stored [var][k][j][i] with i fastest.
