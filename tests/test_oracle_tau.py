@@ -199,6 +199,32 @@ def test_non_isolated_tau(orc):
         assert tn[e, 3] > 1e-3 and tn[e, 4] > 1e-3
 
 
+def test_non_isolated_tau_mixed_orders(orc):
+    """Non-isolated tau with mixed P (orders 2..4 per element and direction):
+    the coarse discretisation has orders min(N, P_e), so at N = (3,3,3) it
+    is itself p-nonconforming.  A continuous pulse-family state of degree
+    (2,2,2) is exact at every order >= 2 on both levels, mortars included, so
+    tau = 0 on interior elements wherever the entry exists (N <= P_e; else -1)
+    and tau > 0 for the entries with an order 1."""
+    nx = 4
+    ph = I.pulse_physics(mach=0.4, velocity=(0.6, 0.4, -0.5))
+    mi = I.box_mesh(nx, orders=I.random_orders(nx ** 3, 2, 4, 41), phys=ph)
+    m = orc.Mesh(mi)
+    q, _ = _pulse_family(ph, m.coords(), m.orders, lambda x, y, z: 2.0 + 0.3 * x * x - 0.2 * y * z + 0.1 * z * z)
+    sweep = np.array([[2, 2, 2], [3, 3, 3], [1, 2, 2], [2, 2, 1]], dtype=np.int32)
+    tn, tt = m.tau(q, sweep, isolated=False)
+    o = np.asarray(m.orders).reshape(-1, 3)
+    interior = [ix + nx * (iy + nx * iz) for iz in (1, 2) for iy in (1, 2) for ix in (1, 2)]
+    reach = (sweep[None, :, :] <= o[:, None, :]).all(2)
+    assert np.array_equal(tn < 0, ~reach) and np.array_equal(tt < 0, ~reach)
+    assert reach[interior, 1].any() and not reach[:, 1].all()   # N = (3,3,3) exists on some interior elements only
+    for e in interior:
+        assert abs(tn[e, 0]) < 1e-11 and abs(tt[e, 0]) < 1e-11
+        if reach[e, 1]:
+            assert abs(tn[e, 1]) < 1e-11 and abs(tt[e, 1]) < 1e-11
+        assert tn[e, 2] > 1e-3 and tn[e, 3] > 1e-3
+
+
 def test_dual_time_stepping_form_converges_to_the_variational_form(orc):
     """Dual time-stepping estimate (Sec. 2.3, item 2): the steady operator
     dQ/dt-discretisation + M^{-1} F (new form) gives
