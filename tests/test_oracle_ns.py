@@ -65,6 +65,26 @@ def test_shear_flow_viscous_residual(orc, mixed):
         np.testing.assert_allclose(R[4], mu * a * a, atol=1e-11)
 
 
+def test_isolated_shear_flow_every_element(orc):
+    """The isolated residual (element-local BR1 gradient, inner fluxes on the
+    faces; Sec. 2.2) sees each element's polynomial alone, so the shear flow
+    u = (a y, 0, 0) gives R_rhoE = mu a^2 and R_mom = 0 on every element,
+    the ones on the periodic seam included, and on a sheared mesh too."""
+    nx, a, mu = 3, 0.8, 0.07
+    A = [[1.0, 0.2, 0.0], [0.1, 1.0, 0.15], [0.0, -0.1, 0.9]]
+    mi = I.box_mesh(nx, mapping=I.affine_map(A), orders=I.random_orders(nx ** 3, 3, 4, 34), phys=_ns_phys(mu))
+    m = orc.Mesh(mi)
+    rho, p = 1.3, 5.0
+    q = I.pointwise_state(m.coords(), m.orders, lambda x, y, z: np.stack(
+        [rho + 0 * x, rho * a * y, 0 * x, 0 * x, p / 0.4 + 0.5 * rho * (a * y) ** 2]))
+    r = m.residual(q, isolated=True)
+    for e in range(m.n_elem):
+        R = m.elem(r, e)
+        np.testing.assert_allclose(R[:4], 0.0, atol=1e-11)
+        np.testing.assert_allclose(R[4], mu * a * a, atol=1e-11)
+    assert np.abs(m.residual(q)).max() > 1.0      # the full residual does see the seam's jump
+
+
 @pytest.mark.parametrize("case", ["wavy_moving", "ogrid_rest"])
 def test_ns_free_stream(orc, case):
     if case == "wavy_moving":
