@@ -1,9 +1,9 @@
 """Benchmark of the DGSEM hot path on GB300.
 
-Workload (default ``pulse16mixed``): the Euler density pulse on 16^3
+Workload (default ``pulse48mixed``): the Euler density pulse on 48^3
 periodic straight hexes. Each element's orders (N1,N2,N3) are drawn i.i.d.
-from {1..6} (seed 2210), so faces are p-nonconforming. One *step* is one
-pass of the whole hot path:
+from {2..8} (seed 2210), so faces are p-nonconforming; 2.4e7 nodes, a state
+of 0.96 GB. One *step* is one pass of the whole hot path:
 
   * 50 explicit RK3 steps in FP64 through dg_advance (batches of steps
     replayed as CUDA graphs). Each RK step is one CFL reduction and three
@@ -12,9 +12,11 @@ pass of the whole hot path:
     order N <= P_e of every element, both forms, max-accumulated.
 
 The timed region runs the steps as a user would, without per-kernel events.
-A second timed region runs the same steps with CUDA events around every
-kernel (launched one by one); the per-kernel shares and the roofline come
-from it.
+A second timed region runs up to PROFILE_STEPS of the same steps with CUDA
+events around every kernel (launched one by one); the per-kernel shares and
+the roofline come from it.  On the 48^3 mixed-order mesh the same step is
+then timed on the uniform-order partner (P = (5,5,5), the same expected
+nodes per element) and reported under ``vs_uniform``.
 
 The metric is DOF-residuals/s: NDOF x residual evaluations per step / step
 time, summed over ranks. tau-estimated elements/s is reported next to it.
@@ -43,6 +45,12 @@ METRIC = "DOF-residuals/s and tau-estimated elements/s at stated error; % of HBM
 UNIT = "DOF-residuals/s"
 CFL = 0.5
 RK_PER_STEP = 50
+DEFAULT_WORKLOAD = "pulse48mixed"
+UNIFORM_PARTNER = {"pulse48mixed": "pulse48uniform"}   # the uniform-order FP64 path at the same nodes per element
+PROFILE_STEPS = 5          # steps of the profiled region, the e2e region and the uniform partner (at most K)
+TAU_FP32_BOUND = ("<= 8 (eps32 S_dev + eps64 S_full) per element, S = (sum_i ||D^(P_i)||) F max|Ja| / min J, F the "
+                  "largest flux-deviation term (deviations from the element's first-node state) or, for the FP64 "
+                  "reference's own rounding, the largest flux term")
 L2_FLUSH_BYTES = 256 << 20
 FP64_FMA_PER_CLK_PER_SM = 2        # GB300: 64 FP64 lanes per 32 clocks per SM (measured 1.20 TFLOP/s)
 FP32_FMA_PER_CLK_PER_SM = 128
@@ -142,23 +150,33 @@ def volume_counts(orders, rk=True, axis_aligned=False):
     return float(flops), float(bytes_)
 
 
-ROE_FLOPS = 160   # one Roe flux through an axis-aligned unit normal, counted below
+# one Roe flux per mortar node (roe_t), counted operation by operation:
+# through an axis-aligned unit normal e_d (every face of an axis-aligned box):
+# 1/rho and sqrt(rho) from two rsqrt and four products 6, velocities 6,
+# pressures 16, rho H and H 4, Roe weights 4, averaged velocity 9, averaged H
+# 3, averaged rho 1, sound speed (|u~|^2 5, c~^2 3, rsqrt and three products
+# 4) 12, jumps 3, wave strengths 8, eigenvalue products and sums 10, the
+# tangential jump and u~ . du~ 5, mass flux 5, momentum fluxes 34, energy flux
+# 14, the face-area factor 1/2 |J a| 1: 141.  Through a general unit normal
+# the normal velocities and momenta (17), the full tangential jump (9 more)
+# and the normal projections of the momentum flux (12 more) add 38: 179.
+ROE_FLOPS_AXIS = 141
+ROE_FLOPS_GENERAL = 179
 
 
-def mortar_counts(mi):
+def mortar_counts(mi, axis_aligned=False):
     """Algorithmic FP64 flops and HBM bytes of one mortar-kernel launch.
 
     For every interior face in the launch (on straight-sided Euler meshes the
     conforming faces too, with no interpolation) with la x lb and ra x rb
-    nodes and mortar Ma x Mb = max per direction:
-    interpolation of the 5 trace variables up to the mortar, per side and
-    tangential direction where the side is coarser (2 * 5 * taps flops per
-    output node), Roe at the Ma*Mb mortar nodes (ROE_FLOPS each: velocities
-    8, pressures 16, enthalpies 4, Roe averages 21, sound speed 6, jumps 5,
-    wave strengths 10, eigenvalues 7, tangential jump 9, physical fluxes 24,
-    dissipation 35, assembly 10) plus 5 for the face area, and the L2
-    projection back in the same passes reversed.  Bytes: each element-face
-    node reads its 5-variable trace and writes 5 values of F*, 80 B."""
+    nodes and mortar Ma x Mb = max per direction: interpolation of the 5
+    trace variables up to the mortar, per side and tangential direction where
+    the side is coarser (2 * 5 * taps flops per output node), one Roe flux per
+    mortar node (ROE_FLOPS_AXIS on an axis-aligned box, else
+    ROE_FLOPS_GENERAL), and the L2 projection back in the same passes
+    reversed.  Bytes: each element-face node reads its 5-variable trace and
+    writes 5 values of F*, 80 B."""
+    roe = ROE_FLOPS_AXIS if axis_aligned else ROE_FLOPS_GENERAL
     o = np.asarray(mi.orders, dtype=np.int64).reshape(-1, 3) + 1
     nb = np.asarray(mi.neighbors).reshape(-1, 6)
     flops = bytes_ = 0.0
@@ -173,7 +191,7 @@ def mortar_counts(mi):
             # interpolation up (xi_a then xi_b) and projection down (the reverse)
             flops += (2 * 2 * 5 * a * Ma * b * up_a).sum() + (2 * 2 * 5 * b * Ma * Mb * up_b).sum()
             bytes_ += (80 * a * b).sum()
-        flops += ((ROE_FLOPS + 5) * Ma * Mb).sum()
+        flops += (roe * Ma * Mb).sum()
     return float(flops), float(bytes_)
 
 
@@ -367,18 +385,23 @@ def adjoint_timing(m, q, dt_adj, reps=10):
 
 
 # ------------------------------------------------------------ our arm
-def run_gb300(args, rank, world):
+def measure(workload, args, steps, warmup, world, sample_clocks=True):
+    """Set up one workload and time `steps` bench steps after `warmup` untimed
+    ones (the timed region: no per-kernel events), then min(steps,
+    PROFILE_STEPS) steps with CUDA events around every kernel (the profiled
+    region: per-kernel shares and the rooflines).  Returns a dict of the
+    mesh, its buffers and the timings."""
     import torch
     from paper_2210_03523_gb300 import dg, inputs as I
 
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
+    dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
-    mi = I.workload(args.workload)
+    mi = I.workload(workload)
     m = dg.Mesh(mi)
     ndof = m.n_nodes
     xyz = m.coords().cpu().numpy()
-    q0_h = initial_state(args.workload, mi, xyz)
+    q0_h = initial_state(workload, mi, xyz)
+    del xyz
     q0 = torch.from_numpy(q0_h).cuda()
     q = q0.clone()
     g = torch.zeros_like(q)
@@ -386,14 +409,12 @@ def run_gb300(args, rank, world):
     t_tune = time.perf_counter()
     tiles = m.tiles() if args.no_autotune else m.autotune(q0, reps=3)
     tune_s = time.perf_counter() - t_tune
-    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
     sweep = full_sweep_for(mi.orders)
     ns = sweep.shape[0]
     map_new = torch.zeros((m.n_elem, ns), dtype=torch.float32, device="cuda")
     map_trad = torch.zeros_like(map_new)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     ev = lambda: torch.cuda.Event(enable_timing=True)
-
     t_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
 
     def advance():
@@ -408,7 +429,7 @@ def run_gb300(args, rank, world):
         g.zero_()
         flush.fill_(1.0)       # evict the working set from L2 between timed steps
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         reset()
         advance()
         sweep_tau()
@@ -418,15 +439,15 @@ def run_gb300(args, rank, world):
         torch.distributed.barrier()
 
     # timed region: K steps, no per-kernel events
-    clocks = ClockSampler(dev)
-    clocks.start()
+    clocks = ClockSampler(dev) if sample_clocks else None
+    if clocks:
+        clocks.start()
     launches0 = m.launch_count()
-    starts, mids, ends = [ev() for _ in range(args.steps)], [ev() for _ in range(args.steps)], \
-        [ev() for _ in range(args.steps)]
+    starts, mids, ends = [ev() for _ in range(steps)], [ev() for _ in range(steps)], [ev() for _ in range(steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(steps):
         reset()
         starts[k].record(stream)
         advance()
@@ -437,16 +458,17 @@ def run_gb300(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     launches = m.launch_count() - launches0
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     rk_ms = [s.elapsed_time(e) for s, e in zip(starts, mids)]
     tau_ms = [s.elapsed_time(e) for s, e in zip(mids, ends)]
 
-    # profiled region: the same K steps with CUDA events around every kernel
+    # profiled region: the same steps with CUDA events around every kernel
     # (launched one by one) for the per-kernel shares and the roofline
+    psteps = min(steps, PROFILE_STEPS)
     m.profile_enable(True)
-    prof_s, prof_e = [ev() for _ in range(args.steps)], [ev() for _ in range(args.steps)]
-    for k in range(args.steps):
+    prof_s, prof_e = [ev() for _ in range(psteps)], [ev() for _ in range(psteps)]
+    for k in range(psteps):
         reset()
         prof_s[k].record(stream)
         advance()
@@ -458,89 +480,123 @@ def run_gb300(args, rank, world):
     m.profile_enable(False)
     err = m.get_error()
     assert err == 0, f"device error {err}"
-
     total_ms = max_over_ranks(float(sum(step_ms)), world)
-    ms_per_step = total_ms / args.steps
-    res_per_step = 3 * args.rk_per_step
-    value = job_value(world, ndof, res_per_step, ms_per_step)
+    return {"mi": mi, "m": m, "q": q, "g": g, "q0_h": q0_h, "flush": flush, "t_dev": t_dev, "sweep": sweep,
+            "map_new": map_new, "map_trad": map_trad, "advance": advance, "sweep_tau": sweep_tau,
+            "ndof": ndof, "steps": steps, "ms_per_step": total_ms / steps, "rk_ms": rk_ms, "tau_ms": tau_ms,
+            "prof_ms": prof_ms, "psteps": psteps, "kern": kern, "clk": clk, "launches": launches,
+            "tiles": tiles, "tune_s": tune_s}
 
-    # end to end through the public API with host buffers
-    q_pin = torch.from_numpy(q0_h).pin_memory()
-    out_q = torch.empty(q.numel(), dtype=torch.float64).pin_memory()
-    out_mn = torch.empty(map_new.shape, dtype=torch.float32).pin_memory()
-    out_mt = torch.empty(map_trad.shape, dtype=torch.float32).pin_memory()
-    e2e_s, e2e_e = [ev() for _ in range(args.steps)], [ev() for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        g.zero_()
-        flush.fill_(1.0)
-        e2e_s[k].record(stream)
-        q.copy_(q_pin, non_blocking=True)
-        advance()
-        sweep_tau()
-        out_q.copy_(q, non_blocking=True)
-        out_mn.copy_(map_new, non_blocking=True)
-        out_mt.copy_(map_trad, non_blocking=True)
-        e2e_e[k].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e2e_s, e2e_e)) / args.steps, world)
-    h2d = q.numel() * 8
-    d2h = q.numel() * 8 + 2 * map_new.numel() * 4
 
-    # static p-adaptation selection on the accumulated map (Sec. 2.4, approach 2,
-    # jump condition (b)); timed once, outside the step
-    t0 = time.perf_counter()
-    sel = m.select_orders(map_new, sweep, 1.0, 1, 8, 2)
-    select_ms = (time.perf_counter() - t0) * 1e3
-    fp32_check = fp32_tau_check(m, q, sweep)
-    sweeps = tau_sweep_timing(m, q, np.asarray(mi.orders).reshape(-1, 3).max(0))
-    adjoint = adjoint_timing(m, q, dt_adj=m.max_dt(q, CFL))
-
-    # roofline of the dominant kernel (by share of the profiled step) and of the volume kernel
-    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+def rooflines(workload, r, sm_mhz):
+    """The rooflines of a measured workload: the volume and mortar kernels
+    against the FP64 peak (algorithmic flops of the mesh at hand: on an
+    axis-aligned box the diagonal-metric volume count and the axis-normal Roe
+    count, the general counts beside them), the tau kernel against the FP32
+    peak, and every kernel kind's share of the profiled step."""
+    mi, kern = r["mi"], r["kern"]
     fp64_peak = N_SM * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     hbm_peak, hbm_src = _peaks()
-    # both kernels launch once per size class of their tiles: time per RK stage
-    stages = args.steps * args.rk_per_step * 3
-    vol_ms, vol_n = kern["volume"]
-    vflops, vbytes = volume_counts(mi.orders, rk=True)
+    axis = is_axis_aligned(mi)
+    stages = r["psteps"] * r["rk_steps"] * 3        # both kernels launch once per size class: time per RK stage
+    vol_ms, _ = kern["volume"]
+    vflops, vbytes = volume_counts(mi.orders, rk=True, axis_aligned=axis)
+    vflops_gen, _ = volume_counts(mi.orders, rk=True, axis_aligned=False)
     vol_avg_s = vol_ms / stages * 1e-3
     mor_ms, mor_n = kern["mortar"]
-    mflops, mbytes = mortar_counts(mi)
+    mflops, mbytes = mortar_counts(mi, axis_aligned=axis)
+    mflops_gen, _ = mortar_counts(mi, axis_aligned=False)
     mor_avg_s = (mor_ms / stages * 1e-3) if mor_n else None
 
-    def fp64_roofline(name, flops, bytes_, avg_s, kind):
-        traffic = MEASURED_TRAFFIC.get((args.workload, kind))
+    def fp64_roofline(name, flops, flops_gen, bytes_, avg_s, kind):
+        traffic = MEASURED_TRAFFIC.get((workload, kind))
         return {"kernel": name, "bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / fp64_peak,
                 "peak_source": f"FP64: {N_SM} SMs x {FP64_FMA_PER_CLK_PER_SM} DFMA/clk x 2 x median SM clock "
                                f"{sm_mhz:.0f} MHz (recipe nominal 1.25 TFLOP/s at 2070 MHz)",
+                "flop_count": ("axis-aligned box: the operations the kernel performs there (diagonal metric, "
+                               "axis-normal Roe without the tangential normal projection)" if axis else
+                               "general affine count"),
+                "frac_general_count": flops_gen / avg_s / 1e12 / fp64_peak,
                 "traffic": traffic, "traffic_source": TRAFFIC_SOURCE if traffic else None,
                 "algorithmic_flops_per_stage": flops, "algorithmic_bytes_per_stage": bytes_,
+                "traffic_over_algorithmic_bytes": traffic / bytes_ if traffic else None,
                 "time_from": "CUDA events around each launch, profiled region; the launches of one RK stage "
                              "(one per tile-size class) summed",
                 "avg_stage_ms": avg_s * 1e3, "hbm_achieved_gbs": bytes_ / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": bytes_ / avg_s / 1e9 / hbm_peak, "hbm_peak_source": hbm_src}
 
-    vol_roof = fp64_roofline("volume_kernel (FP64 residual + fused RK3 stage)", vflops, vbytes, vol_avg_s, "volume")
-    if is_axis_aligned(mi):
-        vflops_ax, _ = volume_counts(mi.orders, rk=True, axis_aligned=True)
-        vol_roof["frac_diagonal_metric_count"] = vflops_ax / vol_avg_s / 1e12 / fp64_peak
-        vol_roof["note"] = ("flops per the general affine count (contravariant fluxes 75 per node); the mesh is "
-                            "an axis-aligned box, where the kernel needs 15: frac_diagonal_metric_count")
-    mor_roof = fp64_roofline("mortar_kernel (p-nonconforming faces)", mflops, mbytes, mor_avg_s, "mortar") if mor_n else None
+    vol_roof = fp64_roofline("volume_kernel (FP64 residual + fused RK3 stage)", vflops, vflops_gen, vbytes,
+                             vol_avg_s, "volume")
+    mor_roof = fp64_roofline("mortar_kernel (p-nonconforming and conforming interior faces)", mflops, mflops_gen,
+                             mbytes, mor_avg_s, "mortar") if mor_n else None
     dominant = mor_roof if (mor_roof and mor_ms > vol_ms) else vol_roof
-    others = [r for r in (vol_roof, mor_roof) if r is not None and r is not dominant]
+    others = [x for x in (vol_roof, mor_roof) if x is not None and x is not dominant]
     kernels_json = {k: {"launches": n, "total_ms": round(ms, 3), "share": None} for k, (ms, n) in kern.items() if n}
-    kernels_json["_region"] = {"ms_per_step": prof_ms, "note": "a second timed region of the same steps, "
-                               "kernels launched one by one with CUDA events around each"}
+    kernels_json["_region"] = {"ms_per_step": r["prof_ms"], "steps": r["psteps"],
+                               "note": "a second timed region of the same steps, kernels launched one by one with "
+                                       "CUDA events around each"}
     ktot = sum(v["total_ms"] for k, v in kernels_json.items() if not k.startswith("_"))
     for k, v in kernels_json.items():
         if not k.startswith("_"):
             v["share"] = round(v["total_ms"] / ktot, 4) if ktot else None
     tau_k_ms, tau_k_n = kern["tau"]
-    tflops = tau_counts(mi.orders, sweep)
+    tflops = tau_counts(mi.orders, r["sweep"])
     fp32_peak = N_SM * FP32_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    tau_s = tau_k_ms / r["psteps"] * 1e-3 if tau_k_n else None      # one sweep per step
+    tau_roof = {"kernel": "tau_kernel<float> + tau_prologue_kernel", "bound": "alu",
+                "achieved": tflops / tau_s / 1e12 if tau_s else None, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": tflops / tau_s / 1e12 / fp32_peak if tau_s else None, "sweep_ms": tau_s * 1e3 if tau_s else None,
+                "algorithmic_flops_per_sweep": tflops,
+                "peak_source": f"FP32: {N_SM} SMs x {FP32_FMA_PER_CLK_PER_SM} FFMA/clk x 2 x {sm_mhz:.0f} MHz"}
+    return dominant, others, tau_roof, kernels_json
+
+
+def run_gb300(args, rank, world):
+    import torch
+    from paper_2210_03523_gb300 import dg
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    r = measure(args.workload, args, args.steps, args.warmup, world)
+    r["rk_steps"] = args.rk_per_step
+    m, q, g, mi, sweep = r["m"], r["q"], r["g"], r["mi"], r["sweep"]
+    map_new, map_trad, flush = r["map_new"], r["map_trad"], r["flush"]
+    ndof, ms_per_step = r["ndof"], r["ms_per_step"]
+    res_per_step = 3 * args.rk_per_step
+    value = job_value(world, ndof, res_per_step, ms_per_step)
+    clk = r["clk"]
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    dominant, others, tau_roof, kernels_json = rooflines(args.workload, r, sm_mhz)
+
+    # end to end through the public API with host buffers: every step copies
+    # the initial state from pinned host memory and reads the state and both
+    # maps back
+    esteps = min(args.steps, PROFILE_STEPS)
+    q_pin = torch.from_numpy(r["q0_h"]).pin_memory()
+    out_q = torch.empty(q.numel(), dtype=torch.float64).pin_memory()
+    out_mn = torch.empty(map_new.shape, dtype=torch.float32).pin_memory()
+    out_mt = torch.empty(map_trad.shape, dtype=torch.float32).pin_memory()
+    e2e_s, e2e_e = [ev() for _ in range(esteps)], [ev() for _ in range(esteps)]
+    torch.cuda.synchronize()
+    for k in range(esteps):
+        g.zero_()
+        flush.fill_(1.0)
+        e2e_s[k].record(stream)
+        q.copy_(q_pin, non_blocking=True)
+        r["advance"]()
+        r["sweep_tau"]()
+        out_q.copy_(q, non_blocking=True)
+        out_mn.copy_(map_new, non_blocking=True)
+        out_mt.copy_(map_trad, non_blocking=True)
+        e2e_e[k].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e2e_s, e2e_e)) / esteps, world)
+    h2d = q.numel() * 8
+    d2h = q.numel() * 8 + 2 * map_new.numel() * 4
+    del q_pin, out_q, out_mn, out_mt
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -548,87 +604,171 @@ def run_gb300(args, rank, world):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": workload_desc(args.workload), "n_elem": m.n_elem,
                    "ndof": ndof, "scalar_dof": 5 * ndof, "rk_steps_per_step": args.rk_per_step,
-                   "residual_evals_per_step": res_per_step, "tau_sweep": {"entries": ns, "dtype": "f32",
+                   "residual_evals_per_step": res_per_step, "tau_sweep": {"entries": int(len(sweep)), "dtype": "f32",
                                                                          "form": "isolated, new + traditional"},
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-        "tau_elements_per_s": world * m.n_elem / (statistics.mean(tau_ms) * 1e-3),
-        "rk_dof_residuals_per_s": world * ndof * res_per_step / (statistics.mean(rk_ms) * 1e-3),
-        "stated_error": {"residual_rk_fp64_rel": 1e-12, "tau_fp32_abs": "<= 8 eps32 (sum_i ||D||) max|f| max|Ja|/min J",
-                         "checked_by": "tests/test_gpu_parity.py"},
+        "tau_elements_per_s": world * m.n_elem / (statistics.mean(r["tau_ms"]) * 1e-3),
+        "rk_dof_residuals_per_s": world * ndof * res_per_step / (statistics.mean(r["rk_ms"]) * 1e-3),
+        "stated_error": {"residual_rk_fp64_rel": 1e-12, "tau_fp32_abs": TAU_FP32_BOUND,
+                         "checked_by": "tests/test_gpu_parity.py, tests/test_gpu_tau_production.py"},
         "roofline": dominant,
         "roofline_other_kernels": others,
-        "tau_roofline": {"kernel": "tau_kernel<float>", "bound": "alu",
-                         "achieved": tflops / (tau_k_ms / tau_k_n * 1e-3) / 1e12 if tau_k_n else None,
-                         "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": (tflops / (tau_k_ms / tau_k_n * 1e-3) / 1e12 / fp32_peak) if tau_k_n else None,
-                         "peak_source": f"FP32: {N_SM} SMs x {FP32_FMA_PER_CLK_PER_SM} FFMA/clk x 2 x {sm_mhz:.0f} MHz"},
+        "tau_roofline": tau_roof,
         "kernels": kernels_json,
-        "fp32_tau_check": fp32_check,
-        "tau_sweep_timing": sweeps,
-        "adjoint": adjoint,
-        "autotune": {"enabled": not args.no_autotune, "seconds": tune_s, "vol_budget": tiles["vol_budget"],
-                     "mortar_budget": tiles["mortar_budget"], "volume_launch_ms_after_class": tiles["vol_ms"],
-                     "volume_launch_ms_before_class": tiles["vol_ms_default"],
-                     "face_launch_ms_after_class": tiles["mortar_ms"],
-                     "face_launch_ms_before_class": tiles["mortar_ms_default"],
-                     "method": "coordinate descent over size classes, whole production launch timed",
-                     "classes": "elements of <= 27 / 125 / 343 / more nodes; mortars of <= 9 / 25 / 49 / more nodes"},
-        "select_orders": {"ms": select_ms, "tau_max": 1.0, "jump_rule": "N_i >= N_j - 1",
-                          "mean_order_after": float(np.mean(sel)), "synchronous_host_call": True},
         "e2e": {"value": job_value(world, ndof, res_per_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": esteps,
                 "path": "pinned host state -> dg_advance (CUDA-graph step batches) -> dg_tau_estimate -> pinned host "
                         "state and maps"},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(r["launches"]),
         "clocks": clk,
+        "autotune": {"enabled": not args.no_autotune, "seconds": r["tune_s"], "vol_budget": r["tiles"]["vol_budget"],
+                     "mortar_budget": r["tiles"]["mortar_budget"],
+                     "volume_launch_ms_after_class": r["tiles"]["vol_ms"],
+                     "volume_launch_ms_before_class": r["tiles"]["vol_ms_default"],
+                     "face_launch_ms_after_class": r["tiles"]["mortar_ms"],
+                     "face_launch_ms_before_class": r["tiles"]["mortar_ms_default"],
+                     "method": "coordinate descent over size classes, whole production launch timed",
+                     "classes": "elements of <= 27 / 125 / 343 / more nodes; mortars of <= 9 / 25 / 49 / more nodes"},
     }
+    if not args.no_extras:
+        # static p-adaptation selection on the accumulated map (Sec. 2.4, approach 2,
+        # jump condition (b)); timed once, outside the step
+        t0 = time.perf_counter()
+        sel = m.select_orders(map_new, sweep, 1.0, 1, 8, 2)
+        line["select_orders"] = {"ms": (time.perf_counter() - t0) * 1e3, "tau_max": 1.0, "jump_rule": "N_i >= N_j - 1",
+                                 "mean_order_after": float(np.mean(sel)), "synchronous_host_call": True}
+        line["fp32_tau_check"] = fp32_tau_check(m, q, sweep)
+        line["tau_sweep_timing"] = tau_sweep_timing(m, q, np.asarray(mi.orders).reshape(-1, 3).max(0))
+        line["adjoint"] = adjoint_timing(m, q, dt_adj=m.max_dt(q, CFL))
+
+    partner = UNIFORM_PARTNER.get(args.workload)
+    if partner and not args.no_uniform:
+        # the plain uniform-order FP64 path at the same expected nodes per element, same step
+        mixed_tau_eps = line["tau_elements_per_s"]
+        m.close()
+        del r, m, q, g, map_new, map_trad
+        torch.cuda.empty_cache()
+        u = measure(partner, args, min(args.steps, PROFILE_STEPS), 3, world, sample_clocks=False)
+        u["rk_steps"] = args.rk_per_step
+        udom, uoth, utau, ukern = rooflines(partner, u, sm_mhz)
+        uval = job_value(world, u["ndof"], res_per_step, u["ms_per_step"])
+        pick = lambda roofs, key: next((x for x in roofs if x and x["kernel"].startswith(key)), None)
+        line["vs_uniform"] = {
+            "workload": partner, "description": workload_desc(partner), "ndof": u["ndof"], "steps": u["steps"],
+            "dof_residuals_per_s": uval,
+            "rk_dof_residuals_per_s": world * u["ndof"] * res_per_step / (statistics.mean(u["rk_ms"]) * 1e-3),
+            "tau_elements_per_s": world * u["m"].n_elem / (statistics.mean(u["tau_ms"]) * 1e-3),
+            "tau_sweep_entries": int(len(u["sweep"])),
+            "mixed_over_uniform": {"dof_residuals_per_s": value / uval,
+                                   "tau_elements_per_s": mixed_tau_eps / (
+                                       world * u["m"].n_elem / (statistics.mean(u["tau_ms"]) * 1e-3))},
+            "dominant_kernel": {"kernel": udom["kernel"], "frac": udom["frac"]},
+            "volume_frac": (pick([udom] + uoth, "volume") or {}).get("frac"),
+            "mortar_frac": (pick([udom] + uoth, "mortar") or {}).get("frac"),
+            "mixed_dominant_kernel": {"kernel": dominant["kernel"], "frac": dominant["frac"]},
+            "mixed_volume_frac": (pick([dominant] + others, "volume") or {}).get("frac"),
+            "mixed_mortar_frac": (pick([dominant] + others, "mortar") or {}).get("frac"),
+            "kernels": ukern, "tau_roofline_frac": utau["frac"],
+            "note": "same step (RK3 steps at CFL 0.5 + one FP32 isolated tau sweep over its own S), timed after the "
+                    "mixed-order run on the same GPU",
+        }
+        u["m"].close()
     return line
 
 
 # ------------------------------------------------------------ the oracle
-def oracle_sample(workload, rk_steps=2, tau=True):
-    """Time the oracle on the full mesh: rk_steps RK3 steps and (optionally) one
-    FP64 isolated tau sweep.  Returns (rk seconds, tau seconds, ndof, n_elem)."""
+def _oracle_setup(workload):
     import oracle
     from paper_2210_03523_gb300 import inputs as I
     mi = I.workload(workload)
     om = oracle.Mesh(mi)
     q = initial_state(workload, mi, om.coords())
-    G = np.zeros_like(q)
-    dt = om.max_dt(q, CFL)
-    t0 = time.perf_counter()
-    for _ in range(rk_steps):
-        om.rk_step(q, G, dt)
-    t1 = time.perf_counter()
-    t_tau = None
-    if tau:
-        sweep = full_sweep_for(mi.orders)
-        t2 = time.perf_counter()
-        om.tau(q, sweep)
-        t_tau = time.perf_counter() - t2
-    return t1 - t0, t_tau, om.n_nodes, om.n_elem
+    return mi, om, q
+
+
+def _tau_sample_mesh(workload, mi, n=8):
+    """The isolated tau sweep is element-local: a sample of the workload's
+    elements is an n^3 block of them (same element size, orders and state
+    recipe), as its own mesh."""
+    from paper_2210_03523_gb300 import inputs as I
+    import oracle
+    if workload in ("pulse4", "cylinder"):
+        return None
+    nx = round(mi.n_elem ** (1 / 3))
+    if nx <= n:
+        return None
+    o = np.asarray(mi.orders).reshape(nx, nx, nx, 3)[:n, :n, :n].reshape(-1, 3)   # e = i + nx (j + nx k)
+    o = np.ascontiguousarray(o)
+    sub = I.box_mesh(n, lo=-1.0, hi=-1.0 + n * 2.0 / nx, orders=o, phys=mi.phys)
+    om = oracle.Mesh(sub)
+    return sub, om, initial_state(workload, sub, om.coords())
 
 
 def cpu_baseline(workload):
-    rk_s, tau_s, ndof, ne = oracle_sample(workload, rk_steps=4, tau=True)
-    return {"value": ndof * 12 / rk_s, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
-            "kind": "oracle",
-            "sample": f"{workload}: 4 RK3 steps (12 FP64 residuals) of the full mesh + 1 FP64 isolated tau sweep; "
-                      f"OpenMP over elements (schedule guided)",
-            "tau_elements_per_s": ne / tau_s, "seconds": rk_s + tau_s}
+    """The oracle (as it stands) on the host cores, on a bounded sample of the
+    workload: residual evaluations of the full mesh (2 for meshes above 1e7
+    nodes, else 4 RK3 steps), and one FP64 isolated tau sweep over the full
+    set S (of an 8^3 block of the elements when the mesh is larger)."""
+    mi, om, q = _oracle_setup(workload)
+    big = om.n_nodes > 10_000_000
+    t0 = time.perf_counter()
+    if big:
+        n_res = 2
+        for _ in range(n_res):
+            om.residual(q)
+        what = f"{n_res} FP64 residuals of the full mesh"
+    else:
+        n_res = 12
+        G = np.zeros_like(q)
+        dt = om.max_dt(q, CFL)
+        for _ in range(4):
+            om.rk_step(q, G, dt)
+        what = "4 RK3 steps (12 FP64 residuals) of the full mesh"
+    rk_s = time.perf_counter() - t0
+    ndof = om.n_nodes
+    sample = _tau_sample_mesh(workload, mi) if big else None
+    if sample is not None:
+        _, omt, qt = sample
+        tau_what = f"one FP64 isolated tau sweep over S of an 8^3 block ({omt.n_elem} elements)"
+    else:
+        omt, qt = om, q
+        tau_what = "one FP64 isolated tau sweep over S of the full mesh"
+    sweep = full_sweep_for(np.asarray(mi.orders))
+    t2 = time.perf_counter()
+    omt.tau(qt, sweep)
+    tau_s = time.perf_counter() - t2
+    return {"value": ndof * n_res / rk_s, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+            "kind": "oracle", "sample": f"{workload}: {what} + {tau_what}; OpenMP over elements (schedule guided)",
+            "tau_elements_per_s": omt.n_elem / tau_s, "seconds": rk_s + tau_s}
 
 
 def run_reference(args):
+    """The reference arm: the oracle on the host cores, each step a bounded
+    sample of the workload (FP64 residuals of the full mesh: 1 per step above
+    1e7 nodes, else 2 RK3 steps), timed on the host clock."""
+    mi, om, q0 = _oracle_setup(args.workload)
+    big = om.n_nodes > 10_000_000
     steps_ms = []
-    sample_rk = 2
     for k in range(args.warmup + args.steps):
-        rk_s, _, ndof, ne = oracle_sample(args.workload, rk_steps=sample_rk, tau=False)
+        q = q0.copy()
+        t0 = time.perf_counter()
+        if big:
+            om.residual(q)
+            n_res = 1
+        else:
+            G = np.zeros_like(q)
+            dt = om.max_dt(q, CFL)
+            for _ in range(2):
+                om.rk_step(q, G, dt)
+            n_res = 6
         if k >= args.warmup:
-            steps_ms.append(rk_s * 1e3)
+            steps_ms.append((time.perf_counter() - t0) * 1e3)
+    ndof = om.n_nodes
     ms = statistics.mean(steps_ms)
-    value = ndof * 3 * sample_rk / (ms * 1e-3)
+    value = ndof * n_res / (ms * 1e-3)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
-    sample = f"{args.workload}: each step = {sample_rk} RK3 steps ({3 * sample_rk} FP64 residuals) of the full mesh"
+    sample = (f"{args.workload}: each step = {n_res} FP64 residual{'s' if n_res > 1 else ''} of the full mesh"
+              + ("" if big else " (2 RK3 steps)"))
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
@@ -789,6 +929,11 @@ def run_dynamic_cylinder(args):
             "uniform_steps": steps_u, "dynamic_steps": res["steps"],
             "final_drag": {"uniform": drag_u, "dynamic": drag_a, "rel_diff": abs(drag_a - drag_u) / abs(drag_u)},
             "timing_note": "the dynamic time includes every estimation, selection, projection and mesh rebuild",
+            "stage_timing_s": {k: [round(x, 5) for x in v] for k, v in res["timing"].items()},
+            "rebuild_share": sum(res["timing"]["rebuild_s"]) / (dyn_ms * 1e-3),
+            "estimate_select_share": sum(res["timing"]["estimate_select_s"]) / (dyn_ms * 1e-3),
+            "rebuild_note": "dg_set_orders: projection on the device, then the host re-buckets the elements and "
+                            "rebuilds the face and mortar lists and uploads them (synchronous, once per stage)",
         },
     }
 
@@ -799,7 +944,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="pulse16mixed",
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["pulse16mixed", "pulse4", "pulse32mixed", "pulse48mixed", "pulse48uniform",
                              "cylinder", "cylinder_static", "cylinder_dynamic"])
     ap.add_argument("--t-est", type=float, default=0.3, help="cylinder_static: estimation time")
@@ -810,6 +955,9 @@ def main():
     ap.add_argument("--rk-per-step", type=int, default=RK_PER_STEP)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default 256-node tiles")
+    ap.add_argument("--no-uniform", action="store_true", help="skip the uniform-order partner run")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e-independent extras (FP32 check, sweep timings, adjoint, selection)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

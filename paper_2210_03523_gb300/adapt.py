@@ -98,7 +98,12 @@ def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min,
     """Fig. 1 on the GPU.  sweep: a fixed list, or a callable orders -> list.
     Returns a dict: orders, q, t, history (orders after every adaptation),
     steps, ndof (of the final orders), ndof_dyn (the mean NDOF over the time
-    steps), mesh."""
+    steps), mesh, and timing: host wall seconds per stage of the time
+    integration (advance_s), of the estimate and the order selection
+    (estimate_select_s; the selection is a synchronous call that waits for
+    the estimate) and of the mesh rebuild with the projection of the state
+    (rebuild_s: dg_set_orders, synchronous, on the host)."""
+    import time
     import torch
     m = dg.Mesh(mi, stream=stream)
     q = _to_device(q0, m.device)
@@ -107,19 +112,26 @@ def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min,
     st = _Stage(form, isolated, fp32, targets, n_fit, decoupled, tau_floor)
     orders = np.array(mi.orders, dtype=np.int32).reshape(-1, 3)
     steps, k, hist, nd_sum = 0, 1, [], 0
+    timing = {"advance_s": [], "estimate_select_s": [], "rebuild_s": []}
     while True:
+        ta = time.perf_counter()
         n = m.advance(q, g, t, min(t0 + k * dt_e, t_final), cfl, count=True)
+        timing["advance_s"].append(time.perf_counter() - ta)
         steps += n
         nd_sum += n * dg.dg_count_nodes(orders)
         if float(t.item()) >= t_final:
             break
         sw = sweep(orders) if callable(sweep) else sweep
+        tb = time.perf_counter()
         mp, lst = st.map(m, q, sw)
         orders = m.select_orders(mp, lst, tau_max, n_min, n_max, jump_rule, max_decrease=max_decrease)
+        tc = time.perf_counter()
         q = m.set_orders(orders, q)
         g = torch.zeros_like(q)
+        timing["estimate_select_s"].append(tc - tb)
+        timing["rebuild_s"].append(time.perf_counter() - tc)
         hist.append(orders)
         k += 1
     nd = dg.dg_count_nodes(orders)
     return dict(orders=orders, q=q, t=float(t.item()), history=hist, steps=steps, ndof=nd,
-                ndof_dyn=nd_sum / steps if steps else float(nd), mesh=m)
+                ndof_dyn=nd_sum / steps if steps else float(nd), mesh=m, timing=timing)

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _run(extra_env):
     env = dict(os.environ, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"), **extra_env)
-    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
+                           "--workload", "pulse16mixed"],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
 
@@ -32,6 +33,14 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == 4 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_default_workload_is_the_largest_single_gpu_config():
+    """With no flags both arms run the 48^3 mesh with orders iid U{2..8}."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.DEFAULT_WORKLOAD == "pulse48mixed"
+    assert bench.UNIFORM_PARTNER["pulse48mixed"] == "pulse48uniform"
 
 
 def test_reference_arm_other_ranks_exit_quietly():
