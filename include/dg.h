@@ -149,9 +149,13 @@ dg_status dg_residual(dg_mesh* mesh, const double* q, double* r, uint32_t flags)
  * routine.
  *   q, r: device state-layout arrays as for dg_residual; r may not alias q.
  *   The mesh's device must be the current device.
- *   The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) once; make that first call before any stream
- *   capture.
+ *   Each call looks up the array's device address on the current device
+ *   (cudaGetSymbolAddress), so the address always belongs to the live
+ *   context, also after a cudaDeviceReset.  While the mesh stream is being
+ *   captured the address of the last lookup on that device is used instead:
+ *   make one call on the device before any stream capture (a first call
+ *   during capture returns DG_ERR_CUDA).  Several host threads may call at
+ *   the same time.
  *   All calls share the one array: calls that overlap on the GPU (two
  *   streams, two meshes) race on it and must be serialised by the caller.
  *   Every call rewrites the whole part of the array it reads, so nothing
@@ -212,6 +216,34 @@ dg_status dg_rk_step(dg_mesh* mesh, double* q, double* g, const double* dt_dev);
  * dg_residual); DG_ERR_NOMEM; DG_ERR_CUDA. */
 dg_status dg_tau_estimate(dg_mesh* mesh, const double* q, const double* r_p, const int32_t* sweep, int32_t n_sweep,
                           uint32_t flags, void* map_new, void* map_trad);
+
+/* Work units of the isolated sweep (DG_TAU_ISOLATED).  Sec. 2.3 estimates
+ * tau at every coarser N of every element; the library runs a tile of
+ * same-order elements and some of its sweep entries as one unit of work.
+ * Sweep entries sharing (N2, N3) form a group; a unit holds either one
+ * group, or every group of one N3 (the xi3 restriction of q^P and R^P is
+ * then computed once for all of them).  How entries are split into units
+ * changes no node's arithmetic: the maps are bitwise the same in every mode.
+ *   mode DG_TAU_UNITS_AUTO (default): groups shared, except in a shared-
+ *        memory size class that would have fewer than 8 x 152 units (too few
+ *        CTAs to fill the GPU), where each unit holds one group;
+ *   DG_TAU_UNITS_GROUPED: groups shared in every class;
+ *   DG_TAU_UNITS_SPLIT: one group per unit in every class.
+ * The mode takes effect at the next isolated dg_tau_estimate (the units are
+ * rebuilt on the host then, synchronously) and survives dg_set_orders.
+ * Errors: DG_ERR_ARG (null mesh, unknown mode). */
+#define DG_TAU_UNITS_AUTO 0
+#define DG_TAU_UNITS_GROUPED 1
+#define DG_TAU_UNITS_SPLIT 2
+dg_status dg_set_tau_units(dg_mesh* mesh, int32_t mode);
+/* The units of the last isolated sweep's list, per shared-memory size class
+ * (host outputs): *n_classes the number of classes (0 before the first
+ * isolated sweep, or after dg_set_tau_units); for k < min(*n_classes,
+ * max_classes), n_units[k] the units and n_shared[k] those holding two or
+ * more groups.  Errors: DG_ERR_ARG (null mesh or n_classes, max_classes < 0,
+ * null arrays with max_classes > 0). */
+dg_status dg_tau_units_info(const dg_mesh* mesh, int32_t max_classes, int32_t* n_classes, int32_t* n_units,
+                            int32_t* n_shared);
 
 /* Change the element orders to new_orders (host [n_elem][3]) and project
  * the state (Sec. 2.4: after adaptation the storage is reallocated and the

@@ -195,6 +195,8 @@ void destroy_impl(dg_mesh_impl* m) {
   m->vol_classes.clear();
   for (auto* u : m->tau_units) if (u) cudaFree(u);
   m->tau_units.clear();
+  for (auto* u : m->tau_units_split) if (u) cudaFree(u);
+  m->tau_units_split.clear();
   if (m->d_tgroups) cudaFree(m->d_tgroups);
   if (m->d_tgentries) cudaFree(m->d_tgentries);
   m->d_tgroups = m->d_tgentries = nullptr;
@@ -623,8 +625,14 @@ dg_status build_tau_units(dg_mesh_impl* m) {
     gmin1.push_back(mn);
   }
   for (auto* u : m->tau_units) if (u) cudaFree(u);
+  for (auto* u : m->tau_units_split) if (u) cudaFree(u);
   m->tau_units.assign(m->tau_classes.size(), nullptr);
+  m->tau_units_split.assign(m->tau_classes.size(), nullptr);
   m->tau_n_units.assign(m->tau_classes.size(), 0);
+  m->tau_n_units_split.assign(m->tau_classes.size(), 0);
+  m->tau_n_shared.assign(m->tau_classes.size(), 0);
+  m->tau_last_units.clear();
+  m->tau_last_shared.clear();
   if (m->d_tgroups) cudaFree(m->d_tgroups);
   if (m->d_tgentries) cudaFree(m->d_tgentries);
   m->d_tgroups = m->d_tgentries = nullptr;
@@ -652,16 +660,20 @@ dg_status build_tau_units(dg_mesh_impl* m) {
       }
     }
     // a small mesh keeps one group per unit: the shared xi3 restriction saves
-    // work, but too few units leave SMs idle
-    if ((int)units.size() / 4 < kMinTauUnits) {
-      std::vector<int32_t> split;
-      for (size_t u = 0; u < units.size(); u += 4)
-        for (int x = units[u + 1]; x < units[u + 1] + units[u + 2]; ++x)
-          if (gmin1[x] <= m->h_items[units[u]].n1) split.insert(split.end(), {units[u], x, 1, 0});
-      units.swap(split);
-    }
+    // work, but too few units leave SMs idle (DG_TAU_UNITS_AUTO); the other
+    // modes force one form
+    std::vector<int32_t> split;   // one group per unit (also what the compact FP64 layout runs)
+    for (size_t u = 0; u < units.size(); u += 4)
+      for (int x = units[u + 1]; x < units[u + 1] + units[u + 2]; ++x)
+        if (gmin1[x] <= m->h_items[units[u]].n1) split.insert(split.end(), {units[u], x, 1, 0});
+    const bool use_split = m->tau_unit_mode == DG_TAU_UNITS_SPLIT ||
+                           (m->tau_unit_mode == DG_TAU_UNITS_AUTO && (int)units.size() / 4 < kMinTauUnits);
+    if (use_split) units = split;
     m->tau_n_units[k] = (int)units.size() / 4;
+    for (size_t u = 0; u < units.size(); u += 4) m->tau_n_shared[k] += units[u + 2] > 1;
+    m->tau_n_units_split[k] = (int)split.size() / 4;
     DG_CUDA(upload(&m->tau_units[k], units.data(), units.size()));
+    DG_CUDA(upload(&m->tau_units_split[k], split.data(), split.size()));
   }
   return DG_OK;
 }
@@ -903,10 +915,9 @@ dg_status dg_tau_estimate(dg_mesh* m, const double* q, const double* r_p, const 
     if (sweep[s] < 1 || sweep[s] > DG_MAX_ORDER) return DG_ERR_ARG;
   const bool fp32 = flags & DG_TAU_FP32, acc = flags & DG_TAU_ACCUM_MAX;
   if (flags & DG_TAU_ISOLATED) {
-    size_t need = dgk::tau_smem_bytes(m, fp32);
     int limit = 0;
     DG_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
-    if (need + 256 > (size_t)limit) return DG_ERR_UNSUPPORTED;   // static reduction buffers
+    if (dgk::tau_smem_bytes(m, fp32, limit) > (size_t)limit) return DG_ERR_UNSUPPORTED;
     dg_status st = build_tau_bank(m);
     if (st != DG_OK) return st;
     if (!r_p && fp32 && !m->d_rp32) DG_CUDA(cudaMalloc(&m->d_rp32, sizeof(float) * 5 * m->n_nodes));
@@ -979,7 +990,29 @@ dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_o
   std::swap(*static_cast<dg_mesh_impl*>(m), *c);
   m->stream = s;
   std::swap(m->d_err, c->d_err);   // keep the sticky error word of the mesh
+  m->tau_unit_mode = c->tau_unit_mode;
   destroy_impl(c);
+  return DG_OK;
+}
+
+dg_status dg_set_tau_units(dg_mesh* m, int32_t mode) {
+  if (!m || mode < DG_TAU_UNITS_AUTO || mode > DG_TAU_UNITS_SPLIT) return DG_ERR_ARG;
+  m->tau_unit_mode = mode;
+  if (m->h_sweep.empty()) return DG_OK;
+  // the next isolated sweep rebuilds the units for its list
+  m->h_sweep.clear();
+  return DG_OK;
+}
+
+dg_status dg_tau_units_info(const dg_mesh* m, int32_t max_classes, int32_t* n_classes, int32_t* n_units,
+                            int32_t* n_shared) {
+  if (!m || max_classes < 0 || !n_classes || (max_classes > 0 && (!n_units || !n_shared))) return DG_ERR_ARG;
+  const int nc = m->h_sweep.empty() ? 0 : (int)m->tau_last_units.size();
+  *n_classes = nc;
+  for (int k = 0; k < nc && k < max_classes; ++k) {
+    n_units[k] = m->tau_last_units[k];
+    n_shared[k] = m->tau_last_shared[k];
+  }
   return DG_OK;
 }
 

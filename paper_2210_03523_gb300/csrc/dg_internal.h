@@ -92,7 +92,10 @@ cudaError_t tau_combine(dg_mesh_impl* m, dg_mesh_impl* coarse, const double* r_p
 // mode 0: interpolate up / L2-project down (set_orders); mode 1: interpolate (restriction)
 cudaError_t project_orders(dg_mesh_impl* m, const int32_t* d_new_orders, const int64_t* d_new_off,
                            const double* q_old, double* q_new, int mode);
-size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32);
+// shared memory (dynamic + static bytes) of the isolated sweep's largest
+// class, each class in the layout it runs with on a device offering `limit`
+// bytes per block (the compact layout where the other does not fit)
+size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32, int limit);
 // CFL reduction only: *bits = max over nodes of the inverse time-step scale
 // (as the bit pattern of a non-negative double)
 cudaError_t max_dt_bits(dg_mesh_impl* m, const double* q, unsigned long long* bits);
@@ -195,6 +198,11 @@ struct dg_mesh_impl {
   // entries sharing (N2, N3) [N2, N3, first, count], entries [sweep index, N1]
   std::vector<int32_t*> tau_units;
   std::vector<int> tau_n_units;
+  std::vector<int> tau_n_shared;       // units of a class holding two groups or more (the xi3 restriction shared)
+  std::vector<int32_t*> tau_units_split;   // the same units with one group each (the compact FP64 layout)
+  std::vector<int> tau_n_units_split;
+  std::vector<int> tau_last_units, tau_last_shared;   // per class, the units the last isolated sweep ran
+  int tau_unit_mode = DG_TAU_UNITS_AUTO;
   int32_t* d_tgroups = nullptr;
   int32_t* d_tgentries = nullptr;
   int n_tgroups = 0, n_tgentries = 0;

@@ -20,10 +20,12 @@
 //                      per-element maxima.
 // FP64 throughout, except tau_kernel<float>.
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <utility>
 
 #include "dg_internal.h"
@@ -52,6 +54,8 @@ constexpr int kFaceWarps = 4;          // faces per CTA in the face kernels
 constexpr int kVolThreads = 256;
 constexpr int kTauChunk = 16;   // at most this many sweep entries share the two barriers of a tau chunk
 constexpr int kTauThreads = 128;
+constexpr int kTauRefElems = 32;   // elements of a tau tile at most (tiles of <= 256 nodes, 8 nodes an element)
+constexpr int kTauRefStride = 16;  // floats of one element's reference record
 
 // ------------------------------------------------------------------ helpers
 // offset (in face nodes) of face f inside an element's surface block
@@ -1532,6 +1536,8 @@ struct TauParams {
   int n_list;
   T* rp_scratch;            // isolated R^P at P, state layout, when rp is null
   T gamma, mu, Pr, Rgas, kappa_R;
+  double gamma64;           // gamma in FP64 (the FP32 sweep's reference records)
+  int compact;              // shared-memory layout with A3 and A1 aliased (units of one group only)
   unsigned* err;
   int n_items_all, n_groups, n_gentries;   // lengths of items, groups and gentries
 };
@@ -1597,12 +1603,11 @@ __device__ __forceinline__ void euler_fluxes(T gm1, const T q[5], T f[3][5]) {
   }
 }
 
+// Navier-Stokes viscous flux of the tau sweep from the primitive variables
+// (1/rho, u, p) and the gradient g[v*3+c] = d q_v / d x_c.
 template <typename T>
-__device__ void viscous_t(const TauParams<T>& P, const T q[5], const T g[15], T fv[3][5]) {
+__device__ void viscous_prim(const TauParams<T>& P, T ir, const T u[3], T pr, const T g[15], T fv[3][5]) {
   T gm1 = P.gamma - (T)1;
-  T ir = (T)1 / q[0];
-  T u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
-  T pr = gm1 * (q[4] - (T)0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
   T pir = pr * ir;
   T half_u2 = (T)0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   T du[3][3], dT[3];
@@ -1621,6 +1626,15 @@ __device__ void viscous_t(const TauParams<T>& P, const T q[5], const T g[15], T 
     fv[d][3] = tau[2];
     fv[d][4] = u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2] + P.kappa_R * dT[d];
   }
+}
+
+template <typename T>
+__device__ void viscous_t(const TauParams<T>& P, const T q[5], const T g[15], T fv[3][5]) {
+  T gm1 = P.gamma - (T)1;
+  T ir = (T)1 / q[0];
+  T u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  T pr = gm1 * (q[4] - (T)0.5 * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  viscous_prim(P, ir, u, pr, g, fv);
 }
 
 template <typename T>
@@ -1731,14 +1745,95 @@ __device__ __forceinline__ const T* tile_met(const TauParams<T>& P, int e, int P
   return P.metric + P.bank_off[e] + 10 * bank_combo_offset(P1, P2, N1, N2, N3);
 }
 
+// The FP32 sweep works on deviations from a per-element reference state, the
+// state at the element's first node, q_r (FP64).  A flux field that is
+// constant over the element has zero divergence: the rows of the GL
+// derivative sum to zero and the curl-form metrics satisfy the discrete
+// metric identities (sum_i D_i (J a^i) = 0).  So R^N(I q) is unchanged, in exact
+// arithmetic, when the constant f(q_r) is taken out of every flux, and the
+// restriction reproduces constants, so I q = q_r + I (q - q_r).  The FP32
+// arithmetic then rounds relative to the deviations q' = q - q_r (formed in
+// FP64) and to the flux deviations f(q) - f(q_r), not to the state itself: at
+// Mach 0.1 the pressure p ~ 143 and the energy flux ~ 500 u of the pulse
+// otherwise put a floor of FP32 rounding under every tau.
+// Reference record (FP32 values formed in FP64): rho_r, u_f (the reference
+// velocity rounded to FP32), m_r, c0 = m_r - u_f rho_r, c1 = (gamma-1) E_r -
+// (gamma-1)/2 rho_r |u_f|^2 - p_f, h_f = E_r + p_f, |u_f|^2, p_f (the
+// reference pressure rounded to FP32).  With rho = rho_r + rho',
+//   u - u_f  = (c0 + m' - u_f rho') / rho,
+//   p - p_f  = c1 + (gamma-1) (E' - rho' |u_f|^2 / 2 - rho (u_f.u' + |u'|^2/2)),
+// and the flux deviations (the constants m_r,d, m_r u_f,d + p_f, h u_f,d
+// dropped): mass m'_d, momentum m_r u'_d + m' u_d + p' e_d, energy
+// h u'_d + (E' + p') u_d.
+enum { kRefRho = 0, kRefU = 1, kRefM = 4, kRefC0 = 7, kRefC1 = 10, kRefH = 11, kRefU2 = 12, kRefP = 13 };
+
+// The reference record of an element from its first node (state layout at
+// q + 5 off_e, n nodes), in FP64.
+__device__ __forceinline__ void tau_ref_make(const double* q, int n, double gm1, float* ref) {
+  const double r = q[0], E = q[4 * n];
+  const double m[3] = {q[n], q[2 * n], q[3 * n]};
+  double uf[3], u2 = 0.0, mu = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const float f = (float)(m[c] / r);
+    uf[c] = f;
+    u2 += uf[c] * uf[c];
+    mu += m[c] * m[c];
+    ref[kRefU + c] = f;
+    ref[kRefM + c] = (float)m[c];
+    ref[kRefC0 + c] = (float)(m[c] - uf[c] * r);
+  }
+  const float pf = (float)(gm1 * (E - 0.5 * mu / r));
+  ref[kRefRho] = (float)r;
+  ref[kRefC1] = (float)(gm1 * E - 0.5 * gm1 * r * u2 - (double)pf);
+  ref[kRefH] = (float)(E + (double)pf);
+  ref[kRefU2] = (float)u2;
+  ref[kRefP] = pf;
+}
+
+// Primitive variables of the deviation form at one node: 1/rho, u (full),
+// u' = u - u_f and p' = p - p_f from the deviations d = q - q_r.
+__device__ __forceinline__ void dev_primitive(float gm1, const float d[5], const float* ref, float& ir, float u[3],
+                                              float ud[3], float& pd) {
+  const float rho = ref[kRefRho] + d[0];
+  ir = 1.0f / rho;
+  float uu = 0.0f, u2 = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    ud[c] = (ref[kRefC0 + c] + d[1 + c] - ref[kRefU + c] * d[0]) * ir;
+    u[c] = ref[kRefU + c] + ud[c];
+    uu += ref[kRefU + c] * ud[c];
+    u2 += ud[c] * ud[c];
+  }
+  pd = ref[kRefC1] + gm1 * (d[4] - 0.5f * d[0] * ref[kRefU2] - rho * (uu + 0.5f * u2));
+}
+
+// Euler flux deviations f_d(q) - f_d(q_r) at one node (deviation form above)
+// from the node's primitive deviations.
+__device__ __forceinline__ void dev_fluxes(const float d[5], const float* ref, const float u[3], const float ud[3],
+                                           float pd, float f[3][5]) {
+  const float ep = d[4] + pd;
+  for (int k = 0; k < 3; ++k) {
+    f[k][0] = d[1 + k];
+    for (int c = 0; c < 3; ++c) f[k][1 + c] = ref[kRefM + c] * ud[k] + d[1 + c] * u[k];
+    f[k][1 + k] += pd;
+    f[k][4] = ref[kRefH] * ud[k] + ep * u[k];
+  }
+}
+
+__device__ __forceinline__ void euler_fluxes_dev(float gm1, const float d[5], const float* ref, float f[3][5]) {
+  float ir, u[3], ud[3], pd;
+  dev_primitive(gm1, d, ref, ir, u, ud, pd);
+  dev_fluxes(d, ref, u, ud, pd, f);
+}
+
 // Contravariant Euler fluxes Ft^i = J a^i . f at one node into F (stride n):
 // the tau sweep's one flux routine, shared by R^P and every coarse residual so
 // that R^N at N = P reproduces R^P bit for bit (tau at N = P is then exactly
 // 0).  AXIS: J a^i = (J a^i_i) e_i.
 template <typename T, bool AFFINE, bool AXIS>
-__device__ __forceinline__ void tau_flux(T gm1, const T* met, int n, int p, const T q[5], T* F) {
+__device__ __forceinline__ void tau_flux(T gm1, const T* met, int n, int p, const T q[5], const float* ref, T* F) {
   T f[3][5];
-  euler_fluxes(gm1, q, f);
+  if constexpr (std::is_same<T, float>::value) euler_fluxes_dev(gm1, q, ref, f);   // q: deviations q - q_r
+  else euler_fluxes(gm1, q, f);
   for (int i = 0; i < 3; ++i) {
     if (AXIS) {
       const T a = met_at(met, AFFINE, n, p, 4 * i);
@@ -1777,12 +1872,19 @@ __device__ __forceinline__ void tau_grad_store(const T* basis, const T* met, int
 // Navier-Stokes contravariant fluxes J a^i . (f - f_v) at node p
 template <typename T, bool AFFINE>
 __device__ __forceinline__ void tau_ns_flux(const TauParams<T>& P, T gm1, const T* met, int n, int p, const T q[5],
-                                            const T* G, T* F) {
+                                            const float* ref, const T* G, T* F) {
   T f[3][5];
-  euler_fluxes(gm1, q, f);
   T g[15], fv[3][5];
   for (int c = 0; c < 15; ++c) g[c] = G[c * n + p];
-  viscous_t(P, q, g, fv);
+  if constexpr (std::is_same<T, float>::value) {   // q: deviations q - q_r; G: the gradient of q - q_r, that of q
+    float ir, u[3], ud[3], pd;
+    dev_primitive(gm1, q, ref, ir, u, ud, pd);
+    dev_fluxes(q, ref, u, ud, pd, f);
+    viscous_prim(P, ir, u, ref[kRefP] + pd, g, fv);
+  } else {
+    euler_fluxes(gm1, q, f);
+    viscous_t(P, q, g, fv);
+  }
   for (int d = 0; d < 3; ++d)
     for (int v = 0; v < 5; ++v) f[d][v] -= fv[d][v];
   for (int i = 0; i < 3; ++i) {
@@ -1830,7 +1932,7 @@ __device__ __forceinline__ void tau_node_norms(const T* basis, const T* met, int
 // e's R to Rout + 5*off_e, [5][n].
 template <typename T, bool AFFINE, bool NS, bool AXIS>
 __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int cnt, int P1, int P2, int N1, int N2,
-                                  int N3, const T* X, int xs, T* Ft, T* Gs, T* Rout) {
+                                  int N3, const T* X, int xs, const float* refs, T* Ft, T* Gs, T* Rout) {
   const int n1 = N1 + 1, n2 = N2 + 1, n3 = N3 + 1, n = n1 * n2 * n3, pts = cnt * n;
   const T gm1 = P.gamma - (T)1;
   const MeshView& m = P.m;
@@ -1855,8 +1957,9 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
     const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, N1, N2, N3);
     T q[5];
     for (int v = 0; v < 5; ++v) q[v] = X[el * xs + v * n + p];
-    if (NS) tau_ns_flux<T, AFFINE>(P, gm1, met, n, p, q, Gs + el * 15 * n, Ft + el * 15 * n);
-    else tau_flux<T, AFFINE, AXIS>(gm1, met, n, p, q, Ft + el * 15 * n + p);
+    const float* ref = std::is_same<T, float>::value ? refs + kTauRefStride * el : nullptr;
+    if (NS) tau_ns_flux<T, AFFINE>(P, gm1, met, n, p, q, ref, Gs + el * 15 * n, Ft + el * 15 * n);
+    else tau_flux<T, AFFINE, AXIS>(gm1, met, n, p, q, ref, Ft + el * 15 * n + p);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < pts; t += blockDim.x) {
@@ -1867,6 +1970,42 @@ __device__ void tau_tile_residual(const TauParams<T>& P, const int32_t* els, int
     tau_node_residual<T, AFFINE>(P.basis, met, n1, n2, n3, p, Ft + el * 15 * n, r, J);
     const int64_t o = m.off[e];
     for (int v = 0; v < 5; ++v) Rout[5 * o + v * n + p] = r[v];
+  }
+  __syncthreads();
+}
+
+// Element el's reference record (FP32 sweep; the FP64 sweep has none).
+template <typename T>
+__device__ __forceinline__ const float* tau_ref_of(const float* refs, int el) {
+  return std::is_same<T, float>::value ? refs + kTauRefStride * el : nullptr;
+}
+
+// Stages a tile's q^P (fields 0..4) and, with_rp, R^P (fields 5..9) in
+// shared memory, [el][10][nP] at X, read once from global memory.  FP64: the
+// values as they are.  FP32: q^P as deviations from the element's
+// first-node state, subtracted in FP64 before the rounding, with each
+// element's reference record in refs (the deviation form of tau_ref_make);
+// R^P (the isolated residual, which the constant drops out of) as it is.
+template <typename T>
+__device__ void tau_stage(const TauParams<T>& P, const int32_t* els, int cnt, int nP, bool with_rp, T* X,
+                          float* refs) {
+  constexpr bool DEV = std::is_same<T, float>::value;
+  const MeshView& m = P.m;
+  if (DEV)
+    for (int el = threadIdx.x; el < cnt; el += blockDim.x)
+      tau_ref_make(P.q + 5 * m.off[els[el]], nP, P.gamma64 - 1.0, refs + kTauRefStride * el);
+  for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
+    const int el = fdiv(t, nP), p = t - el * nP;
+    const int64_t o5 = 5 * m.off[els[el]];
+    const double* qe = P.q + o5;
+    T* x = X + el * 10 * nP + p;
+    for (int v = 0; v < 5; ++v) x[v * nP] = DEV ? (T)(qe[v * nP + p] - qe[v * nP]) : (T)qe[v * nP + p];
+    if (with_rp) {
+      if (P.rp)
+        for (int v = 0; v < 5; ++v) x[(5 + v) * nP] = (T)P.rp[o5 + v * nP + p];
+      else
+        for (int v = 0; v < 5; ++v) x[(5 + v) * nP] = P.rp_scratch[o5 + v * nP + p];
+    }
   }
   __syncthreads();
 }
@@ -1909,12 +2048,12 @@ __device__ __forceinline__ void tau_chunk_item(const int2* gent, int first, int 
 template <typename T, bool AFFINE, bool NS, bool AXIS>
 __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float Ref[std::is_same<T, float>::value ? kTauRefElems : 1][kTauRefStride];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int S = P.S;
-  T* A1 = sm + 20 * S;
-  T* Ft = A1 + 10 * S;
+  T* A1 = P.compact ? sm : sm + 20 * S;
+  T* Ft = sm + (P.compact ? 20 : 30) * S;
   T* Gs = Ft + 15 * S;
-  const MeshView& m = P.m;
   for (int li = blockIdx.x; li < P.n_list; li += gridDim.x) {
     WorkItem w;
     if (!take_item(P.m, P.items, P.ilist[li], P.n_items_all, P.elist, 0, w)) continue;
@@ -1931,13 +2070,15 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
       }
     }
     if (P.rp) continue;
-    for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
-      const int el = fdiv(t, nP), p = t - el * nP;
-      const int64_t o = m.off[els[el]];
-      for (int v = 0; v < 5; ++v) A1[el * 10 * nP + v * nP + p] = (T)P.q[5 * o + v * nP + p];
+#ifdef DG_BOUNDS_CHECK
+    if (std::is_same<T, float>::value && cnt > kTauRefElems) {   // one reference record per element
+      if (threadIdx.x == 0) flag_index(P.m);
+      continue;
     }
-    __syncthreads();
-    tau_tile_residual<T, AFFINE, NS, AXIS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, Ft, Gs, P.rp_scratch);
+#endif
+    tau_stage(P, els, cnt, nP, false, A1, &Ref[0][0]);
+    tau_tile_residual<T, AFFINE, NS, AXIS>(P, els, cnt, P1, P2, P1, P2, P3, A1, 10 * nP, &Ref[0][0], Ft, Gs,
+                                           P.rp_scratch);
   }
 }
 
@@ -1952,12 +2093,20 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
   T* sm = reinterpret_cast<T*>(smem_raw);
   typedef typename Bits<T>::type B;
   __shared__ B na2[2][kVolThreads], nb2[2][kVolThreads];   // per-element norms, two entries in flight
+  __shared__ float Ref[std::is_same<T, float>::value ? kTauRefElems : 1][kTauRefStride];
   const int S = P.S;     // tile capacity in nodes (max count * n_P of the class)
-  T* A3 = sm;            // [el][10][pts3]  q^P, R^P restricted in xi3
-  T* A2 = A3 + 10 * S;   // [el][10][pts2]  ... in xi2, xi3
-  T* A1 = A2 + 10 * S;   // [el][10][nN]    I q^P (0..4), I R^P (5..9) at N
-  T* Ft = A1 + 10 * S;   // [el][15][nN]
-  T* Gs = Ft + 15 * S;   // [el][15][nN]    (NS only: the Euler launch allocates 45 S)
+  // [el][10][nP] q^P and R^P staged (ST); restricted in xi3 (A3: [el][10][pts3]),
+  // in xi2 and xi3 (A2: [el][10][pts2]), at N (A1: [el][XF][nN], I q^P and / or
+  // I R^P); fluxes Ft and (NS) gradients Gs [el][15][nN].  Layout (units of S
+  // values): A3 0-10, A2 10-20, ST and A1 20-30, Ft 30-45, Gs 45-60.  The
+  // compact layout (units of one group) reuses what is dead by then: A3 0-10,
+  // ST 10-20 then A2, A1 0-10 once A3 is read, Ft 20-35, Gs 35-50.
+  T* A3 = sm;
+  T* ST = sm + (P.compact ? 10 : 20) * S;
+  T* A2 = sm + 10 * S;
+  T* A1 = P.compact ? sm : sm + 20 * S;
+  T* Ft = sm + (P.compact ? 20 : 30) * S;
+  T* Gs = Ft + 15 * S;
   const MeshView& m = P.m;
   for (int ui = blockIdx.x; ui < P.n_list; ui += gridDim.x) {
     const int4 u = P.units[ui];
@@ -1965,7 +2114,10 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
     if (!take_item(P.m, P.items, u.x, P.n_items_all, P.elist, 0, w)) continue;
     if (bad_tile(P.m, w, P.S) || bad_group(P, w, u.y)) continue;
 #ifdef DG_BOUNDS_CHECK
-    if (w.count > kVolThreads) {   // one norm slot per element and chunk entry
+    // one norm slot per element and chunk entry; one reference record per
+    // element (FP32); the compact layout holds one group
+    if (w.count > kVolThreads || (std::is_same<T, float>::value && w.count > kTauRefElems) ||
+        (P.compact && u.z != 1)) {
       if (threadIdx.x == 0) flag_index(P.m);
       continue;
     }
@@ -1974,23 +2126,18 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
     const int cnt = w.count;
     const int P1 = w.n1, P2 = w.n2, P3 = w.n3, n1 = P1 + 1, n2 = P2 + 1, n3 = P3 + 1, nP = n1 * n2 * n3;
     const int N3 = P.groups[u.y].y, c3 = N3 + 1, n12 = n1 * n2;
-    const T* rpS = P.rp_scratch;
-    {  // xi3 straight from q^P and R^P in global memory, once for the unit's groups
+    tau_stage(P, els, cnt, nP, true, ST, &Ref[0][0]);   // q^P (FP32: deviations) and R^P, once per unit
+    {  // xi3, once for the unit's groups
       const T* I3 = P.basis + c_boff.I[P3][N3];
       const int per = n12 * c3;
       for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
         const int el = fdiv(t, per), x = t - el * per, k = fdiv(x, n12), ij = x - k * n12;
-        const int64_t o = m.off[els[el]];
+        const T* src = ST + el * 10 * nP + ij;
         T acc[10];
         for (int c = 0; c < 10; ++c) acc[c] = 0;
         for (int mm = 0; mm < n3; ++mm) {
           const T wk = I3[k * n3 + mm];
-          const int src = ij + n12 * mm;
-          for (int v = 0; v < 5; ++v) acc[v] += wk * (T)P.q[5 * o + v * nP + src];
-          if (P.rp)
-            for (int v = 0; v < 5; ++v) acc[5 + v] += wk * (T)P.rp[5 * o + v * nP + src];
-          else
-            for (int v = 0; v < 5; ++v) acc[5 + v] += wk * rpS[5 * o + v * nP + src];
+          for (int c = 0; c < 10; ++c) acc[c] += wk * src[c * nP + n12 * mm];
         }
         for (int c = 0; c < 10; ++c) A3[el * 10 * per + c * per + x] = acc[c];
       }
@@ -2074,7 +2221,8 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
           for (int c = 0; c < 10; ++c) X[c * nN] = acc[c];
         } else {
           const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
-          tau_flux<T, AFFINE, AXIS>(gm1, met, nN, x, acc, Ft + 15 * (base + el * nN) + x);
+          tau_flux<T, AFFINE, AXIS>(gm1, met, nN, x, acc, tau_ref_of<T>(&Ref[0][0], el),
+                                    Ft + 15 * (base + el * nN) + x);
           for (int v = 0; v < 5; ++v) X[v * nN] = acc[5 + v];   // I R^P
         }
       }
@@ -2107,7 +2255,8 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
           const T* X = A1 + XF * (base + el * nN);
           T q[5];
           for (int v = 0; v < 5; ++v) q[v] = X[v * nN + p];
-          tau_ns_flux<T, AFFINE>(P, gm1, met, nN, p, q, Gs + 15 * (base + el * nN), Ft + 15 * (base + el * nN));
+          tau_ns_flux<T, AFFINE>(P, gm1, met, nN, p, q, tau_ref_of<T>(&Ref[0][0], el), Gs + 15 * (base + el * nN),
+                                 Ft + 15 * (base + el * nN));
         }
         __syncthreads();
       }
@@ -2613,16 +2762,33 @@ cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev)
   return cudaGetLastError();
 }
 
-// Shared memory of the isolated sweep for a class of elements with at most
-// S nodes: restriction buffers A3, A2, A1 (10 S each) and fluxes (15 S), plus
-// the BR1 gradient (15 S) for Navier-Stokes.
-size_t tau_smem_for(int S, bool ns, bool fp32) {
-  return (size_t)(ns ? 60 : 45) * S * (fp32 ? sizeof(float) : sizeof(double));
+// Dynamic shared memory of the isolated sweep for a class of elements with at
+// most S nodes: restriction buffers A3, A2, A1 / staging (10 S each) and
+// fluxes (15 S), plus the BR1 gradient (15 S) for Navier-Stokes; the compact
+// layout (units of one group) needs 10 S less of the restriction buffers and
+// A1 within A3's place.
+size_t tau_smem_for(int S, bool ns, bool fp32, bool compact) {
+  const int fields = compact ? (ns ? 50 : 35) : (ns ? 60 : 45);
+  return (size_t)fields * S * (fp32 ? sizeof(float) : sizeof(double));
 }
 
-size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32) {
+// Static shared memory of the sweep kernel: the double-buffered norm slots,
+// the FP32 reference records, and the bytes the compiler may add.
+size_t tau_static_bytes(bool fp32) {
+  return 2 * 2 * kVolThreads * (fp32 ? sizeof(unsigned) : sizeof(unsigned long long)) +
+         (fp32 ? kTauRefElems : 1) * kTauRefStride * sizeof(float) + 256;
+}
+
+// The compact layout where the other does not fit the device.
+bool tau_use_compact(int S, bool ns, bool fp32, int limit) {
+  return tau_smem_for(S, ns, fp32, false) + tau_static_bytes(fp32) > (size_t)limit;
+}
+
+size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32, int limit) {
   size_t mx = 0;
-  for (auto& c : m->tau_classes) mx = std::max(mx, tau_smem_for(c.S, m->phys.eqs == DG_NAVIER_STOKES, fp32));
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  for (auto& c : m->tau_classes)
+    mx = std::max(mx, tau_smem_for(c.S, ns, fp32, tau_use_compact(c.S, ns, fp32, limit)) + tau_static_bytes(fp32));
   return mx;
 }
 
@@ -2638,16 +2804,26 @@ static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
   P.elist = m->d_elist;
   P.groups = reinterpret_cast<const int4*>(m->d_tgroups);
   P.gentries = reinterpret_cast<const int2*>(m->d_tgentries);
+  int limit = 0;
+  if ((err = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device))) return err;
+  m->tau_last_units.assign(m->tau_classes.size(), 0);
+  m->tau_last_shared.assign(m->tau_classes.size(), 0);
   // prologue over every class first, then the sweep units of every class
   for (int phase = 0; phase < 2; ++phase) {
     for (size_t k = 0; k < m->tau_classes.size(); ++k) {
       const auto& c = m->tau_classes[k];
+      const bool compact = tau_use_compact(c.S, ns, fp32, limit);   // then units of one group each
       P.S = c.S;
+      P.compact = compact;
       P.ilist = c.d_list;
-      P.units = reinterpret_cast<const int4*>(m->tau_units[k]);
-      P.n_list = phase == 0 ? c.n : m->tau_n_units[k];
+      P.units = reinterpret_cast<const int4*>(compact ? m->tau_units_split[k] : m->tau_units[k]);
+      P.n_list = phase == 0 ? c.n : (compact ? m->tau_n_units_split[k] : m->tau_n_units[k]);
+      if (phase == 1) {
+        m->tau_last_units[k] = P.n_list;
+        m->tau_last_shared[k] = compact ? 0 : m->tau_n_shared[k];
+      }
       if (P.n_list == 0) continue;
-      const size_t smem = tau_smem_for(c.S, ns, fp32);
+      const size_t smem = tau_smem_for(c.S, ns, fp32, compact);
       const int grid = grid_for(P.n_list, 16);
 #define DG_TAU_CASE(AFF, NSV, AXV)                                                             \
   if (phase == 0) {                                                                             \
@@ -2684,6 +2860,7 @@ cudaError_t tau_isolated(dg_mesh_impl* m, const double* q, const double* r_p, co
     P.Pr = m->phys.Pr;
     P.Rgas = m->phys.Rgas;
     P.kappa_R = m->phys.kappa_R;
+    P.gamma64 = m->phys.gamma;
     P.err = m->d_err;
     P.bank_off = m->d_taugeo_off;
   };
@@ -2759,25 +2936,32 @@ static_assert(DG_NOALLOC_SURF_DOUBLES == (4u << 20), "fixed face-buffer size");
 static __device__ __align__(256) double g_noalloc_surf[DG_NOALLOC_SURF_DOUBLES];
 
 // Device address of g_noalloc_surf on device dev.  In host code the array's
-// name is only a host-side stand-in, so the address is looked up once per
-// device with that device current (the caller's current device) and cached.
-static double* noalloc_surf_address(int dev, cudaError_t* err) {
-  static double* addr[64] = {};
+// name is only a host-side stand-in, so the address is looked up with that
+// device current (the caller's current device).  Outside stream capture every
+// call looks it up again, so an address never outlives the context it came
+// from (a cudaDeviceReset in the caller makes a new one); while the stream is
+// being captured the address of the last lookup on this device is used.  The
+// per-device entries are atomics: two host threads may make their first call
+// at the same time.
+static std::atomic<double*> g_noalloc_addr[64];
+
+static double* noalloc_surf_address(int dev, cudaStream_t stream, cudaError_t* err) {
   *err = cudaSuccess;
   if (dev < 0 || dev >= 64) {
     *err = cudaErrorInvalidDevice;
     return nullptr;
   }
-  if (!addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_surf);
-    if (e != cudaSuccess) {
-      *err = e;
-      return nullptr;
-    }
-    addr[dev] = static_cast<double*>(p);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((*err = cudaStreamIsCapturing(stream, &cs)) != cudaSuccess) return nullptr;
+  if (cs != cudaStreamCaptureStatusNone) {
+    double* p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!p) *err = cudaErrorStreamCaptureUnsupported;   // no lookup made on this device before the capture
+    return p;
   }
-  return addr[dev];
+  void* p = nullptr;
+  if ((*err = cudaGetSymbolAddress(&p, g_noalloc_surf)) != cudaSuccess) return nullptr;
+  g_noalloc_addr[dev].store(static_cast<double*>(p), std::memory_order_release);
+  return static_cast<double*>(p);
 }
 
 extern "C" dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double* r) {
@@ -2789,7 +2973,7 @@ extern "C" dg_status dg_residual_noalloc(dg_mesh* mesh, const double* q, double*
   if (cudaGetDevice(&dev) != cudaSuccess) return DG_ERR_CUDA;
   if (dev != mesh->device) return DG_ERR_ARG;                      // the mesh's device must be current
   cudaError_t err;
-  double* surf = noalloc_surf_address(dev, &err);
+  double* surf = noalloc_surf_address(dev, mesh->stream, &err);
   if (!surf) return DG_ERR_CUDA;
   // face pass: every element-face node of the buffer is written (interior
   // faces for both sides, boundary faces for theirs) before the volume pass

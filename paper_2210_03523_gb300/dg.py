@@ -26,6 +26,7 @@ DG_MAX_ORDER = 8
 DG_EXTRAP_DECOUPLED = 0x1
 DG_EXTRAP_ACCUM_MAX = 0x2
 DG_ADVANCE_EAGER = 0x1
+DG_TAU_UNITS_AUTO, DG_TAU_UNITS_GROUPED, DG_TAU_UNITS_SPLIT = 0, 1, 2
 KERNELS = {"face_flux": 0, "face_qhat": 1, "gradient": 2, "volume": 3, "max_dt": 4, "tau": 5, "tau_combine": 6,
            "project": 7, "select": 8, "extrap": 9, "mortar": 10, "adjoint": 11}
 STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_NOMEM", 3: "DG_ERR_CUDA", 4: "DG_ERR_UNSUPPORTED",
@@ -104,6 +105,8 @@ def _lib():
             "dg_profile_enable": [vp, C.c_int],
             "dg_profile_read": [vp, C.c_int, C.POINTER(C.c_double), i64p],
             "dg_launch_count": [vp, i64p],
+            "dg_set_tau_units": [vp, C.c_int32],
+            "dg_tau_units_info": [vp, C.c_int32, i32p, i32p, i32p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -119,7 +122,7 @@ def exported_symbols():
             "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc",
             "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles",
             "dg_residual_vjp", "dg_rk_step_vjp", "dg_wall_force", "dg_wall_force_vjp", "dg_state_write",
-            "dg_state_info", "dg_state_read", "dg_debug_set_index"]
+            "dg_state_info", "dg_state_read", "dg_debug_set_index", "dg_set_tau_units", "dg_tau_units_info"]
 
 
 def _check(st, where):
@@ -246,9 +249,12 @@ class Mesh:
 
     def residual_noalloc(self, q, r):
         """dg_residual_noalloc: same residual, face scratch in the library's fixed
-        device array; r must be a caller-allocated state-layout tensor."""
+        device array; r must be a caller-allocated state-layout tensor.  The
+        C function needs the mesh's device current; this call makes it so."""
+        import torch
         self._check_state(q, r)
-        _check(_lib().dg_residual_noalloc(self.h, _ptr(q), _ptr(r)), "dg_residual_noalloc")
+        with torch.cuda.device(self.device):
+            _check(_lib().dg_residual_noalloc(self.h, _ptr(q), _ptr(r)), "dg_residual_noalloc")
         return r
 
     def max_dt(self, q, cfl, dt=None):
@@ -282,6 +288,19 @@ class Mesh:
         _check(_lib().dg_tau_estimate(self.h, _ptr(q), _ptr(r_p), sw.ctypes.data_as(C.POINTER(C.c_int32)), ns, flags,
                                       _ptr(map_new), _ptr(map_trad)), "dg_tau_estimate")
         return map_new, map_trad
+
+    def set_tau_units(self, mode):
+        """dg_set_tau_units: DG_TAU_UNITS_AUTO, _GROUPED or _SPLIT (how the
+        isolated sweep's entries are split into units of work)."""
+        _check(_lib().dg_set_tau_units(self.h, int(mode)), "dg_set_tau_units")
+
+    def tau_units_info(self):
+        """dg_tau_units_info: per shared-memory size class of the last isolated
+        sweep, (units, units holding two or more groups)."""
+        nu, ns_ = (C.c_int32 * 8)(), (C.c_int32 * 8)()
+        nc = C.c_int32()
+        _check(_lib().dg_tau_units_info(self.h, 8, C.byref(nc), nu, ns_), "dg_tau_units_info")
+        return [(nu[k], ns_[k]) for k in range(min(nc.value, 8))]
 
     def set_orders(self, new_orders, q_old):
         import torch

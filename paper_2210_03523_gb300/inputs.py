@@ -277,6 +277,24 @@ def pointwise_state(coords, orders, fn) -> np.ndarray:
     return q
 
 
+def smooth_state(coords, orders, phys: Physics, amp=0.05, width=0.3) -> np.ndarray:
+    """A smooth state in which every conservative variable varies: the
+    density pulse of the given width on top of velocity and pressure
+    variations of relative size amp (periods 2 and 1 across [-1, 1]^3)."""
+    u0 = np.array(phys.qinf[1:4]) / phys.qinf[0]
+    p0 = (phys.gamma - 1.0) * (phys.qinf[4] - 0.5 * phys.qinf[0] * float(u0 @ u0))
+    s = max(float(np.linalg.norm(u0)), 1.0)
+
+    def fn(x, y, z):
+        rho = pulse_primitive(x, y, z, 0.5, width)
+        u = u0[0] + amp * s * np.sin(np.pi * x) * np.cos(np.pi * z)
+        v = u0[1] + amp * s * np.cos(np.pi * y + 0.3) * np.sin(2 * np.pi * x)
+        w = u0[2] + amp * s * np.sin(np.pi * (z - y))
+        p = p0 * (1.0 + amp * np.cos(np.pi * x + 0.7) * np.cos(np.pi * y) * np.sin(np.pi * z + 0.2))
+        return np.stack([rho, rho * u, rho * v, rho * w, p / (phys.gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)])
+    return pointwise_state(coords, orders, fn)
+
+
 def seeded_perturbation(n_scalars, seed, amplitude) -> np.ndarray:
     return amplitude * np.random.default_rng(seed).standard_normal(n_scalars)
 

@@ -54,6 +54,32 @@ def test_noalloc_residual_matches_dg_residual_twice(torch_cuda, name):
     assert m.get_error() == 0
 
 
+def test_noalloc_allocates_nothing(torch_cuda):
+    """Free device memory (cudaMemGetInfo) and torch's allocator are unchanged
+    across calls, after one warm-up call (the first launch of a kernel may
+    load its code); the results of calls before and after agree."""
+    torch = torch_cuda
+    from paper_2210_03523_gb300 import dg
+    mi = I.workload("pulse16mixed")
+    m = dg.Mesh(mi)
+    om, q = _state(mi, (0.1, 0.0, -0.1))
+    qg = torch.from_numpy(q).cuda()
+    out = torch.empty_like(qg)
+    m.residual_noalloc(qg, out)
+    torch.cuda.synchronize()
+    first = out.clone()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        m.residual_noalloc(qg, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.equal(out, first)
+    assert m.get_error() == 0
+
+
 def test_noalloc_refuses_what_does_not_fit(torch_cuda):
     torch = torch_cuda
     from paper_2210_03523_gb300 import dg
