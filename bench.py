@@ -195,21 +195,30 @@ def mortar_counts(mi, axis_aligned=False):
     return float(flops), float(bytes_)
 
 
-def tau_counts(orders, sweep):
+# FP32 operations of the deviation-form Euler flux at one node of the tau
+# sweep (tau_flux_nm): primitives rho, 1/rho, u' (12), u (3), u_f.u' and
+# |u'|^2 (12), p' (9) = 38; flux deviations: momentum 27 + 3, energy 9 + 1 = 40.
+TAU_FLUX_FLOPS = 78
+
+
+def tau_counts(orders, sweep, axis_aligned=False):
     """Algorithmic FP32 flops of one isolated tau sweep (Euler): per element,
-    the isolated R^P (as the volume term: 12+16+75+10 sum(P_i+1)+6 per node),
-    then per applicable entry N: restriction of 10 fields in xi3, xi2, xi1
-    (2*10*(P3+1) per output node of each pass; the xi3 / xi2 passes only when
-    N3 / (N2,N3) change), the coarse isolated residual, and the two norms
-    (5*(1 + 4) per node)."""
+    the isolated R^P (per node: the flux deviations TAU_FLUX_FLOPS, the
+    contravariant fluxes 75, or 15 on an axis-aligned box, the derivative
+    10 sum(P_i+1), the 1/J scaling 6), then per applicable entry N:
+    restriction of 10 fields in xi3, xi2, xi1 (2*10*(P_i+1) per output node of
+    each pass; the xi3 / xi2 passes only when N3 / (N2,N3) change), the coarse
+    isolated residual (as R^P) and the two norms (tau~ 5, |.| and max 10, J w
+    and its products 3 + 5, max 5)."""
     o = np.asarray(orders, dtype=np.int64).reshape(-1, 3)
     sw = np.asarray(sweep, dtype=np.int64).reshape(-1, 3)
+    node = TAU_FLUX_FLOPS + (15 if axis_aligned else 75) + 6
     total = 0.0
     for P in {tuple(r) for r in o}:
         cnt = int((o == P).all(1).sum())
         P1, P2, P3 = P
         nP = (P1 + 1) * (P2 + 1) * (P3 + 1)
-        f = nP * (109 + 10 * (P1 + P2 + P3 + 3))
+        f = nP * (node + 10 * (P1 + P2 + P3 + 3))
         cur3 = cur2 = None
         for N1, N2, N3 in sw:
             if N1 > P1 or N2 > P2 or N3 > P3:
@@ -222,7 +231,7 @@ def tau_counts(orders, sweep):
                 cur2 = N2
             nN = (N1 + 1) * (N2 + 1) * (N3 + 1)
             f += 20 * (P1 + 1) * nN
-            f += nN * (109 + 10 * (N1 + N2 + N3 + 3) + 25)
+            f += nN * (node + 10 * (N1 + N2 + N3 + 3) + 28)
         total += cnt * f
     return total
 
@@ -541,13 +550,18 @@ def rooflines(workload, r, sm_mhz):
         if not k.startswith("_"):
             v["share"] = round(v["total_ms"] / ktot, 4) if ktot else None
     tau_k_ms, tau_k_n = kern["tau"]
-    tflops = tau_counts(mi.orders, r["sweep"])
+    tflops = tau_counts(mi.orders, r["sweep"], axis_aligned=axis)
+    tflops_gen = tau_counts(mi.orders, r["sweep"], axis_aligned=False)
     fp32_peak = N_SM * FP32_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     tau_s = tau_k_ms / r["psteps"] * 1e-3 if tau_k_n else None      # one sweep per step
-    tau_roof = {"kernel": "tau_kernel<float> + tau_prologue_kernel", "bound": "alu",
+    tau_roof = {"kernel": "tau_euler_kernel<float> + tau_euler_prologue_kernel" if mi.phys.eqs == 0 else
+                          "tau_kernel<float> + tau_prologue_kernel (Navier-Stokes)", "bound": "alu",
                 "achieved": tflops / tau_s / 1e12 if tau_s else None, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": tflops / tau_s / 1e12 / fp32_peak if tau_s else None, "sweep_ms": tau_s * 1e3 if tau_s else None,
                 "algorithmic_flops_per_sweep": tflops,
+                "frac_general_count": tflops_gen / tau_s / 1e12 / fp32_peak if tau_s else None,
+                "flop_count": ("axis-aligned box: diagonal contravariant fluxes" if axis else "general affine count")
+                              + "; FP32 deviation-form fluxes",
                 "peak_source": f"FP32: {N_SM} SMs x {FP32_FMA_PER_CLK_PER_SM} FFMA/clk x 2 x {sm_mhz:.0f} MHz"}
     return dominant, others, tau_roof, kernels_json
 

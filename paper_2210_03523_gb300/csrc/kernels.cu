@@ -2042,9 +2042,11 @@ __device__ __forceinline__ void tau_chunk_item(const int2* gent, int first, int 
   }
 }
 
-// Prologue of the isolated sweep, one tile per CTA iteration: the isolated
-// R^P of every element (into the scratch, unless the caller gave R^P), and
-// -1 in the maps for every sweep entry the element's orders cannot reach.
+// Prologue of the isolated Navier-Stokes sweep (field-major tiles; the Euler
+// sweep runs tau_euler_prologue_kernel), one tile per CTA iteration: the
+// isolated R^P of every element (into the scratch, unless the caller gave
+// R^P), and -1 in the maps for every sweep entry the element's orders cannot
+// reach.
 template <typename T, bool AFFINE, bool NS, bool AXIS>
 __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2082,8 +2084,9 @@ __global__ void __launch_bounds__(kVolThreads) tau_prologue_kernel(TauParams<T> 
   }
 }
 
-// The sweep proper, one unit per CTA iteration: a tile and the groups of one
-// N3 (a group is the sweep entries sharing (N2, N3)).  The unit restricts
+// The isolated Navier-Stokes sweep (the Euler sweep runs tau_euler_kernel),
+// one unit per CTA iteration: a tile and the groups of one N3 (a group is the
+// sweep entries sharing (N2, N3)).  The unit restricts
 // q^P and R^P in xi3 once, each group in xi2, then runs the group's entries
 // in chunks: restriction in xi1, coarse isolated residual fused with both
 // tau norms, map store.
@@ -2286,6 +2289,345 @@ __global__ void __launch_bounds__(kVolThreads) tau_kernel(TauParams<T> P) {
       map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
     }
     __syncthreads();
+    }   // groups of the unit
+  }
+}
+
+// ------------------------------------------------- isolated sweep, Euler
+// The Euler sweep keeps its shared-memory tiles node-major: the staged and
+// restricted tiles hold the 10 fields of a node (q^P or its deviations, then
+// R^P) at a stride of TS values, the fluxes the 15 values J a^i . f_v of a
+// node at FS, the restricted R^P at N its 5 at RS.  Every field of a node
+// then sits at a fixed offset from one address.  R^P (prologue) and every R^N
+// of the sweep go through the same flux and derivative routines, so that R^N
+// at N = P reproduces R^P bit for bit and tau there is exactly 0.
+template <typename T>
+struct TauTiles {
+  static constexpr int TS = 11;   // odd strides: one field of 32 consecutive nodes spans 32 banks
+  static constexpr int FS = 15;
+  static constexpr int RS = 5;
+  // slot of J a^d . f_v within a node's flux record
+  __host__ __device__ static constexpr int fo(int d, int v) { return 5 * d + v; }
+};
+
+// One output node of a restriction pass: acc[c] = sum_m w[m] src[m stride + c]
+// over the nt taps m of an interpolation row w (10 fields c, node-major).
+// The tap loop runs to a runtime count: one loop body for every order keeps
+// the kernel's code small (fully unrolled per tap count it ran 11-19% slower,
+// with more instruction-fetch stalls).
+template <typename T>
+__device__ __forceinline__ void restrict_node(int nt, const T* __restrict__ w, const T* src, int stride, T acc[10]) {
+#pragma unroll
+  for (int c = 0; c < 10; ++c) acc[c] = 0;
+  for (int m = 0; m < nt; ++m) {
+    const T wm = w[m];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) acc[c] += wm * src[c];
+    src += stride;
+  }
+}
+
+// acc[v] += sum_m d[m] J a^dir . f_v of the node at src + m stride, over the
+// nt taps m (5 variables v; src points at node records)
+template <typename T>
+__device__ __forceinline__ void deriv_line(int nt, const T* __restrict__ d, const T* src, int dir, int stride,
+                                           T acc[5]) {
+  typedef TauTiles<T> L;
+  for (int m = 0; m < nt; ++m) {
+    const T dm = d[m];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] += dm * src[L::fo(dir, v)];
+    src += stride;
+  }
+}
+
+// sum_i D^(i) Ft^i at node (i, j, k) of a c1 x c2 x c3 element whose flux
+// records start at Fb (node-major, FS values a node)
+template <typename T>
+__device__ __forceinline__ void tau_div_nm(const T* basis, const T* Fb, int c1, int c2, int c3, int i, int j, int k,
+                                           T acc[5]) {
+  constexpr int FS = TauTiles<T>::FS;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) acc[v] = 0;
+  deriv_line(c1, basis + c_boff.D[c1 - 1] + i * c1, Fb + FS * (c1 * (j + c2 * k)), 0, FS, acc);
+  deriv_line(c2, basis + c_boff.D[c2 - 1] + j * c2, Fb + FS * (i + c1 * c2 * k), 1, FS * c1, acc);
+  deriv_line(c3, basis + c_boff.D[c3 - 1] + k * c3, Fb + FS * (i + c1 * j), 2, FS * c1 * c2, acc);
+}
+
+// The contravariant Euler fluxes J a^i . f_v at one node into its flux
+// record F (FP32: the flux deviations of the deviations q in tau_flux's sense).
+template <typename T, bool AFFINE, bool AXIS>
+__device__ __forceinline__ void tau_flux_nm(T gm1, const T* met, int n, int p, const T q[5], const float* ref, T* F) {
+  T f[3][5];
+  if constexpr (std::is_same<T, float>::value) euler_fluxes_dev(gm1, q, ref, f);
+  else euler_fluxes(gm1, q, f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (AXIS) {
+      const T a = met_at(met, AFFINE, n, p, 4 * i);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) F[TauTiles<T>::fo(i, v)] = a * f[i][v];
+    } else {
+      const T ja0 = met_at(met, AFFINE, n, p, 3 * i), ja1 = met_at(met, AFFINE, n, p, 3 * i + 1),
+              ja2 = met_at(met, AFFINE, n, p, 3 * i + 2);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) F[TauTiles<T>::fo(i, v)] = ja0 * f[0][v] + ja1 * f[1][v] + ja2 * f[2][v];
+    }
+  }
+}
+
+// Stages a tile's q^P (fields 0..4; FP32: deviations from the element's
+// first-node state, with its reference record in refs) and, with_rp, R^P
+// (fields 5..9) node-major, [el][p][TS] at X, each value read once.
+template <typename T>
+__device__ void tau_stage_nm(const TauParams<T>& P, const int32_t* els, int cnt, int nP, bool with_rp, T* X,
+                             float* refs) {
+  constexpr bool DEV = std::is_same<T, float>::value;
+  const MeshView& m = P.m;
+  if (DEV)
+    for (int el = threadIdx.x; el < cnt; el += blockDim.x)
+      tau_ref_make(P.q + 5 * m.off[els[el]], nP, P.gamma64 - 1.0, refs + kTauRefStride * el);
+  for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
+    const int el = fdiv(t, nP), p = t - el * nP;
+    const int64_t o5 = 5 * m.off[els[el]];
+    const double* qe = P.q + o5;
+    T* x = X + TauTiles<T>::TS * t;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) x[v] = DEV ? (T)(qe[v * nP + p] - qe[v * nP]) : (T)qe[v * nP + p];
+    if (with_rp) {
+      if (P.rp) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) x[5 + v] = (T)P.rp[o5 + v * nP + p];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) x[5 + v] = P.rp_scratch[o5 + v * nP + p];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Prologue of the isolated Euler sweep, one tile per CTA iteration: the
+// isolated R^P of every element into the scratch (unless the caller gave
+// R^P), and -1 in the maps for every sweep entry the element's orders
+// cannot reach.  Layout: the staged q^P at ST, the fluxes at Ft.
+template <typename T, bool AFFINE, bool AXIS>
+__global__ void __launch_bounds__(kVolThreads, sizeof(T) == 4 ? 4 : 2) tau_euler_prologue_kernel(TauParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float Ref[std::is_same<T, float>::value ? kTauRefElems : 1][kTauRefStride];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  constexpr int TS = TauTiles<T>::TS, FS = TauTiles<T>::FS;
+  const int S = P.S;
+  T* ST = sm;            // [el][p][TS]
+  T* Ft = sm + TS * S;   // [el][p][FS]
+  const T gm1 = P.gamma - (T)1;
+  const MeshView& m = P.m;
+  for (int li = blockIdx.x; li < P.n_list; li += gridDim.x) {
+    WorkItem w;
+    if (!take_item(P.m, P.items, P.ilist[li], P.n_items_all, P.elist, 0, w)) continue;
+    if (bad_tile(P.m, w, P.S)) continue;
+    const int32_t* els = P.elist + w.first;
+    const int cnt = w.count;
+    const int P1 = w.n1, P2 = w.n2, P3 = w.n3, n1 = P1 + 1, n2 = P2 + 1, n3 = P3 + 1, nP = n1 * n2 * n3;
+    for (int t = threadIdx.x; t < cnt * P.n_sweep; t += blockDim.x) {
+      const int el = fdiv(t, P.n_sweep), s = t - el * P.n_sweep;
+      if (P.sweep[3 * s] > P1 || P.sweep[3 * s + 1] > P2 || P.sweep[3 * s + 2] > P3) {
+        const int64_t idx = (int64_t)els[el] * P.n_sweep + s;
+        if (P.map_new) P.map_new[idx] = (T)-1;
+        if (P.map_trad) P.map_trad[idx] = (T)-1;
+      }
+    }
+    if (P.rp) continue;
+#ifdef DG_BOUNDS_CHECK
+    if (std::is_same<T, float>::value && cnt > kTauRefElems) {   // one reference record per element
+      if (threadIdx.x == 0) flag_index(P.m);
+      continue;
+    }
+#endif
+    tau_stage_nm(P, els, cnt, nP, false, ST, &Ref[0][0]);
+    for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
+      const int el = fdiv(t, nP), p = t - el * nP;
+      const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, P1, P2, P3);
+      T q[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) q[v] = ST[TS * t + v];
+      tau_flux_nm<T, AFFINE, AXIS>(gm1, met, nP, p, q, tau_ref_of<T>(&Ref[0][0], el), Ft + FS * t);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt * nP; t += blockDim.x) {
+      const int el = fdiv(t, nP), p = t - el * nP;
+      const int pj = fdiv(p, n1), k = fdiv(pj, n2), i = p - pj * n1, j = pj - k * n2;
+      const int e = els[el];
+      const T* met = tile_met<T, AFFINE>(P, e, P1, P2, P1, P2, P3);
+      T acc[5];
+      tau_div_nm(P.basis, Ft + FS * (el * nP), n1, n2, n3, i, j, k, acc);
+      const T iJ = -(T)1 / met_at(met, AFFINE, nP, p, 9);
+      const int64_t o5 = 5 * m.off[e];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) P.rp_scratch[o5 + v * nP + p] = mul_rn(acc[v], iJ);
+    }
+    __syncthreads();
+  }
+}
+
+// The isolated Euler sweep, one unit per CTA iteration (a tile and the
+// groups (N2, N3) of one N3): q^P and R^P staged once, restricted in xi3 once
+// for the unit, in xi2 once per group, then the group's entries in chunks
+// (tau_chunk): (1) previous chunk's norms stored, this chunk's slots
+// cleared, restriction in xi1 and the fluxes of every coarse node; (2) the
+// GL derivative, tau~ = I R^P - R^N and both norms.  Shared memory in S node
+// slots of TS, RS or FS values: A3, A2, then A1 and Ft, with the staged tile
+// ST over A1 and Ft (it is read only by the xi3 pass, before them); compact
+// (units of one group): A3 and then A1, ST and then A2, Ft.
+template <typename T, bool AFFINE, bool AXIS>
+__global__ void __launch_bounds__(kVolThreads, sizeof(T) == 4 ? 4 : 2) tau_euler_kernel(TauParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  typedef typename Bits<T>::type B;
+  __shared__ B na2[2][kVolThreads], nb2[2][kVolThreads];   // per-element norms, two chunks in flight
+  __shared__ float Ref[std::is_same<T, float>::value ? kTauRefElems : 1][kTauRefStride];
+  constexpr int TS = TauTiles<T>::TS, FS = TauTiles<T>::FS, RS = TauTiles<T>::RS;
+  const int S = P.S;
+  T* A3 = sm;
+  T* A2 = sm + TS * S;
+  T* A1 = P.compact ? sm : sm + 2 * TS * S;
+  T* Ft = P.compact ? sm + 2 * TS * S : A1 + RS * S;
+  T* ST = P.compact ? A2 : A1;
+  const MeshView& m = P.m;
+  const T gm1 = P.gamma - (T)1;
+  for (int ui = blockIdx.x; ui < P.n_list; ui += gridDim.x) {
+    const int4 u = P.units[ui];
+    WorkItem w;
+    if (!take_item(P.m, P.items, u.x, P.n_items_all, P.elist, 0, w)) continue;
+    if (bad_tile(P.m, w, P.S) || bad_group(P, w, u.y)) continue;
+#ifdef DG_BOUNDS_CHECK
+    // one norm slot per element and chunk entry; one reference record per
+    // element (FP32); the compact layout holds one group
+    if (w.count > kVolThreads || (std::is_same<T, float>::value && w.count > kTauRefElems) ||
+        (P.compact && u.z != 1)) {
+      if (threadIdx.x == 0) flag_index(P.m);
+      continue;
+    }
+#endif
+    const int32_t* els = P.elist + w.first;
+    const int cnt = w.count;
+    const int P1 = w.n1, P2 = w.n2, P3 = w.n3, n1 = P1 + 1, n2 = P2 + 1, n3 = P3 + 1, nP = n1 * n2 * n3;
+    const int N3 = P.groups[u.y].y, c3 = N3 + 1, n12 = n1 * n2;
+    tau_stage_nm(P, els, cnt, nP, true, ST, &Ref[0][0]);
+    {  // xi3, once for the unit's groups: A3[el][i + n1 (j + n2 k)]
+      const T* I3 = P.basis + c_boff.I[P3][N3];
+      const int per = n12 * c3;
+      for (int t = threadIdx.x; t < cnt * per; t += blockDim.x) {
+        const int el = fdiv(t, per), x = t - el * per, k = fdiv(x, n12), ij = x - k * n12;
+        T acc[10];
+        restrict_node(n3, I3 + k * n3, ST + TS * (el * nP + ij), TS * n12, acc);
+        T* o = A3 + TS * t;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) o[c] = acc[c];
+      }
+      __syncthreads();
+    }
+    for (int gi = u.y; gi < u.y + u.z; ++gi) {   // the groups (N2, N3) of this N3, N2 ascending
+      if (gi > u.y && bad_group(P, w, gi)) continue;
+      const int4 g = P.groups[gi];      // N2, N3, first entry, entry count
+      const int N2 = g.x, c2 = N2 + 1, c23 = c2 * c3;
+#ifdef DG_BOUNDS_CHECK
+      if (g.y != N3) {
+        if (threadIdx.x == 0) flag_index(m);
+        continue;
+      }
+#endif
+      const int pin = n12 * c3, per2 = n1 * c23;
+      {  // xi2: A2[el][i + n1 (j' + c2 k')]
+        const T* I2 = P.basis + c_boff.I[P2][N2];
+        for (int t = threadIdx.x; t < cnt * per2; t += blockDim.x) {
+          const int el = fdiv(t, per2), x = t - el * per2, xj = fdiv(x, n1), k = fdiv(xj, c2), i = x - xj * n1,
+                    j = xj - k * c2;
+          T acc[10];
+          restrict_node(n2, I2 + j * n2, A3 + TS * (el * pin + i + n12 * k), TS * n1, acc);
+          T* o = A2 + TS * t;
+#pragma unroll
+          for (int c = 0; c < 10; ++c) o[c] = acc[c];
+        }
+        __syncthreads();
+      }
+      const T* w2 = P.basis + c_boff.W[N2];
+      const T* w3 = P.basis + c_boff.W[N3];
+      const int2* gent = P.gentries + g.z;      // (sweep index, N1) per entry
+      int prev_first = 0, prev_k = 0, buf = 0;
+      for (int first = 0; first < g.w;) {
+        int total;
+        const int k = tau_chunk(gent, first, g.w, P1, cnt, c23, S, total);   // the same in every thread
+        const int nsl = (prev_k > k ? prev_k : k) * cnt;
+        for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) {
+          const int j = fdiv(sl, cnt), el = sl - j * cnt;
+          if (j < prev_k) {
+            const int2 pe = gent[prev_first + j];
+            if (pe.y <= P1) {
+              const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
+              map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
+              map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
+            }
+          }
+          if (j < k) {
+            na2[buf][sl] = 0;
+            nb2[buf][sl] = 0;
+          }
+        }
+        // (1) xi1 restriction and the fluxes of every coarse node of the chunk
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+          int base, j, M1;
+          tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
+          const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
+          const int el = fdiv(tt, nN), x = tt - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
+          T acc[10];
+          restrict_node(n1, P.basis + c_boff.I[P1][M1] + i * n1, A2 + TS * (el * per2 + n1 * jk), TS, acc);
+          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
+          tau_flux_nm<T, AFFINE, AXIS>(gm1, met, nN, x, acc, tau_ref_of<T>(&Ref[0][0], el), Ft + FS * t);
+          T* o = A1 + RS * t;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) o[v] = acc[5 + v];    // I R^P
+        }
+        __syncthreads();
+        // (2) derivative, tau~ and both norms
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+          int base, j, M1;
+          tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
+          const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
+          const int el = fdiv(tt, nN), p = tt - el * nN, pj = fdiv(p, c1), kk = fdiv(pj, c2), i = p - pj * c1,
+                    jj = pj - kk * c2;
+          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
+          T acc[5];
+          tau_div_nm(P.basis, Ft + FS * (base + el * nN), c1, c2, c3, i, jj, kk, acc);
+          const T J = met_at(met, AFFINE, nN, p, 9);
+          const T iJ = -(T)1 / J;
+          const T Jw = J * P.basis[c_boff.W[M1] + i] * w2[jj] * w3[kk];
+          const T* ir = A1 + RS * t;
+          T a = 0, b = 0;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const T d = ir[v] - mul_rn(acc[v], iJ);   // tau~ = I R^P - R^N(I q^P)
+            a = tmax(a, (T)fabs(d));
+            b = tmax(b, (T)fabs(Jw * d));
+          }
+          smax_bits(na2[buf] + j * cnt + el, a);
+          smax_bits(nb2[buf] + j * cnt + el, b);
+        }
+        __syncthreads();
+        prev_first = first;
+        prev_k = k;
+        buf ^= 1;
+        first += k;
+      }
+      for (int sl = threadIdx.x; sl < prev_k * cnt; sl += blockDim.x) {
+        const int j = fdiv(sl, cnt), el = sl - j * cnt;
+        const int2 pe = gent[prev_first + j];
+        if (pe.y > P1) continue;
+        const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
+        map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
+        map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
+      }
+      __syncthreads();
     }   // groups of the unit
   }
 }
@@ -2768,7 +3110,11 @@ cudaError_t max_dt(dg_mesh_impl* m, const double* q, double cfl, double* dt_dev)
 // layout (units of one group) needs 10 S less of the restriction buffers and
 // A1 within A3's place.
 size_t tau_smem_for(int S, bool ns, bool fp32, bool compact) {
-  const int fields = compact ? (ns ? 50 : 35) : (ns ? 60 : 45);
+  // Euler: node-major tiles, A3 and A2 (TS values a node slot each), A1 (RS)
+  // and Ft (FS); the compact layout has A1 inside A3's place
+  const int TS = fp32 ? TauTiles<float>::TS : TauTiles<double>::TS;
+  const int FS = fp32 ? TauTiles<float>::FS : TauTiles<double>::FS;
+  const int fields = ns ? (compact ? 50 : 60) : (compact ? 2 * TS + FS : 2 * TS + TauTiles<float>::RS + FS);
   return (size_t)fields * S * (fp32 ? sizeof(float) : sizeof(double));
 }
 
@@ -2833,12 +3179,21 @@ static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
     if ((err = allow_smem(tau_kernel<T, AFF, NSV, AXV>, smem))) return err;                     \
     tau_kernel<T, AFF, NSV, AXV><<<grid, kVolThreads, smem, m->stream>>>(P);                    \
   }
-      if (m->axis && !ns) { DG_TAU_CASE(true, false, true) }
-      else if (m->affine && !ns) { DG_TAU_CASE(true, false, false) }
+#define DG_TAU_EULER(AFF, AXV)                                                                  \
+  if (phase == 0) {                                                                             \
+    if ((err = allow_smem(tau_euler_prologue_kernel<T, AFF, AXV>, smem))) return err;           \
+    tau_euler_prologue_kernel<T, AFF, AXV><<<grid, kVolThreads, smem, m->stream>>>(P);          \
+  } else {                                                                                      \
+    if ((err = allow_smem(tau_euler_kernel<T, AFF, AXV>, smem))) return err;                    \
+    tau_euler_kernel<T, AFF, AXV><<<grid, kVolThreads, smem, m->stream>>>(P);                   \
+  }
+      if (m->axis && !ns) { DG_TAU_EULER(true, true) }
+      else if (m->affine && !ns) { DG_TAU_EULER(true, false) }
+      else if (!ns) { DG_TAU_EULER(false, false) }
       else if (m->affine) { DG_TAU_CASE(true, true, false) }
-      else if (!ns) { DG_TAU_CASE(false, false, false) }
       else { DG_TAU_CASE(false, true, false) }
 #undef DG_TAU_CASE
+#undef DG_TAU_EULER
       if ((err = cudaGetLastError())) return err;
     }
   }
