@@ -1115,13 +1115,50 @@ __device__ __forceinline__ void div_tile(const double* __restrict__ F, int n1, i
   }
 }
 
+// The off-diagonal part of div_tile: the GL derivative matrix has a zero
+// diagonal at interior nodes and D_00 = -D_NN = -N(N+1)/4 at the end nodes,
+// which the volume kernel applies with the surface lift (it multiplies the
+// same end-node flux).  Each node runs the n-1 taps m != i in the rotated
+// order i+1, ..., n-1, 0, ..., i-1, so the lanes of a warp (consecutive i)
+// issue the same number of FP64 instructions: one DFMA per variable and tap
+// fewer than with the diagonal, n-1 instead of n.
+template <int NVAR>
+__device__ __forceinline__ void div_tile_offdiag(const double* __restrict__ F, int n1, int n2, int n3, int i, int j,
+                                                 int k, const double* D1, const double* D2, const double* D3,
+                                                 double out[NVAR]) {
+  const int n = n1 * n2 * n3;
+  for (int v = 0; v < NVAR; ++v) out[v] = 0.0;
+  const double* F1 = F + n1 * (j + n2 * k);
+  const double* F2 = F + NVAR * n + i + n1 * n2 * k;
+  const double* F3 = F + 2 * NVAR * n + i + n1 * j;
+  for (int t = 1, mm = i; t < n1; ++t) {
+    mm = mm + 1 == n1 ? 0 : mm + 1;
+    const double d = __ldg(D1 + i * n1 + mm);
+    for (int v = 0; v < NVAR; ++v) out[v] += d * F1[v * n + mm];
+  }
+  for (int t = 1, mm = j; t < n2; ++t) {
+    mm = mm + 1 == n2 ? 0 : mm + 1;
+    const double d = __ldg(D2 + j * n2 + mm);
+    for (int v = 0; v < NVAR; ++v) out[v] += d * F2[v * n + n1 * mm];
+  }
+  for (int t = 1, mm = k; t < n3; ++t) {
+    mm = mm + 1 == n3 ? 0 : mm + 1;
+    const double d = __ldg(D3 + k * n3 + mm);
+    for (int v = 0; v < NVAR; ++v) out[v] += d * F3[v * n + n1 * n2 * mm];
+  }
+}
+
 // Volume residual of one work item per iteration (a tile of same-order
 // elements), in four shared-memory phases:
 //  1. per node: primitive variables, contravariant fluxes Ft^i = J a^i . f
 //     (AXIS: J a^i = (J a^i_i) e_i, so Ft^i = J a^i_i f_i);
-//  2. per node: sum-factorised GL derivative sum_i D^(i) Ft^i -> V;
+//  2. per node: the off-diagonal part of the sum-factorised GL derivative
+//     sum_i D^(i) Ft^i -> V (div_tile_offdiag);
 //  3. per face node, one direction at a time (the two faces of a direction
-//     touch disjoint nodes): V += +-(F* - Ft^dir)/w_end, with every lane busy;
+//     touch disjoint nodes): the surface lift +-(F* - Ft^dir)/w_end and the
+//     derivative's end-node diagonal D_ee Ft^dir = -+Ft^dir/(2 w_end)
+//     together, V += +-(F* / w_end - Ft^dir / (2 w_end)), with every lane
+//     busy; the isolated residual (F* = Ft) keeps the diagonal alone;
 //  4. per node: R = -V/J, written or fused into the RK3 stage.
 template <bool AFFINE, bool AXIS, bool NS>
 __global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
@@ -1194,32 +1231,34 @@ __global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
       const int el = s / n, p = s - el * n;
       const int i = p % n1, j = (p / n1) % n2, k = p / (n1 * n2);
       double vol[5];
-      div_tile<5>(Ft + (size_t)el * 15 * n, n1, n2, n3, i, j, k, D1, D2, D3, vol);
+      div_tile_offdiag<5>(Ft + (size_t)el * 15 * n, n1, n2, n3, i, j, k, D1, D2, D3, vol);
       double* Vv = V + (size_t)el * 5 * n;
       for (int v = 0; v < 5; ++v) Vv[v * n + p] = vol[v];
     }
     __syncthreads();
     // phase 3
-    if (!P.isolated) {
-      for (int dir = 0; dir < 3; ++dir) {
-        const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, fsz = na * nb;
-        const int Nd = dir == 0 ? w.n1 : (dir == 1 ? w.n2 : w.n3);
-        const double inv_w = 0.5 * Nd * (Nd + 1);   // 1 / w_0 = 1 / w_N = N(N+1)/2
-        const int per_el = 2 * fsz;
-        for (int s = threadIdx.x; s < w.count * per_el; s += blockDim.x) {
-          const int el = s / per_el, r = s - el * per_el;
-          const int side = r / fsz, fn = r - side * fsz;
-          const int f = 2 * dir + side;
-          const int p = face_vidx(n1, n2, n3, f, fn % na, fn / na);
+    for (int dir = 0; dir < 3; ++dir) {
+      const int na = dir == 0 ? n2 : n1, nb = dir == 2 ? n2 : n3, fsz = na * nb;
+      const int Nd = dir == 0 ? w.n1 : (dir == 1 ? w.n2 : w.n3);
+      const double inv_w = 0.5 * Nd * (Nd + 1);   // 1 / w_0 = 1 / w_N = N(N+1)/2
+      const int per_el = 2 * fsz;
+      for (int s = threadIdx.x; s < w.count * per_el; s += blockDim.x) {
+        const int el = s / per_el, r = s - el * per_el;
+        const int side = r / fsz, fn = r - side * fsz;
+        const int f = 2 * dir + side;
+        const int p = face_vidx(n1, n2, n3, f, fn % na, fn / na);
+        const double* F = Ft + (size_t)el * 15 * n + dir * 5 * n + p;
+        double* Vv = V + (size_t)el * 5 * n + p;
+        const double sg = side ? inv_w : -inv_w;     // the lift's sign and 1 / w_end
+        if (P.isolated) {
+          for (int v = 0; v < 5; ++v) Vv[v * n] += (0.5 * sg) * F[v * n];   // D_ee Ft^dir
+        } else {
           const int e = P.elist[w.first + el];
           const double* Fs = P.surf + 5 * (m.soff[e] + face_offset(n1, n2, n3, f)) + fn;
-          const double* F = Ft + (size_t)el * 15 * n + dir * 5 * n + p;
-          double* Vv = V + (size_t)el * 5 * n + p;
-          const double sg = side ? inv_w : -inv_w;
-          for (int v = 0; v < 5; ++v) Vv[v * n] += sg * (Fs[v * fsz] - F[v * n]);
+          for (int v = 0; v < 5; ++v) Vv[v * n] += sg * Fs[v * fsz] - (0.5 * sg) * F[v * n];
         }
-        __syncthreads();
       }
+      __syncthreads();
     }
     // phase 4
     for (int s = threadIdx.x; s < slots; s += blockDim.x) {
@@ -1229,11 +1268,11 @@ __global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
       const double miJ = -metric<AFFINE>(m.metric, e, o, n, p, 10);
       const double* Vv = V + (size_t)el * 5 * n + p;
       if (P.rk) {
-        const double dt = *P.dt;
+        const double c = *P.dt * miJ;   // dt R = (-dt/J) V
         for (int v = 0; v < 5; ++v) {
           const int64_t idx = 5 * o + v * n + p;
-          const double r = Vv[v * n] * miJ;
-          const double g = P.rk_first ? dt * r : P.rkA * P.g_io[idx] + dt * r;
+          const double dr = c * Vv[v * n];
+          const double g = P.rk_first ? dr : P.rkA * P.g_io[idx] + dr;
           P.g_io[idx] = g;
           P.q_io[idx] = P.q_io[idx] + P.rkB * g;
         }
