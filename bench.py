@@ -78,6 +78,8 @@ def workload_desc(name):
                         "step = 50 RK3 steps + 1 FP32 tau sweep",
         "pulse48uniform": "Euler density pulse, 48^3 periodic straight hexes, P=(5,5,5); step = 50 RK3 steps + 1 "
                           "FP32 tau sweep",
+        "pulse24mixed": "Euler density pulse, 24^3 periodic straight hexes, orders iid U{2..8} (seed 2210); step = "
+                        "50 RK3 steps + 1 FP32 tau sweep",
         "cylinder": "Navier-Stokes flow past a cylinder, Re=100, Ma=0.2, Pr=0.72, 40x24x1 curved O-grid (geometry "
                     "order 3), P=(6,6,1), BR1, no-slip adiabatic wall; step = 50 RK3 steps + 1 FP32 tau sweep",
     }[name]
@@ -959,7 +961,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=["pulse16mixed", "pulse4", "pulse32mixed", "pulse48mixed", "pulse48uniform",
+                    choices=["pulse16mixed", "pulse4", "pulse32mixed", "pulse48mixed", "pulse48uniform", "pulse24mixed",
                              "cylinder", "cylinder_static", "cylinder_dynamic"])
     ap.add_argument("--t-est", type=float, default=0.3, help="cylinder_static: estimation time")
     ap.add_argument("--t-post", type=float, default=0.3, help="cylinder_static: time advanced after adaptation")

@@ -299,15 +299,17 @@ dg_status build_volume_items(dg_mesh_impl* m) {
   }
   m->n_vitems = (int)items.size();
   m->h_vitems = items;
-  // two launches: tiles up to 400 nodes (<= 64 KB of FP64 shared memory,
-  // three CTAs per SM) and larger ones, so that a few 9^3 elements do not set
-  // the occupancy of all the others; in each, the largest tiles first
-  std::vector<std::vector<int32_t>> cl(2);
-  std::vector<int> cS(2, 0);
+  // three launches by tile size, each with shared memory for its largest
+  // tile (20 doubles a node): up to 400 nodes (<= 64 KB, three CTAs per SM),
+  // up to 700 (<= 112 KB, two CTAs per SM) and larger ones (one CTA per SM), so
+  // that a few 9^3 elements do not set the occupancy of all the others; in
+  // each, the largest tiles first
+  std::vector<std::vector<int32_t>> cl(3);
+  std::vector<int> cS(3, 0);
   for (int i = 0; i < (int)items.size(); ++i) {
     const WorkItem& w = items[i];
     const int tile = w.count * (w.n1 + 1) * (w.n2 + 1) * (w.n3 + 1);
-    const int k = tile <= 400 ? 0 : 1;
+    const int k = tile <= 400 ? 0 : (tile <= 700 ? 1 : 2);
     cl[k].push_back(i);
     cS[k] = std::max(cS[k], tile);
   }
@@ -325,7 +327,7 @@ dg_status build_volume_items(dg_mesh_impl* m) {
   m->d_velist = nullptr;
   DG_CUDA(upload(&m->d_vitems, items.data(), items.size()));
   DG_CUDA(upload(&m->d_velist, elist.data(), elist.size()));
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 3; ++k) {
     if (cl[k].empty()) continue;
     dg_mesh_impl::TauClass c{nullptr, (int)cl[k].size(), cS[k]};
     DG_CUDA(upload(&c.d_list, cl[k].data(), cl[k].size()));

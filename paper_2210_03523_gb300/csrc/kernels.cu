@@ -52,6 +52,8 @@ namespace {
 
 constexpr int kFaceWarps = 4;          // faces per CTA in the face kernels
 constexpr int kVolThreads = 256;
+// volume tiles' shared memory above which two CTAs, or one, fit an SM
+constexpr size_t kVolThreeCtaBytes = 400 * 20 * sizeof(double), kVolTwoCtaBytes = 700 * 20 * sizeof(double);
 constexpr int kTauChunk = 16;   // at most this many sweep entries share the two barriers of a tau chunk
 constexpr int kTauThreads = 128;
 constexpr int kTauRefElems = 32;   // elements of a tau tile at most (tiles of <= 256 nodes, 8 nodes an element)
@@ -1160,8 +1162,8 @@ __device__ __forceinline__ void div_tile_offdiag(const double* __restrict__ F, i
 //     together, V += +-(F* / w_end - Ft^dir / (2 w_end)), with every lane
 //     busy; the isolated residual (F* = Ft) keeps the diagonal alone;
 //  4. per node: R = -V/J, written or fused into the RK3 stage.
-template <bool AFFINE, bool AXIS, bool NS>
-__global__ void __launch_bounds__(kVolThreads) volume_kernel(VolParams P) {
+template <bool AFFINE, bool AXIS, bool NS, int THREADS>
+__global__ void __launch_bounds__(THREADS) volume_kernel(VolParams P) {
   extern __shared__ double smem[];
   const MeshView& m = P.m;
   const double gm1 = m.ph.gamma - 1.0;
@@ -2876,9 +2878,21 @@ cudaError_t dispatch_face(dg_mesh_impl* m, const FaceParams& P, size_t smem, int
 
 template <bool AFF, bool AX, bool NSV>
 cudaError_t launch_volume(dg_mesh_impl* m, const VolParams& P, size_t smem, int grid) {
-  cudaError_t err = allow_smem(volume_kernel<AFF, AX, NSV>, smem);
-  if (err) return err;
-  volume_kernel<AFF, AX, NSV><<<grid, kVolThreads, smem, m->stream>>>(P);
+  // Tiles whose shared memory admits two CTAs per SM (401-700 nodes, 20
+  // doubles a node) run 384 threads and those admitting one (more than 700
+  // nodes) 768, so that every class keeps about 24 warps per SM to feed the
+  // FP64 pipe (8 a CTA of 256 threads otherwise).
+  cudaError_t err;
+  if (smem > kVolTwoCtaBytes) {
+    if ((err = allow_smem(volume_kernel<AFF, AX, NSV, 3 * kVolThreads>, smem))) return err;
+    volume_kernel<AFF, AX, NSV, 3 * kVolThreads><<<grid, 3 * kVolThreads, smem, m->stream>>>(P);
+  } else if (smem > kVolThreeCtaBytes) {
+    if ((err = allow_smem(volume_kernel<AFF, AX, NSV, 3 * kVolThreads / 2>, smem))) return err;
+    volume_kernel<AFF, AX, NSV, 3 * kVolThreads / 2><<<grid, 3 * kVolThreads / 2, smem, m->stream>>>(P);
+  } else {
+    if ((err = allow_smem(volume_kernel<AFF, AX, NSV, kVolThreads>, smem))) return err;
+    volume_kernel<AFF, AX, NSV, kVolThreads><<<grid, kVolThreads, smem, m->stream>>>(P);
+  }
   return cudaGetLastError();
 }
 

@@ -309,7 +309,10 @@ def workload(name: str) -> MeshInput:
     pulse32mixed: 32^3, orders iid U{1..6} (seed 2210), a working set above L2;
     cylinder: 40x24x1 curved O-grid, geometry order 3, P=(6,6,1);
     pulse48mixed: 48^3, orders iid U{2..8} (seed 2210);
-    pulse48uniform: 48^3, P=(5,5,5)."""
+    pulse48uniform: 48^3, P=(5,5,5);
+    pulse24mixed: 24^3, orders iid U{2..8} (seed 2210): the 48^3 mesh's order
+    distribution at an eighth of its size (a working set above L2, small
+    enough for multi-pass profiler captures)."""
     if name == "pulse4":
         return box_mesh(4, orders=(4, 4, 4), phys=pulse_physics())
     if name == "pulse16mixed":
@@ -320,6 +323,8 @@ def workload(name: str) -> MeshInput:
         return box_mesh(32, orders=random_orders(32 ** 3, 1, 6, 2210), phys=pulse_physics())
     if name == "pulse48mixed":
         return box_mesh(48, orders=random_orders(48 ** 3, 2, 8, 2210), phys=pulse_physics())
+    if name == "pulse24mixed":
+        return box_mesh(24, orders=random_orders(24 ** 3, 2, 8, 2210), phys=pulse_physics())
     if name == "pulse48uniform":
         return box_mesh(48, orders=(5, 5, 5), phys=pulse_physics())
     raise KeyError(name)
