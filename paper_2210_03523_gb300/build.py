@@ -54,8 +54,8 @@ def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = 
     def comp(src):
         obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
-        if src.endswith(".cpp"):
-            cmd = [cc, *FLAGS, *extra, "-x", "c++", "-c", src, "-o", obj]
+        if src.endswith(".cpp"):   # host code: mesh construction loops run on the host cores (OpenMP)
+            cmd = [cc, *FLAGS, "-Xcompiler", "-fopenmp", *extra, "-x", "c++", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -66,7 +66,8 @@ def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = 
     with cf.ThreadPoolExecutor(max_workers=len(sources())) as ex:
         objs = list(ex.map(comp, sources()))
     tmp = lib + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xcompiler", "-fopenmp"],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, lib)

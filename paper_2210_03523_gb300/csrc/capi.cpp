@@ -382,18 +382,21 @@ dg_status build(dg_mesh_impl* m) {
     }
   } else {
     met.assign(11 * (size_t)m->n_nodes, 0.0);
-    std::vector<double> X, Ja, J;
+    int bad_jacobian = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(| : bad_jacobian)
     for (int e = 0; e < ne; ++e) {
+      std::vector<double> X, Ja, J;
       element_geometry(&m->h_geom[(size_t)e * ng3 * 3], G, &m->h_ord[3 * e], X, Ja, J);
       const int64_t n = m->h_off[e + 1] - m->h_off[e];
       double* dst = &met[11 * m->h_off[e]];
       for (int k = 0; k < 9; ++k) std::copy(Ja.begin() + k * n, Ja.begin() + (k + 1) * n, dst + k * n);
       for (int64_t p = 0; p < n; ++p) {
-        if (!(J[p] > 0.0)) return DG_ERR_ARG;
+        if (!(J[p] > 0.0)) bad_jacobian = 1;
         dst[9 * n + p] = J[p];
         dst[10 * n + p] = 1.0 / J[p];
       }
     }
+    if (bad_jacobian) return DG_ERR_ARG;
   }
   // faces
   std::vector<FaceRec> faces;
@@ -581,8 +584,11 @@ dg_status build_tau_bank(dg_mesh_impl* m) {
     off[e + 1] = off[e] + 10 * s;
   }
   std::vector<double> bank(off[ne]);
-  std::vector<double> X, Ja, J;
+  // elements in parallel on the host cores (the per-order geometry is the
+  // bulk of the first isolated sweep on a curved mesh)
+#pragma omp parallel for schedule(dynamic, 4)
   for (int e = 0; e < ne; ++e) {
+    std::vector<double> X, Ja, J;
     const int* P = &m->h_ord[3 * e];
     int64_t pos = off[e];
     for (int N3 = 1; N3 <= P[2]; ++N3)
@@ -874,8 +880,9 @@ dg_status dg_node_coords(dg_mesh* m, double* xyz) {
   if (!m || !xyz) return DG_ERR_ARG;
   const int ng3 = (m->G + 1) * (m->G + 1) * (m->G + 1);
   std::vector<double> out(3 * (size_t)m->n_nodes);
-  std::vector<double> X, Ja, J;
+#pragma omp parallel for schedule(dynamic, 64)
   for (int e = 0; e < m->n_elem; ++e) {
+    std::vector<double> X, Ja, J;
     element_geometry(&m->h_geom[(size_t)e * ng3 * 3], m->G, &m->h_ord[3 * e], X, Ja, J);
     std::copy(X.begin(), X.end(), out.begin() + 3 * m->h_off[e]);
   }

@@ -326,6 +326,12 @@ class Mesh:
         """the current element orders, host [n_elem, 3] (a copy)"""
         return self._ord.copy()
 
+    def offsets(self):
+        """node offsets of the state layout, host [n_elem + 1] (off_e: element e
+        starts at 5 off_e)"""
+        n = np.prod(self._ord.astype(np.int64) + 1, axis=1)
+        return np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+
     def save_state(self, path, q, t=0.0):
         """Checkpoint: this mesh's orders, the device state q and the time t
         (a float or a device scalar) to a dg_state_write file."""

@@ -1,11 +1,13 @@
-"""The recursive checkpointing of the reversed RK time integration
-(autograd.reverse_steps), on the CPU with a stand-in mesh whose step is a
-small nonlinear map and whose step VJP is that map's exact transposed
-Jacobian: the reversed cotangent equals torch.autograd through the unrolled
-steps for every snapshot budget, each step is reversed at the state it
-started from, the functional's end-of-step callbacks see the trajectory from
-the last step to the first, and the recomputed forward steps follow the
-recursion's count for each budget."""
+"""The checkpointed reversal of the RK time integration
+(autograd.reverse_steps, binomial schedule), on the CPU with a stand-in mesh
+whose step is a small nonlinear map and whose step VJP is that map's exact
+transposed Jacobian: the reversed cotangent equals torch.autograd through the
+unrolled steps for every snapshot budget, each step is reversed at the state
+it started from, the functional's end-of-step callbacks see the trajectory
+from the last step to the first, and the recomputed forward steps are the
+minimum of Griewank's binomial bound for every length and budget."""
+from math import comb
+
 import pytest
 import torch
 
@@ -81,16 +83,48 @@ def test_end_of_step_callbacks_run_last_step_first(snapshots):
                           atol=1e-13)
 
 
-def test_recomputation_falls_as_the_budget_grows():
-    """the forward steps the reverse sweep recomputes: quadratic with no
-    snapshot, about n log2(n) / 2 with enough for the recursion depth"""
-    n = 64
-    costs = {}
-    for s in (0, 1, 2, 6):
-        mesh = StepMesh(3)
-        lam = torch.ones(3, dtype=torch.float64)
-        AG.reverse_steps(mesh, torch.zeros(3, dtype=torch.float64), torch.tensor([0.1], dtype=torch.float64), n, lam, s)
-        costs[s] = mesh.forward_steps
-    assert costs[0] == n * (n - 1) // 2
-    assert costs[0] > costs[1] > costs[2] > costs[6]
-    assert costs[6] == (n // 2) * 6    # log2(64) levels of halves: n/2 steps recomputed per level
+def _griewank(n, snapshots):
+    """The least forward steps that reverse n steps with c = snapshots + 1
+    checkpoints (the start state held too): r n - C(c + r, r - 1) for the least
+    r with C(c + r, c) >= n (Griewank 1992)."""
+    c, r = snapshots + 1, 0
+    while comb(c + r, c) < n:
+        r += 1
+    return r * n - comb(c + r, r - 1) if r else 0
+
+
+@pytest.mark.parametrize("snapshots", [0, 1, 2, 3, 6, 12])
+def test_schedule_meets_the_binomial_bound(snapshots):
+    for n in range(1, 130):
+        assert AG.reversal_cost(n, snapshots) == _griewank(n, snapshots), n
+
+
+@pytest.mark.parametrize("n,snapshots", [(64, 0), (64, 1), (64, 2), (64, 6), (400, 12), (37, 3)])
+def test_recomputed_steps_are_the_schedules(n, snapshots):
+    """the forward steps the reverse sweep actually takes are the schedule's
+    count (the last end state supplied by the forward run)"""
+    mesh = StepMesh(3)
+    lam = torch.ones(3, dtype=torch.float64)
+    q0 = torch.zeros(3, dtype=torch.float64)
+    dt = torch.tensor([0.1], dtype=torch.float64)
+    qn = AG.advance_fixed(StepMesh(3), q0, dt, n)
+    AG.reverse_steps(mesh, q0, dt, n, lam, snapshots, at_end=lambda q, l: None, q_end=qn)
+    assert mesh.forward_steps == AG.reversal_cost(n, snapshots) == _griewank(n, snapshots)
+    if snapshots == 0:
+        assert mesh.forward_steps == n * (n - 1) // 2
+
+
+def test_cylinder_budget_is_far_below_bisection():
+    """400 steps with 12 snapshots (the cylinder adjoint): 1080 recomputed
+    steps, 2.7 n, against the 1664 of recursive bisection (half the interval
+    recomputed at each of its levels)"""
+    assert AG.reversal_cost(400, 12) == 1080
+
+    def bisect(n, s):
+        if n <= 1:
+            return 0
+        if s <= 0:
+            return n * (n - 1) // 2
+        h = n // 2
+        return h + bisect(n - h, s - 1) + bisect(h, s)
+    assert bisect(400, 12) > 1.5 * AG.reversal_cost(400, 12)
