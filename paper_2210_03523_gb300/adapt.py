@@ -59,11 +59,14 @@ class _Stage:
 
 def static_adaptation(mi, q0, *, t0, t_est, dt_e, t_final, cfl, sweep, tau_max, n_min, n_max, jump_rule=0,
                       form="new", isolated=True, fp32=False, targets=None, n_fit=0, decoupled=False, tau_floor=0.0,
-                      stream=None):
+                      stream=None, keep_estimation_state=False):
     """Fig. 2 on the GPU.  mi: a MeshInput; q0: the initial state (host or
     device).  Returns a dict: orders (host), q (device), t, total (device F_max
     map or None), n_estimates, steps (before, after adaptation), ndof (of the
-    adapted orders), ndof_dyn (the step-weighted mean over the run), mesh."""
+    adapted orders), ndof_dyn (the step-weighted mean over the run), mesh;
+    with keep_estimation_state, q_est: a copy of the state at the initial
+    orders when the estimation phase ended (at t_est_state), before the
+    projection."""
     import torch
     m = dg.Mesh(mi, stream=stream)
     q = _to_device(q0, m.device)
@@ -83,13 +86,15 @@ def static_adaptation(mi, q0, *, t0, t_est, dt_e, t_final, cfl, sweep, tau_max, 
         orders = np.array(mi.orders, dtype=np.int32).reshape(-1, 3)
     else:
         orders = m.select_orders(total, lst, tau_max, n_min, n_max, jump_rule)
+    t_est_state = float(t.item())
+    q_est = q.clone() if keep_estimation_state else None
     q = m.set_orders(orders, q)
     g = torch.zeros_like(q)
     n2 = m.advance(q, g, t, t_final, cfl, count=True)
     nd = dg.dg_count_nodes(orders)
     ndyn = (steps * nd0 + n2 * nd) / (steps + n2) if steps + n2 else float(nd)
     return dict(orders=orders, q=q, t=float(t.item()), total=total, n_estimates=n_est, steps=(steps, n2), ndof=nd,
-                ndof_dyn=ndyn, mesh=m)
+                ndof_dyn=ndyn, mesh=m, q_est=q_est, t_est_state=t_est_state)
 
 
 def dynamic_adaptation(mi, q0, *, t0, dt_e, t_final, cfl, sweep, tau_max, n_min, n_max, jump_rule=0,
