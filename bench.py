@@ -109,14 +109,17 @@ def full_sweep_for(orders):
     return I.full_sweep(np.asarray(orders).max(0))
 
 
-# DRAM bytes per launch (one launch per RK stage, the mean of a step's three
-# stages) from ncu captures of these kernels as they stand; the commands and
-# the per-stage figures are in profiles/traffic_mortar_volume_pulse16mixed_pulse32mixed.txt
+# DRAM bytes per RK stage (the launches of one stage summed; the volume
+# kernel the mean of a step's three stages, the mortar kernel a stage that
+# reads the face traces, as all but the first of a replayed batch of steps
+# do) from ncu captures of these kernels as they stand; the commands and the
+# per-launch figures are in profiles/traffic_mortar_volume_pulse32mixed_pulse48mixed.md
 MEASURED_TRAFFIC = {
-    ("pulse16mixed", "mortar"): 16.0e6, ("pulse16mixed", "volume"): 45.9e6,
-    ("pulse32mixed", "mortar"): 442.9e6, ("pulse32mixed", "volume"): 557.3e6,
+    ("pulse32mixed", "mortar"): 299.2e6, ("pulse32mixed", "volume"): 713.0e6,
+    ("pulse48mixed", "mortar"): 2033.6e6, ("pulse48mixed", "volume"): 5362.7e6,
 }
-TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/traffic_mortar_volume_pulse16mixed_pulse32mixed.txt"
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                  "profiles/traffic_mortar_volume_pulse32mixed_pulse48mixed.md")
 
 
 # ------------------------------------------------------------ algorithmic counts
@@ -133,22 +136,23 @@ def is_axis_aligned(mi):
     return True
 
 
-def volume_counts(orders, rk=True, axis_aligned=False):
+def volume_counts(orders, rk=True, axis_aligned=False, traces=True):
     """Algorithmic FP64 flops and HBM bytes of one volume-kernel launch (Euler,
     straight elements, fused RK stage).  Per node: primitive variables 12,
     Cartesian fluxes 16, contravariant fluxes 75, sum-factorised derivative
     10*sum_i(N_i+1), 1/J scaling 6, RK update 25 (axis_aligned: the
     contravariant fluxes are 15, the metric being diagonal); per face node of the
     element's own six faces: lift 15.  Bytes per node: q read 40, G read and
-    write 80, q write 40 (RK) or R write 40; per face node 40 (F* read);
-    per element 80 (metrics)."""
+    write 80, q write 40 (RK) or R write 40; per face node 40 (F* read) and,
+    in an RK stage with traces, 40 (the new state's face trace written for
+    the next stage's mortars); per element 80 (metrics)."""
     o = np.asarray(orders, dtype=np.int64).reshape(-1, 3) + 1
     n = o.prod(1)
     faces = 2 * (o[:, 1] * o[:, 2] + o[:, 0] * o[:, 2] + o[:, 0] * o[:, 1])
     flops = (n * (134 + 10 * o.sum(1)) + 15 * faces).sum() - (0 if rk else (n * 25).sum())
     if axis_aligned:      # diagonal J a^i: the contravariant fluxes take 15 instead of 75
         flops -= (60 * n).sum()
-    bytes_ = ((160 if rk else 80) * n + 40 * faces + 80).sum()
+    bytes_ = ((160 if rk else 80) * n + (80 if rk and traces else 40) * faces + 80).sum()
     return float(flops), float(bytes_)
 
 

@@ -41,8 +41,10 @@ dg_status status_of(cudaError_t e) {
   return e == cudaSuccess ? DG_OK : e == cudaErrorMemoryAllocation ? DG_ERR_NOMEM : DG_ERR_CUDA;
 }
 
-// one step on m->stream: CFL reduction, clip, RK3 (three stages)
-dg_status advance_step(dg_mesh_impl* m, double* q, double* g, double* t) {
+// one step on m->stream: CFL reduction, clip, RK3 (three stages);
+// trace_valid: the step before ran on the same q in this same sequence of
+// launches, so its last stage left q's face traces in the mesh's buffer
+dg_status advance_step(dg_mesh_impl* m, double* q, double* g, double* t, bool trace_valid) {
   unsigned long long* bits = reinterpret_cast<unsigned long long*>(m->d_scratch);
   AdvState* a = reinterpret_cast<AdvState*>(m->d_adv);
   cudaError_t e = dgk::max_dt_bits(m, q, bits);
@@ -51,7 +53,7 @@ dg_status advance_step(dg_mesh_impl* m, double* q, double* g, double* t) {
   advance_clip_kernel<<<1, 1, 0, m->stream>>>(bits, a, t);
   dg_prof_end(m, DG_KERNEL_MAX_DT);
   if ((e = cudaGetLastError())) return status_of(e);
-  return dg_rk_step(static_cast<dg_mesh*>(m), q, g, &m->d_adv[2]);
+  return rk_step_impl(m, q, g, &m->d_adv[2], trace_valid);
 }
 
 constexpr size_t kMaxGraphs = 24;
@@ -74,7 +76,7 @@ dg_status advance_graph(dg_mesh_impl* m, double* q, double* g, double* t, int n)
     if ((e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal))) return status_of(e);
     m->stream = m->cap_stream;
     dg_status st = DG_OK;
-    for (int k = 0; k < n && st == DG_OK; ++k) st = advance_step(m, q, g, t);
+    for (int k = 0; k < n && st == DG_OK; ++k) st = advance_step(m, q, g, t, k > 0);   // a replay starts afresh
     m->stream = saved;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(m->cap_stream, &graph);
@@ -99,14 +101,17 @@ dg_status advance_graph(dg_mesh_impl* m, double* q, double* g, double* t, int n)
 }
 
 dg_status run_steps(dg_mesh_impl* m, double* q, double* g, double* t, int64_t n, bool graphs) {
+  bool traced = false;   // an eager step of this call ran before: q's face traces are in the buffer
   while (n > 0) {
     if (!graphs || !m->adv_warm) {
-      dg_status st = advance_step(m, q, g, t);
+      dg_status st = advance_step(m, q, g, t, traced);
       if (st != DG_OK) return st;
       m->adv_warm = true;
+      traced = true;
       --n;
       continue;
     }
+    traced = false;
     int b = 32;
     while (b > n) b >>= 1;
     dg_status st = advance_graph(m, q, g, t, b);

@@ -162,7 +162,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 }
 
 void free_device(dg_mesh_impl* m) {
-  void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_surfq,
+  void* ptrs[] = {m->d_mfaces, m->d_mbatches, m->d_ord, m->d_nbr, m->d_off, m->d_soff, m->d_metric, m->d_metric32, m->d_surf, m->d_trace, m->d_surfq,
                   m->d_grad, m->d_xyz, m->d_faces, m->d_fnodes, m->d_items, m->d_elist, m->d_err, m->d_scratch,
                   m->d_taugeo,
                   m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv,
@@ -171,7 +171,7 @@ void free_device(dg_mesh_impl* m) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
-  m->d_metric32 = nullptr; m->d_surf = nullptr; m->d_surfq = nullptr; m->d_grad = nullptr; m->d_xyz = nullptr;
+  m->d_metric32 = nullptr; m->d_surf = nullptr; m->d_trace = nullptr; m->d_surfq = nullptr; m->d_grad = nullptr; m->d_xyz = nullptr;
   m->d_faces = nullptr; m->d_fnodes = nullptr; m->d_items = nullptr; m->d_elist = nullptr; m->d_err = nullptr; m->d_scratch = nullptr;
   m->d_taugeo = nullptr; m->d_taugeo32 = nullptr; m->d_taugeo_off = nullptr; m->d_rp = nullptr; m->d_qc = nullptr;
   m->d_rc = nullptr; m->d_sweep = nullptr; m->d_mfaces = nullptr; m->d_mbatches = nullptr; m->d_rp32 = nullptr;
@@ -530,6 +530,8 @@ dg_status build(dg_mesh_impl* m) {
   DG_CUDA(upload(&m->d_items, items.data(), items.size()));
   DG_CUDA(upload(&m->d_elist, elist.data(), elist.size()));
   DG_CUDA(upload<double>(&m->d_surf, nullptr, 5 * (size_t)m->h_soff[ne]));
+  if (m->affine && !ns && m->n_mbatches)   // the mortar kernel's face traces (dgk::face_flux_rk)
+    DG_CUDA(upload<double>(&m->d_trace, nullptr, 5 * (size_t)m->h_soff[ne]));
   if (ns) {
     DG_CUDA(upload<double>(&m->d_surfq, nullptr, 15 * (size_t)m->h_soff[ne]));
     DG_CUDA(upload<double>(&m->d_grad, nullptr, 15 * (size_t)m->n_nodes));
@@ -753,6 +755,23 @@ void dg_prof_end(dg_mesh_impl* m, int kernel_id) {
   m->prof_open = nullptr;
 }
 
+// One Williamson RK3 step.  trace_valid: m->d_trace holds the face traces of
+// q (the last stage of the step before wrote them and q has not changed
+// since); the stages after the first always find them there.
+dg_status rk_step_impl(dg_mesh_impl* m, double* q, double* g, const double* dt_dev, bool trace_valid) {
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  cudaError_t e;
+  for (int k = 0; k < 3; ++k) {
+    if (ns) {
+      if ((e = dgk::face_qhat(m, q))) return from_cuda(e);
+      if ((e = dgk::gradient(m, q, m->d_grad, false))) return from_cuda(e);
+    }
+    if ((e = dgk::face_flux_rk(m, q, k > 0 || trace_valid))) return from_cuda(e);
+    if ((e = dgk::volume(m, q, m->d_grad, nullptr, false, k, q, g, dt_dev))) return from_cuda(e);
+  }
+  return DG_OK;
+}
+
 extern "C" {
 
 dg_status dg_profile_enable(dg_mesh* m, int on) {
@@ -903,17 +922,7 @@ dg_status dg_max_dt(dg_mesh* m, const double* q, double cfl, double* dt_dev) {
 dg_status dg_rk_step(dg_mesh* m, double* q, double* g, const double* dt_dev) {
   if (!m || !q || !g || !dt_dev || q == g) return DG_ERR_ARG;
   if (m->faces_unsupported) return DG_ERR_UNSUPPORTED;
-  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
-  cudaError_t e;
-  for (int k = 0; k < 3; ++k) {
-    if (ns) {
-      if ((e = dgk::face_qhat(m, q))) return from_cuda(e);
-      if ((e = dgk::gradient(m, q, m->d_grad, false))) return from_cuda(e);
-    }
-    if ((e = dgk::face_flux(m, q, m->d_grad, false))) return from_cuda(e);
-    if ((e = dgk::volume(m, q, m->d_grad, nullptr, false, k, q, g, dt_dev))) return from_cuda(e);
-  }
-  return DG_OK;
+  return rk_step_impl(m, q, g, dt_dev, false);   // the caller may have changed q since the last step
 }
 
 dg_status dg_tau_estimate(dg_mesh* m, const double* q, const double* r_p, const int32_t* sweep, int32_t n_sweep,

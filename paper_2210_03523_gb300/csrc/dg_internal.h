@@ -79,6 +79,10 @@ namespace dgk {
 void upload_basis(int device, const BasisOffsets& off, const std::vector<double>& data, const double** d64,
                   const float** d32);
 cudaError_t face_flux(dg_mesh_impl* m, const double* q, const double* grad, bool isolated);
+// the face fluxes of an RK stage: p-nonconforming and conforming interior
+// faces of affine Euler meshes read the face traces of q from m->d_trace when
+// trace_valid (the previous stage's volume kernel wrote them), else gather them
+cudaError_t face_flux_rk(dg_mesh_impl* m, const double* q, bool trace_valid);
 cudaError_t face_qhat(dg_mesh_impl* m, const double* q);
 cudaError_t gradient(dg_mesh_impl* m, const double* q, double* grad, bool isolated);
 cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double* r, bool isolated, int rk_stage,
@@ -119,6 +123,10 @@ dg_status build_mortar_batches(dg_mesh_impl* m);
 // releases the dg_advance graphs and capture stream of a mesh
 void dg_advance_release(dg_mesh_impl* m);
 
+// one RK3 step (capi.cpp); trace_valid: the mesh's face-trace buffer holds the
+// traces of q (the step before ran on the same q and nothing changed it)
+dg_status rk_step_impl(dg_mesh_impl* m, double* q, double* g, const double* dt_dev, bool trace_valid);
+
 // ---------------------------------------------------------------------------
 // The mesh
 // ---------------------------------------------------------------------------
@@ -148,6 +156,8 @@ struct dg_mesh_impl {
   double* d_metric = nullptr;      // affine: [e][16] (J a^i_d, J, 1/J, pad); curved: [11][n] at 11*off_e
   float* d_metric32 = nullptr;     // affine: FP32 copy for the FP32 tau sweep
   double* d_surf = nullptr;        // [5 * soff_total] numerical contravariant flux per element face node
+  double* d_trace = nullptr;       // affine Euler meshes: [5 * soff_total] the state at every element face node,
+                                   // written by each RK stage's volume kernel for the next stage's mortar fluxes
   double* d_surfq = nullptr;       // NS: [15 * soff_total] BR1 q-hat * J a^dir
   double* d_grad = nullptr;        // NS: [15 * n_nodes] gradient [c][v][node]
   double* d_xyz = nullptr;         // lazily uploaded coordinates

@@ -552,6 +552,7 @@ struct MortarParams {
   double* surf;
   const double* basis;
   const double* grad;     // general mortars, Navier-Stokes flux: the BR1 gradient
+  const double* trace;    // affine Euler mortars: q's face traces (surf layout), or null to gather them from q
 };
 
 // shared memory (doubles) of one mortar batch
@@ -635,11 +636,16 @@ __global__ void __launch_bounds__(kVolThreads) mortar_kernel(MortarParams P) {
       const int e = isL ? fr[0] : fr[1], dir = fr[2];
       int n1, n2, n3;
       orders_of(m, e, n1, n2, n3);
-      const int n = n1 * n2 * n3;
-      const int vi = face_vidx(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir, p % na, p / na);
-      const int64_t o = m.off[e];
       double* T = (isL ? TL + f * 5 * nfl : TR + f * 5 * nfr) + p;
-      for (int v = 0; v < 5; ++v) T[v * nf] = P.q[5 * o + v * n + vi];
+      if (P.trace) {   // the face's trace, contiguous [var][face node]
+        const double* src = P.trace + 5 * (m.soff[e] + face_offset(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir)) + p;
+        for (int v = 0; v < 5; ++v) T[v * nf] = src[v * nf];
+      } else {
+        const int n = n1 * n2 * n3;
+        const int vi = face_vidx(n1, n2, n3, isL ? 2 * dir + 1 : 2 * dir, p % na, p / na);
+        const int64_t o = m.off[e];
+        for (int v = 0; v < 5; ++v) T[v * nf] = P.q[5 * o + v * n + vi];
+      }
     }
     for (int f = threadIdx.x; f < cnt; f += blockDim.x) {
       const int* fr = P.faces + 3 * (B.first + f);
@@ -1076,6 +1082,7 @@ struct VolParams {
   double* out;        // residual or gradient
   double* q_io;       // RK: state updated in place
   double* g_io;       // RK: register
+  double* trace_out;  // RK, affine Euler: the updated state at every element face node (surf layout), or null
   const double* dt;
   double rkA, rkB;
   int rk;             // 0: write residual; 1: RK stage
@@ -1268,21 +1275,43 @@ __global__ void __launch_bounds__(THREADS) volume_kernel(VolParams P) {
       const int e = P.elist[w.first + el];
       const int64_t o = m.off[e];
       const double miJ = -metric<AFFINE>(m.metric, e, o, n, p, 10);
-      const double* Vv = V + (size_t)el * 5 * n + p;
+      double* Vv = V + (size_t)el * 5 * n + p;
       if (P.rk) {
         const double c = *P.dt * miJ;   // dt R = (-dt/J) V
+        double qn[5];
         for (int v = 0; v < 5; ++v) {
           const int64_t idx = 5 * o + v * n + p;
           const double dr = c * Vv[v * n];
           const double g = P.rk_first ? dr : P.rkA * P.g_io[idx] + dr;
           P.g_io[idx] = g;
-          P.q_io[idx] = P.q_io[idx] + P.rkB * g;
+          qn[v] = P.q_io[idx] + P.rkB * g;
+          P.q_io[idx] = qn[v];
         }
+        if (P.trace_out)   // the new state replaces V (read by this thread only) for phase 5
+          for (int v = 0; v < 5; ++v) Vv[v * n] = qn[v];
       } else {
         for (int v = 0; v < 5; ++v) P.out[5 * o + v * n + p] = Vv[v * n] * miJ;
       }
     }
     __syncthreads();
+    // phase 5 (RK, affine Euler): the new state at every element face node into
+    // the trace buffer, contiguous per face as the next stage's mortars read it
+    if (P.rk && P.trace_out) {
+      const int fs[3] = {n2 * n3, n1 * n3, n1 * n2};
+      const int per_el = 2 * (fs[0] + fs[1] + fs[2]);
+      for (int s = threadIdx.x; s < w.count * per_el; s += blockDim.x) {
+        const int el = s / per_el;
+        int r = s - el * per_el, f = 0;
+        while (r >= fs[f >> 1]) r -= fs[f++ >> 1];
+        const int na = f < 2 ? n2 : n1;
+        const int p = face_vidx(n1, n2, n3, f, r % na, r / na);
+        const int e = P.elist[w.first + el];
+        const double* Vv = V + (size_t)el * 5 * n + p;
+        double* t = P.trace_out + 5 * (m.soff[e] + face_offset(n1, n2, n3, f)) + r;
+        for (int v = 0; v < 5; ++v) t[v * fs[f >> 1]] = Vv[v * n];
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -1519,6 +1548,17 @@ __global__ void __launch_bounds__(kVolThreads) dt_kernel(VolParams P, const unsi
         bool ok;
         const float v = node_scale<AFFINE, AXIS, float>(m, P.k32, P.metric32, P.q, e, m.off[e], n, p, nn, &ok);
         cand = !ok || !(v < thr);
+        if (AFFINE && cand && p > 0) {
+          // on a straight-sided element s depends on the node's state alone:
+          // a node whose state equals the first node's bit for bit has its s,
+          // and the first node is a candidate too (a uniform region otherwise
+          // queues every node of its elements for the FP64 pass)
+          const double* qe = P.q + 5 * m.off[e];
+          bool same = true;
+          for (int v5 = 0; v5 < 5; ++v5)
+            same = same && __double_as_longlong(qe[v5 * n + p]) == __double_as_longlong(qe[v5 * n]);
+          cand = !same;
+        }
       }
       const unsigned mask = __ballot_sync(0xffffffffu, cand);
       if (cand) queue[warp][cnt + __popc(mask & ((1u << lane) - 1u))] = make_int2(e, p);
@@ -2907,7 +2947,8 @@ cudaError_t dispatch_volume_one(dg_mesh_impl* m, const VolParams& P, size_t smem
 
 // Every numerical face flux into the face buffer surf: conforming and
 // boundary faces one warp each, p-nonconforming faces in shape batches.
-cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* grad, double* surf) {
+cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* grad, double* surf,
+                             const double* trace = nullptr) {
   cudaError_t err;
   if (m->n_faces) {
     FaceParams P = dgk_face_params_for(m, q, surf);
@@ -2918,7 +2959,7 @@ cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* gra
   }
   if (m->n_mbatches) {
     Prof pr(m, DG_KERNEL_MORTAR);
-    MortarParams M;
+    MortarParams M{};
     M.m = view(m);
     M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
     M.n_batches = m->n_mbatches;
@@ -2928,6 +2969,7 @@ cudaError_t launch_all_faces(dg_mesh_impl* m, const double* q, const double* gra
     M.surf = surf;
     M.basis = m->basis64;
     M.grad = grad;
+    M.trace = m->general_mortars ? nullptr : trace;
     const size_t smem = sizeof(double) * m->mortar_smem;
     const int grid = m->n_mbatches;   // one CTA per batch, largest first
     if (m->general_mortars) {
@@ -3031,6 +3073,10 @@ cudaError_t face_flux(dg_mesh_impl* m, const double* q, const double* grad, bool
   return launch_all_faces(m, q, grad, m->d_surf);
 }
 
+cudaError_t face_flux_rk(dg_mesh_impl* m, const double* q, bool trace_valid) {
+  return launch_all_faces(m, q, m->d_grad, m->d_surf, trace_valid ? m->d_trace : nullptr);
+}
+
 cudaError_t face_qhat(dg_mesh_impl* m, const double* q) {
   cudaError_t err;
   Prof pr(m, DG_KERNEL_FACE_QHAT);
@@ -3042,7 +3088,7 @@ cudaError_t face_qhat(dg_mesh_impl* m, const double* q) {
     if ((err = cudaGetLastError())) return err;
   }
   if (m->n_mbatches && m->general_mortars) {   // BR1 q-hat on the mortars
-    MortarParams M;
+    MortarParams M{};
     M.m = view(m);
     M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
     M.n_batches = m->n_mbatches;
@@ -3117,6 +3163,7 @@ cudaError_t volume(dg_mesh_impl* m, const double* q, const double* grad, double*
     P.q_io = q_io;
     P.g_io = g_io;
     P.dt = dt_dev;
+    P.trace_out = q_io == q ? m->d_trace : nullptr;   // the stepped state's traces (dg_rk_step's own q)
   }
   Prof pr(m, DG_KERNEL_VOLUME, (int)m->vol_classes.size());
   return dispatch_volume(m, P, 0, 0);
@@ -4872,7 +4919,7 @@ static cudaError_t launch_adj_volume(dg_mesh_impl* m, AdjParams A) {
 }
 
 static MortarParams mortar_params(dg_mesh_impl* m, const double* q) {
-  MortarParams M;
+  MortarParams M{};
   M.m = view(m);
   M.batches = reinterpret_cast<const MortarBatch*>(m->d_mbatches);
   M.n_batches = m->n_mbatches;
