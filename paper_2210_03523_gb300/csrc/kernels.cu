@@ -2492,8 +2492,9 @@ __device__ void tau_stage_nm(const TauParams<T>& P, const int32_t* els, int cnt,
 // isolated R^P of every element into the scratch (unless the caller gave
 // R^P), and -1 in the maps for every sweep entry the element's orders
 // cannot reach.  Layout: the staged q^P at ST, the fluxes at Ft.
-template <typename T, bool AFFINE, bool AXIS>
-__global__ void __launch_bounds__(kVolThreads, sizeof(T) == 4 ? 4 : 2) tau_euler_prologue_kernel(TauParams<T> P) {
+template <typename T, bool AFFINE, bool AXIS, int THREADS>
+__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1024 : 512) / THREADS) tau_euler_prologue_kernel(
+    TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float Ref[std::is_same<T, float>::value ? kTauRefElems : 1][kTauRefStride];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -2560,8 +2561,8 @@ __global__ void __launch_bounds__(kVolThreads, sizeof(T) == 4 ? 4 : 2) tau_euler
 // slots of TS, RS or FS values: A3, A2, then A1 and Ft, with the staged tile
 // ST over A1 and Ft (it is read only by the xi3 pass, before them); compact
 // (units of one group): A3 and then A1, ST and then A2, Ft.
-template <typename T, bool AFFINE, bool AXIS>
-__global__ void __launch_bounds__(kVolThreads, sizeof(T) == 4 ? 4 : 2) tau_euler_kernel(TauParams<T> P) {
+template <typename T, bool AFFINE, bool AXIS, int THREADS>
+__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1024 : 512) / THREADS) tau_euler_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   typedef typename Bits<T>::type B;
@@ -3230,6 +3231,18 @@ bool tau_use_compact(int S, bool ns, bool fp32, int limit) {
   return tau_smem_for(S, ns, fp32, false) + tau_static_bytes(fp32) > (size_t)limit;
 }
 
+// CTA size of the Euler sweep for a CTA of `bytes` of shared memory: 256
+// threads while three or more fit an SM, 512 for two, 1024 for one (FP32);
+// FP64 at up to 128 registers a thread stops at 512.  (Measured: 512 threads
+// in a class that fits three 256-thread CTAs ran 2% slower; a class of one
+// or two CTAs per SM ran 8% faster on the 48^3 mesh with orders 2-8.)
+int tau_euler_threads(size_t bytes, bool fp32) {
+  const size_t sm_bytes = 228 * 1024;
+  const int ctas = (int)(sm_bytes / (bytes + 1024));
+  const int t = ctas >= 3 ? 256 : (ctas == 2 ? 512 : 1024);
+  return fp32 ? t : (t > 512 ? 512 : t);
+}
+
 size_t tau_smem_bytes(dg_mesh_impl* m, bool fp32, int limit) {
   size_t mx = 0;
   const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
@@ -3279,14 +3292,22 @@ static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
     if ((err = allow_smem(tau_kernel<T, AFF, NSV, AXV>, smem))) return err;                     \
     tau_kernel<T, AFF, NSV, AXV><<<grid, kVolThreads, smem, m->stream>>>(P);                    \
   }
-#define DG_TAU_EULER(AFF, AXV)                                                                  \
+#define DG_TAU_EULER_T(AFF, AXV, TH)                                                            \
   if (phase == 0) {                                                                             \
-    if ((err = allow_smem(tau_euler_prologue_kernel<T, AFF, AXV>, smem))) return err;           \
-    tau_euler_prologue_kernel<T, AFF, AXV><<<grid, kVolThreads, smem, m->stream>>>(P);          \
+    if ((err = allow_smem(tau_euler_prologue_kernel<T, AFF, AXV, TH>, smem))) return err;       \
+    tau_euler_prologue_kernel<T, AFF, AXV, TH><<<grid, TH, smem, m->stream>>>(P);              \
   } else {                                                                                      \
-    if ((err = allow_smem(tau_euler_kernel<T, AFF, AXV>, smem))) return err;                    \
-    tau_euler_kernel<T, AFF, AXV><<<grid, kVolThreads, smem, m->stream>>>(P);                   \
+    if ((err = allow_smem(tau_euler_kernel<T, AFF, AXV, TH>, smem))) return err;                \
+    tau_euler_kernel<T, AFF, AXV, TH><<<grid, TH, smem, m->stream>>>(P);                       \
   }
+      // the Euler sweep's CTA grows when shared memory admits fewer CTAs per SM,
+      // so that every class keeps ~32 warps per SM (FP32; FP64 as registers allow)
+      const int threads = tau_euler_threads(smem + tau_static_bytes(fp32), fp32);
+      constexpr int kTauMaxThreads = sizeof(T) == 4 ? 1024 : 512;
+#define DG_TAU_EULER(AFF, AXV)                                                                  \
+  if (threads >= 1024) { DG_TAU_EULER_T(AFF, AXV, kTauMaxThreads) }                             \
+  else if (threads >= 512) { DG_TAU_EULER_T(AFF, AXV, 512) }                                    \
+  else { DG_TAU_EULER_T(AFF, AXV, 256) }
       if (m->axis && !ns) { DG_TAU_EULER(true, true) }
       else if (m->affine && !ns) { DG_TAU_EULER(true, false) }
       else if (!ns) { DG_TAU_EULER(false, false) }
@@ -3294,6 +3315,7 @@ static cudaError_t tau_launch(dg_mesh_impl* m, TauParams<T> P, bool fp32) {
       else { DG_TAU_CASE(false, true, false) }
 #undef DG_TAU_CASE
 #undef DG_TAU_EULER
+#undef DG_TAU_EULER_T
       if ((err = cudaGetLastError())) return err;
     }
   }
