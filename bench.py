@@ -113,13 +113,12 @@ def full_sweep_for(orders):
 # kernel the mean of a step's three stages, the mortar kernel a stage that
 # reads the face traces, as all but the first of a replayed batch of steps
 # do) from ncu captures of these kernels as they stand; the commands and the
-# per-launch figures are in profiles/traffic_mortar_volume_pulse32mixed_pulse48mixed.md
+# per-launch figures are in profiles/traffic_mortar_volume_pulse24mixed_pulse48mixed.md
 MEASURED_TRAFFIC = {
-    ("pulse32mixed", "mortar"): 299.2e6, ("pulse32mixed", "volume"): 713.0e6,
-    ("pulse48mixed", "mortar"): 2033.6e6, ("pulse48mixed", "volume"): 5362.7e6,
+    ("pulse48mixed", "mortar"): 2033.6e6, ("pulse48mixed", "volume"): 5362.5e6,
 }
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                  "profiles/traffic_mortar_volume_pulse32mixed_pulse48mixed.md")
+                  "profiles/traffic_mortar_volume_pulse24mixed_pulse48mixed.md")
 
 
 # ------------------------------------------------------------ algorithmic counts
