@@ -55,6 +55,8 @@ constexpr int kVolThreads = 256;
 // volume tiles' shared memory above which two CTAs, or one, fit an SM
 constexpr size_t kVolThreeCtaBytes = 400 * 20 * sizeof(double), kVolTwoCtaBytes = 700 * 20 * sizeof(double);
 constexpr int kTauChunk = 16;   // at most this many sweep entries share the two barriers of a tau chunk
+constexpr int kTauBatchGroups = 16;    // (N2, N3) groups of one Euler tau batch at most
+constexpr int kTauBatchEntries = 64;   // entries of a batch's table at most (a larger batch runs in pieces)
 constexpr int kTauThreads = 128;
 constexpr int kTauRefElems = 32;   // elements of a tau tile at most (tiles of <= 256 nodes, 8 nodes an element)
 constexpr int kTauRefStride = 16;  // floats of one element's reference record
@@ -1806,6 +1808,27 @@ __device__ __forceinline__ void smax_bits(unsigned int* slot, float v) { atomicM
 __device__ __forceinline__ void smax_bits(unsigned long long* slot, double v) {
   atomicMax(slot, (unsigned long long)__double_as_longlong(v));
 }
+// Both norms of a warp's items into their slots (all 32 lanes call it;
+// slot < 0: the lane has no item).  FP32: the lanes of one slot reduce their
+// maxima first and one of them makes the atomic, since the items of a warp
+// mostly belong to one or two elements (32 atomics on one address serialise).
+// The maxima are taken over the bit patterns of nonnegative values.
+__device__ __forceinline__ void warp_norm_max(unsigned* na, unsigned* nb, int slot, float a, float b) {
+  const unsigned peers = __match_any_sync(0xffffffffu, slot);
+  const unsigned ma = __reduce_max_sync(peers, __float_as_uint(a));
+  const unsigned mb = __reduce_max_sync(peers, __float_as_uint(b));
+  if (slot >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+    atomicMax(na + slot, ma);
+    atomicMax(nb + slot, mb);
+  }
+}
+__device__ __forceinline__ void warp_norm_max(unsigned long long* na, unsigned long long* nb, int slot, double a,
+                                              double b) {
+  if (slot >= 0) {
+    smax_bits(na + slot, a);
+    smax_bits(nb + slot, b);
+  }
+}
 template <typename T>
 struct Bits;
 template <>
@@ -2123,6 +2146,65 @@ __device__ __forceinline__ void tau_chunk_item(const int2* gent, int first, int 
   }
 }
 
+// Thread 0 of the Euler sweep: the next piece of a batch's entry table, from
+// group btab[2], entry btab[3] of the batch's nb groups (from group gb of
+// the list): every entry with N1 <= P1, as (sweep index, N1, N2 + 1, the
+// group's A2 offset), at most kTauBatchEntries; btab[1] the count, btab[2..3]
+// where the next piece starts.
+template <typename T>
+__device__ void tau_fill_entries(const TauParams<T>& P, int gb, int nb, int P1, const int4* gtab, int4* etab,
+                                 int* btab) {
+  int k = 0, g = btab[2], e = btab[3];
+  while (g < nb && k < kTauBatchEntries) {
+    const int4 gr = P.groups[gb + g];   // N2, N3, first entry, entry count
+    if (e >= gr.w) {
+      ++g;
+      e = 0;
+      continue;
+    }
+    const int2 ent = P.gentries[gr.z + e];
+    if (ent.y <= P1) etab[k++] = make_int4(ent.x, ent.y, gtab[g].x, gtab[g].y);
+    ++e;
+  }
+  btab[1] = k;
+  btab[2] = g;
+  btab[3] = e;
+}
+
+// The chunk of table entries [first, first + k): entries while their items
+// (cnt (N1+1)(N2+1) c3 each) fit the tile capacity S and their norm slots
+// (cnt each) fit kVolThreads; one entry at least (its items <= cnt n_P <= S).
+// Returns k; total = the items.
+__device__ __forceinline__ int tau_batch_chunk(const int4* etab, int first, int n_tab, int cnt, int c3, int S,
+                                               int& total) {
+  int k = 0;
+  total = 0;
+  while (first + k < n_tab && k < kTauChunk) {
+    const int4 en = etab[first + k];
+    const int sz = cnt * (en.y + 1) * en.z * c3;
+    if (k > 0 && (total + sz > S || (k + 1) * cnt > kVolThreads)) break;
+    total += sz;
+    ++k;
+  }
+  return k;
+}
+
+// Item t of a chunk: its entry (returned), the entry's index j in the chunk
+// and the entry's first item base.
+__device__ __forceinline__ int4 tau_batch_item(const int4* etab, int first, int t, int cnt, int c3, int& base,
+                                               int& j) {
+  base = 0;
+  j = 0;
+  int4 en = etab[first];
+  int sz = cnt * (en.y + 1) * en.z * c3;
+  while (t >= base + sz) {
+    base += sz;
+    en = etab[first + ++j];
+    sz = cnt * (en.y + 1) * en.z * c3;
+  }
+  return en;
+}
+
 // Prologue of the isolated Navier-Stokes sweep (field-major tiles; the Euler
 // sweep runs tau_euler_prologue_kernel), one tile per CTA iteration: the
 // isolated R^P of every element (into the scratch, unless the caller gave
@@ -2390,6 +2472,39 @@ struct TauTiles {
   // slot of J a^d . f_v within a node's flux record
   __host__ __device__ static constexpr int fo(int d, int v) { return 5 * d + v; }
 };
+// FP32: records of an even number of floats, each direction's five fluxes
+// starting at an even slot, so that the restriction and the derivative load
+// pairs of fields (8-byte shared loads; strides of 10 and 18 floats keep the
+// 16 lanes of each half-warp phase on distinct banks) and run packed FP32x2
+// FMAs, two fields an instruction.
+template <>
+struct TauTiles<float> {
+  static constexpr int TS = 10;
+  static constexpr int FS = 18;
+  static constexpr int RS = 5;
+  __host__ __device__ static constexpr int fo(int d, int v) { return 6 * d + v; }
+};
+
+// Packed FP32x2 arithmetic (sm_100 and later): two lanes of a 64-bit
+// register pair, each rounded as the scalar FMA would be, so that a packed
+// and a scalar sum of the same terms in the same order have the same bits.
+__device__ __forceinline__ unsigned long long f2_splat(float a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_load(const float* p) {   // 8-byte aligned shared address
+  return *reinterpret_cast<const unsigned long long*>(p);
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
 
 // One output node of a restriction pass: acc[c] = sum_m w[m] src[m stride + c]
 // over the nt taps m of an interpolation row w (10 fields c, node-major).
@@ -2407,6 +2522,22 @@ __device__ __forceinline__ void restrict_node(int nt, const T* __restrict__ w, c
     src += stride;
   }
 }
+// FP32: the ten fields as five packed pairs (src and stride even)
+template <>
+__device__ __forceinline__ void restrict_node<float>(int nt, const float* __restrict__ w, const float* src,
+                                                     int stride, float acc[10]) {
+  unsigned long long a[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) a[c] = 0ull;
+  for (int m = 0; m < nt; ++m) {
+    const unsigned long long wm = f2_splat(w[m]);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) a[c] = f2_fma(wm, f2_load(src + 2 * c), a[c]);
+    src += stride;
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) f2_unpack(a[c], acc[2 * c], acc[2 * c + 1]);
+}
 
 // acc[v] += sum_m d[m] J a^dir . f_v of the node at src + m stride, over the
 // nt taps m (5 variables v; src points at node records)
@@ -2420,6 +2551,28 @@ __device__ __forceinline__ void deriv_line(int nt, const T* __restrict__ d, cons
     for (int v = 0; v < 5; ++v) acc[v] += dm * src[L::fo(dir, v)];
     src += stride;
   }
+}
+// FP32: variables (0,1) and (2,3) as packed pairs, 4 alone
+template <>
+__device__ __forceinline__ void deriv_line<float>(int nt, const float* __restrict__ d, const float* src, int dir,
+                                                  int stride, float acc[5]) {
+  typedef TauTiles<float> L;
+  unsigned long long a01, a23;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a01) : "f"(acc[0]), "f"(acc[1]));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a23) : "f"(acc[2]), "f"(acc[3]));
+  float a4 = acc[4];
+  src += L::fo(dir, 0);
+  for (int m = 0; m < nt; ++m) {
+    const float dm = d[m];
+    const unsigned long long dd = f2_splat(dm);
+    a01 = f2_fma(dd, f2_load(src), a01);
+    a23 = f2_fma(dd, f2_load(src + 2), a23);
+    a4 = fmaf(dm, src[4], a4);
+    src += stride;
+  }
+  f2_unpack(a01, acc[0], acc[1]);
+  f2_unpack(a23, acc[2], acc[3]);
+  acc[4] = a4;
 }
 
 // sum_i D^(i) Ft^i at node (i, j, k) of a c1 x c2 x c3 element whose flux
@@ -2558,9 +2711,10 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1024 : 512) / THREA
 // (tau_chunk): (1) previous chunk's norms stored, this chunk's slots
 // cleared, restriction in xi1 and the fluxes of every coarse node; (2) the
 // GL derivative, tau~ = I R^P - R^N and both norms.  Shared memory in S node
-// slots of TS, RS or FS values: A3, A2, then A1 and Ft, with the staged tile
-// ST over A1 and Ft (it is read only by the xi3 pass, before them); compact
-// (units of one group): A3 and then A1, ST and then A2, Ft.
+// slots of TS, FS or RS values: A3, A2, then Ft and A1, with the staged tile
+// ST over Ft and A1 (it is read only by the xi3 pass, before them); compact
+// (units of one group): A3 and then A1, ST and then A2, Ft.  Every region
+// starts at an even float, as the packed FP32 loads need.
 template <typename T, bool AFFINE, bool AXIS, int THREADS>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1024 : 512) / THREADS) tau_euler_kernel(TauParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2568,13 +2722,16 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1024 : 512) / THREA
   typedef typename Bits<T>::type B;
   __shared__ B na2[2][kVolThreads], nb2[2][kVolThreads];   // per-element norms, two chunks in flight
   __shared__ float Ref[std::is_same<T, float>::value ? kTauRefElems : 1][kTauRefStride];
+  __shared__ int4 gtab[kTauBatchGroups];    // a batch's groups: N2 + 1, A2 offset and size (nodes)
+  __shared__ int4 etab[kTauBatchEntries];   // its entries: sweep index, N1, N2 + 1, A2 offset
+  __shared__ int btab[4];                   // groups in the batch, entries in etab, next group and entry
   constexpr int TS = TauTiles<T>::TS, FS = TauTiles<T>::FS, RS = TauTiles<T>::RS;
   const int S = P.S;
   T* A3 = sm;
   T* A2 = sm + TS * S;
-  T* A1 = P.compact ? sm : sm + 2 * TS * S;
-  T* Ft = P.compact ? sm + 2 * TS * S : A1 + RS * S;
-  T* ST = P.compact ? A2 : A1;
+  T* Ft = sm + 2 * TS * S;
+  T* A1 = P.compact ? sm : Ft + FS * S;
+  T* ST = P.compact ? A2 : Ft;
   const MeshView& m = P.m;
   const T gm1 = P.gamma - (T)1;
   for (int ui = blockIdx.x; ui < P.n_list; ui += gridDim.x) {
@@ -2595,6 +2752,19 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1024 : 512) / THREA
     const int cnt = w.count;
     const int P1 = w.n1, P2 = w.n2, P3 = w.n3, n1 = P1 + 1, n2 = P2 + 1, n3 = P3 + 1, nP = n1 * n2 * n3;
     const int N3 = P.groups[u.y].y, c3 = N3 + 1, n12 = n1 * n2;
+#ifdef DG_BOUNDS_CHECK
+    {  // every group of the unit: inside the group list, orders within the tile's, entries inside the sweep, one N3
+      bool bad = false;
+      for (int gi = u.y + 1; gi < u.y + u.z && !bad; ++gi) {
+        bad = bad_group(P, w, gi);
+        if (!bad && P.groups[gi].y != N3) {
+          if (threadIdx.x == 0) flag_index(m);
+          bad = true;
+        }
+      }
+      if (bad) continue;
+    }
+#endif
     tau_stage_nm(P, els, cnt, nP, true, ST, &Ref[0][0]);
     {  // xi3, once for the unit's groups: A3[el][i + n1 (j + n2 k)]
       const T* I3 = P.basis + c_boff.I[P3][N3];
@@ -2609,108 +2779,133 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1024 : 512) / THREA
       }
       __syncthreads();
     }
-    for (int gi = u.y; gi < u.y + u.z; ++gi) {   // the groups (N2, N3) of this N3, N2 ascending
-      if (gi > u.y && bad_group(P, w, gi)) continue;
-      const int4 g = P.groups[gi];      // N2, N3, first entry, entry count
-      const int N2 = g.x, c2 = N2 + 1, c23 = c2 * c3;
-#ifdef DG_BOUNDS_CHECK
-      if (g.y != N3) {
-        if (threadIdx.x == 0) flag_index(m);
-        continue;
+    // The groups of this N3 run in batches whose xi2-restricted tiles fit the
+    // S node slots of A2 together (the compact layout: one group), and the
+    // chunks of a batch draw on the entries of all its groups: a small group
+    // alone would leave most of the CTA idle in its passes.  Thread 0 lays
+    // out the batch (gtab) and its entries within the tile's orders (etab,
+    // in pieces of at most kTauBatchEntries); every other value below is the
+    // same in every thread.
+    for (int gb = u.y; gb < u.y + u.z;) {
+      if (threadIdx.x == 0) {
+        int ge = gb, used = 0;
+        while (ge < u.y + u.z && ge - gb < kTauBatchGroups) {
+          const int c2 = P.groups[ge].x + 1, sz = cnt * n1 * c2 * c3;
+          if (ge > gb && (P.compact || used + sz > S)) break;
+          gtab[ge - gb] = make_int4(c2, used, sz, 0);
+          used += sz;
+          ++ge;
+        }
+        btab[0] = ge - gb;
+        btab[2] = 0;   // next group and entry of the batch's entry table
+        btab[3] = 0;
+        tau_fill_entries(P, gb, ge - gb, P1, gtab, etab, btab);
       }
-#endif
-      const int pin = n12 * c3, per2 = n1 * c23;
-      {  // xi2: A2[el][i + n1 (j' + c2 k')]
-        const T* I2 = P.basis + c_boff.I[P2][N2];
-        for (int t = threadIdx.x; t < cnt * per2; t += blockDim.x) {
-          const int el = fdiv(t, per2), x = t - el * per2, xj = fdiv(x, n1), k = fdiv(xj, c2), i = x - xj * n1,
+      __syncthreads();
+      const int nb = btab[0];
+      const int pin = n12 * c3;
+      {  // xi2 for every group of the batch: A2[gtab.y + el per2 + i + n1 (j' + c2 k')]
+        const int4 gl = gtab[nb - 1];
+        const int tot = gl.y + gl.z;
+        for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+          int b = 0;
+          while (b + 1 < nb && t >= gtab[b + 1].y) ++b;
+          const int4 gg = gtab[b];
+          const int c2 = gg.x, per2 = n1 * c2 * c3, tt = t - gg.y;
+          const int el = fdiv(tt, per2), x = tt - el * per2, xj = fdiv(x, n1), k = fdiv(xj, c2), i = x - xj * n1,
                     j = xj - k * c2;
           T acc[10];
-          restrict_node(n2, I2 + j * n2, A3 + TS * (el * pin + i + n12 * k), TS * n1, acc);
+          restrict_node(n2, P.basis + c_boff.I[P2][c2 - 1] + j * n2, A3 + TS * (el * pin + i + n12 * k), TS * n1,
+                        acc);
           T* o = A2 + TS * t;
 #pragma unroll
           for (int c = 0; c < 10; ++c) o[c] = acc[c];
         }
         __syncthreads();
       }
-      const T* w2 = P.basis + c_boff.W[N2];
       const T* w3 = P.basis + c_boff.W[N3];
-      const int2* gent = P.gentries + g.z;      // (sweep index, N1) per entry
-      int prev_first = 0, prev_k = 0, buf = 0;
-      for (int first = 0; first < g.w;) {
-        int total;
-        const int k = tau_chunk(gent, first, g.w, P1, cnt, c23, S, total);   // the same in every thread
-        const int nsl = (prev_k > k ? prev_k : k) * cnt;
-        for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) {
-          const int j = fdiv(sl, cnt), el = sl - j * cnt;
-          if (j < prev_k) {
-            const int2 pe = gent[prev_first + j];
-            if (pe.y <= P1) {
-              const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
+      for (;;) {   // the pieces of the batch's entry table
+        const int n_tab = btab[1], next_g = btab[2];
+        int prev_first = 0, prev_k = 0, buf = 0;
+        for (int first = 0; first < n_tab;) {
+          int total;
+          const int k = tau_batch_chunk(etab, first, n_tab, cnt, c3, S, total);
+          const int nsl = (prev_k > k ? prev_k : k) * cnt;
+          for (int sl = threadIdx.x; sl < nsl; sl += blockDim.x) {
+            const int j = fdiv(sl, cnt), el = sl - j * cnt;
+            if (j < prev_k) {
+              const int64_t idx = (int64_t)els[el] * P.n_sweep + etab[prev_first + j].x;
               map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
               map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
             }
+            if (j < k) {
+              na2[buf][sl] = 0;
+              nb2[buf][sl] = 0;
+            }
           }
-          if (j < k) {
-            na2[buf][sl] = 0;
-            nb2[buf][sl] = 0;
-          }
-        }
-        // (1) xi1 restriction and the fluxes of every coarse node of the chunk
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-          int base, j, M1;
-          tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
-          const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
-          const int el = fdiv(tt, nN), x = tt - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
-          T acc[10];
-          restrict_node(n1, P.basis + c_boff.I[P1][M1] + i * n1, A2 + TS * (el * per2 + n1 * jk), TS, acc);
-          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
-          tau_flux_nm<T, AFFINE, AXIS>(gm1, met, nN, x, acc, tau_ref_of<T>(&Ref[0][0], el), Ft + FS * t);
-          T* o = A1 + RS * t;
+          // (1) xi1 restriction and the fluxes of every coarse node of the chunk
+          for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int base, j;
+            const int4 en = tau_batch_item(etab, first, t, cnt, c3, base, j);
+            const int M1 = en.y, c1 = M1 + 1, c2 = en.z, nN = c1 * c2 * c3, tt = t - base;
+            const int el = fdiv(tt, nN), x = tt - el * nN, jk = fdiv(x, c1), i = x - jk * c1;
+            T acc[10];
+            restrict_node(n1, P.basis + c_boff.I[P1][M1] + i * n1, A2 + TS * (en.w + el * (n1 * c2 * c3) + n1 * jk),
+                          TS, acc);
+            const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, c2 - 1, N3);
+            tau_flux_nm<T, AFFINE, AXIS>(gm1, met, nN, x, acc, tau_ref_of<T>(&Ref[0][0], el), Ft + FS * t);
+            T* o = A1 + RS * t;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) o[v] = acc[5 + v];    // I R^P
-        }
-        __syncthreads();
-        // (2) derivative, tau~ and both norms
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-          int base, j, M1;
-          tau_chunk_item(gent, first, t, P1, cnt, c23, base, j, M1);
-          const int c1 = M1 + 1, nN = c1 * c23, tt = t - base;
-          const int el = fdiv(tt, nN), p = tt - el * nN, pj = fdiv(p, c1), kk = fdiv(pj, c2), i = p - pj * c1,
-                    jj = pj - kk * c2;
-          const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, N2, N3);
-          T acc[5];
-          tau_div_nm(P.basis, Ft + FS * (base + el * nN), c1, c2, c3, i, jj, kk, acc);
-          const T J = met_at(met, AFFINE, nN, p, 9);
-          const T iJ = -(T)1 / J;
-          const T Jw = J * P.basis[c_boff.W[M1] + i] * w2[jj] * w3[kk];
-          const T* ir = A1 + RS * t;
-          T a = 0, b = 0;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const T d = ir[v] - mul_rn(acc[v], iJ);   // tau~ = I R^P - R^N(I q^P)
-            a = tmax(a, (T)fabs(d));
-            b = tmax(b, (T)fabs(Jw * d));
+            for (int v = 0; v < 5; ++v) o[v] = acc[5 + v];    // I R^P
           }
-          smax_bits(na2[buf] + j * cnt + el, a);
-          smax_bits(nb2[buf] + j * cnt + el, b);
+          __syncthreads();
+          // (2) derivative, tau~ and both norms (whole warps, for the norms' warp reduction)
+          for (int t0 = threadIdx.x & ~31; t0 < total; t0 += blockDim.x) {
+            const int t = t0 + (threadIdx.x & 31);
+            int slot = -1;
+            T a = 0, b = 0;
+            if (t < total) {
+              int base, j;
+              const int4 en = tau_batch_item(etab, first, t, cnt, c3, base, j);
+              const int M1 = en.y, c1 = M1 + 1, c2 = en.z, nN = c1 * c2 * c3, tt = t - base;
+              const int el = fdiv(tt, nN), p = tt - el * nN, pj = fdiv(p, c1), kk = fdiv(pj, c2), i = p - pj * c1,
+                        jj = pj - kk * c2;
+              const T* met = tile_met<T, AFFINE>(P, els[el], P1, P2, M1, c2 - 1, N3);
+              T acc[5];
+              tau_div_nm(P.basis, Ft + FS * (base + el * nN), c1, c2, c3, i, jj, kk, acc);
+              const T J = met_at(met, AFFINE, nN, p, 9);
+              const T iJ = -(T)1 / J;
+              const T Jw = J * P.basis[c_boff.W[M1] + i] * P.basis[c_boff.W[c2 - 1] + jj] * w3[kk];
+              const T* ir = A1 + RS * t;
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                const T d = ir[v] - mul_rn(acc[v], iJ);   // tau~ = I R^P - R^N(I q^P)
+                a = tmax(a, (T)fabs(d));
+                b = tmax(b, (T)fabs(Jw * d));
+              }
+              slot = j * cnt + el;
+            }
+            warp_norm_max(na2[buf], nb2[buf], slot, a, b);
+          }
+          __syncthreads();
+          prev_first = first;
+          prev_k = k;
+          buf ^= 1;
+          first += k;
         }
+        for (int sl = threadIdx.x; sl < prev_k * cnt; sl += blockDim.x) {
+          const int j = fdiv(sl, cnt), el = sl - j * cnt;
+          const int64_t idx = (int64_t)els[el] * P.n_sweep + etab[prev_first + j].x;
+          map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
+          map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
+        }
+        __syncthreads();   // the tables and norm slots are free again
+        if (next_g >= nb) break;
+        if (threadIdx.x == 0) tau_fill_entries(P, gb, nb, P1, gtab, etab, btab);
         __syncthreads();
-        prev_first = first;
-        prev_k = k;
-        buf ^= 1;
-        first += k;
       }
-      for (int sl = threadIdx.x; sl < prev_k * cnt; sl += blockDim.x) {
-        const int j = fdiv(sl, cnt), el = sl - j * cnt;
-        const int2 pe = gent[prev_first + j];
-        if (pe.y > P1) continue;
-        const int64_t idx = (int64_t)els[el] * P.n_sweep + pe.x;
-        map_store(P.map_new, idx, P.accumulate, Bits<T>::val(na2[buf ^ 1][sl]));
-        map_store(P.map_trad, idx, P.accumulate, Bits<T>::val(nb2[buf ^ 1][sl]));
-      }
-      __syncthreads();
-    }   // groups of the unit
+      gb += nb;
+    }   // batches of groups
   }
 }
 
@@ -3223,7 +3418,8 @@ size_t tau_smem_for(int S, bool ns, bool fp32, bool compact) {
 // the FP32 reference records, and the bytes the compiler may add.
 size_t tau_static_bytes(bool fp32) {
   return 2 * 2 * kVolThreads * (fp32 ? sizeof(unsigned) : sizeof(unsigned long long)) +
-         (fp32 ? kTauRefElems : 1) * kTauRefStride * sizeof(float) + 256;
+         (fp32 ? kTauRefElems : 1) * kTauRefStride * sizeof(float) +
+         (kTauBatchGroups + kTauBatchEntries) * sizeof(int4) + 256;
 }
 
 // The compact layout where the other does not fit the device.
