@@ -1002,8 +1002,10 @@ def run_dynamic_cylinder(args):
             "stage_timing_s": {k: [round(x, 5) for x in v] for k, v in res["timing"].items()},
             "rebuild_share": sum(res["timing"]["rebuild_s"]) / (dyn_ms * 1e-3),
             "estimate_select_share": sum(res["timing"]["estimate_select_s"]) / (dyn_ms * 1e-3),
-            "rebuild_note": "dg_set_orders: projection on the device, then the host re-buckets the elements and "
-                            "rebuilds the face and mortar lists and uploads them (synchronous, once per stage)",
+            "rebuild_note": "dg_set_orders (synchronous, once per stage): the projection, the offsets, the curved "
+                            "metrics at the new orders, the order buckets and the face classification and shape "
+                            "sort on the device; the host tiles the sorted buckets and shape groups into work items "
+                            "and batches",
         },
     }
 

@@ -167,7 +167,7 @@ void free_device(dg_mesh_impl* m) {
                   m->d_taugeo,
                   m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv,
                   m->d_vitems, m->d_velist, m->d_sadj, m->d_adjw, m->d_gadj, m->d_lG, m->d_lS, m->d_adjt,
-                  m->d_force};
+                  m->d_force, m->d_geom};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
@@ -185,6 +185,7 @@ void free_device(dg_mesh_impl* m) {
   m->d_lS = nullptr;
   m->d_adjt = nullptr;
   m->d_force = nullptr;
+  m->d_geom = nullptr;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
@@ -343,9 +344,6 @@ dg_status build(dg_mesh_impl* m) {
   const int ne = m->n_elem;
   const int G = m->G;
   const int ng3 = (G + 1) * (G + 1) * (G + 1);
-  // offsets
-  m->h_off.assign(ne + 1, 0);
-  m->h_soff.assign(ne + 1, 0);
   m->max_order = 1;
   for (int e = 0; e < ne; ++e) {
     const int* N = &m->h_ord[3 * e];
@@ -353,11 +351,7 @@ dg_status build(dg_mesh_impl* m) {
       if (N[d] < 1 || N[d] > DG_MAX_ORDER) return DG_ERR_ARG;
       m->max_order = std::max(m->max_order, N[d]);
     }
-    int64_t a = N[0] + 1, b = N[1] + 1, c = N[2] + 1;
-    m->h_off[e + 1] = m->h_off[e] + a * b * c;
-    m->h_soff[e + 1] = m->h_soff[e] + 2 * (b * c + a * c + a * b);
   }
-  m->n_nodes = m->h_off[ne];
   // geometry
   // metric record: fields 0..8 J a^i_d, 9 J, 10 1/J; affine: 16 doubles per
   // element with 11..13 |J a^i|, curved: [11][n] per element
@@ -380,7 +374,39 @@ dg_status build(dg_mesh_impl* m) {
         for (int d = 0; d < 3; ++d)
           if (i != d && r[3 * i + d] != 0.0) m->axis = false;
     }
+  }
+  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  // offsets; on the device build also the warp-list faces and the sorted
+  // buckets and batched faces (dg_device_lists)
+  DgDeviceLists dl;
+  if (m->device_build) {
+    DG_CUDA(upload(&m->d_ord, m->h_ord.data(), m->h_ord.size()));
+    DG_CUDA(upload(&m->d_nbr, m->h_nbr.data(), m->h_nbr.size()));
+    dg_status st = dg_device_lists(m, !ns && m->affine, &dl);
+    if (st != DG_OK) return st;
+    m->h_off.swap(dl.off);
+    m->h_soff.swap(dl.soff);
   } else {
+    m->h_off.assign(ne + 1, 0);
+    m->h_soff.assign(ne + 1, 0);
+    for (int e = 0; e < ne; ++e) {
+      const int* N = &m->h_ord[3 * e];
+      int64_t a = N[0] + 1, b = N[1] + 1, c = N[2] + 1;
+      m->h_off[e + 1] = m->h_off[e] + a * b * c;
+      m->h_soff[e + 1] = m->h_soff[e] + 2 * (b * c + a * c + a * b);
+    }
+  }
+  m->n_nodes = m->h_off[ne];
+  if (!m->affine && m->device_build) {
+    // curved metrics at the element orders on the device
+    if (!m->d_geom) DG_CUDA(upload(&m->d_geom, m->h_geom.data(), m->h_geom.size()));
+    DG_CUDA(upload<double>(&m->d_metric, nullptr, 11 * (size_t)m->n_nodes));
+    std::vector<DgGeomJob> jobs(ne);
+    for (int e = 0; e < ne; ++e)
+      jobs[e] = {e, m->h_ord[3 * e] + 1, m->h_ord[3 * e + 1] + 1, m->h_ord[3 * e + 2] + 1, 11 * m->h_off[e]};
+    dg_status st = dg_device_metrics(m, jobs, 11, m->d_metric, nullptr);
+    if (st != DG_OK) return st;
+  } else if (!m->affine) {
     met.assign(11 * (size_t)m->n_nodes, 0.0);
     int bad_jacobian = 0;
 #pragma omp parallel for schedule(dynamic, 8) reduction(| : bad_jacobian)
@@ -400,7 +426,19 @@ dg_status build(dg_mesh_impl* m) {
   }
   // faces
   std::vector<FaceRec> faces;
-  const bool ns = m->phys.eqs == DG_NAVIER_STOKES;
+  std::vector<int32_t> fnodes;
+  std::map<std::tuple<int, int, int, int>, std::vector<int32_t>> msig;
+  const bool batch_conforming = !ns && m->affine;
+  if (m->device_build) {
+    m->n_face_conf = dl.n_conf;
+    m->n_face_mortar = dl.n_mortar;
+    m->n_face_bnd = dl.n_bnd;
+    for (size_t i = 0; i < dl.msig.size(); ++i) {
+      const int sg = dl.msig[i];
+      auto& v = msig[std::make_tuple(sg >> 12, (sg >> 8) & 15, (sg >> 4) & 15, sg & 15)];
+      v.insert(v.end(), dl.mfaces.begin() + 3 * i, dl.mfaces.begin() + 3 * i + 3);
+    }
+  } else {
   for (int e = 0; e < ne; ++e)
     for (int d = 0; d < 3; ++d) {
       const int t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
@@ -426,9 +464,7 @@ dg_status build(dg_mesh_impl* m) {
   // affine Euler meshes the conforming interior faces join them: the batched
   // kernel keeps every lane busy, while one warp per face leaves lanes idle
   // whenever a face has not a multiple of 32 nodes.
-  std::map<std::tuple<int, int, int, int>, std::vector<int32_t>> msig;
   std::vector<FaceRec> wfaces;
-  const bool batch_conforming = !ns && m->affine;
   for (auto& f : faces) {
     if (!(f.kind == 1 || (f.kind == 0 && batch_conforming))) {
       wfaces.push_back(f);
@@ -446,7 +482,6 @@ dg_status build(dg_mesh_impl* m) {
   m->n_faces = (int)faces.size();
   // (face, node) of every node of the listed faces: the face kernel runs one
   // thread per face node
-  std::vector<int32_t> fnodes;
   for (int i = 0; i < m->n_faces; ++i) {
     const FaceRec& f = faces[i];
     const int e = f.L, d = f.kind == 2 ? f.face / 2 : f.face, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
@@ -457,6 +492,7 @@ dg_status build(dg_mesh_impl* m) {
     }
   }
   m->n_fnodes = (int)fnodes.size() / 2;
+  }   // host face lists
   // the batched faces by shape, faces of one direction together: the
   // axis-aligned Roe flux branches on the direction, so a warp that spans
   // two directions runs both variants
@@ -467,9 +503,10 @@ dg_status build(dg_mesh_impl* m) {
     const int nf = (int)kv.second.size() / 3;
     std::vector<std::array<int32_t, 3>> fs(nf);
     for (int i = 0; i < nf; ++i) fs[i] = {kv.second[3 * i], kv.second[3 * i + 1], kv.second[3 * i + 2]};
-    std::stable_sort(fs.begin(), fs.end(), [](const std::array<int32_t, 3>& a, const std::array<int32_t, 3>& b) {
-      return a[2] < b[2];
-    });
+    if (!m->device_build)   // the device sort already ordered them by direction
+      std::stable_sort(fs.begin(), fs.end(), [](const std::array<int32_t, 3>& a, const std::array<int32_t, 3>& b) {
+        return a[2] < b[2];
+      });
     g.faces.resize(3 * (size_t)nf);
     for (int i = 0; i < nf; ++i)
       for (int k = 0; k < 3; ++k) g.faces[3 * i + k] = fs[i][k];
@@ -492,7 +529,14 @@ dg_status build(dg_mesh_impl* m) {
   }
   // work items: elements bucketed by order triple
   std::map<std::tuple<int, int, int>, std::vector<int32_t>> buckets;
-  for (int e = 0; e < ne; ++e) buckets[{m->h_ord[3 * e], m->h_ord[3 * e + 1], m->h_ord[3 * e + 2]}].push_back(e);
+  if (m->device_build) {   // sorted on the device: runs of equal keys
+    for (int i = 0; i < ne; ++i) {
+      const int k = dl.bucket_key[i];
+      buckets[{k / 64 + 1, (k / 8) % 8 + 1, k % 8 + 1}].push_back(dl.bucket_elems[i]);
+    }
+  } else {
+    for (int e = 0; e < ne; ++e) buckets[{m->h_ord[3 * e], m->h_ord[3 * e + 1], m->h_ord[3 * e + 2]}].push_back(e);
+  }
   m->h_bucket_key.clear();
   m->h_buckets.clear();
   for (auto& kv : buckets) {
@@ -516,17 +560,19 @@ dg_status build(dg_mesh_impl* m) {
   m->n_items = (int)items.size();
   m->h_items = items;
   // device
-  DG_CUDA(upload(&m->d_ord, m->h_ord.data(), m->h_ord.size()));
-  DG_CUDA(upload(&m->d_nbr, m->h_nbr.data(), m->h_nbr.size()));
-  DG_CUDA(upload(&m->d_off, m->h_off.data(), m->h_off.size()));
-  DG_CUDA(upload(&m->d_soff, m->h_soff.data(), m->h_soff.size()));
-  DG_CUDA(upload(&m->d_metric, met.data(), met.size()));
+  if (!m->device_build) {
+    DG_CUDA(upload(&m->d_ord, m->h_ord.data(), m->h_ord.size()));
+    DG_CUDA(upload(&m->d_nbr, m->h_nbr.data(), m->h_nbr.size()));
+    DG_CUDA(upload(&m->d_off, m->h_off.data(), m->h_off.size()));
+    DG_CUDA(upload(&m->d_soff, m->h_soff.data(), m->h_soff.size()));
+    DG_CUDA(upload(&m->d_faces, faces.data(), faces.size()));
+    DG_CUDA(upload(&m->d_fnodes, fnodes.data(), fnodes.size()));
+  }
+  if (!m->device_build || m->affine) DG_CUDA(upload(&m->d_metric, met.data(), met.size()));
   if (m->affine) {
     std::vector<float> m32(met.begin(), met.end());
     DG_CUDA(upload(&m->d_metric32, m32.data(), m32.size()));
   }
-  DG_CUDA(upload(&m->d_faces, faces.data(), faces.size()));
-  DG_CUDA(upload(&m->d_fnodes, fnodes.data(), fnodes.size()));
   DG_CUDA(upload(&m->d_items, items.data(), items.size()));
   DG_CUDA(upload(&m->d_elist, elist.data(), elist.size()));
   DG_CUDA(upload<double>(&m->d_surf, nullptr, 5 * (size_t)m->h_soff[ne]));
@@ -577,36 +623,27 @@ dg_status build(dg_mesh_impl* m) {
 // each [10][n_N].
 dg_status build_tau_bank(dg_mesh_impl* m) {
   if (m->affine || m->d_taugeo) return DG_OK;
-  const int ne = m->n_elem, ng3 = (m->G + 1) * (m->G + 1) * (m->G + 1);
+  const int ne = m->n_elem;
   std::vector<int64_t> off(ne + 1, 0);
+  std::vector<DgGeomJob> jobs;
   for (int e = 0; e < ne; ++e) {
-    const int* P = &m->h_ord[3 * e];
-    int64_t s = 1;
-    for (int d = 0; d < 3; ++d) s *= (int64_t)P[d] * (P[d] + 3) / 2;
-    off[e + 1] = off[e] + 10 * s;
-  }
-  std::vector<double> bank(off[ne]);
-  // elements in parallel on the host cores (the per-order geometry is the
-  // bulk of the first isolated sweep on a curved mesh)
-#pragma omp parallel for schedule(dynamic, 4)
-  for (int e = 0; e < ne; ++e) {
-    std::vector<double> X, Ja, J;
     const int* P = &m->h_ord[3 * e];
     int64_t pos = off[e];
     for (int N3 = 1; N3 <= P[2]; ++N3)
       for (int N2 = 1; N2 <= P[1]; ++N2)
         for (int N1 = 1; N1 <= P[0]; ++N1) {
-          int N[3] = {N1, N2, N3};
-          element_geometry(&m->h_geom[(size_t)e * ng3 * 3], m->G, N, X, Ja, J);
-          int n = (N1 + 1) * (N2 + 1) * (N3 + 1);
-          std::copy(Ja.begin(), Ja.end(), bank.begin() + pos);
-          std::copy(J.begin(), J.end(), bank.begin() + pos + 9 * n);
-          pos += 10 * n;
+          jobs.push_back({e, N1 + 1, N2 + 1, N3 + 1, pos});
+          pos += 10 * (int64_t)(N1 + 1) * (N2 + 1) * (N3 + 1);
         }
+    off[e + 1] = pos;
   }
-  std::vector<float> bank32(bank.begin(), bank.end());
-  DG_CUDA(upload(&m->d_taugeo, bank.data(), bank.size()));
-  DG_CUDA(upload(&m->d_taugeo32, bank32.data(), bank32.size()));
+  // every (element, coarse order) on the device, one CTA each (on the host
+  // cores this construction was the bulk of the first sweep on a curved mesh)
+  if (!m->d_geom) DG_CUDA(upload(&m->d_geom, m->h_geom.data(), m->h_geom.size()));
+  DG_CUDA(upload<double>(&m->d_taugeo, nullptr, off[ne]));
+  DG_CUDA(upload<float>(&m->d_taugeo32, nullptr, off[ne]));
+  dg_status st = dg_device_metrics(m, jobs, 10, m->d_taugeo, m->d_taugeo32);
+  if (st != DG_OK) return st;
   DG_CUDA(upload(&m->d_taugeo_off, off.data(), off.size()));
   return DG_OK;
 }
@@ -705,9 +742,11 @@ dg_status residual_impl(dg_mesh_impl* m, const double* q, double* r, bool isolat
   return from_cuda(dgk::volume(m, q, m->d_grad, r, isolated, -1, nullptr, nullptr, nullptr));
 }
 
-dg_mesh_impl* make_child(const dg_mesh_impl* m, const std::vector<int32_t>& orders, dg_status* st) {
+dg_mesh_impl* make_child(const dg_mesh_impl* m, const std::vector<int32_t>& orders, dg_status* st,
+                         bool on_device = false) {
   dg_mesh* c = new dg_mesh();
   c->stream = m->stream;
+  c->device_build = on_device;
   c->n_elem = m->n_elem;
   c->G = m->G;
   c->phys = m->phys;
@@ -995,7 +1034,9 @@ dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_o
   if (dg_count_nodes(m->n_elem, new_orders, &nn) != DG_OK) return DG_ERR_ARG;
   std::vector<int32_t> no(new_orders, new_orders + 3 * (size_t)m->n_elem);
   dg_status st;
-  dg_mesh_impl* c = make_child(m, no, &st);
+  // the new mesh's offsets, metrics, buckets and face lists are built on the
+  // device (rebuild.cu); the host tiles them into work items and batches
+  dg_mesh_impl* c = make_child(m, no, &st, true);
   if (!c) return st;
   cudaError_t e = dgk::project_orders(m, c->d_ord, c->d_off, q_old, q_new, 0);
   if (e == cudaSuccess) e = m->stream ? cudaStreamSynchronize(m->stream) : cudaDeviceSynchronize();

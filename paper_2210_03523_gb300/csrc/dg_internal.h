@@ -116,6 +116,31 @@ size_t mortar_adj_smem_max(dg_mesh_impl* m);
 cudaError_t axpby(dg_mesh_impl* m, double* y, const double* x, double a, double b, int64_t n);
 }  // namespace dgk
 
+// One metric job of the device construction (rebuild.cu): element e at
+// orders (n1-1, n2-1, n3-1), written at out (doubles) as fields
+// [J a^i_d (9), J, with 11 fields also 1/J][n].
+struct DgGeomJob {
+  int32_t e, n1, n2, n3;
+  int64_t out;
+};
+// Metrics of every job on the mesh's stream (out32: an FP32 copy of the
+// fields, or null), from the lattices at m->d_geom; DG_ERR_ARG where a
+// Jacobian is not positive.  Synchronous.
+dg_status dg_device_metrics(dg_mesh_impl* m, const std::vector<DgGeomJob>& jobs, int fields, double* out,
+                            float* out32);
+
+// The order-dependent lists built on the device (rebuild.cu): the mesh's
+// d_off / d_soff, the warp-list faces d_faces and d_fnodes are set; the host
+// copies below feed the tiling of buckets and shape groups.
+struct DgDeviceLists {
+  std::vector<int64_t> off, soff;                  // node and face-node offsets
+  std::vector<int32_t> bucket_key, bucket_elems;   // elements sorted by order triple (key ((N1-1) 8 + N2-1) 8 + N3-1)
+  std::vector<int32_t> mfaces;                     // batched faces [L, R, dir], sorted by shape, then direction
+  std::vector<int32_t> msig;                       // their shapes ((la 16 + lb) 16 + ra) 16 + rb
+  int n_conf = 0, n_mortar = 0, n_bnd = 0;         // conforming interior, p-nonconforming, boundary faces
+};
+dg_status dg_device_lists(dg_mesh_impl* m, bool batch_conforming, DgDeviceLists* out);
+
 // work-list (re)builders with the mesh's tile budgets (capi.cpp)
 dg_status build_volume_items(dg_mesh_impl* m);
 dg_status build_mortar_batches(dg_mesh_impl* m);
@@ -144,6 +169,8 @@ struct dg_mesh_impl {
 
   // host copies (for rebuilds and coarse meshes)
   std::vector<double> h_geom;
+  double* d_geom = nullptr;        // curved meshes: the geometry lattices on the device (metric construction)
+  bool device_build = false;       // the order-dependent lists and metrics are built on the device (rebuild.cu)
   std::vector<int32_t> h_nbr, h_ord;
   std::vector<int64_t> h_off, h_soff;
   std::vector<double> h_xyz;       // node coordinates (state-order [d][node] per element)
