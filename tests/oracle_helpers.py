@@ -128,3 +128,10 @@ def fp32_tau_ratio(tau32, tau64, S):
     unit = np.finfo(np.float32).eps * S[0] + np.finfo(np.float64).eps * S[1]
     ok = tau64 >= 0
     return float((np.abs(tau32 - tau64) / unit[:, None])[ok].max())
+
+
+def plain_rel_err(a, b, nvar_off):
+    """per-variable ||a-b||_inf / ||b||_inf over a state-layout array, with no
+    floor: next to rel_err it shows how much of the error budget the floor
+    (the flux scale of terms that cancel) grants a small residual"""
+    return rel_err(a, b, nvar_off, None)

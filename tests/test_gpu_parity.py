@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2210_03523_gb300 import inputs as I
-from oracle_helpers import rel_err, scale_per_var, state_scale
+from oracle_helpers import plain_rel_err, rel_err, scale_per_var, state_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -85,6 +85,14 @@ def test_residual_parity_full_size_pulse16_mixed(torch_cuda):
     ro = om.residual(q)
     err = rel_err(r, ro, om.off, scale_per_var(q, mi.phys, 2.0 / 16))
     assert err.max() < RTOL, err
+    # The same errors without the floor, against each variable's own residual:
+    # density 1.9e-12, x / y momentum 2e-10 / 3e-10, energy 1e-9 measured.  At
+    # Mach 0.1 the pressure flux (p0 ~ 143) that cancels in the momentum and
+    # energy derivatives is ~1e3 times the residual it leaves, which is the
+    # factor between these and the floored errors.  The z momentum residual is
+    # zero in exact arithmetic (w = 0), so only the floored error measures it.
+    plain = plain_rel_err(r, ro, om.off)
+    assert plain[0] < 1e-11 and plain[1] < 5e-9 and plain[2] < 5e-9 and plain[4] < 1e-8, plain
 
 
 @pytest.mark.parametrize("name,steps", [("pulse4_P4", 20), ("mixed5_1to6", 8), ("sheared_mixed", 5),
