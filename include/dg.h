@@ -326,6 +326,28 @@ dg_status dg_tau_extrapolate(dg_mesh* mesh, const void* map, int32_t map_fp32, c
 dg_status dg_advance(dg_mesh* mesh, double* q, double* g, double* t_dev, double t_end, double cfl, int64_t max_steps,
                      uint32_t flags, int64_t* steps_out);
 
+/* One pass of the hot path on host buffers: time stepping (Sec. 3.1) then
+ * the estimate (Sec. 2.3) of one estimation stage.  The state q_in (host,
+ * 5 * n_nodes doubles, state layout) is copied to the device, advanced by
+ * dg_advance(t_end, cfl, max_steps) from time t0 with a zeroed RK register,
+ * the sweep of dg_tau_estimate(tau_flags) is run on the advanced state, and
+ * the state and the maps are copied back:
+ *   q_out: host, 5 * n_nodes doubles (may equal q_in);
+ *   map_new / map_trad: host [n_elem][n_sweep], float if DG_TAU_FP32 else
+ *      double; either may be NULL (not computed), not both;
+ *   t_out: host, optional: the time reached.
+ * The device buffers are the mesh's own: allocated at the first call (and
+ * again when the map size changes), kept until the mesh is destroyed or its
+ * orders change; with DG_TAU_ACCUM_MAX the mesh's device maps keep the
+ * F_max accumulation across calls (they start at 0).  Page-locked host
+ * buffers make the copies asynchronous DMA on the mesh stream.  Synchronous:
+ * returns once the copies back have finished.
+ * Errors: DG_ERR_ARG (null q_in, q_out or sweep, n_sweep <= 0, both maps
+ * NULL), DG_ERR_NOMEM, then as dg_advance and dg_tau_estimate. */
+dg_status dg_step_host(dg_mesh* mesh, const double* q_in, double* q_out, double t0, double t_end, double cfl,
+                       int64_t max_steps, const int32_t* sweep, int32_t n_sweep, uint32_t tau_flags, void* map_new,
+                       void* map_trad, double* t_out);
+
 /* Tile shapes (Sec. 2.4: elements of mixed anisotropic orders run in one
  * launch, bucketed by (N1,N2,N3)).  The volume kernels run one CTA per tile
  * of same-order elements, at most vol_budget nodes per tile (one element at

@@ -167,7 +167,7 @@ void free_device(dg_mesh_impl* m) {
                   m->d_taugeo,
                   m->d_taugeo32, m->d_taugeo_off, m->d_rp, m->d_rp32, m->d_qc, m->d_rc, m->d_sweep, m->d_adv,
                   m->d_vitems, m->d_velist, m->d_sadj, m->d_adjw, m->d_gadj, m->d_lG, m->d_lS, m->d_adjt,
-                  m->d_force, m->d_geom};
+                  m->d_force, m->d_geom, m->d_hq, m->d_hg, m->d_ht, m->d_hmap_new, m->d_hmap_trad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_ord = nullptr; m->d_nbr = nullptr; m->d_off = nullptr; m->d_soff = nullptr; m->d_metric = nullptr;
@@ -186,6 +186,9 @@ void free_device(dg_mesh_impl* m) {
   m->d_adjt = nullptr;
   m->d_force = nullptr;
   m->d_geom = nullptr;
+  m->d_hq = m->d_hg = m->d_ht = nullptr;
+  m->d_hmap_new = m->d_hmap_trad = nullptr;
+  m->hmap_bytes = 0;
 }
 
 void destroy_impl(dg_mesh_impl* m) {
@@ -1051,6 +1054,48 @@ dg_status dg_set_orders(dg_mesh* m, const int32_t* new_orders, const double* q_o
   std::swap(m->d_err, c->d_err);   // keep the sticky error word of the mesh
   m->tau_unit_mode = c->tau_unit_mode;
   destroy_impl(c);
+  return DG_OK;
+}
+
+dg_status dg_step_host(dg_mesh* m, const double* q_in, double* q_out, double t0, double t_end, double cfl,
+                       int64_t max_steps, const int32_t* sweep, int32_t n_sweep, uint32_t tau_flags, void* map_new,
+                       void* map_trad, double* t_out) {
+  if (!m || !q_in || !q_out || !sweep || n_sweep <= 0 || (!map_new && !map_trad)) return DG_ERR_ARG;
+  const size_t nq = 5 * (size_t)m->n_nodes;
+  const size_t mb = (size_t)m->n_elem * n_sweep * ((tau_flags & DG_TAU_FP32) ? sizeof(float) : sizeof(double));
+  cudaStream_t s = m->stream;
+  if (!m->d_hq) {
+    DG_CUDA(cudaMalloc(&m->d_hq, sizeof(double) * nq));
+    DG_CUDA(cudaMalloc(&m->d_hg, sizeof(double) * nq));
+    DG_CUDA(cudaMalloc(&m->d_ht, sizeof(double)));
+  }
+  if (m->hmap_bytes != mb) {   // a new sweep size or precision: new maps, accumulation from 0
+    if (m->d_hmap_new) cudaFree(m->d_hmap_new);
+    if (m->d_hmap_trad) cudaFree(m->d_hmap_trad);
+    m->d_hmap_new = m->d_hmap_trad = nullptr;
+    m->hmap_bytes = 0;
+    DG_CUDA(cudaMalloc(&m->d_hmap_new, mb));
+    DG_CUDA(cudaMalloc(&m->d_hmap_trad, mb));
+    DG_CUDA(cudaMemsetAsync(m->d_hmap_new, 0, mb, s));
+    DG_CUDA(cudaMemsetAsync(m->d_hmap_trad, 0, mb, s));
+    m->hmap_bytes = mb;
+  }
+  DG_CUDA(cudaMemcpyAsync(m->d_hq, q_in, sizeof(double) * nq, cudaMemcpyHostToDevice, s));
+  DG_CUDA(cudaMemsetAsync(m->d_hg, 0, sizeof(double) * nq, s));
+  DG_CUDA(cudaMemcpyAsync(m->d_ht, &t0, sizeof(double), cudaMemcpyHostToDevice, s));
+  DG_CUDA(cudaStreamSynchronize(s));   // t0 lives on this call's stack
+  dg_status st = dg_advance(m, m->d_hq, m->d_hg, m->d_ht, t_end, cfl, max_steps, 0, nullptr);
+  if (st != DG_OK) return st;
+  st = dg_tau_estimate(m, m->d_hq, nullptr, sweep, n_sweep, tau_flags, map_new ? m->d_hmap_new : nullptr,
+                       map_trad ? m->d_hmap_trad : nullptr);
+  if (st != DG_OK) return st;
+  DG_CUDA(cudaMemcpyAsync(q_out, m->d_hq, sizeof(double) * nq, cudaMemcpyDeviceToHost, s));
+  if (map_new) DG_CUDA(cudaMemcpyAsync(map_new, m->d_hmap_new, mb, cudaMemcpyDeviceToHost, s));
+  if (map_trad) DG_CUDA(cudaMemcpyAsync(map_trad, m->d_hmap_trad, mb, cudaMemcpyDeviceToHost, s));
+  double t = 0.0;
+  if (t_out) DG_CUDA(cudaMemcpyAsync(&t, m->d_ht, sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (t_out) *t_out = t;
   return DG_OK;
 }
 

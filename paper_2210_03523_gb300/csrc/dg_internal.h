@@ -273,6 +273,14 @@ struct dg_mesh_impl {
   double* d_lS = nullptr;
   double* d_adjt = nullptr;
   double* d_force = nullptr;   // wall force: one partial per warp-list face
+  // dg_step_host: the device copies of its host buffers (state, RK register,
+  // time, both maps of map_bytes each)
+  double* d_hq = nullptr;
+  double* d_hg = nullptr;
+  double* d_ht = nullptr;
+  void* d_hmap_new = nullptr;
+  void* d_hmap_trad = nullptr;
+  size_t hmap_bytes = 0;
   cudaStream_t cap_stream = nullptr;
   bool adv_warm = false;             // one eager step taken (kernel attributes set)
   struct AdvGraph { const void *q, *g, *t; int steps; cudaGraphExec_t exec; int64_t launches; };

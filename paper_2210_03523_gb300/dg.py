@@ -86,6 +86,8 @@ def _lib():
             "dg_tau_extrapolate": [vp, vp, C.c_int32, i32p, C.c_int32, i32p, C.c_int32, C.c_int32, C.c_double,
                                    C.c_uint32, vp],
             "dg_advance": [vp, vp, vp, vp, C.c_double, C.c_double, C.c_int64, C.c_uint32, i64p],
+            "dg_step_host": [vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_int64, i32p, C.c_int32, C.c_uint32,
+                             vp, vp, C.POINTER(C.c_double)],
             "dg_autotune": [vp, vp, C.c_int32, C.POINTER(dg_tiles)],
             "dg_residual_vjp": [vp, vp, vp, vp, vp],
             "dg_rk_step_vjp": [vp, vp, vp, vp, vp],
@@ -122,7 +124,8 @@ def exported_symbols():
             "dg_status_str", "dg_profile_enable", "dg_profile_read", "dg_launch_count", "dg_residual_noalloc",
             "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles",
             "dg_residual_vjp", "dg_rk_step_vjp", "dg_wall_force", "dg_wall_force_vjp", "dg_state_write",
-            "dg_state_info", "dg_state_read", "dg_debug_set_index", "dg_set_tau_units", "dg_tau_units_info"]
+            "dg_state_info", "dg_state_read", "dg_debug_set_index", "dg_set_tau_units", "dg_tau_units_info",
+            "dg_step_host"]
 
 
 def _check(st, where):
@@ -301,6 +304,32 @@ class Mesh:
         nc = C.c_int32()
         _check(_lib().dg_tau_units_info(self.h, 8, C.byref(nc), nu, ns_), "dg_tau_units_info")
         return [(nu[k], ns_[k]) for k in range(min(nc.value, 8))]
+
+    def step_host(self, q_in, q_out, t0, t_end, cfl, max_steps, sweep, isolated=True, fp32=True, accumulate=False,
+                  map_new=None, map_trad=None):
+        """dg_step_host: one pass of time stepping and the tau sweep on host
+        buffers (torch CPU tensors, page-locked for asynchronous copies):
+        q_in / q_out the state (float64), map_new / map_trad [n_elem][n_sweep]
+        (float32 if fp32 else float64, either may be None).  Returns the time
+        reached.  The mesh's device must be current."""
+        sw = np.ascontiguousarray(np.asarray(sweep, dtype=np.int32).reshape(-1, 3))
+        n = 5 * self.n_nodes
+        mt = "float32" if fp32 else "float64"
+        for x, name in ((q_in, "q_in"), (q_out, "q_out")):
+            if x.device.type != "cpu" or str(x.dtype) != "torch.float64" or x.numel() != n or not x.is_contiguous():
+                raise ValueError(f"{name}: a contiguous CPU float64 tensor of {n} values")
+        for x, name in ((map_new, "map_new"), (map_trad, "map_trad")):
+            if x is not None and (x.device.type != "cpu" or str(x.dtype) != f"torch.{mt}" or
+                                  x.numel() != self.n_elem * sw.shape[0] or not x.is_contiguous()):
+                raise ValueError(f"{name}: a contiguous CPU {mt} tensor of n_elem x n_sweep values")
+        flags = (DG_TAU_ISOLATED if isolated else 0) | (DG_TAU_FP32 if fp32 else 0) | \
+                (DG_TAU_ACCUM_MAX if accumulate else 0)
+        t = C.c_double(0.0)
+        _check(_lib().dg_step_host(self.h, _ptr(q_in), _ptr(q_out), float(t0), float(t_end), float(cfl),
+                                   int(max_steps), sw.ctypes.data_as(C.POINTER(C.c_int32)), sw.shape[0], flags,
+                                   _ptr(map_new) if map_new is not None else None,
+                                   _ptr(map_trad) if map_trad is not None else None, C.byref(t)), "dg_step_host")
+        return t.value
 
     def set_orders(self, new_orders, q_old):
         import torch
