@@ -110,6 +110,14 @@ dg_status dg_mesh_destroy(dg_mesh* mesh);
 /* Number of nodes and elements (host outputs; either may be NULL).
  * Errors: DG_ERR_ARG (null mesh). */
 dg_status dg_mesh_info(const dg_mesh* mesh, int64_t* n_nodes, int32_t* n_elem);
+/* The state layout (Sec. 2.1: the solution of element e holds its 5
+ * variables at its (N1+1)(N2+1)(N3+1) GL nodes): *n_nodes the node count,
+ * *elem_offset the device array off[0..n_elem] (int64) with element e's
+ * nodes at off[e] .. off[e+1]-1, so its values start at 5 off[e] in a state
+ * array, [var][k][j][i] with i fastest.  The array is owned by the mesh and
+ * valid until dg_set_orders or dg_mesh_destroy; either output may be NULL.
+ * Errors: DG_ERR_ARG (null mesh). */
+dg_status dg_mesh_layout(const dg_mesh* mesh, int64_t* n_nodes, const int64_t** elem_offset);
 /* Number of nodes sum_e prod_i (N_i+1) of a layout with the given host
  * orders [n_elem][3]; host only.  Errors: DG_ERR_ARG (n_elem < 0, null
  * orders with n_elem > 0, null n_nodes, an order outside 1..DG_MAX_ORDER). */

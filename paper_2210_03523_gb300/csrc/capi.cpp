@@ -930,6 +930,13 @@ dg_status dg_mesh_info(const dg_mesh* m, int64_t* n_nodes, int32_t* n_elem) {
   return DG_OK;
 }
 
+dg_status dg_mesh_layout(const dg_mesh* m, int64_t* n_nodes, const int64_t** elem_offset) {
+  if (!m) return DG_ERR_ARG;
+  if (n_nodes) *n_nodes = m->n_nodes;
+  if (elem_offset) *elem_offset = m->d_off;
+  return DG_OK;
+}
+
 dg_status dg_set_stream(dg_mesh* m, void* stream) {
   if (!m) return DG_ERR_ARG;
   m->stream = static_cast<cudaStream_t>(stream);

@@ -76,6 +76,7 @@ def _lib():
             "dg_mesh_create": [C.POINTER(dg_mesh_desc), vp, C.POINTER(vp)],
             "dg_mesh_destroy": [vp],
             "dg_mesh_info": [vp, i64p, i32p],
+            "dg_mesh_layout": [vp, i64p, C.POINTER(vp)],
             "dg_count_nodes": [C.c_int32, i32p, i64p],
             "dg_set_stream": [vp, vp],
             "dg_node_coords": [vp, vp],
@@ -125,7 +126,7 @@ def exported_symbols():
             "dg_select_orders", "dg_tau_extrapolate", "dg_advance", "dg_autotune", "dg_get_tiles", "dg_set_tiles",
             "dg_residual_vjp", "dg_rk_step_vjp", "dg_wall_force", "dg_wall_force_vjp", "dg_state_write",
             "dg_state_info", "dg_state_read", "dg_debug_set_index", "dg_set_tau_units", "dg_tau_units_info",
-            "dg_step_host"]
+            "dg_step_host", "dg_mesh_layout"]
 
 
 def _check(st, where):
@@ -237,6 +238,21 @@ class Mesh:
     def set_stream(self, stream):
         self._stream = stream
         _check(_lib().dg_set_stream(self.h, _stream_handle(stream)), "dg_set_stream")
+
+    def layout(self):
+        """dg_mesh_layout: (node count, the element node offsets as a torch
+        int64 tensor of n_elem + 1 values viewing the mesh's device array: valid
+        until set_orders or the mesh's end, not to be written)."""
+        import torch
+        n = C.c_int64(0)
+        ptr = C.c_void_p(0)
+        _check(_lib().dg_mesh_layout(self.h, C.byref(n), C.byref(ptr)), "dg_mesh_layout")
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (self.n_elem + 1,), "typestr": "<i8",
+                                        "data": (ptr.value, False), "version": 2}
+        with torch.cuda.device(self.device):
+            return n.value, torch.as_tensor(_View(), device=self.device)
 
     def coords(self):
         import torch

@@ -66,6 +66,13 @@ def test_set_orders_mesh_equals_a_mesh_built_on_the_host(torch_cuda, case):
     h = dg.Mesh(mi.with_orders(np.asarray(new, dtype=np.int32)))  # host-built mesh
     assert m.n_nodes == h.n_nodes
     assert torch.equal(m.coords(), h.coords())
+    # the device offsets (dg_mesh_layout) of both equal the node counts' prefix sums
+    off = I.node_offsets(np.asarray(new, dtype=np.int32))
+    for mesh in (m, h):
+        n, dev_off = mesh.layout()
+        assert n == off[-1]
+        torch.cuda.synchronize()
+        assert np.array_equal(dev_off.cpu().numpy(), np.asarray(off, dtype=np.int64))
     ra, rb = m.residual(q), h.residual(q)
     assert torch.isfinite(ra).all()
     assert torch.equal(ra, rb)
