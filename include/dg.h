@@ -350,8 +350,10 @@ dg_status dg_advance(dg_mesh* mesh, double* q, double* g, double* t_dev, double 
  * F_max accumulation across calls (they start at 0).  Page-locked host
  * buffers make the copies asynchronous DMA on the mesh stream.  Synchronous:
  * returns once the copies back have finished.
+ * The mesh's device must be the current device.
  * Errors: DG_ERR_ARG (null q_in, q_out or sweep, n_sweep <= 0, both maps
- * NULL), DG_ERR_NOMEM, then as dg_advance and dg_tau_estimate. */
+ * NULL, another device current), DG_ERR_NOMEM, then as dg_advance and
+ * dg_tau_estimate. */
 dg_status dg_step_host(dg_mesh* mesh, const double* q_in, double* q_out, double t0, double t_end, double cfl,
                        int64_t max_steps, const int32_t* sweep, int32_t n_sweep, uint32_t tau_flags, void* map_new,
                        void* map_trad, double* t_out);

@@ -1068,6 +1068,9 @@ dg_status dg_step_host(dg_mesh* m, const double* q_in, double* q_out, double t0,
                        int64_t max_steps, const int32_t* sweep, int32_t n_sweep, uint32_t tau_flags, void* map_new,
                        void* map_trad, double* t_out) {
   if (!m || !q_in || !q_out || !sweep || n_sweep <= 0 || (!map_new && !map_trad)) return DG_ERR_ARG;
+  int dev = -1;
+  DG_CUDA(cudaGetDevice(&dev));
+  if (dev != m->device) return DG_ERR_ARG;   // the device buffers are allocated on the current device
   const size_t nq = 5 * (size_t)m->n_nodes;
   const size_t mb = (size_t)m->n_elem * n_sweep * ((tau_flags & DG_TAU_FP32) ? sizeof(float) : sizeof(double));
   cudaStream_t s = m->stream;

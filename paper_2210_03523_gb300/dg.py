@@ -327,7 +327,7 @@ class Mesh:
         buffers (torch CPU tensors, page-locked for asynchronous copies):
         q_in / q_out the state (float64), map_new / map_trad [n_elem][n_sweep]
         (float32 if fp32 else float64, either may be None).  Returns the time
-        reached.  The mesh's device must be current."""
+        reached.  The call makes the mesh's device current."""
         sw = np.ascontiguousarray(np.asarray(sweep, dtype=np.int32).reshape(-1, 3))
         n = 5 * self.n_nodes
         mt = "float32" if fp32 else "float64"
@@ -340,11 +340,14 @@ class Mesh:
                 raise ValueError(f"{name}: a contiguous CPU {mt} tensor of n_elem x n_sweep values")
         flags = (DG_TAU_ISOLATED if isolated else 0) | (DG_TAU_FP32 if fp32 else 0) | \
                 (DG_TAU_ACCUM_MAX if accumulate else 0)
+        import torch
         t = C.c_double(0.0)
-        _check(_lib().dg_step_host(self.h, _ptr(q_in), _ptr(q_out), float(t0), float(t_end), float(cfl),
-                                   int(max_steps), sw.ctypes.data_as(C.POINTER(C.c_int32)), sw.shape[0], flags,
-                                   _ptr(map_new) if map_new is not None else None,
-                                   _ptr(map_trad) if map_trad is not None else None, C.byref(t)), "dg_step_host")
+        with torch.cuda.device(self.device):
+            _check(_lib().dg_step_host(self.h, _ptr(q_in), _ptr(q_out), float(t0), float(t_end), float(cfl),
+                                       int(max_steps), sw.ctypes.data_as(C.POINTER(C.c_int32)), sw.shape[0], flags,
+                                       _ptr(map_new) if map_new is not None else None,
+                                       _ptr(map_trad) if map_trad is not None else None, C.byref(t)),
+                   "dg_step_host")
         return t.value
 
     def set_orders(self, new_orders, q_old):
